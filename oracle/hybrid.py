@@ -1,0 +1,583 @@
+"""Plain FP64 CPU oracle of the hybrid FEM/FDM scheme (arXiv 1509.01399).
+
+TEST INFRASTRUCTURE ONLY.  This package exists to check the CUDA path; only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs
+of ``bench.py`` may import it.  It shares no code with the CUDA library and
+never calls it.
+
+What it computes, in the paper's order and notation (numpy / scipy.sparse,
+float64 throughout):
+
+* Mesh (Sec. 6.1, Sec. 3): a structured lattice of nodes x = origin + h (i, j, k);
+  a finite-element block of nodes lo..hi whose voxels are each cut into the six
+  Kuhn tetrahedra along the voxel diagonal; the node classes of Algorithm 1:
+  omega_o (the block's boundary shell, owned by the FDM), omega_diamond (the
+  next shell inward, owned by the FEM), omega_* (the FEM interior) and
+  omega_+ (every other lattice node, FDM).
+* FEM operators (Sec. 6.2): element mass and stiffness of P1 functions,
+  M^K_ij = (phi_i, phi_j)_K and K^K_ij = (a_h grad phi_i, grad phi_j)_K, with
+  the mass matrix lumped by rows and the coefficient a_h piecewise constant
+  (Eq. (p0)), one value per voxel.  The explicit scheme is Eq. (fem):
+  u^{k+1} = (2 - tau^2 (M^L)^{-1} K) u^k - u^{k-1} (the G term only acts on
+  rows of nodes on the FEM block boundary, which Algorithm 1 overwrites from
+  the FDM, so it never reaches an owned row).
+* FDM (Sec. 6.3): the leapfrog Eq. (fdmschemeforward) with the 7-point
+  Laplacian; Neumann faces by a mirror ghost; the plane-wave source
+  d_n u = p(t) of Model Problem 2 (Eq. (model2), Eq. (f)) by the ghost
+  u_g = u_in + 2 h p.
+* Absorbing faces (Sec. 6.4): Eq. (eq:abs2),
+  u_b^{k+1} = u_{b1}^k + r u_b^k - r u_{b1}^{k+1},  r = (h - tau) / (h + tau),
+  applied after the interior rows of the same time level; a node on several
+  absorbing faces takes the mean of its per-face formulas, faces before edges
+  before corners.
+* Algorithm 2 (Sec. 6.5): per time step, update the FDM-owned rows, update
+  the FEM-owned rows, copy omega_diamond from FEM to FDM and omega_o from FDM
+  to FEM, swap levels.
+* Adjoint and gradient (Sec. 5, Eq. (lagrangian1) - Eq. (grad1new),
+  Eq. (gradient1)): the exact discrete adjoint of the time stepping, obtained
+  by writing each step as E_k u^{k+1} = B_k u^k - C_k u^{k-1} + s_k and
+  transposing those matrices literally; the conductivity gradient is
+  dJ/da_c = -tau^2 sum_k (lambda^{k+1})^T (M^L)^{-1} K_c u^k, the discrete
+  form of int_0^T grad u . grad lambda dt.
+* Tikhonov functional (Eq. (functional)) and one conjugate-gradient update of
+  Algorithm 3 (Sec. 7) with a quadratic-fit step length.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import scipy.sparse as sp
+
+BC_NEUMANN0 = 0
+BC_ABC = 1
+
+
+def p1_element(X: np.ndarray):
+    """Volumes and barycentric gradients of P1 tetrahedra.
+
+    X: (T, 4, 3) vertex coordinates.  Returns vol (T,) and grads (T, 4, 3)
+    where grads[t, i] = grad phi_i on tetrahedron t (Sec. 6.2: the P1 basis
+    functions of the reference element mapped by F_K)."""
+    T = X.shape[0]
+    A = np.concatenate([np.ones((T, 4, 1)), X], axis=2)  # rows: (1, x_v)
+    Ainv = np.linalg.inv(A)  # column i holds the coefficients of phi_i
+    grads = np.transpose(Ainv[:, 1:, :], (0, 2, 1))
+    e = X[:, 1:, :] - X[:, :1, :]
+    vol = np.abs(np.linalg.det(e)) / 6.0
+    return vol, grads
+
+
+def element_stiffness(vol, grads, a_tet):
+    """K^K_ij = a_K |K| grad phi_i . grad phi_j (Sec. 6.2)."""
+    return (a_tet * vol)[:, None, None] * np.einsum("tid,tjd->tij", grads, grads)
+
+
+def kuhn_tets(origin_nodes: np.ndarray):
+    """The six Kuhn tetrahedra of a unit voxel with corner `origin_nodes`
+    (V, 3) lattice coordinates: each is the path 0 -> e_p -> e_p + e_q -> (1,1,1)
+    for a permutation (p, q, s) of the axes.  Returns (V, 6, 4, 3)."""
+    V = origin_nodes.shape[0]
+    out = np.zeros((V, 6, 4, 3), dtype=np.int64)
+    for t, perm in enumerate(itertools.permutations(range(3))):
+        v = np.zeros(3, dtype=np.int64)
+        out[:, t, 0] = origin_nodes
+        for s in range(3):
+            v[perm[s]] = 1
+            out[:, t, s + 1] = origin_nodes + v
+    return out
+
+
+@dataclass
+class Phase:
+    """Boundary state of one time step: the set of absorbing faces and the
+    source face (with its flux p(t_k)) in force at that step."""
+
+    abc_faces: tuple
+    src_face: int  # -1: none
+    p: float
+
+
+class Problem:
+    """Lattice, FEM block, node classes and assembled operators."""
+
+    def __init__(self, n, h, fem_lo=None, fem_hi=None, bc=(BC_ABC,) * 6, origin=(0.0, 0.0, 0.0)):
+        self.n = tuple(int(v) for v in n)
+        if min(self.n) < 3:
+            raise ValueError("every axis needs at least 3 nodes")
+        self.h = float(h)
+        self.bc = tuple(int(b) for b in bc)
+        self.origin = tuple(float(o) for o in origin)
+        nx, ny, nz = self.n
+        self.N = nx * ny * nz
+        kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        self.I = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)
+        self.on_face = []
+        for f in range(6):
+            ax, side = divmod(f, 2)
+            self.on_face.append(self.I[:, ax] == (0 if side == 0 else self.n[ax] - 1))
+        self.stride = (1, nx, nx * ny)
+
+        self.has_fem = fem_lo is not None
+        if self.has_fem:
+            lo = np.array(fem_lo, dtype=np.int64)
+            hi = np.array(fem_hi, dtype=np.int64)
+            if (lo < 0).any() or (hi > np.array(self.n) - 1).any() or (hi - lo < 2).any():
+                raise ValueError("bad FEM block")
+            self.lo, self.hi = lo, hi
+            in_box = np.all((self.I >= lo) & (self.I <= hi), axis=1)
+            self.owned = np.all((self.I >= lo + 1) & (self.I <= hi - 1), axis=1)
+            inner = np.all((self.I >= lo + 2) & (self.I <= hi - 2), axis=1)
+            self.omega_o = in_box & ~self.owned
+            self.omega_diamond = self.owned & ~inner
+            # voxels of the FEM block and their Kuhn tetrahedra
+            cz, cy, cx = np.meshgrid(*[np.arange(lo[d], hi[d]) for d in (2, 1, 0)], indexing="ij")
+            vox = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
+            unk = np.all((vox >= lo + 1) & (vox <= hi - 2), axis=1)
+            ud = np.maximum(hi - lo - 2, 0)
+            self.unknown_dims = tuple(int(v) for v in ud)
+            self.n_unknown = int(np.prod(ud))
+            uid = np.full(vox.shape[0], -1, dtype=np.int64)
+            rel = vox[unk] - (lo + 1)
+            uid[unk] = rel[:, 0] + ud[0] * (rel[:, 1] + ud[1] * rel[:, 2])
+            tets = kuhn_tets(vox)  # (V, 6, 4, 3)
+            self.tet_nodes = self.node_id(tets.reshape(-1, 3)).reshape(-1, 4)
+            self.tet_unknown = np.repeat(uid, 6)
+            X = self.h * tets.reshape(-1, 4, 3).astype(np.float64)
+            self.tet_vol, self.tet_grads = p1_element(X)
+            self.voxel_volume = self.h ** 3
+        else:
+            self.owned = np.zeros(self.N, dtype=bool)
+            self.omega_o = np.zeros(self.N, dtype=bool)
+            self.omega_diamond = np.zeros(self.N, dtype=bool)
+            self.unknown_dims = (0, 0, 0)
+            self.n_unknown = 0
+            self.voxel_volume = self.h ** 3
+        self.fdm_owned = ~self.owned
+        self.owned_nodes = np.flatnonzero(self.owned)
+        self.owned_pos = np.full(self.N, -1, dtype=np.int64)
+        self.owned_pos[self.owned_nodes] = np.arange(self.owned_nodes.size)
+        self.D = self._fdm_laplacian()
+        self._phase_cache = {}
+
+    # ------------------------------------------------------------------ mesh
+    def node_id(self, ijk):
+        ijk = np.asarray(ijk, dtype=np.int64)
+        return ijk[..., 0] + self.n[0] * (ijk[..., 1] + self.n[1] * ijk[..., 2])
+
+    def face_nodes(self, f):
+        """Nodes of face f in trace order: the two in-face axes p < q, index
+        = c_p + n_p * c_q."""
+        ax = f // 2
+        p, q = [d for d in range(3) if d != ax]
+        nodes = np.flatnonzero(self.on_face[f])
+        key = self.I[nodes, p] + self.n[p] * self.I[nodes, q]
+        return nodes[np.argsort(key, kind="stable")]
+
+    def face_weights(self, f):
+        """Lumped surface quadrature weight of each face node: h^2 halved for
+        every in-face coordinate that sits on the face's own border."""
+        nodes = self.face_nodes(f)
+        ax = f // 2
+        w = np.full(nodes.size, self.h ** 2)
+        for d in range(3):
+            if d == ax:
+                continue
+            edge = (self.I[nodes, d] == 0) | (self.I[nodes, d] == self.n[d] - 1)
+            w[edge] *= 0.5
+        return w
+
+    # ------------------------------------------------------------- operators
+    def _fdm_laplacian(self):
+        """7-point Delta_h of Sec. 6.3 on every lattice node, Neumann mirror
+        ghost u_{-1} = u_{1} on the outer faces (the ghost values of source
+        faces add a constant, handled in the source term)."""
+        rows, cols, vals = [], [], []
+        ids = np.arange(self.N)
+        inv_h2 = 1.0 / self.h ** 2
+        for d in range(3):
+            c = self.I[:, d]
+            st = self.stride[d]
+            lowb = c == 0
+            highb = c == self.n[d] - 1
+            mid = ~lowb & ~highb
+            rows += [ids[mid], ids[mid], ids[lowb], ids[highb]]
+            cols += [ids[mid] - st, ids[mid] + st, ids[lowb] + st, ids[highb] - st]
+            vals += [np.full(mid.sum(), inv_h2), np.full(mid.sum(), inv_h2),
+                     np.full(lowb.sum(), 2 * inv_h2), np.full(highb.sum(), 2 * inv_h2)]
+            rows.append(ids)
+            cols.append(ids)
+            vals.append(np.full(self.N, -2 * inv_h2))
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(self.N, self.N))
+
+    def tet_coefficient(self, a_unknown):
+        """a_K per tetrahedron: the voxel's value on unknown voxels, 1 on the
+        other voxels of the FEM block (a = 1 near Omega_FDM, Eq. (2.3))."""
+        a_unknown = np.asarray(a_unknown, dtype=np.float64)
+        a_tet = np.ones(self.tet_nodes.shape[0])
+        m = self.tet_unknown >= 0
+        a_tet[m] = a_unknown[self.tet_unknown[m]]
+        return a_tet
+
+    def assemble(self, a_unknown):
+        """Global stiffness K(a) and lumped mass M^L over the FEM block."""
+        if not self.has_fem:
+            return sp.csr_matrix((self.N, self.N)), np.zeros(self.N)
+        Kloc = element_stiffness(self.tet_vol, self.tet_grads, self.tet_coefficient(a_unknown))
+        r = np.repeat(self.tet_nodes, 4, axis=1).ravel()
+        c = np.tile(self.tet_nodes, (1, 4)).ravel()
+        K = sp.csr_matrix((Kloc.ravel(), (r, c)), shape=(self.N, self.N))
+        ML = np.bincount(self.tet_nodes.ravel(), weights=np.repeat(self.tet_vol / 4.0, 4),
+                         minlength=self.N)
+        return K, ML
+
+    def space_operator(self, a_unknown):
+        """L such that a non-absorbing row reads u^{k+1} = 2u^k - u^{k-1} - tau^2 (L u^k)_i:
+        -Delta_h on FDM-owned rows, (M^L)^{-1} K on FEM-owned rows."""
+        K, ML = self.assemble(a_unknown)
+        inv_ml = np.zeros(self.N)
+        inv_ml[self.owned] = 1.0 / ML[self.owned]
+        Lfe = sp.diags(inv_ml) @ K
+        Lfd = -self.D
+        return (sp.diags(self.fdm_owned.astype(float)) @ Lfd + sp.diags(self.owned.astype(float)) @ Lfe).tocsr()
+
+    # ----------------------------------------------------------------- phase
+    def phase(self, src, k, dt):
+        """Boundary state for the step from t_k = k dt: the source face acts as
+        a Neumann face with flux p(t_k) while t_k <= t1 = 2 pi / omega, and
+        takes the mesh's own condition afterwards (Model Problem 2)."""
+        abc = [f for f in range(6) if self.bc[f] == BC_ABC]
+        if src is not None:
+            t = k * dt
+            if t <= 2.0 * math.pi / src.omega:
+                abc = [f for f in abc if f != src.face]
+                return Phase(tuple(abc), src.face, src.amp * math.sin(src.omega * t))
+        return Phase(tuple(abc), -1, 0.0)
+
+    def abc_structure(self, abc_faces):
+        """Level (number of absorbing faces a node lies on) and, per absorbing
+        face, its nodes b with the inward neighbours b1."""
+        key = tuple(abc_faces)
+        if key in self._phase_cache:
+            return self._phase_cache[key]
+        level = np.zeros(self.N, dtype=np.int64)
+        for f in abc_faces:
+            level += self.on_face[f]
+        pairs = []
+        for f in abc_faces:
+            ax, side = divmod(f, 2)
+            b = np.flatnonzero(self.on_face[f])
+            b1 = b + (self.stride[ax] if side == 0 else -self.stride[ax])
+            pairs.append((b, b1))
+        self._phase_cache[key] = (level, pairs)
+        return level, pairs
+
+    def step_matrices(self, Lop, phase: Phase, dt):
+        """E, B, C and the source vector s of one step written as
+        E u^{k+1} = B u^k - C u^{k-1} + s."""
+        level, pairs = self.abc_structure(phase.abc_faces)
+        r = (self.h - dt) / (self.h + dt)
+        nonabc = (level == 0).astype(float)
+        I = sp.identity(self.N, format="csr")
+        Dn = sp.diags(nonabc)
+        B = Dn @ (2.0 * I - dt * dt * Lop)
+        E = Dn @ I
+        C = Dn @ I
+        rb, cb, vb, ve = [], [], [], []
+        abcn = np.flatnonzero(level > 0)
+        rb.append(abcn)
+        cb.append(abcn)
+        vb.append(np.full(abcn.size, r))
+        ve.append(np.ones(abcn.size))
+        for b, b1 in pairs:
+            Lb = level[b].astype(float)
+            rb.append(b)
+            cb.append(b1)
+            vb.append(1.0 / Lb)
+            ve.append(r / Lb)
+        rr, cc = np.concatenate(rb), np.concatenate(cb)
+        B = (B + sp.csr_matrix((np.concatenate(vb), (rr, cc)), shape=B.shape)).tocsr()
+        E = (E + sp.csr_matrix((np.concatenate(ve), (rr, cc)), shape=E.shape)).tocsr()
+        s = np.zeros(self.N)
+        if phase.src_face >= 0:
+            m = self.on_face[phase.src_face] & (level == 0)
+            s[m] = dt * dt * 2.0 * phase.p / self.h
+        return E, B, C.tocsr(), s
+
+    # --------------------------------------------------------------- forward
+    def forward(self, a_unknown, src, nsteps, dt, init=None, keep_hist=False, keep_fields=False):
+        """Algorithm 2, forward in time, with separate FDM and FEM arrays and
+        the two copies of Algorithm 1 per step.
+
+        Returns a dict with the trace on the source face (rows t_0 .. t_N),
+        the final level u^N (and u^{N-1}), optionally u^k on the FEM-owned
+        nodes for k = 0 .. N-1 (for the gradient) and every full level."""
+        h = self.h
+        tau2 = dt * dt
+        r = (h - dt) / (h + dt)
+        K, ML = self.assemble(a_unknown)
+        own = self.owned
+        obs = self.face_nodes(src.face) if src is not None else np.zeros(0, dtype=np.int64)
+        if init is None:
+            u_fd = np.zeros(self.N)
+            u_fd_prev = np.zeros(self.N)
+        else:
+            u_fd = np.array(init[0], dtype=np.float64)
+            u_fd_prev = np.array(init[1], dtype=np.float64)
+        u_fe, u_fe_prev = u_fd.copy(), u_fd_prev.copy()
+        trace = np.zeros((nsteps + 1, obs.size))
+        trace[0] = u_fd[obs]
+        hist = np.zeros((nsteps, self.owned_nodes.size)) if keep_hist else None
+        fields = [self._combine(u_fd, u_fe)] if keep_fields else None
+        for k in range(nsteps):
+            if keep_hist:
+                hist[k] = u_fe[self.owned_nodes]
+            ph = self.phase(src, k, dt)
+            level, pairs = self.abc_structure(ph.abc_faces)
+            # 1. FDM rows at omega_+ and omega_o (non-absorbing rows)
+            rows = self.fdm_owned & (level == 0)
+            lap = self.D @ u_fd
+            new_fd = np.zeros(self.N)
+            new_fd[rows] = 2.0 * u_fd[rows] - u_fd_prev[rows] + tau2 * lap[rows]
+            if ph.src_face >= 0:
+                m = rows & self.on_face[ph.src_face]
+                new_fd[m] += tau2 * 2.0 * ph.p / h
+            # 2. FEM rows at omega_* and omega_diamond, Eq. (fem)
+            new_fe = np.zeros(self.N)
+            if self.has_fem:
+                Ku = K @ u_fe
+                new_fe[own] = 2.0 * u_fe[own] - u_fe_prev[own] - tau2 * Ku[own] / ML[own]
+                # 3. FEM values at omega_diamond become FDM boundary values
+                new_fd[self.omega_diamond] = new_fe[self.omega_diamond]
+            # absorbing rows, Eq. (eq:abs2), faces before edges before corners
+            for L in (1, 2, 3):
+                acc = None
+                for b, b1 in pairs:
+                    sel = level[b] == L
+                    if not sel.any():
+                        continue
+                    bb, bb1 = b[sel], b1[sel]
+                    if acc is None:
+                        acc = np.zeros(self.N)
+                    acc[bb] += u_fd[bb1] - r * new_fd[bb1]
+                if acc is not None:
+                    m = level == L
+                    new_fd[m] = r * u_fd[m] + acc[m] / L
+            if self.has_fem:
+                # 4. FDM values at omega_o become FEM boundary values
+                new_fe[self.omega_o] = new_fd[self.omega_o]
+            # 5. swap
+            u_fd_prev, u_fd = u_fd, new_fd
+            u_fe_prev, u_fe = u_fe, new_fe
+            trace[k + 1] = u_fd[obs]
+            if keep_fields:
+                fields.append(self._combine(u_fd, u_fe))
+        return dict(trace=trace, u=self._combine(u_fd, u_fe), u_prev=self._combine(u_fd_prev, u_fe_prev),
+                    hist=hist, fields=fields)
+
+    def _combine(self, u_fd, u_fe):
+        u = u_fd.copy()
+        u[self.owned] = u_fe[self.owned]
+        return u
+
+    # ------------------------------------------------- matrix form and adjoint
+    def operators(self, a_unknown, src, nsteps, dt):
+        """Step matrices for every distinct boundary phase of the run."""
+        Lop = self.space_operator(a_unknown)
+        cache = {}
+        seq = []
+        for k in range(nsteps + 2):
+            ph = self.phase(src, k, dt)
+            key = (ph.abc_faces, ph.src_face)
+            if key not in cache:
+                cache[key] = self.step_matrices(Lop, ph, dt)
+            E, B, C, s = cache[key]
+            if ph.src_face >= 0:
+                s = s * 0.0
+                m = self.on_face[ph.src_face] & (self.abc_structure(ph.abc_faces)[0] == 0)
+                s[m] = dt * dt * 2.0 * ph.p / self.h
+            seq.append((key, s))
+        return cache, seq
+
+    @staticmethod
+    def _strict_part(E, transpose=False):
+        Nm = (E - sp.identity(E.shape[0], format="csr")).tocsr()
+        Nm.eliminate_zeros()
+        return Nm.T.tocsr() if transpose else Nm
+
+    @staticmethod
+    def _solve_unit(Nm, y):
+        """Solve (I + N) x = y, where N only couples a node on l absorbing
+        faces to nodes on l - 1 of them (or the transpose of that): N is
+        nilpotent with N^4 = 0, so the fixed point x = y - N x is exact after
+        4 sweeps."""
+        x = y.copy()
+        for _ in range(4):
+            x = y - Nm @ x
+        return x
+
+    def forward_matrix(self, a_unknown, src, nsteps, dt, forcing=None, init=None):
+        """The same time stepping as `forward`, written as
+        E_k u^{k+1} = B_k u^k - C_k u^{k-1} + s_k (+ f_k); returns the trace."""
+        cache, seq = self.operators(a_unknown, src, nsteps, dt)
+        obs = self.face_nodes(src.face)
+        u = np.zeros(self.N) if init is None else np.array(init[0], dtype=np.float64)
+        up = np.zeros(self.N) if init is None else np.array(init[1], dtype=np.float64)
+        trace = np.zeros((nsteps + 1, obs.size))
+        trace[0] = u[obs]
+        strict = {key: self._strict_part(E) for key, (E, _, _, _) in cache.items()}
+        for k in range(nsteps):
+            key, s = seq[k]
+            E, B, C, _ = cache[key]
+            y = B @ u - C @ up + s
+            if forcing is not None:
+                y = y + forcing[k]
+            un = self._solve_unit(strict[key], y)
+            up, u = u, un
+            trace[k + 1] = u[obs]
+        return trace, u
+
+    def adjoint(self, a_unknown, src, nsteps, dt, cot, hist, return_lambda=False, keep_lambdas=False):
+        """Exact discrete adjoint, backward in time:
+        E_{j-1}^T lambda^j = B_j^T lambda^{j+1} - C_{j+1}^T lambda^{j+2} + c^j,
+        j = N .. 1, lambda^{N+1} = lambda^{N+2} = 0, where c^j is dJ/du^j
+        (non-zero on the observation face only).  Returns dJ/da per unknown
+        voxel: -tau^2 sum_k (lambda^{k+1})^T (M^L)^{-1} K_c u^k."""
+        cache, seq = self.operators(a_unknown, src, nsteps, dt)
+        K, ML = self.assemble(a_unknown)
+        obs = self.face_nodes(src.face)
+        lam1 = np.zeros(self.N)
+        lam2 = np.zeros(self.N)
+        Gacc = np.zeros(self.n_unknown)
+        lams = [None] * (nsteps + 2) if keep_lambdas else None
+        tr = {key: (self._strict_part(E, transpose=True), B.T.tocsr(), C.T.tocsr())
+              for key, (E, B, C, _) in cache.items()}
+        for j in range(nsteps, 0, -1):
+            _, BT, _ = tr[seq[j][0]]
+            _, _, CT = tr[seq[j + 1][0]]
+            NT, _, _ = tr[seq[j - 1][0]]
+            rhs = BT @ lam1 - CT @ lam2
+            rhs[obs] += cot[j]
+            lam = self._solve_unit(NT, rhs)
+            if j <= nsteps - 1 and self.n_unknown:
+                Gacc += self.pair(hist[j], lam1, ML)
+            lam2, lam1 = lam1, lam
+            if keep_lambdas:
+                lams[j] = lam
+        if self.n_unknown:
+            Gacc += self.pair(hist[0], lam1, ML)
+        out = -dt * dt * Gacc
+        if keep_lambdas:
+            return out, lams
+        if return_lambda:
+            return out, lam1
+        return out
+
+    def pair(self, u_owned, lam, ML):
+        """Per unknown voxel c: (lambda / M^L)^T K_c u = sum over the voxel's
+        tetrahedra of |K| grad u . grad (lambda / M^L), with K_c the a = 1
+        stiffness of the voxel."""
+        m = self.tet_unknown >= 0
+        tn = self.tet_nodes[m]
+        uK = u_owned[self.owned_pos[tn]]
+        lhat = lam / np.where(ML > 0, ML, 1.0)
+        lK = lhat[tn]
+        gu = np.einsum("ti,tid->td", uK, self.tet_grads[m])
+        gl = np.einsum("ti,tid->td", lK, self.tet_grads[m])
+        val = self.tet_vol[m] * np.sum(gu * gl, axis=1)
+        return np.bincount(self.tet_unknown[m], weights=val, minlength=self.n_unknown)
+
+
+# ------------------------------------------------------------ functional, CG
+def data_weights(prob: Problem, face: int, nsteps: int, dt: float, mode: str = "plain"):
+    """Weights of the misfit 1/2 int_{S_T} (u - u~)^2 z_delta (Eq. (functional)).
+
+    'plain': 1/2 sum_{k>=1} sum_j (u - u~)^2 (the plain least-squares loss);
+    'quadrature': time weight tau for k >= 1 and the lumped face weight of
+    each node."""
+    wk = np.ones(nsteps + 1)
+    wk[0] = 0.0
+    if mode == "plain":
+        return wk, np.ones(prob.face_nodes(face).size)
+    if mode == "quadrature":
+        return wk * dt, prob.face_weights(face)
+    raise ValueError(mode)
+
+
+def misfit(trace, obs, wk, mj):
+    d = trace - obs
+    return 0.5 * float(np.sum(wk[:, None] * mj[None, :] * d * d)), wk[:, None] * mj[None, :] * d
+
+
+def value_and_grad(prob: Problem, a, sources, nsteps, dt, obs_traces, gamma=0.0, a0=1.0,
+                   mode="plain", need_grad=True):
+    """F(a) = sum over sources of the data misfit + gamma/2 sum_c |c| (a_c - a0)^2
+    and its Euclidean gradient dF/da_c (Eq. (functional), Eq. (grad1new))."""
+    J = 0.5 * gamma * prob.voxel_volume * float(np.sum((a - a0) ** 2))
+    g = gamma * prob.voxel_volume * (a - a0)
+    traces = []
+    for s, src in enumerate(sources):
+        res = prob.forward(a, src, nsteps, dt, keep_hist=need_grad)
+        wk, mj = data_weights(prob, src.face, nsteps, dt, mode)
+        Jd, cot = misfit(res["trace"], obs_traces[s], wk, mj)
+        J += Jd
+        traces.append(res["trace"])
+        if need_grad:
+            g = g + prob.adjoint(a, src, nsteps, dt, cot, res["hist"])
+    return J, (g if need_grad else None), traces
+
+
+def quadratic_step(J0, dJ0, alpha_t, Jt):
+    """Step length from the parabola through J(0), J'(0) and J(alpha_t),
+    clamped to [0, 4 alpha_t]; alpha_t itself when the parabola has no
+    minimum.  (Algorithm 3 leaves the step-size rule open.)"""
+    curv = Jt - J0 - dJ0 * alpha_t
+    if curv <= 0.0:
+        alpha = alpha_t
+    else:
+        alpha = -dJ0 * alpha_t * alpha_t / (2.0 * curv)
+    return min(max(alpha, 0.0), 4.0 * alpha_t)
+
+
+def cg_direction(g, d_prev, gn2_prev, vol):
+    """Fletcher-Reeves direction of Algorithm 3, Step 2: d^m = -g^m + beta^m d^{m-1},
+    beta^m = ||g^m||^2 / ||g^{m-1}||^2 (L2 norms over the unknown voxels),
+    d^0 = -g^0."""
+    gn2 = vol * float(np.sum(g * g))
+    if d_prev is None or gn2_prev is None or gn2_prev <= 0.0:
+        return -g, 0.0, gn2
+    beta = gn2 / gn2_prev
+    return -g + beta * d_prev, beta, gn2
+
+
+def cg_step(prob: Problem, a, sources, nsteps, dt, obs_traces, state: dict, gamma=0.01, a0=1.0,
+            a_min=1.0, a_max=5.0, mode="quadrature"):
+    """One iteration of Algorithm 3: state and adjoint at a^m (Step 1), the
+    gradient g^m = int grad u . grad lambda dt + gamma (a^m - a0) as an L2
+    function on the voxels, the Fletcher-Reeves update with a quadratic-fit
+    step, and projection onto the admissible set [a_min, a_max] (Eq. (admpar))."""
+    vol = prob.voxel_volume
+    J0, ge, _ = value_and_grad(prob, a, sources, nsteps, dt, obs_traces, gamma, a0, mode)
+    g = ge / vol
+    d, beta, gn2 = cg_direction(g, state.get("d"), state.get("gn2"), vol)
+    dJ0 = float(np.sum(ge * d))
+    if dJ0 >= 0.0:
+        d, beta, dJ0 = -g, 0.0, -gn2
+    alpha_t = state.get("alpha")
+    if alpha_t is None or alpha_t <= 0.0:
+        alpha_t = 0.5 / max(float(np.max(np.abs(d))), 1e-300)
+    a_t = np.clip(a + alpha_t * d, a_min, a_max)
+    Jt, _, _ = value_and_grad(prob, a_t, sources, nsteps, dt, obs_traces, gamma, a0, mode, need_grad=False)
+    alpha = quadratic_step(J0, dJ0, alpha_t, Jt)
+    a_new = np.clip(a + alpha * d, a_min, a_max)
+    new_state = dict(d=d, gn2=gn2, alpha=alpha, iter=state.get("iter", 0) + 1)
+    report = dict(J=J0, gnorm=math.sqrt(gn2), alpha=alpha, beta=beta, dJ0=dJ0, J_trial=Jt, alpha_trial=alpha_t)
+    return a_new, new_state, report
+
+
+def problem_from_workload(w) -> Problem:
+    return Problem(w.n, w.h, w.fem_lo, w.fem_hi, w.bc, w.origin)
