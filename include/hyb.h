@@ -1,0 +1,211 @@
+/*
+ * hyb.h - C ABI of the GB300 hybrid FEM/FDM wave solver for conductivity
+ * reconstruction (Beilina, arXiv 1509.01399).
+ *
+ * The library advances the hyperbolic model u_tt - div(a grad u) = 0 of
+ * Model Problem 2 (Sec. 5, Eq. (model2)) on a box: a structured lattice of
+ * nodes x = origin + h (i, j, k) on which the finite-difference leapfrog
+ * Eq. (fdmschemeforward) runs, and a central finite-element block whose voxels
+ * are cut into Kuhn tetrahedra and updated by the explicit lumped-mass scheme
+ * Eq. (fem).  The two meshes overlap by one cell as in Algorithm 1: the FEM
+ * block's boundary shell (omega_o) is owned by the FDM, the next shell inward
+ * (omega_diamond) and everything inside it by the FEM.  Both schemes write one
+ * shared field, so the copies of Algorithm 1 are identities.
+ *
+ * The unknown coefficient a is piecewise constant (Eq. (p0)), one value per
+ * "unknown voxel": a cell of the FEM block whose eight corners are all
+ * FEM-owned (cells fem_lo+1 .. fem_hi-2 on every axis).  a = 1 everywhere
+ * else (Eq. (2.3)).  Unknown voxels are stored x fastest:
+ *   a[(cz * uy + cy) * ux + cx],  (ux, uy, uz) = hyb_mesh_info.unknown_dims.
+ *
+ * Conventions common to every call:
+ *  - Every array argument is a caller-owned DEVICE pointer unless stated.
+ *    Field-typed arrays (trace, cotangent, observations, fields) are double
+ *    for HYB_FP64 meshes and float for HYB_FP32 meshes; coefficient,
+ *    gradient and CG arrays are always double.
+ *  - Calls are asynchronous on the mesh's stream (hyb_set_stream).  Argument
+ *    errors are returned synchronously; device-side failures surface at
+ *    hyb_sync.  Every call returns a hyb_status and never throws or aborts.
+ *    hyb_last_error() gives a message for the calling thread's last failure.
+ *  - One mesh is used by one host thread at a time.
+ *  - Faces are numbered f = 2 * axis + side: 0 = x-low, 1 = x-high,
+ *    2 = y-low, 3 = y-high, 4 = z-low, 5 = z-high.
+ *  - A trace row of face f lists its nodes with in-face coordinates (c_p, c_q),
+ *    p < q the two other axes, at index c_p + n_p * c_q; rows are padded to
+ *    hyb_mesh_info.obs_stride entries.
+ */
+#ifndef HYB_H_
+#define HYB_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hyb_mesh hyb_mesh;
+
+typedef enum {
+  HYB_OK = 0,
+  HYB_ERR_ARG = -1,     /* invalid argument (sizes, enums, null pointers) */
+  HYB_ERR_CFL = -2,     /* dt above the stability bound, or a > a_max */
+  HYB_ERR_OOM = -3,     /* device allocation failed */
+  HYB_ERR_CUDA = -4,    /* a CUDA call failed */
+  HYB_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up */
+  HYB_ERR_STATE = -6    /* call out of order (e.g. adjoint before forward) */
+} hyb_status;
+
+enum { HYB_BC_NEUMANN0 = 0, HYB_BC_ABC = 1 };
+enum { HYB_FP64 = 0, HYB_FP32 = 1 };
+enum { HYB_WEIGHTS_PLAIN = 0, HYB_WEIGHTS_QUADRATURE = 1 };
+enum { HYB_FIELD_U_LAST = 0, HYB_FIELD_U_PREV = 1, HYB_FIELD_LAMBDA_FIRST = 2 };
+
+/* Mesh description (Sec. 8 geometry; Algorithm 1 node classes). */
+typedef struct {
+  int32_t n[3];        /* lattice nodes per axis, each >= 3 */
+  double h;            /* lattice spacing, the same on every axis (Eq. (CFL)) */
+  double origin[3];    /* world coordinates of node (0,0,0) */
+  int32_t fem_lo[3];   /* FEM block node range, inclusive; fem_lo[0] < 0 = no */
+  int32_t fem_hi[3];   /*   FEM block.  Needs 0 <= lo, hi <= n-1, hi - lo >= 2 */
+  int32_t bc[6];       /* HYB_BC_* per face: d_n u = 0, or d_n u = -d_t u
+                          discretised by Eq. (eq:abs2) */
+  int32_t precision;   /* HYB_FP64, or HYB_FP32 (FP32 fields and stencils,
+                          FP64 gradient accumulation and CG reductions) */
+  int32_t ckpt_every;  /* 0: the forward keeps u on the FEM-owned nodes at
+                          every level for the gradient; C > 0: it keeps full
+                          fields every C steps and the adjoint recomputes each
+                          segment */
+  double a_max;        /* upper admissible bound of a (Eq. (admpar)); sets
+                          dt_max = h / sqrt(3 a_max) (Eq. (CFL)) */
+} hyb_mesh_desc;
+
+typedef struct {
+  int64_t n_nodes;         /* lattice nodes */
+  int64_t n_unknown;       /* unknown voxels */
+  int64_t n_fem_owned;     /* FEM-owned nodes */
+  int32_t unknown_dims[3];
+  int32_t obs_stride;      /* padded length of one trace row */
+  double dt_max;           /* CFL bound for a <= a_max */
+  double voxel_volume;     /* h^3 */
+  int64_t device_bytes;    /* device memory currently held by the mesh */
+  int64_t launches;        /* kernels launched by this mesh so far */
+} hyb_mesh_info;
+
+/* Plane-wave source of Eq. (f): a Neumann flux d_n u = amp sin(omega t) on
+   `face` for t <= 2 pi / omega (the S_{1,1} part of Eq. (model2)); after that
+   the face takes the mesh's own condition.  The source face is also the
+   observation face S_T whose trace is recorded. */
+typedef struct {
+  int32_t face;
+  double omega;
+  double amp;
+} hyb_source;
+
+/* Create a mesh: node classes, FEM block, device workspaces.  `stream` is a
+   cudaStream_t (NULL = the legacy default stream).  Errors: HYB_ERR_ARG for
+   an invalid description, HYB_ERR_OOM, HYB_ERR_CUDA. */
+hyb_status hyb_mesh_create(const hyb_mesh_desc* desc, void* stream, hyb_mesh** out);
+hyb_status hyb_mesh_query(const hyb_mesh* mesh, hyb_mesh_info* out);
+hyb_status hyb_mesh_destroy(hyb_mesh* mesh);
+hyb_status hyb_set_stream(hyb_mesh* mesh, void* stream);
+
+/* Forward solve, Algorithm 2 forward in time from u^0 = u^{-1} = 0
+   (Model Problem 2), one independent problem per source, all sources
+   advanced by the same launches.
+   a:      device double[n_unknown], the coefficient on the unknown voxels.
+   src:    HOST array of n_src sources (1 <= n_src <= 16).
+   nsteps: number of time steps N (u^1 .. u^N are computed).
+   dt:     time step tau, 0 < dt <= dt_max (else HYB_ERR_CFL).
+   trace:  device field[n_src][nsteps + 1][obs_stride]; row k receives u^k on
+           the source's face (row 0 = u^0 = 0).
+   The mesh keeps what the adjoint needs (coefficient, sources, time grid,
+   the FEM-owned part of every level or the checkpoints).  An a value above
+   a_max is reported by hyb_sync as HYB_ERR_CFL. */
+hyb_status hyb_forward(hyb_mesh* mesh, const double* a, const hyb_source* src, int32_t n_src,
+                       int32_t nsteps, double dt, void* trace);
+
+/* Exact discrete adjoint of the last hyb_forward, backward in time
+   (the discrete counterpart of Eq. (adjoint1)): with c^k = dJ/d(trace row k)
+   given in `cotangent` (device field[n_src][nsteps + 1][obs_stride]; row 0 is
+   ignored), it solves the transposed time stepping from lambda^{N+1} =
+   lambda^{N+2} = 0 and accumulates, in FP64,
+       dJ/da_c = -tau^2 sum_{k=0}^{N-1} (lambda^{k+1})^T (M^L)^{-1} K_c u^k,
+   the discrete form of int_0^T grad u . grad lambda dt (Eq. (gradient1)),
+   summed over sources.  accumulate = 0 clears the accumulator first.
+   Errors: HYB_ERR_STATE without a preceding forward. */
+hyb_status hyb_adjoint(hyb_mesh* mesh, const void* cotangent, int32_t accumulate);
+
+/* Gradient of the Tikhonov functional Eq. (functional) with respect to the
+   unknown-voxel values (Euclidean, i.e. dF/da_c):
+       g_out[c] = dJ/da_c + gamma |c| (a[c] - a0),
+   dJ/da_c from the adjoint accumulator, |c| = h^3.  g_out: device
+   double[n_unknown].  The accumulator is left unchanged. */
+hyb_status hyb_gradient(hyb_mesh* mesh, const double* a, double gamma, double a0, double* g_out);
+
+/* Data misfit part of Eq. (functional) for a trace recorded by the last
+   forward's sources and time grid, against observations u_obs (both device
+   fields shaped like the trace):
+     J_data = 1/2 sum_{s, k>=1, j} w_k m_j (u - u_obs)^2
+   with w_k = 1, m_j = 1 (HYB_WEIGHTS_PLAIN) or w_k = tau and m_j the lumped
+   face weight h^2, halved on each border of the face
+   (HYB_WEIGHTS_QUADRATURE).  If J_host != NULL the FP64 value is written
+   there (host pointer; the call then synchronises the stream).  If
+   cotangent != NULL it receives c = w m (u - u_obs), the input of
+   hyb_adjoint.  Padding entries of each row are written as 0. */
+hyb_status hyb_misfit(hyb_mesh* mesh, const void* trace, const void* u_obs, int32_t weights,
+                      double* J_host, void* cotangent);
+
+typedef struct {
+  double gamma;      /* Tikhonov weight (Eq. (functional)) */
+  double a0;         /* reference coefficient */
+  double a_min;      /* admissible set [a_min, a_max] (Eq. (admpar)) */
+  double a_max;
+  int32_t weights;   /* HYB_WEIGHTS_* of the misfit */
+} hyb_cg_params;
+
+typedef struct {
+  double* d;         /* device double[n_unknown], previous direction (caller-owned) */
+  double gnorm2;     /* ||g^{m-1}||^2, 0 before the first iteration */
+  double alpha;      /* previous step length, 0 before the first iteration */
+  int32_t iter;      /* m, 0 before the first iteration */
+} hyb_cg_state;
+
+typedef struct {
+  double J;          /* F(a^m) */
+  double J_data;
+  double gnorm;      /* ||g^m||_{L2} over the unknown voxels */
+  double alpha;      /* step taken */
+  double beta;       /* Fletcher-Reeves beta^m */
+  double dJ0;        /* directional derivative along d^m */
+  double alpha_trial;
+  double J_trial;
+} hyb_cg_report;
+
+/* One iteration of Algorithm 3: forward and adjoint at a^m (Step 1), the L2
+   gradient g^m = int grad u . grad lambda dt + gamma (a^m - a0), the
+   Fletcher-Reeves direction d^m = -g^m + beta^m d^{m-1} (Step 2; d^0 = -g^0,
+   reset to -g^m when d^m is not a descent direction), a step length from a
+   parabola through F(0), F'(0) and F at one trial step (the paper leaves this
+   rule open), and the update a^{m+1} = clip(a^m + alpha d^m, a_min, a_max).
+   a: device double[n_unknown], updated in place.  u_obs: device field shaped
+   like the trace.  state, report: host structs.  Synchronises the stream
+   twice (for the line search). */
+hyb_status hyb_cg_step(hyb_mesh* mesh, double* a, const void* u_obs, const hyb_source* src,
+                       int32_t n_src, int32_t nsteps, double dt, const hyb_cg_params* params,
+                       hyb_cg_state* state, hyb_cg_report* report);
+
+/* Copy a field of source `isrc` (HYB_FIELD_*: u^N or u^{N-1} of the last
+   forward, lambda^1 of the last adjoint) into `out` (device field[n_nodes],
+   x fastest). */
+hyb_status hyb_get_field(hyb_mesh* mesh, int32_t which, int32_t isrc, void* out);
+
+/* Wait for the mesh's stream, then report any device-side error flag. */
+hyb_status hyb_sync(hyb_mesh* mesh);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* hyb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYB_H_ */

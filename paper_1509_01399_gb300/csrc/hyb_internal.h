@@ -1,0 +1,102 @@
+// Internal declarations of the hybrid FEM/FDM library: launch arguments of
+// the step kernels and the host-side launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hyb.h"
+
+namespace hyb {
+
+constexpr int kMaxSlots = 16;   // problems advanced by one step launch
+constexpr int kStepThreads = 256;
+constexpr int kReduceBlocks = 512;
+constexpr int kReduceThreads = 256;
+
+// One problem (one source of one mesh) inside a step launch.
+template <typename T>
+struct Slot {
+  const T* cur;      // forward: u^k        adjoint: lambda^{j+1}
+  const T* prev;     // forward: u^{k-1}    adjoint: lambda^{j+2}
+  T* next;           // forward: u^{k+1}    adjoint: lambda^j
+  T* obs_w;          // forward: trace row k+1 (nullptr: not recorded)
+  const T* obs_r;    // adjoint: cotangent row j
+  T* hist_w;         // forward: FEM-owned box slot for u^{k+1} (or nullptr)
+  const T* hist_r;   // adjoint: FEM-owned box slot holding u^j (or nullptr)
+  T srcval;          // forward: tau^2 * 2 p(t_k) / h while the source is on
+  int mask_f;        // absorbing faces of the step (forward: step k, adjoint: B_j)
+  int mask_e;        // adjoint: absorbing faces of E_{j-1}
+  int mask_c;        // adjoint: absorbing faces of C_{j+1}
+  int src_face;      // forward: face carrying the source flux, or -1
+  int obs_face;      // face recorded in the trace / receiving the cotangent
+};
+
+template <typename T>
+struct StepArgs {
+  int nx, ny, nz;
+  int fl[3], fh[3];  // FEM-owned node range (inclusive); fl[0] > fh[0]: no FEM
+  int fn[3];         // FEM-owned box dims (history layout)
+  int wl[3], wn[3];  // edge-weight box: nodes fl-1 .. fh+1
+  long long wsz;     // entries per axis array of the edge-weight box
+  const T* W;        // [3][wsz]: weight of the edge (p, p + e_axis)
+  double* G;         // FP64 gradient accumulator over unknown voxels (adjoint)
+  int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
+  T c2;              // tau^2 / h^2
+  T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
+  int npb;           // thread blocks per lattice plane
+  int zchunk, nzc;   // planes per block, blocks along z
+  int nslots;
+  Slot<T> s[kMaxSlots];
+};
+
+template <typename T>
+void launch_forward(const StepArgs<T>& a, cudaStream_t st);
+template <typename T>
+void launch_adjoint(const StepArgs<T>& a, cudaStream_t st);
+// G[c] += voxel pairing of (u^0 in hist box, lambda^1) for one slot.
+template <typename T>
+void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t st);
+// Edge weights W from the per-voxel coefficient; raises *flag when a value
+// exceeds a_max or is not finite.
+template <typename T>
+void launch_set_coef(const StepArgs<T>& a, T* W, const double* acoef, double a_max, int* flag,
+                     cudaStream_t st);
+// Copy the FEM-owned box of a lattice field into a history slot.
+template <typename T>
+void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStream_t st);
+
+// ---- reductions and CG vector kernels (FP64) ----
+// Misfit over [n_src][nsteps+1][stride]: partials of 1/2 w m (u-obs)^2 and
+// (optionally) cot = w m (u - obs).
+struct MisfitGeom {
+  int n_src, nsteps, stride;
+  int face[kMaxSlots];
+  int np[kMaxSlots], nq[kMaxSlots];  // in-face extents (fast, slow)
+  double wt;                         // time weight for k >= 1
+  double hh;                         // face weight scale (1 or h^2)
+  int halve;                         // halve the face weight on the face border
+};
+template <typename T>
+void launch_misfit(const MisfitGeom& g, const T* trace, const T* obs, T* cot, double* partials,
+                   cudaStream_t st);
+// out[0] = sum of `n` partials (one block, fixed order).
+void launch_sum(const double* partials, int n, double* out, cudaStream_t st);
+// g = scale * sum_s G_s + gamma * vol * (a - a0), G holding n_src arrays of n
+void launch_grad_finalize(const double* G, int n_src, const double* a, double scale, double gamma,
+                          double vol, double a0, double* g, long long n, cudaStream_t st);
+// partials of: [0] sum g^2, [1] sum (a - a0)^2
+void launch_cg_norms(const double* g, const double* a, double a0, long long n, double* partials,
+                     cudaStream_t st);
+// d = -g / vol + beta * d (beta = 0: d = -g / vol)
+void launch_cg_direction(const double* g, double vol, double beta, double* d, long long n,
+                         cudaStream_t st);
+// partials of: [0] sum g d, [1] max |d|
+void launch_cg_dir_stats(const double* g, const double* d, long long n, double* partials,
+                         cudaStream_t st);
+void launch_max(const double* partials, int n, double* out, cudaStream_t st);
+// out = clip(a + alpha d, lo, hi); partials of sum (out - a0)^2
+void launch_cg_axpy_clip(const double* a, const double* d, double alpha, double lo, double hi,
+                         double a0, double* out, long long n, double* partials, cudaStream_t st);
+
+}  // namespace hyb

@@ -1,0 +1,454 @@
+// Time-step kernels of the hybrid FEM/FDM scheme.
+//
+// One launch advances every slot (source / problem) by one time level.  A
+// thread owns one (x, y) column of the lattice and marches a chunk of z
+// planes, keeping u at z-1, z, z+1 in registers; x/y neighbours come through
+// L1.  Three row kinds share the launch:
+//  * FDM rows, Eq. (fdmschemeforward): u^{k+1} = 2u^k - u^{k-1} + tau^2 Delta_h u^k,
+//  * FEM rows on the FEM-owned nodes, Eq. (fem) with lumped mass: on the
+//    Kuhn-cut voxels the row is a 7-point stencil whose axis-edge weight is
+//    W = sum over the four voxels around the edge of a_c / 3 (edge touching
+//    the voxel's diagonal corners) or a_c / 6,
+//  * boundary rows: Neumann mirror ghosts, the plane-wave flux of Eq. (f),
+//    and the absorbing rows of Eq. (eq:abs2), which use the new value of the
+//    inward neighbour; a boundary thread recomputes that value itself, so no
+//    intra-step synchronisation is needed.
+// Both schemes write the same field, so the omega_o / omega_diamond copies
+// of Algorithm 1 need no data movement.
+//
+// The adjoint kernel is the exact transpose of the forward step (the
+// discrete form of Eq. (adjoint1)).  Away from the outer boundary the
+// mass-weighted operator is symmetric, so the transposed row is the forward
+// stencil; within one node of the boundary each node gathers the transposed
+// coefficients of its neighbours' rows (mirror factors, absorbing rows) and
+// solves the transposed absorbing coupling by recomputing the outer values.
+// The same launch accumulates, per unknown voxel and in FP64, the sum over
+// the voxel's 12 axis edges of w_e (u_p - u_q)(lambda_p - lambda_q) with
+// w_e = 1/3 or 1/6; the host scales it by -tau^2 / h^2 (Eq. (gradient1)).
+#include "hyb_internal.h"
+
+namespace hyb {
+namespace {
+
+__device__ __forceinline__ int face_bits(int i, int j, int k, int nx, int ny, int nz) {
+  return (i == 0 ? 1 : 0) | (i == nx - 1 ? 2 : 0) | (j == 0 ? 4 : 0) | (j == ny - 1 ? 8 : 0) |
+         (k == 0 ? 16 : 0) | (k == nz - 1 ? 32 : 0);
+}
+
+template <typename T>
+__device__ __forceinline__ long long lin(const StepArgs<T>& A, int i, int j, int k) {
+  return (long long)i + (long long)A.nx * ((long long)j + (long long)A.ny * k);
+}
+
+template <typename T>
+__device__ __forceinline__ bool fem_owned(const StepArgs<T>& A, int i, int j, int k) {
+  return i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1] && k >= A.fl[2] &&
+         k <= A.fh[2];
+}
+
+template <typename T>
+__device__ __forceinline__ long long widx(const StepArgs<T>& A, int i, int j, int k) {
+  return (long long)(i - A.wl[0]) +
+         (long long)A.wn[0] * ((long long)(j - A.wl[1]) + (long long)A.wn[1] * (k - A.wl[2]));
+}
+
+// sum over the six axis edges of W_e (u_nb - u_c) at a FEM-owned node
+template <typename T>
+__device__ __forceinline__ T fem_lap(const StepArgs<T>& A, const T* __restrict__ u, long long id,
+                                     int i, int j, int k, T c, T zm, T zp) {
+  const long long w = widx(A, i, j, k);
+  const T* Wx = A.W;
+  const T* Wy = A.W + A.wsz;
+  const T* Wz = A.W + 2 * A.wsz;
+  const long long wy = A.wn[0];
+  const long long wz = (long long)A.wn[0] * A.wn[1];
+  return Wx[w] * (u[id + 1] - c) + Wx[w - 1] * (u[id - 1] - c) + Wy[w] * (u[id + A.nx] - c) +
+         Wy[w - wy] * (u[id - A.nx] - c) + Wz[w] * (zp - c) + Wz[w - wz] * (zm - c);
+}
+
+// Laplacian part (without 1/h^2) of a non-absorbing row at any node:
+// FEM stencil on FEM-owned nodes, 7-point with mirror ghosts elsewhere.
+template <typename T>
+__device__ __noinline__ T row_lap(const StepArgs<T>& A, const T* __restrict__ u, int i, int j, int k) {
+  const long long id = lin(A, i, j, k);
+  const long long sz = (long long)A.nx * A.ny;
+  const T c = u[id];
+  if (fem_owned(A, i, j, k)) return fem_lap(A, u, id, i, j, k, c, u[id - sz], u[id + sz]);
+  T lap = T(0);
+  if (i == 0) lap += T(2) * (u[id + 1] - c);
+  else if (i == A.nx - 1) lap += T(2) * (u[id - 1] - c);
+  else lap += (u[id - 1] - c) + (u[id + 1] - c);
+  if (j == 0) lap += T(2) * (u[id + A.nx] - c);
+  else if (j == A.ny - 1) lap += T(2) * (u[id - A.nx] - c);
+  else lap += (u[id - A.nx] - c) + (u[id + A.nx] - c);
+  if (k == 0) lap += T(2) * (u[id + sz] - c);
+  else if (k == A.nz - 1) lap += T(2) * (u[id - sz] - c);
+  else lap += (u[id - sz] - c) + (u[id + sz] - c);
+  return lap;
+}
+
+// u^{k+1} at any node, recursing into the inward neighbours of absorbing
+// rows (depth D bounds the recursion: a node lies on at most 3 faces).
+template <typename T, int D>
+__device__ __noinline__ T fwd_new(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k) {
+  const long long id = lin(A, i, j, k);
+  const int fall = face_bits(i, j, k, A.nx, A.ny, A.nz);
+  if constexpr (D > 0) {
+    const int fb = fall & S.mask_f;
+    if (fb) {
+      T acc = T(0);
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        if (fb & (1 << f)) {
+          const int ax = f >> 1;
+          const int step = (f & 1) ? -1 : 1;  // inward
+          const int i1 = i + (ax == 0 ? step : 0);
+          const int j1 = j + (ax == 1 ? step : 0);
+          const int k1 = k + (ax == 2 ? step : 0);
+          acc += S.cur[lin(A, i1, j1, k1)] - A.r * fwd_new<T, D - 1>(A, S, i1, j1, k1);
+        }
+      }
+      return A.r * S.cur[id] + acc / T(__popc(fb));
+    }
+  }
+  T v = T(2) * S.cur[id] - S.prev[id] + A.c2 * row_lap(A, S.cur, i, j, k);
+  if (S.src_face >= 0 && ((fall >> S.src_face) & 1)) v += S.srcval;
+  return v;
+}
+
+// Coefficient of the non-absorbing row of node (i,j,k) on its neighbour
+// (i,j,k) + s e_ax (Laplacian part, without 1/h^2).
+template <typename T>
+__device__ T row_coef(const StepArgs<T>& A, int i, int j, int k, int ax, int s) {
+  if (fem_owned(A, i, j, k)) {
+    const long long w = widx(A, i, j, k);
+    const long long ws = ax == 0 ? 1 : (ax == 1 ? (long long)A.wn[0] : (long long)A.wn[0] * A.wn[1]);
+    return A.W[ax * A.wsz + (s > 0 ? w : w - ws)];
+  }
+  const int c = ax == 0 ? i : (ax == 1 ? j : k);
+  const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
+  if ((s > 0 && c == 0) || (s < 0 && c == n - 1)) return T(2);
+  return T(1);
+}
+
+template <typename T>
+__device__ T row_diag(const StepArgs<T>& A, int i, int j, int k) {
+  if (fem_owned(A, i, j, k)) {
+    const long long w = widx(A, i, j, k);
+    const long long wy = A.wn[0];
+    const long long wz = (long long)A.wn[0] * A.wn[1];
+    const T* W = A.W;
+    return -(W[w] + W[w - 1] + W[A.wsz + w] + W[A.wsz + w - wy] + W[2 * A.wsz + w] +
+             W[2 * A.wsz + w - wz]);
+  }
+  return T(-6);
+}
+
+__device__ __forceinline__ int face_index(int f, int i, int j, int k, int nx, int ny) {
+  const int ax = f >> 1;
+  if (ax == 2) return i + nx * j;
+  if (ax == 1) return i + nx * k;
+  return j + ny * k;
+}
+
+// Right-hand side of the transposed step at node m:
+// (B_j^T lambda^{j+1})_m - (C_{j+1}^T lambda^{j+2})_m + c^j_m.
+template <typename T>
+__device__ __noinline__ T adj_rhs(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k) {
+  const T* __restrict__ l1 = S.cur;
+  const long long id = lin(A, i, j, k);
+  const int fbm = face_bits(i, j, k, A.nx, A.ny, A.nz);
+  T rhs;
+  if (fbm & S.mask_f) rhs = A.r * l1[id];
+  else rhs = (T(2) + A.c2 * row_diag(A, i, j, k)) * l1[id];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int s = t ? 1 : -1;
+      const int ni = i + (ax == 0 ? s : 0);
+      const int nj = j + (ax == 1 ? s : 0);
+      const int nk = k + (ax == 2 ? s : 0);
+      if (ni < 0 || ni >= A.nx || nj < 0 || nj >= A.ny || nk < 0 || nk >= A.nz) continue;
+      const long long nid = lin(A, ni, nj, nk);
+      const int fbn = face_bits(ni, nj, nk, A.nx, A.ny, A.nz) & S.mask_f;
+      if (fbn) {
+        // absorbing row of the neighbour couples to m only when m is its
+        // inward neighbour across the face on side s of axis ax
+        const int f = 2 * ax + (s > 0 ? 1 : 0);
+        if (fbn & (1 << f)) rhs += l1[nid] / T(__popc(fbn));
+      } else {
+        rhs += A.c2 * row_coef(A, ni, nj, nk, ax, -s) * l1[nid];
+      }
+    }
+  }
+  if (!(fbm & S.mask_c)) rhs -= S.prev[id];
+  if (S.obs_r && ((fbm >> S.obs_face) & 1)) rhs += S.obs_r[face_index(S.obs_face, i, j, k, A.nx, A.ny)];
+  return rhs;
+}
+
+// lambda^j at node m: solve E_{j-1}^T lambda^j = rhs, where E couples an
+// absorbing node b to its inward neighbours with r / L_b.
+template <typename T, int D>
+__device__ __noinline__ T adj_new(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k) {
+  T v = adj_rhs(A, S, i, j, k);
+  if constexpr (D > 0) {
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int s = t ? 1 : -1;
+        const int bi = i + (ax == 0 ? s : 0);
+        const int bj = j + (ax == 1 ? s : 0);
+        const int bk = k + (ax == 2 ? s : 0);
+        if (bi < 0 || bi >= A.nx || bj < 0 || bj >= A.ny || bk < 0 || bk >= A.nz) continue;
+        const int f = 2 * ax + (s > 0 ? 1 : 0);
+        const int fbb = face_bits(bi, bj, bk, A.nx, A.ny, A.nz) & S.mask_e;
+        if (fbb & (1 << f)) v -= (A.r / T(__popc(fbb))) * adj_new<T, D - 1>(A, S, bi, bj, bk);
+      }
+    }
+  }
+  return v;
+}
+
+// sum over the 12 axis edges of voxel (i,j,k) of w_e (u_p - u_q)(l_p - l_q)
+template <typename T>
+__device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restrict__ hb,
+                                        const T* __restrict__ lam, int i, int j, int k) {
+  const long long hy = A.fn[0];
+  const long long hz = (long long)A.fn[0] * A.fn[1];
+  const long long h0 = (long long)(i - A.fl[0]) + hy * (j - A.fl[1]) + hz * (k - A.fl[2]);
+  const long long ly = A.nx;
+  const long long lz = (long long)A.nx * A.ny;
+  const long long l0 = lin(A, i, j, k);
+  T u[8], l[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+    u[c] = hb[h0 + a + b * hy + d * hz];
+    l[c] = lam[l0 + a + b * ly + d * lz];
+  }
+  const T d3 = (u[1] - u[0]) * (l[1] - l[0]) + (u[7] - u[6]) * (l[7] - l[6]) +
+               (u[2] - u[0]) * (l[2] - l[0]) + (u[7] - u[5]) * (l[7] - l[5]) +
+               (u[4] - u[0]) * (l[4] - l[0]) + (u[7] - u[3]) * (l[7] - l[3]);
+  const T d6 = (u[3] - u[2]) * (l[3] - l[2]) + (u[5] - u[4]) * (l[5] - l[4]) +
+               (u[3] - u[1]) * (l[3] - l[1]) + (u[6] - u[4]) * (l[6] - l[4]) +
+               (u[5] - u[1]) * (l[5] - l[1]) + (u[6] - u[2]) * (l[6] - l[2]);
+  return d3 / T(3) + d6 / T(6);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStepThreads) fwd_kernel(const __grid_constant__ StepArgs<T> A) {
+  const int tps = A.npb * A.nzc;
+  const int si = blockIdx.x / tps;
+  const int rem = blockIdx.x - si * tps;
+  const int zc = rem / A.npb;
+  const int pb = rem - zc * A.npb;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int q = pb * kStepThreads + threadIdx.x;
+  if (q >= nx * ny) return;
+  const int j = q / nx;
+  const int i = q - j * nx;
+  const Slot<T>& S = A.s[si];
+  const long long plane = (long long)nx * ny;
+  const int z0 = zc * A.zchunk;
+  const int z1 = min(z0 + A.zchunk, nz);
+  const T* __restrict__ u = S.cur;
+  const T* __restrict__ up = S.prev;
+  T* __restrict__ un = S.next;
+  const bool xy_bnd = (i == 0 || i == nx - 1 || j == 0 || j == ny - 1);
+  const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
+  const int obs_ax = S.obs_face >> 1;
+  long long id = q + (long long)z0 * plane;
+  T cm = z0 > 0 ? u[id - plane] : T(0);
+  T c0 = u[id];
+  for (int k = z0; k < z1; ++k, id += plane) {
+    const T cp = (k + 1 < nz) ? u[id + plane] : T(0);
+    T val;
+    if (xy_bnd || k == 0 || k == nz - 1) {
+      val = fwd_new<T, 3>(A, S, i, j, k);
+    } else if (xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
+      val = T(2) * c0 - up[id] + A.c2 * fem_lap(A, u, id, i, j, k, c0, cm, cp);
+    } else {
+      const T lap = (u[id - 1] - c0) + (u[id + 1] - c0) + (u[id - nx] - c0) + (u[id + nx] - c0) +
+                    (cm - c0) + (cp - c0);
+      val = T(2) * c0 - up[id] + A.c2 * lap;
+    }
+    un[id] = val;
+    if (S.obs_w) {
+      const int side = S.obs_face & 1;
+      const int c = obs_ax == 0 ? i : (obs_ax == 1 ? j : k);
+      const int n = obs_ax == 0 ? nx : (obs_ax == 1 ? ny : nz);
+      if (c == (side ? n - 1 : 0)) S.obs_w[face_index(S.obs_face, i, j, k, nx, ny)] = val;
+    }
+    if (S.hist_w && xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
+      S.hist_w[(long long)(i - A.fl[0]) +
+               (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] = val;
+    }
+    cm = c0;
+    c0 = cp;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStepThreads) adj_kernel(const __grid_constant__ StepArgs<T> A) {
+  const int tps = A.npb * A.nzc;
+  const int si = blockIdx.x / tps;
+  const int rem = blockIdx.x - si * tps;
+  const int zc = rem / A.npb;
+  const int pb = rem - zc * A.npb;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int q = pb * kStepThreads + threadIdx.x;
+  if (q >= nx * ny) return;
+  const int j = q / nx;
+  const int i = q - j * nx;
+  const Slot<T>& S = A.s[si];
+  const long long plane = (long long)nx * ny;
+  const int z0 = zc * A.zchunk;
+  const int z1 = min(z0 + A.zchunk, nz);
+  const T* __restrict__ l1 = S.cur;
+  const T* __restrict__ l2 = S.prev;
+  T* __restrict__ ln = S.next;
+  const bool xy_near = (i <= 1 || i >= nx - 2 || j <= 1 || j >= ny - 2);
+  const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
+  const bool xy_vox = S.hist_r != nullptr && i >= A.fl[0] && i < A.fl[0] + A.un[0] &&
+                      j >= A.fl[1] && j < A.fl[1] + A.un[1];
+  double* __restrict__ grad = A.G;
+  long long id = q + (long long)z0 * plane;
+  T cm = z0 > 0 ? l1[id - plane] : T(0);
+  T c0 = l1[id];
+  for (int k = z0; k < z1; ++k, id += plane) {
+    const T cp = (k + 1 < nz) ? l1[id + plane] : T(0);
+    T val;
+    if (xy_near || k <= 1 || k >= nz - 2) {
+      val = adj_new<T, 3>(A, S, i, j, k);
+    } else if (xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
+      val = T(2) * c0 - l2[id] + A.c2 * fem_lap(A, l1, id, i, j, k, c0, cm, cp);
+    } else {
+      const T lap = (l1[id - 1] - c0) + (l1[id + 1] - c0) + (l1[id - nx] - c0) +
+                    (l1[id + nx] - c0) + (cm - c0) + (cp - c0);
+      val = T(2) * c0 - l2[id] + A.c2 * lap;
+    }
+    ln[id] = val;
+    if (xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
+      const long long vid = (long long)(i - A.fl[0]) +
+                            (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
+      double* g = grad + (long long)si * A.un[0] * A.un[1] * A.un[2];
+      g[vid] += (double)voxel_pair(A, S.hist_r, l1, i, j, k);
+    }
+    cm = c0;
+    c0 = cp;
+  }
+}
+
+template <typename T>
+__global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __restrict__ hist,
+                            const T* __restrict__ lam, double* __restrict__ grad) {
+  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv) return;
+  const int x = (int)(t % A.un[0]);
+  const long long r = t / A.un[0];
+  const int y = (int)(r % A.un[1]);
+  const int z = (int)(r / A.un[1]);
+  grad[t] += (double)voxel_pair(A, hist, lam, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z);
+}
+
+template <typename T>
+__global__ void set_coef_kernel(const __grid_constant__ StepArgs<T> A, T* __restrict__ W,
+                                const double* __restrict__ a, double a_max, int* flag) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+  if (t < nv) {
+    const double v = a[t];
+    if (!(v <= a_max * (1.0 + 1e-12)) || !(v == v)) atomicExch(flag, 1);
+  }
+  if (t >= A.wsz) return;
+  const int p[3] = {A.wl[0] + (int)(t % A.wn[0]), A.wl[1] + (int)((t / A.wn[0]) % A.wn[1]),
+                    A.wl[2] + (int)(t / ((long long)A.wn[0] * A.wn[1]))};
+  for (int ax = 0; ax < 3; ++ax) {
+    double w = 0.0;
+    if (p[ax] + 1 <= A.wl[ax] + A.wn[ax] - 1) {
+      const int P = ax == 0 ? 1 : 0;
+      const int Q = ax == 2 ? 1 : 2;
+      for (int bp = 0; bp < 2; ++bp) {
+        for (int bq = 0; bq < 2; ++bq) {
+          int v[3] = {p[0], p[1], p[2]};
+          v[P] -= bp;
+          v[Q] -= bq;
+          double av = 1.0;
+          if (v[0] >= A.fl[0] && v[0] < A.fl[0] + A.un[0] && v[1] >= A.fl[1] &&
+              v[1] < A.fl[1] + A.un[1] && v[2] >= A.fl[2] && v[2] < A.fl[2] + A.un[2]) {
+            av = a[(long long)(v[0] - A.fl[0]) +
+                   (long long)A.un[0] * ((v[1] - A.fl[1]) + (long long)A.un[1] * (v[2] - A.fl[2]))];
+          }
+          w += av * (bp == bq ? (1.0 / 3.0) : (1.0 / 6.0));
+        }
+      }
+    }
+    W[ax * A.wsz + t] = (T)w;
+  }
+}
+
+template <typename T>
+__global__ void extract_owned_kernel(const __grid_constant__ StepArgs<T> A, const T* __restrict__ f,
+                                     T* __restrict__ box) {
+  const long long n = (long long)A.fn[0] * A.fn[1] * A.fn[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int x = (int)(t % A.fn[0]);
+  const long long r = t / A.fn[0];
+  const int y = (int)(r % A.fn[1]);
+  const int z = (int)(r / A.fn[1]);
+  box[t] = f[lin(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z)];
+}
+
+}  // namespace
+
+template <typename T>
+void launch_forward(const StepArgs<T>& a, cudaStream_t st) {
+  const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
+  fwd_kernel<T><<<grid, kStepThreads, 0, st>>>(a);
+}
+
+template <typename T>
+void launch_adjoint(const StepArgs<T>& a, cudaStream_t st) {
+  const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
+  adj_kernel<T><<<grid, kStepThreads, 0, st>>>(a);
+}
+
+template <typename T>
+void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t st) {
+  const long long nv = (long long)a.un[0] * a.un[1] * a.un[2];
+  if (nv == 0) return;
+  pair_kernel<T><<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(a, hist, lam, a.G);
+}
+
+template <typename T>
+void launch_set_coef(const StepArgs<T>& a, T* W, const double* acoef, double a_max, int* flag,
+                     cudaStream_t st) {
+  const long long nv = (long long)a.un[0] * a.un[1] * a.un[2];
+  const long long n = a.wsz > nv ? a.wsz : nv;
+  if (n == 0) return;
+  set_coef_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, W, acoef, a_max, flag);
+}
+
+template <typename T>
+void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStream_t st) {
+  const long long n = (long long)a.fn[0] * a.fn[1] * a.fn[2];
+  if (n == 0) return;
+  extract_owned_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, field, box);
+}
+
+#define HYB_INSTANTIATE(T)                                                                       \
+  template void launch_forward<T>(const StepArgs<T>&, cudaStream_t);                             \
+  template void launch_adjoint<T>(const StepArgs<T>&, cudaStream_t);                             \
+  template void launch_pair<T>(const StepArgs<T>&, const T*, const T*, cudaStream_t);            \
+  template void launch_set_coef<T>(const StepArgs<T>&, T*, const double*, double, int*,         \
+                                   cudaStream_t);                                                \
+  template void launch_extract_owned<T>(const StepArgs<T>&, const T*, T*, cudaStream_t);
+
+HYB_INSTANTIATE(float)
+HYB_INSTANTIATE(double)
+
+}  // namespace hyb
