@@ -60,7 +60,7 @@ enum { HYB_FP64 = 0, HYB_FP32 = 1 };
 enum { HYB_WEIGHTS_PLAIN = 0, HYB_WEIGHTS_QUADRATURE = 1 };
 enum { HYB_FIELD_U_LAST = 0, HYB_FIELD_U_PREV = 1, HYB_FIELD_LAMBDA_FIRST = 2 };
 
-/* Mesh description (Sec. 8 geometry; Algorithm 1 node classes). */
+/* Mesh description (Sec. 9 geometry; Algorithm 1 node classes). */
 typedef struct {
   int32_t n[3];        /* lattice nodes per axis, each >= 3 */
   double h;            /* lattice spacing, the same on every axis (Eq. (CFL)) */

@@ -8,39 +8,39 @@ never calls it.
 What it computes, in the paper's order and notation (numpy / scipy.sparse,
 float64 throughout):
 
-* Mesh (Sec. 6.1, Sec. 3): a structured lattice of nodes x = origin + h (i, j, k);
+* Mesh (Sec. 7.1, Sec. 3): a structured lattice of nodes x = origin + h (i, j, k);
   a finite-element block of nodes lo..hi whose voxels are each cut into the six
   Kuhn tetrahedra along the voxel diagonal; the node classes of Algorithm 1:
   omega_o (the block's boundary shell, owned by the FDM), omega_diamond (the
   next shell inward, owned by the FEM), omega_* (the FEM interior) and
   omega_+ (every other lattice node, FDM).
-* FEM operators (Sec. 6.2): element mass and stiffness of P1 functions,
+* FEM operators (Sec. 7.1-7.2): element mass and stiffness of P1 functions,
   M^K_ij = (phi_i, phi_j)_K and K^K_ij = (a_h grad phi_i, grad phi_j)_K, with
   the mass matrix lumped by rows and the coefficient a_h piecewise constant
   (Eq. (p0)), one value per voxel.  The explicit scheme is Eq. (fem):
   u^{k+1} = (2 - tau^2 (M^L)^{-1} K) u^k - u^{k-1} (the G term only acts on
   rows of nodes on the FEM block boundary, which Algorithm 1 overwrites from
   the FDM, so it never reaches an owned row).
-* FDM (Sec. 6.3): the leapfrog Eq. (fdmschemeforward) with the 7-point
+* FDM (Sec. 7.3): the leapfrog Eq. (fdmschemeforward) with the 7-point
   Laplacian; Neumann faces by a mirror ghost; the plane-wave source
   d_n u = p(t) of Model Problem 2 (Eq. (model2), Eq. (f)) by the ghost
   u_g = u_in + 2 h p.
-* Absorbing faces (Sec. 6.4): Eq. (eq:abs2),
+* Absorbing faces (Sec. 7.4): Eq. (eq:abs2),
   u_b^{k+1} = u_{b1}^k + r u_b^k - r u_{b1}^{k+1},  r = (h - tau) / (h + tau),
   applied after the interior rows of the same time level; a node on several
   absorbing faces takes the mean of its per-face formulas, faces before edges
   before corners.
-* Algorithm 2 (Sec. 6.5): per time step, update the FDM-owned rows, update
+* Algorithm 2 (Sec. 7.5): per time step, update the FDM-owned rows, update
   the FEM-owned rows, copy omega_diamond from FEM to FDM and omega_o from FDM
   to FEM, swap levels.
-* Adjoint and gradient (Sec. 5, Eq. (lagrangian1) - Eq. (grad1new),
+* Adjoint and gradient (Sec. 6, Eq. (lagrangian1) - Eq. (grad1new),
   Eq. (gradient1)): the exact discrete adjoint of the time stepping, obtained
   by writing each step as E_k u^{k+1} = B_k u^k - C_k u^{k-1} + s_k and
   transposing those matrices literally; the conductivity gradient is
   dJ/da_c = -tau^2 sum_k (lambda^{k+1})^T (M^L)^{-1} K_c u^k, the discrete
   form of int_0^T grad u . grad lambda dt.
 * Tikhonov functional (Eq. (functional)) and one conjugate-gradient update of
-  Algorithm 3 (Sec. 7) with a quadratic-fit step length.
+  Algorithm 3 (Sec. 8) with a quadratic-fit step length.
 """
 from __future__ import annotations
 
@@ -60,7 +60,7 @@ def p1_element(X: np.ndarray):
     """Volumes and barycentric gradients of P1 tetrahedra.
 
     X: (T, 4, 3) vertex coordinates.  Returns vol (T,) and grads (T, 4, 3)
-    where grads[t, i] = grad phi_i on tetrahedron t (Sec. 6.2: the P1 basis
+    where grads[t, i] = grad phi_i on tetrahedron t (Sec. 7.2: the P1 basis
     functions of the reference element mapped by F_K)."""
     T = X.shape[0]
     A = np.concatenate([np.ones((T, 4, 1)), X], axis=2)  # rows: (1, x_v)
@@ -72,7 +72,7 @@ def p1_element(X: np.ndarray):
 
 
 def element_stiffness(vol, grads, a_tet):
-    """K^K_ij = a_K |K| grad phi_i . grad phi_j (Sec. 6.2)."""
+    """K^K_ij = a_K |K| grad phi_i . grad phi_j (Sec. 7.2)."""
     return (a_tet * vol)[:, None, None] * np.einsum("tid,tjd->tij", grads, grads)
 
 
@@ -192,7 +192,7 @@ class Problem:
 
     # ------------------------------------------------------------- operators
     def _fdm_laplacian(self):
-        """7-point Delta_h of Sec. 6.3 on every lattice node, Neumann mirror
+        """7-point Delta_h of Sec. 7.3 on every lattice node, Neumann mirror
         ghost u_{-1} = u_{1} on the outer faces (the ghost values of source
         faces add a constant, handled in the source term)."""
         rows, cols, vals = [], [], []

@@ -33,6 +33,39 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Identity of one sweep's launch sequence: everything baked into the kernel
+// parameters of a captured CUDA graph.
+struct SweepKey {
+  int kind = -1;  // 0 forward keeping history, 1 forward without, 2 adjoint
+  const void* io = nullptr;
+  int accumulate = 0;
+  int nsteps = 0, nsrc = 0;
+  double dt = 0.0;
+  int face[16] = {0};
+  double omega[16] = {0.0}, amp[16] = {0.0};
+  const void* bufs[8] = {nullptr};
+};
+
+bool same_key(const SweepKey& a, const SweepKey& b) {
+  if (a.kind != b.kind || a.io != b.io || a.accumulate != b.accumulate || a.nsteps != b.nsteps ||
+      a.nsrc != b.nsrc || a.dt != b.dt)
+    return false;
+  for (int i = 0; i < a.nsrc; ++i)
+    if (a.face[i] != b.face[i] || a.omega[i] != b.omega[i] || a.amp[i] != b.amp[i]) return false;
+  for (int i = 0; i < 8; ++i)
+    if (a.bufs[i] != b.bufs[i]) return false;
+  return true;
+}
+
+// A sweep is captured into a graph the second time the same key is seen and
+// replayed while the key stays the same.
+struct SweepGraph {
+  SweepKey key, last;
+  bool seen = false;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+};
+
 }  // namespace
 
 struct hyb_mesh {
@@ -55,6 +88,8 @@ struct hyb_mesh {
   hyb_source src[kMaxSlots];
   long long launches = 0;
   long long bytes = 0;
+  cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
+  SweepGraph graphs[3];
 };
 
 #define HYB_CU(call)                                                                      \
@@ -108,6 +143,74 @@ void release(DevBuf& b) {
 
 size_t esize(const hyb_mesh* m) { return m->d.precision == HYB_FP64 ? 8 : 4; }
 
+SweepKey make_key(const hyb_mesh* m, int kind, const void* io, int accumulate, int nsteps, int nsrc, double dt,
+                  const hyb_source* src) {
+  SweepKey k;
+  k.kind = kind;
+  k.io = io;
+  k.accumulate = accumulate;
+  k.nsteps = nsteps;
+  k.nsrc = nsrc;
+  k.dt = dt;
+  for (int i = 0; i < nsrc; ++i) {
+    k.face[i] = src[i].face;
+    k.omega[i] = src[i].omega;
+    k.amp[i] = src[i].amp;
+  }
+  const void* b[8] = {m->U.p, m->L.p, m->hist.p, m->ckpt.p, m->G.p, m->W.p, nullptr, nullptr};
+  for (int i = 0; i < 8; ++i) k.bufs[i] = b[i];
+  return k;
+}
+
+// Run a sweep body (memsets, copies and step launches on the given stream):
+// replay its graph when the key matches the captured one, capture it on the
+// second call with the same key, run it directly otherwise.  Bodies must not
+// allocate or synchronise.
+template <class Body>
+hyb_status run_sweep(hyb_mesh* m, SweepGraph& g, const SweepKey& key, Body body) {
+  if (g.exec && same_key(g.key, key)) {
+    HYB_CU(cudaGraphLaunch(g.exec, m->st));
+    m->launches += g.launches;
+    return HYB_OK;
+  }
+  const bool capture = g.seen && same_key(g.last, key);
+  g.last = key;
+  g.seen = true;
+  if (!capture) return body(m->st);
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return body(m->st);
+  }
+  const long long l0 = m->launches;
+  const hyb_status st = body(m->cap);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(m->cap, &graph);
+  const long long n = m->launches - l0;
+  m->launches = l0;
+  if (st != HYB_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st != HYB_OK) return st;
+    return body(m->st);
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    g.exec = nullptr;
+    return body(m->st);
+  }
+  g.key = key;
+  g.launches = n;
+  HYB_CU(cudaGraphLaunch(g.exec, m->st));
+  m->launches += n;
+  return HYB_OK;
+}
+
 // Boundary state of the step leaving t_k = k dt for one source: the source
 // face carries the Neumann flux p(t_k) = amp sin(omega t_k) while
 // t_k <= 2 pi / omega (Eq. (f), Model Problem 2) and otherwise takes the
@@ -133,23 +236,35 @@ int mask_at(const hyb_mesh* m, const hyb_source& s, int k, double dt) {
   return mask;
 }
 
-void tile_shape(const hyb_mesh* m, int nslots, int* npb, int* zchunk, int* nzc) {
-  const long long plane = (long long)m->n[0] * m->n[1];
+// Launch geometry of one step: the interior box (nodes TH .. n-1-TH on every
+// axis) goes to the z-marching interior kernel, the rest of the lattice (the
+// boundary shell of thickness TH) to the shell kernel.
+void step_geometry(const hyb_mesh* m, int nslots, int TH, int* npb, int* zchunk, int* nzc, long long* nshell) {
+  const long long bx = std::max(m->n[0] - 2 * TH, 0);
+  const long long by = std::max(m->n[1] - 2 * TH, 0);
+  const long long bz = std::max(m->n[2] - 2 * TH, 0);
+  *nshell = m->N - bx * by * bz;
+  const long long plane = bx * by;
+  if (plane == 0 || bz == 0) {
+    *npb = 0;
+    *zchunk = 1;
+    *nzc = 0;
+    return;
+  }
   *npb = (int)((plane + kStepThreads - 1) / kStepThreads);
   const long long target = 152LL * 8;  // resident blocks wanted on 152 SMs
   const long long per_z = (long long)(*npb) * nslots;
   long long want = (target + per_z - 1) / per_z;
   if (want < 1) want = 1;
-  const int nz = m->n[2];
-  long long z = (nz + want - 1) / want;
+  long long z = (bz + want - 1) / want;
   z = std::max<long long>(z, 2);
-  z = std::min<long long>(z, nz);
+  z = std::min<long long>(z, bz);
   *zchunk = (int)z;
-  *nzc = (int)((nz + z - 1) / z);
+  *nzc = (int)((bz + z - 1) / z);
 }
 
 template <typename T>
-void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
+void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots, int TH) {
   std::memset(&A, 0, sizeof(A));
   A.nx = m->n[0];
   A.ny = m->n[1];
@@ -168,7 +283,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   const double h = m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
   A.r = (T)((h - dt) / (h + dt));
-  tile_shape(m, nslots, &A.npb, &A.zchunk, &A.nzc);
+  step_geometry(m, nslots, TH, &A.npb, &A.zchunk, &A.nzc, &A.nshell);
   A.nslots = nslots;
 }
 
@@ -220,34 +335,38 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
     }
   }
   StepArgs<T> A;
-  base_args(m, A, dt, nsrc);
+  base_args(m, A, dt, nsrc, 1);
   if (m->fem) {
     launch_set_coef<T>(A, (T*)m->W.p, a, m->d.a_max, (int*)m->flag.p, m->st);
     HYB_LAUNCHED(m);
   }
-  for (int s = 0; s < nsrc; ++s) {
-    HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, 0), 0, fb, m->st));
-    HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, -1), 0, fb, m->st));
-  }
-  if (trace) HYB_CU(cudaMemsetAsync(trace, 0, (size_t)nsrc * (nsteps + 1) * m->obs_stride * sizeof(T), m->st));
-  T* hist = (T*)m->hist.p;
-  if (keep && !ckpt && m->nown > 0) HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->nown * sizeof(T), m->st));
-  const size_t lvl = (size_t)nsrc * m->nown;
-  for (int k = 0; k < nsteps; ++k) {
-    if (keep && ckpt && m->nown > 0 && k > 0 && k % C == 0) {
-      const size_t seg = (size_t)(k / C);
-      for (int s = 0; s < nsrc; ++s) {
-        char* base = (char*)m->ckpt.p + ((seg * nsrc + s) * 2) * fb;
-        HYB_CU(cudaMemcpyAsync(base, field_buf<T>(m, m->U, nsrc, s, k), fb, cudaMemcpyDeviceToDevice, m->st));
-        HYB_CU(cudaMemcpyAsync(base + fb, field_buf<T>(m, m->U, nsrc, s, k - 1), fb,
-                               cudaMemcpyDeviceToDevice, m->st));
-      }
+  auto body = [&](cudaStream_t st) -> hyb_status {
+    for (int s = 0; s < nsrc; ++s) {
+      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, 0), 0, fb, st));
+      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, -1), 0, fb, st));
     }
-    T* hl = (keep && !ckpt && m->nown > 0 && k + 1 <= nsteps - 1) ? hist + (size_t)(k + 1) * lvl : nullptr;
-    forward_slots<T>(m, A, src, nsrc, nsteps, dt, k, trace, hl);
-    launch_forward<T>(A, m->st);
-    HYB_LAUNCHED(m);
-  }
+    if (trace) HYB_CU(cudaMemsetAsync(trace, 0, (size_t)nsrc * (nsteps + 1) * m->obs_stride * sizeof(T), st));
+    T* hist = (T*)m->hist.p;
+    if (keep && !ckpt && m->nown > 0) HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->nown * sizeof(T), st));
+    const size_t lvl = (size_t)nsrc * m->nown;
+    for (int k = 0; k < nsteps; ++k) {
+      if (keep && ckpt && m->nown > 0 && k > 0 && k % C == 0) {
+        const size_t seg = (size_t)(k / C);
+        for (int s = 0; s < nsrc; ++s) {
+          char* base = (char*)m->ckpt.p + ((seg * nsrc + s) * 2) * fb;
+          HYB_CU(cudaMemcpyAsync(base, field_buf<T>(m, m->U, nsrc, s, k), fb, cudaMemcpyDeviceToDevice, st));
+          HYB_CU(cudaMemcpyAsync(base + fb, field_buf<T>(m, m->U, nsrc, s, k - 1), fb, cudaMemcpyDeviceToDevice,
+                                 st));
+        }
+      }
+      T* hl = (keep && !ckpt && m->nown > 0 && k + 1 <= nsteps - 1) ? hist + (size_t)(k + 1) * lvl : nullptr;
+      forward_slots<T>(m, A, src, nsrc, nsteps, dt, k, trace, hl);
+      launch_forward<T>(A, st);
+      HYB_LAUNCHED(m);
+    }
+    return HYB_OK;
+  };
+  HYB_TRY(run_sweep(m, m->graphs[keep ? 0 : 1], make_key(m, keep ? 0 : 1, trace, 0, nsteps, nsrc, dt, src), body));
   m->nsteps = nsteps;
   m->nsrc = nsrc;
   m->dt = dt;
@@ -280,11 +399,11 @@ void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const
 }
 
 template <typename T>
-hyb_status pair_first(hyb_mesh* m, StepArgs<T>& A, const T* level0) {
+hyb_status pair_first(hyb_mesh* m, StepArgs<T>& A, const T* level0, cudaStream_t st) {
   for (int s = 0; s < m->nsrc; ++s) {
     StepArgs<T> B = A;
     B.G = (double*)m->G.p + (size_t)s * m->nu;
-    launch_pair<T>(B, level0 + (size_t)s * m->nown, field_buf<T>(m, m->L, m->nsrc, s, 1), m->st);
+    launch_pair<T>(B, level0 + (size_t)s * m->nown, field_buf<T>(m, m->L, m->nsrc, s, 1), st);
     HYB_LAUNCHED(m);
   }
   return HYB_OK;
@@ -300,27 +419,31 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   const bool ckpt = C > 0;
   HYB_TRY(ensure(m, m->L, 3 * (size_t)nsrc * fb));
   HYB_TRY(ensure(m, m->G, (size_t)nsrc * m->nu * sizeof(double)));
-  if (!accumulate) HYB_CU(cudaMemsetAsync(m->G.p, 0, (size_t)nsrc * m->nu * sizeof(double), m->st));
-  StepArgs<T> A;
-  base_args(m, A, dt, nsrc);
-  for (int s = 0; s < nsrc; ++s) {
-    HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, nsteps + 1), 0, fb, m->st));
-    HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, nsteps + 2), 0, fb, m->st));
-  }
-  T* hist = (T*)m->hist.p;
-  const size_t lvl = (size_t)nsrc * m->nown;
-  const bool pairing = m->nu > 0 && m->nown > 0;
-  if (!ckpt) {
-    for (int j = nsteps; j >= 1; --j) {
-      const T* hl = (pairing && j <= nsteps - 1) ? hist + (size_t)j * lvl : nullptr;
-      adjoint_slots<T>(m, A, cot, j, hl);
-      launch_adjoint<T>(A, m->st);
-      HYB_LAUNCHED(m);
+  StepArgs<T> A;   // adjoint steps (boundary shell of thickness 2)
+  base_args(m, A, dt, nsrc, 2);
+  StepArgs<T> F;   // recomputed forward steps (shell of thickness 1)
+  base_args(m, F, dt, nsrc, 1);
+  auto body = [&](cudaStream_t st) -> hyb_status {
+    if (!accumulate) HYB_CU(cudaMemsetAsync(m->G.p, 0, (size_t)nsrc * m->nu * sizeof(double), st));
+    for (int s = 0; s < nsrc; ++s) {
+      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, nsteps + 1), 0, fb, st));
+      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, nsteps + 2), 0, fb, st));
     }
-    if (pairing) HYB_TRY(pair_first<T>(m, A, hist));
-  } else {
+    T* hist = (T*)m->hist.p;
+    const size_t lvl = (size_t)nsrc * m->nown;
+    const bool pairing = m->nu > 0 && m->nown > 0;
+    if (!ckpt) {
+      for (int j = nsteps; j >= 1; --j) {
+        const T* hl = (pairing && j <= nsteps - 1) ? hist + (size_t)j * lvl : nullptr;
+        adjoint_slots<T>(m, A, cot, j, hl);
+        launch_adjoint<T>(A, st);
+        HYB_LAUNCHED(m);
+      }
+      if (pairing) HYB_TRY(pair_first<T>(m, A, hist, st));
+      return HYB_OK;
+    }
     adjoint_slots<T>(m, A, cot, nsteps, nullptr);
-    launch_adjoint<T>(A, m->st);
+    launch_adjoint<T>(A, st);
     HYB_LAUNCHED(m);
     const int nseg = (nsteps + C - 1) / C;
     for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -331,30 +454,32 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
           T* u0 = field_buf<T>(m, m->U, nsrc, s, kb);
           T* um = field_buf<T>(m, m->U, nsrc, s, kb - 1);
           if (seg == 0) {
-            HYB_CU(cudaMemsetAsync(u0, 0, fb, m->st));
-            HYB_CU(cudaMemsetAsync(um, 0, fb, m->st));
+            HYB_CU(cudaMemsetAsync(u0, 0, fb, st));
+            HYB_CU(cudaMemsetAsync(um, 0, fb, st));
           } else {
             const char* base = (const char*)m->ckpt.p + (((size_t)seg * nsrc + s) * 2) * fb;
-            HYB_CU(cudaMemcpyAsync(u0, base, fb, cudaMemcpyDeviceToDevice, m->st));
-            HYB_CU(cudaMemcpyAsync(um, base + fb, fb, cudaMemcpyDeviceToDevice, m->st));
+            HYB_CU(cudaMemcpyAsync(u0, base, fb, cudaMemcpyDeviceToDevice, st));
+            HYB_CU(cudaMemcpyAsync(um, base + fb, fb, cudaMemcpyDeviceToDevice, st));
           }
-          launch_extract_owned<T>(A, u0, hist + (size_t)s * m->nown, m->st);
+          launch_extract_owned<T>(F, u0, hist + (size_t)s * m->nown, st);
           HYB_LAUNCHED(m);
         }
         for (int k = kb; k < ke; ++k) {
-          forward_slots<T>(m, A, m->src, nsrc, nsteps, dt, k, nullptr, hist + (size_t)(k + 1 - kb) * lvl);
-          launch_forward<T>(A, m->st);
+          forward_slots<T>(m, F, m->src, nsrc, nsteps, dt, k, nullptr, hist + (size_t)(k + 1 - kb) * lvl);
+          launch_forward<T>(F, st);
           HYB_LAUNCHED(m);
         }
       }
       for (int j = ke; j >= std::max(kb, 1); --j) {
         adjoint_slots<T>(m, A, cot, j, pairing ? hist + (size_t)(j - kb) * lvl : nullptr);
-        launch_adjoint<T>(A, m->st);
+        launch_adjoint<T>(A, st);
         HYB_LAUNCHED(m);
       }
     }
-    if (pairing) HYB_TRY(pair_first<T>(m, A, hist));
-  }
+    if (pairing) HYB_TRY(pair_first<T>(m, A, hist, st));
+    return HYB_OK;
+  };
+  HYB_TRY(run_sweep(m, m->graphs[2], make_key(m, 2, cot, accumulate, nsteps, nsrc, dt, m->src), body));
   m->have_adj = true;
   return HYB_OK;
 }
@@ -576,6 +701,11 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   }
   if (st == HYB_OK && cudaMemsetAsync(m->flag.p, 0, sizeof(int), m->st) != cudaSuccess)
     st = fail(HYB_ERR_CUDA, "cudaMemsetAsync failed");
+  if (st == HYB_OK && cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    m->cap = nullptr;
+    st = fail(HYB_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+  }
   if (st != HYB_OK) {
     hyb_mesh_destroy(m);
     return st;
@@ -605,6 +735,9 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
                     &m->g, &m->atrial, &m->cot, &m->trace};
   for (DevBuf* b : bufs) release(*b);
   if (m->hscal) cudaFreeHost(m->hscal);
+  for (SweepGraph& g : m->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (m->cap) cudaStreamDestroy(m->cap);
   delete m;
   return HYB_OK;
 }
@@ -633,9 +766,10 @@ hyb_status hyb_adjoint(hyb_mesh* m, const void* cot, int32_t accumulate) {
 }
 
 hyb_status hyb_gradient(hyb_mesh* m, const double* a, double gamma, double a0, double* g_out) {
-  if (!m || !g_out) return fail(HYB_ERR_ARG, "null argument");
-  if (m->nu > 0 && !a) return fail(HYB_ERR_ARG, "null coefficient");
+  if (!m) return fail(HYB_ERR_ARG, "null mesh");
+  if (m->nu > 0 && (!a || !g_out)) return fail(HYB_ERR_ARG, "null coefficient or output");
   if (!m->have_adj) return fail(HYB_ERR_STATE, "hyb_gradient needs a preceding hyb_adjoint");
+  if (m->nu == 0) return HYB_OK;
   const double h = m->d.h;
   launch_grad_finalize((const double*)m->G.p, m->nsrc, a, -m->dt * m->dt / (h * h), gamma, h * h * h, a0,
                        g_out, m->nu, m->st);

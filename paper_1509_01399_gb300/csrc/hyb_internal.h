@@ -44,12 +44,16 @@ struct StepArgs {
   int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
   T c2;              // tau^2 / h^2
   T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
-  int npb;           // thread blocks per lattice plane
-  int zchunk, nzc;   // planes per block, blocks along z
+  int npb;           // interior kernel: thread blocks per plane of the interior box
+  int zchunk, nzc;   // interior kernel: planes per block, blocks along z
+  long long nshell;  // boundary-shell kernel: nodes per slot
   int nslots;
   Slot<T> s[kMaxSlots];
 };
 
+// One time level: interior kernel + boundary-shell kernel (2 launches).
+// The interior/shell split must match shell thickness 1 (forward) and 2
+// (adjoint): see step_geometry().
 template <typename T>
 void launch_forward(const StepArgs<T>& a, cudaStream_t st);
 template <typename T>

@@ -237,108 +237,189 @@ __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restric
   return d3 / T(3) + d6 / T(6);
 }
 
+// Node t of the boundary shell of thickness TH (every node with a coordinate
+// closer than TH to a face), enumerated as whole z planes, then whole y rows
+// of the remaining planes, then the x ends of the remaining rows.
+template <typename T, int TH>
+__device__ __forceinline__ void shell_node(const StepArgs<T>& A, long long t, int& i, int& j, int& k) {
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int ix = max(nx - 2 * TH, 0), iy = max(ny - 2 * TH, 0), iz = max(nz - 2 * TH, 0);
+  const long long plane = (long long)nx * ny;
+  const long long na = (long long)(nz - iz) * plane;
+  if (t < na) {
+    const int p = (int)(t / plane);
+    const long long r = t - (long long)p * plane;
+    k = p < TH ? p : p + iz;
+    j = (int)(r / nx);
+    i = (int)(r - (long long)j * nx);
+    return;
+  }
+  t -= na;
+  const long long rowsz = (long long)(ny - iy) * nx;
+  const long long nb = (long long)iz * rowsz;
+  if (t < nb) {
+    const int pk = (int)(t / rowsz);
+    const long long r = t - (long long)pk * rowsz;
+    k = TH + pk;
+    const int row = (int)(r / nx);
+    j = row < TH ? row : row + iy;
+    i = (int)(r - (long long)row * nx);
+    return;
+  }
+  t -= nb;
+  const int w = nx - ix;
+  const long long idx = t / w;
+  const int c = (int)(t - idx * w);
+  k = TH + (int)(idx / iy);
+  j = TH + (int)(idx % iy);
+  i = c < TH ? c : c + ix;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kStepThreads) fwd_kernel(const __grid_constant__ StepArgs<T> A) {
+__device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T>& S, int si, int i, int j,
+                                              int k) {
+  if (S.hist_r == nullptr) return;
+  if (i < A.fl[0] || i >= A.fl[0] + A.un[0] || j < A.fl[1] || j >= A.fl[1] + A.un[1] || k < A.fl[2] ||
+      k >= A.fl[2] + A.un[2])
+    return;
+  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+  const long long vid = (long long)(i - A.fl[0]) +
+                        (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
+  A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, S.cur, i, j, k);
+}
+
+// Interior nodes (1 .. n-2 on every axis): FDM or FEM rows only.
+template <typename T>
+__global__ void __launch_bounds__(kStepThreads) fwd_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
   const int tps = A.npb * A.nzc;
   const int si = blockIdx.x / tps;
   const int rem = blockIdx.x - si * tps;
   const int zc = rem / A.npb;
   const int pb = rem - zc * A.npb;
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int nx = A.nx;
+  const int bx = nx - 2, by = A.ny - 2;
   const int q = pb * kStepThreads + threadIdx.x;
-  if (q >= nx * ny) return;
-  const int j = q / nx;
-  const int i = q - j * nx;
+  if (q >= bx * by) return;
+  const int jj = q / bx;
+  const int i = 1 + q - jj * bx;
+  const int j = 1 + jj;
   const Slot<T>& S = A.s[si];
-  const long long plane = (long long)nx * ny;
-  const int z0 = zc * A.zchunk;
-  const int z1 = min(z0 + A.zchunk, nz);
+  const long long plane = (long long)nx * A.ny;
+  const int z0 = 1 + zc * A.zchunk;
+  const int z1 = min(z0 + A.zchunk, A.nz - 1);
+  if (z0 >= z1) return;
   const T* __restrict__ u = S.cur;
   const T* __restrict__ up = S.prev;
   T* __restrict__ un = S.next;
-  const bool xy_bnd = (i == 0 || i == nx - 1 || j == 0 || j == ny - 1);
   const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
-  const int obs_ax = S.obs_face >> 1;
-  long long id = q + (long long)z0 * plane;
-  T cm = z0 > 0 ? u[id - plane] : T(0);
+  T* __restrict__ hw = S.hist_w;
+  long long id = (long long)i + (long long)nx * j + plane * z0;
+  T cm = u[id - plane];
   T c0 = u[id];
+  const T c2 = A.c2;
   for (int k = z0; k < z1; ++k, id += plane) {
-    const T cp = (k + 1 < nz) ? u[id + plane] : T(0);
+    const T cp = u[id + plane];
     T val;
-    if (xy_bnd || k == 0 || k == nz - 1) {
-      val = fwd_new<T, 3>(A, S, i, j, k);
-    } else if (xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
-      val = T(2) * c0 - up[id] + A.c2 * fem_lap(A, u, id, i, j, k, c0, cm, cp);
+    if (xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
+      val = T(2) * c0 - up[id] + c2 * fem_lap(A, u, id, i, j, k, c0, cm, cp);
+      if (hw)
+        hw[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] = val;
     } else {
-      const T lap = (u[id - 1] - c0) + (u[id + 1] - c0) + (u[id - nx] - c0) + (u[id + nx] - c0) +
-                    (cm - c0) + (cp - c0);
-      val = T(2) * c0 - up[id] + A.c2 * lap;
+      const T lap = (u[id - 1] - c0) + (u[id + 1] - c0) + (u[id - nx] - c0) + (u[id + nx] - c0) + (cm - c0) +
+                    (cp - c0);
+      val = T(2) * c0 - up[id] + c2 * lap;
     }
     un[id] = val;
-    if (S.obs_w) {
-      const int side = S.obs_face & 1;
-      const int c = obs_ax == 0 ? i : (obs_ax == 1 ? j : k);
-      const int n = obs_ax == 0 ? nx : (obs_ax == 1 ? ny : nz);
-      if (c == (side ? n - 1 : 0)) S.obs_w[face_index(S.obs_face, i, j, k, nx, ny)] = val;
+    cm = c0;
+    c0 = cp;
+  }
+}
+
+// Outer faces: Neumann, source and absorbing rows; trace record.
+template <typename T>
+__global__ void __launch_bounds__(128) fwd_shell_kernel(const __grid_constant__ StepArgs<T> A) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ns = A.nshell;
+  if (t >= ns * A.nslots) return;
+  const int si = (int)(t / ns);
+  int i, j, k;
+  shell_node<T, 1>(A, t - (long long)si * ns, i, j, k);
+  const Slot<T>& S = A.s[si];
+  const T val = fwd_new<T, 3>(A, S, i, j, k);
+  S.next[lin(A, i, j, k)] = val;
+  if (S.obs_w) {
+    const int ax = S.obs_face >> 1;
+    const int c = ax == 0 ? i : (ax == 1 ? j : k);
+    const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
+    if (c == ((S.obs_face & 1) ? n - 1 : 0)) S.obs_w[face_index(S.obs_face, i, j, k, A.nx, A.ny)] = val;
+  }
+}
+
+// Nodes at least two nodes away from every face: the transposed row is the
+// forward stencil (the mass-weighted operator is symmetric there).
+template <typename T>
+__global__ void __launch_bounds__(kStepThreads) adj_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
+  const int tps = A.npb * A.nzc;
+  const int si = blockIdx.x / tps;
+  const int rem = blockIdx.x - si * tps;
+  const int zc = rem / A.npb;
+  const int pb = rem - zc * A.npb;
+  const int nx = A.nx;
+  const int bx = nx - 4, by = A.ny - 4;
+  const int q = pb * kStepThreads + threadIdx.x;
+  if (q >= bx * by) return;
+  const int jj = q / bx;
+  const int i = 2 + q - jj * bx;
+  const int j = 2 + jj;
+  const Slot<T>& S = A.s[si];
+  const long long plane = (long long)nx * A.ny;
+  const int z0 = 2 + zc * A.zchunk;
+  const int z1 = min(z0 + A.zchunk, A.nz - 2);
+  if (z0 >= z1) return;
+  const T* __restrict__ l1 = S.cur;
+  const T* __restrict__ l2 = S.prev;
+  T* __restrict__ ln = S.next;
+  const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
+  const bool xy_vox = S.hist_r != nullptr && i >= A.fl[0] && i < A.fl[0] + A.un[0] && j >= A.fl[1] &&
+                      j < A.fl[1] + A.un[1];
+  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+  long long id = (long long)i + (long long)nx * j + plane * z0;
+  T cm = l1[id - plane];
+  T c0 = l1[id];
+  const T c2 = A.c2;
+  for (int k = z0; k < z1; ++k, id += plane) {
+    const T cp = l1[id + plane];
+    T val;
+    if (xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
+      val = T(2) * c0 - l2[id] + c2 * fem_lap(A, l1, id, i, j, k, c0, cm, cp);
+    } else {
+      const T lap = (l1[id - 1] - c0) + (l1[id + 1] - c0) + (l1[id - nx] - c0) + (l1[id + nx] - c0) +
+                    (cm - c0) + (cp - c0);
+      val = T(2) * c0 - l2[id] + c2 * lap;
     }
-    if (S.hist_w && xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
-      S.hist_w[(long long)(i - A.fl[0]) +
-               (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] = val;
+    ln[id] = val;
+    if (xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
+      const long long vid = (long long)(i - A.fl[0]) +
+                            (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
+      A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, l1, i, j, k);
     }
     cm = c0;
     c0 = cp;
   }
 }
 
+// Nodes within one node of a face: gather of the transposed rows.
 template <typename T>
-__global__ void __launch_bounds__(kStepThreads) adj_kernel(const __grid_constant__ StepArgs<T> A) {
-  const int tps = A.npb * A.nzc;
-  const int si = blockIdx.x / tps;
-  const int rem = blockIdx.x - si * tps;
-  const int zc = rem / A.npb;
-  const int pb = rem - zc * A.npb;
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int q = pb * kStepThreads + threadIdx.x;
-  if (q >= nx * ny) return;
-  const int j = q / nx;
-  const int i = q - j * nx;
+__global__ void __launch_bounds__(128) adj_shell_kernel(const __grid_constant__ StepArgs<T> A) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ns = A.nshell;
+  if (t >= ns * A.nslots) return;
+  const int si = (int)(t / ns);
+  int i, j, k;
+  shell_node<T, 2>(A, t - (long long)si * ns, i, j, k);
   const Slot<T>& S = A.s[si];
-  const long long plane = (long long)nx * ny;
-  const int z0 = zc * A.zchunk;
-  const int z1 = min(z0 + A.zchunk, nz);
-  const T* __restrict__ l1 = S.cur;
-  const T* __restrict__ l2 = S.prev;
-  T* __restrict__ ln = S.next;
-  const bool xy_near = (i <= 1 || i >= nx - 2 || j <= 1 || j >= ny - 2);
-  const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
-  const bool xy_vox = S.hist_r != nullptr && i >= A.fl[0] && i < A.fl[0] + A.un[0] &&
-                      j >= A.fl[1] && j < A.fl[1] + A.un[1];
-  double* __restrict__ grad = A.G;
-  long long id = q + (long long)z0 * plane;
-  T cm = z0 > 0 ? l1[id - plane] : T(0);
-  T c0 = l1[id];
-  for (int k = z0; k < z1; ++k, id += plane) {
-    const T cp = (k + 1 < nz) ? l1[id + plane] : T(0);
-    T val;
-    if (xy_near || k <= 1 || k >= nz - 2) {
-      val = adj_new<T, 3>(A, S, i, j, k);
-    } else if (xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
-      val = T(2) * c0 - l2[id] + A.c2 * fem_lap(A, l1, id, i, j, k, c0, cm, cp);
-    } else {
-      const T lap = (l1[id - 1] - c0) + (l1[id + 1] - c0) + (l1[id - nx] - c0) +
-                    (l1[id + nx] - c0) + (cm - c0) + (cp - c0);
-      val = T(2) * c0 - l2[id] + A.c2 * lap;
-    }
-    ln[id] = val;
-    if (xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
-      const long long vid = (long long)(i - A.fl[0]) +
-                            (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
-      double* g = grad + (long long)si * A.un[0] * A.un[1] * A.un[2];
-      g[vid] += (double)voxel_pair(A, S.hist_r, l1, i, j, k);
-    }
-    cm = c0;
-    c0 = cp;
-  }
+  S.next[lin(A, i, j, k)] = adj_new<T, 3>(A, S, i, j, k);
+  pair_if_voxel(A, S, si, i, j, k);
 }
 
 template <typename T>
@@ -408,13 +489,17 @@ __global__ void extract_owned_kernel(const __grid_constant__ StepArgs<T> A, cons
 template <typename T>
 void launch_forward(const StepArgs<T>& a, cudaStream_t st) {
   const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
-  fwd_kernel<T><<<grid, kStepThreads, 0, st>>>(a);
+  if (grid) fwd_bulk_kernel<T><<<grid, kStepThreads, 0, st>>>(a);
+  const long long n = a.nshell * a.nslots;
+  fwd_shell_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
 }
 
 template <typename T>
 void launch_adjoint(const StepArgs<T>& a, cudaStream_t st) {
   const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
-  adj_kernel<T><<<grid, kStepThreads, 0, st>>>(a);
+  if (grid) adj_bulk_kernel<T><<<grid, kStepThreads, 0, st>>>(a);
+  const long long n = a.nshell * a.nslots;
+  adj_shell_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
 }
 
 template <typename T>

@@ -207,6 +207,7 @@ class HybMesh:
         self.obs_stride = int(self.info.obs_stride)
         self.nsteps = None
         self.n_src = None
+        self._generation = 0
 
     @classmethod
     def from_workload(cls, w, precision=None, ckpt_every=None, **kw):
@@ -243,6 +244,7 @@ class HybMesh:
         if trace is None:
             trace = self.new_trace(len(sources), nsteps)
         hyb_forward(self.handle, a.data_ptr(), sources, nsteps, dt, trace.data_ptr())
+        self._generation += 1
         self._a_keep = a
         self.nsteps, self.n_src = nsteps, len(sources)
         return trace

@@ -6,7 +6,7 @@ contains none of the method's arithmetic (no stencil, no element matrix, no
 time step), so both the FP64 oracle and the CUDA path can take their inputs
 from here without sharing any computation.
 
-Shapes follow the paper's numerical study (Sec. 8): a box domain, a central
+Shapes follow the paper's numerical study (Sec. 9): a box domain, a central
 finite-element block, a plane wave launched from one face with
 p(t) = sin(omega t) on (0, 2 pi / omega) (Eq. (f)), small cubic scatterers in
 which the coefficient a exceeds its background value 1 (Eq. (2.3)), and
@@ -173,7 +173,7 @@ def gaussian_bumps(fem_lo, fem_hi, h, origin, count, amp_range, width_range, rng
 
 def add_noise(trace: np.ndarray, level: float, seed: int = 1) -> np.ndarray:
     """u_obs = u + level * max|u| * xi with xi ~ N(0, 1) i.i.d. per entry
-    (additive noise on the backscattered data, Sec. 8)."""
+    (additive noise on the backscattered data, Sec. 9)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t = np.asarray(trace, dtype=np.float64)
     return t + level * np.abs(t).max() * rng.standard_normal(t.shape)

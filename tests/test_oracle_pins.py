@@ -32,7 +32,7 @@ def _load_kuhn_golden():
 def test_reference_tetrahedron_textbook_matrices():
     """Unit right tetrahedron: phi_0 = 1 - x - y - z, phi_i = x_i, so
     K = (1/6) [[3,-1,-1,-1],[-1,1,0,0],[-1,0,1,0],[-1,0,0,1]] and |K| = 1/6
-    (Sec. 6.2 element stiffness for a = 1)."""
+    (Sec. 7.2 element stiffness for a = 1)."""
     X = np.array([[[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]], dtype=float)
     vol, g = oracle.p1_element(X)
     K = oracle.element_stiffness(vol, g, np.ones(1))[0]
@@ -85,7 +85,7 @@ def test_kuhn_voxel_closed_form(h):
 def test_fem_rows_coincide_with_7point_fdm():
     """With a = 1 the lumped-mass Kuhn FEM row at every FEM-owned node equals
     the FDM row -Delta_h (the structured overlap where the two schemes
-    coincide, Sec. 3 and Sec. 6)."""
+    coincide, Sec. 1 and Sec. 7)."""
     P = Problem((11, 10, 12), 0.1, (2, 2, 3), (8, 7, 9))
     L = P.space_operator(np.ones(P.n_unknown))
     own = P.owned_nodes
