@@ -199,6 +199,29 @@ hyb_status hyb_cg_step(hyb_mesh* mesh, double* a, const void* u_obs, const hyb_s
    x fastest). */
 hyb_status hyb_get_field(hyb_mesh* mesh, int32_t which, int32_t isrc, void* out);
 
+/* Allocation-free data misfit.  The paper has no counterpart: this exists
+   for callers that cannot allocate device memory when they need the misfit
+   (code running while a stream is captured into a CUDA graph, loops where
+   cudaMalloc's implicit device synchronisation is not allowed, hosts that
+   serve all device memory from their own pool).  It computes what
+   hyb_misfit computes, without a mesh: trace, u_obs (device fields of
+   `precision`, shape [n_src][nsteps + 1][obs_stride]), face_dims (HOST
+   int32[n_src][2]: the in-face extents (n_p, n_q) of each source's face),
+   dt, h and `weights` as for hyb_misfit.  Writes J_data to *J_dev (a DEVICE
+   double) and, if cotangent != NULL, the cotangent, asynchronously on
+   `stream` (a cudaStream_t; NULL = legacy default stream).
+   It allocates nothing: its per-block partial sums live in a static
+   128 KiB device array that every GPU loading the library holds until the
+   process exits.  The trace may have at most 16384 * 4096 = 67,108,864
+   entries (HYB_ERR_ARG beyond).  The first call on a device looks up that
+   array's device address (cudaGetSymbolAddress) and caches it; make that
+   first call before any stream capture.  All calls share the array, so calls
+   that overlap on the GPU (different streams, or different host threads)
+   race and must be serialised by the caller. */
+hyb_status hyb_misfit_noalloc(const void* trace, const void* u_obs, int32_t precision, int32_t n_src,
+                              int32_t nsteps, int32_t obs_stride, const int32_t* face_dims, double dt,
+                              double h, int32_t weights, double* J_dev, void* cotangent, void* stream);
+
 /* Wait for the mesh's stream, then report any device-side error flag. */
 hyb_status hyb_sync(hyb_mesh* mesh);
 

@@ -239,19 +239,22 @@ int mask_at(const hyb_mesh* m, const hyb_source& s, int k, double dt) {
 // Launch geometry of one step: the interior box (nodes TH .. n-1-TH on every
 // axis) goes to the z-marching interior kernel, the rest of the lattice (the
 // boundary shell of thickness TH) to the shell kernel.
-void step_geometry(const hyb_mesh* m, int nslots, int TH, int* npb, int* zchunk, int* nzc, long long* nshell) {
+void step_geometry(const hyb_mesh* m, int nslots, int TH, int* npb, int* ntx, int* zchunk, int* nzc,
+                   long long* nshell) {
   const long long bx = std::max(m->n[0] - 2 * TH, 0);
   const long long by = std::max(m->n[1] - 2 * TH, 0);
   const long long bz = std::max(m->n[2] - 2 * TH, 0);
   *nshell = m->N - bx * by * bz;
-  const long long plane = bx * by;
-  if (plane == 0 || bz == 0) {
+  if (bx == 0 || by == 0 || bz == 0) {
     *npb = 0;
+    *ntx = 1;
     *zchunk = 1;
     *nzc = 0;
     return;
   }
-  *npb = (int)((plane + kStepThreads - 1) / kStepThreads);
+  *ntx = (int)((bx + kTileX - 1) / kTileX);
+  const int nty = (int)((by + kTileY - 1) / kTileY);
+  *npb = *ntx * nty;
   const long long target = 152LL * 8;  // resident blocks wanted on 152 SMs
   const long long per_z = (long long)(*npb) * nslots;
   long long want = (target + per_z - 1) / per_z;
@@ -283,7 +286,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots, int TH)
   const double h = m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
   A.r = (T)((h - dt) / (h + dt));
-  step_geometry(m, nslots, TH, &A.npb, &A.zchunk, &A.nzc, &A.nshell);
+  step_geometry(m, nslots, TH, &A.npb, &A.ntx, &A.zchunk, &A.nzc, &A.nshell);
   A.nslots = nslots;
 }
 
@@ -818,6 +821,46 @@ hyb_status hyb_get_field(hyb_mesh* m, int32_t which, int32_t isrc, void* out) {
     return fail(HYB_ERR_ARG, "bad field selector");
   }
   HYB_CU(cudaMemcpyAsync(out, src, fb, cudaMemcpyDeviceToDevice, m->st));
+  return HYB_OK;
+}
+
+hyb_status hyb_misfit_noalloc(const void* trace, const void* u_obs, int32_t precision, int32_t n_src,
+                              int32_t nsteps, int32_t obs_stride, const int32_t* face_dims, double dt, double h,
+                              int32_t weights, double* J_dev, void* cot, void* stream) {
+  if (!trace || !u_obs || !face_dims || !J_dev) return fail(HYB_ERR_ARG, "null argument");
+  if (precision != HYB_FP64 && precision != HYB_FP32) return fail(HYB_ERR_ARG, "bad precision");
+  if (weights != HYB_WEIGHTS_PLAIN && weights != HYB_WEIGHTS_QUADRATURE) return fail(HYB_ERR_ARG, "bad weights");
+  if (n_src < 1 || n_src > kMaxSlots) return fail(HYB_ERR_ARG, "n_src must be in [1, %d]", kMaxSlots);
+  if (nsteps < 0 || obs_stride < 1) return fail(HYB_ERR_ARG, "bad nsteps or obs_stride");
+  const long long total = (long long)n_src * (nsteps + 1) * obs_stride;
+  if (total > noalloc_max_entries())
+    return fail(HYB_ERR_ARG, "trace of %lld entries exceeds the %lld entries hyb_misfit_noalloc can reduce", total,
+                noalloc_max_entries());
+  MisfitGeom g;
+  std::memset(&g, 0, sizeof g);
+  g.n_src = n_src;
+  g.nsteps = nsteps;
+  g.stride = obs_stride;
+  for (int s = 0; s < n_src; ++s) {
+    g.np[s] = face_dims[2 * s];
+    g.nq[s] = face_dims[2 * s + 1];
+    if (g.np[s] < 1 || g.nq[s] < 1 || (long long)g.np[s] * g.nq[s] > obs_stride)
+      return fail(HYB_ERR_ARG, "source %d: face dims do not fit obs_stride", s);
+  }
+  const bool quad = weights == HYB_WEIGHTS_QUADRATURE;
+  g.wt = quad ? dt : 1.0;
+  g.hh = quad ? h * h : 1.0;
+  g.halve = quad ? 1 : 0;
+  double* scratch = nullptr;
+  HYB_CU(noalloc_scratch(&scratch));
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (precision == HYB_FP64)
+    launch_misfit_noalloc<double>(g, (const double*)trace, (const double*)u_obs, (double*)cot, scratch, total,
+                                  J_dev, st);
+  else
+    launch_misfit_noalloc<float>(g, (const float*)trace, (const float*)u_obs, (float*)cot, scratch, total, J_dev,
+                                 st);
+  HYB_CU(cudaGetLastError());
   return HYB_OK;
 }
 

@@ -11,6 +11,8 @@ namespace hyb {
 
 constexpr int kMaxSlots = 16;   // problems advanced by one step launch
 constexpr int kStepThreads = 256;
+constexpr int kTileX = 32;       // interior kernel thread tile (x)
+constexpr int kTileY = 8;        // interior kernel thread tile (y)
 constexpr int kReduceBlocks = 512;
 constexpr int kReduceThreads = 256;
 
@@ -45,6 +47,7 @@ struct StepArgs {
   T c2;              // tau^2 / h^2
   T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
   int npb;           // interior kernel: thread blocks per plane of the interior box
+  int ntx;           // interior kernel: tiles along x
   int zchunk, nzc;   // interior kernel: planes per block, blocks along z
   long long nshell;  // boundary-shell kernel: nodes per slot
   int nslots;
@@ -102,5 +105,14 @@ void launch_max(const double* partials, int n, double* out, cudaStream_t st);
 // out = clip(a + alpha d, lo, hi); partials of sum (out - a0)^2
 void launch_cg_axpy_clip(const double* a, const double* d, double alpha, double lo, double hi,
                          double a0, double* out, long long n, double* partials, cudaStream_t st);
+
+// Allocation-free misfit (hyb_misfit_noalloc): block partials in a static
+// device array.  noalloc_scratch() returns its device address on the current
+// device; noalloc_max_entries() is the largest trace it accepts.
+long long noalloc_max_entries();
+cudaError_t noalloc_scratch(double** out);
+template <typename T>
+void launch_misfit_noalloc(const MisfitGeom& g, const T* trace, const T* obs, T* cot, double* scratch,
+                           long long total, double* J_dev, cudaStream_t st);
 
 }  // namespace hyb

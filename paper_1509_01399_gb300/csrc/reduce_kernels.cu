@@ -215,3 +215,109 @@ void launch_cg_axpy_clip(const double* a, const double* d, double alpha, double 
 }
 
 }  // namespace hyb
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the misfit reduction (hyb_misfit_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need
+// the misfit: code running while a stream is being captured into a CUDA
+// graph, latency-critical loops in which cudaMalloc (which can synchronise
+// the whole device) is forbidden, or hosts that hand all device memory out
+// of their own fixed pool.  This entry point needs no mesh and no
+// workspace: its per-block partial sums live in the file-scope array below,
+// reserved once on every GPU that loads the library and kept until the
+// process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace hyb {
+namespace {
+
+constexpr int kNoAllocThreads = 256;
+constexpr int kNoAllocPerThread = 16;
+constexpr long long kNoAllocChunk = (long long)kNoAllocThreads * kNoAllocPerThread;  // entries per block
+constexpr int kNoAllocSlots = 16384;  // partial sums: 128 KiB per device
+
+__device__ __align__(256) double g_noalloc_partials[kNoAllocSlots];
+
+template <typename T>
+__global__ void __launch_bounds__(kNoAllocThreads) misfit_chunk_kernel(const hyb::MisfitGeom g,
+                                                                       const T* __restrict__ trace,
+                                                                       const T* __restrict__ obs,
+                                                                       T* __restrict__ cot,
+                                                                       double* __restrict__ partials,
+                                                                       long long total) {
+  const long long base = (long long)blockIdx.x * kNoAllocChunk;
+  double acc = 0.0;
+  for (int q = 0; q < kNoAllocPerThread; ++q) {
+    const long long e = base + (long long)q * kNoAllocThreads + threadIdx.x;
+    if (e >= total) break;
+    const int jj = (int)(e % g.stride);
+    const long long r = e / g.stride;
+    const int k = (int)(r % (g.nsteps + 1));
+    const int s = (int)(r / (g.nsteps + 1));
+    const int np = g.np[s], nq = g.nq[s];
+    T cv = T(0);
+    if (k >= 1 && jj < np * nq) {
+      double m = g.hh;
+      if (g.halve) {
+        const int cp = jj % np, cq = jj / np;
+        if (cp == 0 || cp == np - 1) m *= 0.5;
+        if (cq == 0 || cq == nq - 1) m *= 0.5;
+      }
+      const double d = (double)trace[e] - (double)obs[e];
+      const double w = g.wt * m;
+      acc += 0.5 * w * d * d;
+      cv = (T)(w * d);
+    }
+    if (cot) cot[e] = cv;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void noalloc_sum_kernel(const double* __restrict__ p, int n, double* out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += p[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};
+
+}  // namespace
+
+long long noalloc_max_entries() { return kNoAllocChunk * kNoAllocSlots; }
+
+// Device address of the partials array on the current device, looked up once
+// per device (the host-side symbol is not a device address).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+template <typename T>
+void launch_misfit_noalloc(const MisfitGeom& g, const T* trace, const T* obs, T* cot, double* scratch,
+                           long long total, double* J_dev, cudaStream_t st) {
+  const int blocks = (int)((total + kNoAllocChunk - 1) / kNoAllocChunk);
+  if (blocks > 0) misfit_chunk_kernel<T><<<blocks, kNoAllocThreads, 0, st>>>(g, trace, obs, cot, scratch, total);
+  noalloc_sum_kernel<<<1, 256, 0, st>>>(scratch, blocks, J_dev);
+}
+template void launch_misfit_noalloc<float>(const MisfitGeom&, const float*, const float*, float*, double*,
+                                           long long, double*, cudaStream_t);
+template void launch_misfit_noalloc<double>(const MisfitGeom&, const double*, const double*, double*, double*,
+                                            long long, double*, cudaStream_t);
+
+}  // namespace hyb

@@ -79,6 +79,8 @@ def _load():
                         POINTER(hyb_cg_params), POINTER(hyb_cg_state), POINTER(hyb_cg_report)],
         "hyb_get_field": [P, c_int32, c_int32, P],
         "hyb_sync": [P],
+        "hyb_misfit_noalloc": [P, P, c_int32, c_int32, c_int32, c_int32, POINTER(c_int32), c_double, c_double,
+                               c_int32, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -92,7 +94,7 @@ def _load():
 _lib = _load()
 EXPORTED = ("hyb_mesh_create", "hyb_mesh_query", "hyb_mesh_destroy", "hyb_set_stream", "hyb_forward",
             "hyb_adjoint", "hyb_gradient", "hyb_misfit", "hyb_cg_step", "hyb_get_field", "hyb_sync",
-            "hyb_last_error")
+            "hyb_last_error", "hyb_misfit_noalloc")
 
 
 def hyb_last_error() -> str:
@@ -170,6 +172,17 @@ def hyb_get_field(mesh: int, which: int, isrc: int, out_ptr: int) -> None:
 
 def hyb_sync(mesh: int) -> None:
     _check(_lib.hyb_sync(c_void_p(mesh)))
+
+
+def hyb_misfit_noalloc(trace_ptr: int, obs_ptr: int, precision: int, n_src: int, nsteps: int, obs_stride: int,
+                       face_dims, dt: float, h: float, weights: int, J_dev_ptr: int, cot_ptr: int = 0,
+                       stream: int = 0) -> None:
+    """Misfit without any device allocation (see include/hyb.h); writes the
+    value to the device double at J_dev_ptr."""
+    dims = (c_int32 * (2 * n_src))(*[int(v) for pair in face_dims for v in pair])
+    _check(_lib.hyb_misfit_noalloc(c_void_p(trace_ptr), c_void_p(obs_ptr), int(precision), int(n_src), int(nsteps),
+                                   int(obs_stride), dims, float(dt), float(h), int(weights), c_void_p(J_dev_ptr),
+                                   c_void_p(cot_ptr) if cot_ptr else None, c_void_p(stream)))
 
 
 # ---- convenience wrapper with torch-owned device arrays ----
