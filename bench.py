@@ -49,6 +49,11 @@ def parse():
     p.add_argument("--nsteps", type=int, default=1500, help="time steps of the workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-steps", type=int, default=30)
+    p.add_argument("--workload", default="inverse_129", choices=["inverse_129", "large_257"])
+    p.add_argument("--sources", type=int, default=0, help="with --sweeps-only: use the first K sources")
+    p.add_argument("--sweeps-only", type=int, default=0,
+                   help="profiling aid: run this many forward+adjoint sweep pairs of the workload "
+                        "(FP32, --nsteps steps) and exit without timing")
     return p.parse_args()
 
 
@@ -147,9 +152,32 @@ def recorded_traffic(kernel: str):
     return None
 
 
-def make_workload(nsteps):
+def make_workload(nsteps, name="inverse_129"):
     import synth
+    if name == "large_257":
+        return synth.large_257(nsteps=nsteps)
     return synth.inverse_129(nsteps=nsteps)
+
+
+def run_sweeps_only(args):
+    """Forward + adjoint sweeps of the workload with all its sources, for
+    ncu captures: no data generation, no CG, no timing."""
+    import torch
+    from paper_1509_01399_gb300 import hyb as H
+    w = make_workload(args.nsteps, args.workload)
+    srcs = w.sources[: args.sources] if args.sources > 0 else w.sources
+    m = H.HybMesh.from_workload(w, precision="fp32", ckpt_every=0)
+    a = torch.tensor(w.a_true(), dtype=torch.float64, device="cuda")
+    tr = m.new_trace(len(srcs), w.nsteps)
+    cot = torch.randn_like(tr) * 1e-3
+    for _ in range(args.sweeps_only):
+        m.forward(a, srcs, w.nsteps, w.dt, tr)
+        m.adjoint(cot)
+    m.sync()
+    m.close()
+    print(json.dumps({"sweeps": args.sweeps_only, "workload": w.name, "nsteps": w.nsteps,
+                      "sources": len(srcs)}))
+    return 0
 
 
 def algorithmic_bytes(w, es=4):
@@ -286,6 +314,8 @@ def run_ours(args):
     m.forward(a, srcs, nsteps, dt, trace)
     e1.record(stream)
     J, cot = m.misfit(trace, obs, H.HYB_WEIGHTS_QUADRATURE, want_cot=True)
+    for _ in range(2):  # the second call captures the adjoint sweep graph
+        m.adjoint(cot)
     e1b = torch.cuda.Event(enable_timing=True)
     e1b.record(stream)
     m.adjoint(cot)
@@ -360,6 +390,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweeps_only:
+        return run_sweeps_only(args)
     return run_ours(args)
 
 

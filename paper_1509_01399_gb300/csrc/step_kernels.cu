@@ -119,7 +119,7 @@ __device__ __noinline__ T fwd_new(const StepArgs<T>& A, const Slot<T>& S, int i,
 // Coefficient of the non-absorbing row of node (i,j,k) on its neighbour
 // (i,j,k) + s e_ax (Laplacian part, without 1/h^2).
 template <typename T>
-__device__ T row_coef(const StepArgs<T>& A, int i, int j, int k, int ax, int s) {
+__device__ __forceinline__ T row_coef(const StepArgs<T>& A, int i, int j, int k, int ax, int s) {
   if (fem_owned(A, i, j, k)) {
     const long long w = widx(A, i, j, k);
     const long long ws = ax == 0 ? 1 : (ax == 1 ? (long long)A.wn[0] : (long long)A.wn[0] * A.wn[1]);
@@ -132,7 +132,7 @@ __device__ T row_coef(const StepArgs<T>& A, int i, int j, int k, int ax, int s) 
 }
 
 template <typename T>
-__device__ T row_diag(const StepArgs<T>& A, int i, int j, int k) {
+__device__ __forceinline__ T row_diag(const StepArgs<T>& A, int i, int j, int k) {
   if (fem_owned(A, i, j, k)) {
     const long long w = widx(A, i, j, k);
     const long long wy = A.wn[0];
@@ -288,54 +288,89 @@ __device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T
   A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, S.cur, i, j, k);
 }
 
-// Interior nodes (1 .. n-2 on every axis): FDM or FEM rows only.
+// Laplacian part of the row of a node that lies on no face (all six
+// neighbours exist, no mirror): FEM stencil or 7-point FDM.
 template <typename T>
-__global__ void __launch_bounds__(kStepThreads) fwd_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
+__device__ __forceinline__ T interior_lap(const StepArgs<T>& A, const T* __restrict__ u, long long id, int i,
+                                          int j, int k) {
+  const long long pl = (long long)A.nx * A.ny;
+  const T c = u[id];
+  if (fem_owned(A, i, j, k)) return fem_lap(A, u, id, i, j, k, c, u[id - pl], u[id + pl]);
+  return (u[id - 1] - c) + (u[id + 1] - c) + (u[id - A.nx] - c) + (u[id + A.nx] - c) + (u[id - pl] - c) +
+         (u[id + pl] - c);
+}
+
+template <typename T>
+__device__ __forceinline__ long long axis_stride(const StepArgs<T>& A, int ax) {
+  return ax == 0 ? 1LL : (ax == 1 ? (long long)A.nx : (long long)A.nx * A.ny);
+}
+
+// Interior kernel shared by the forward (TH = 1) and adjoint (TH = 2)
+// steps: 32 x 8 thread tiles of the interior box, each thread marching a
+// chunk of z planes with u at z-1, z, z+1 in registers and the next plane
+// and the previous-level value loaded one iteration ahead.
+template <typename T, int TH, bool ADJ>
+__global__ void __launch_bounds__(kTileX * kTileY) bulk_kernel(const __grid_constant__ StepArgs<T> A) {
   const int tps = A.npb * A.nzc;
   const int si = blockIdx.x / tps;
-  const int rem = blockIdx.x - si * tps;
+  int rem = blockIdx.x - si * tps;
   const int zc = rem / A.npb;
-  const int pb = rem - zc * A.npb;
-  const int nx = A.nx;
-  const int bx = nx - 2, by = A.ny - 2;
-  const int q = pb * kStepThreads + threadIdx.x;
-  if (q >= bx * by) return;
-  const int jj = q / bx;
-  const int i = 1 + q - jj * bx;
-  const int j = 1 + jj;
-  const Slot<T>& S = A.s[si];
-  const long long plane = (long long)nx * A.ny;
-  const int z0 = 1 + zc * A.zchunk;
-  const int z1 = min(z0 + A.zchunk, A.nz - 1);
+  rem -= zc * A.npb;
+  const int tyy = rem / A.ntx;
+  const int txx = rem - tyy * A.ntx;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int i = TH + txx * kTileX + (threadIdx.x % kTileX);
+  const int j = TH + tyy * kTileY + (threadIdx.x / kTileX);
+  if (i > nx - 1 - TH || j > ny - 1 - TH) return;
+  const int z0 = TH + zc * A.zchunk;
+  const int z1 = min(z0 + A.zchunk, nz - TH);
   if (z0 >= z1) return;
-  const T* __restrict__ u = S.cur;
-  const T* __restrict__ up = S.prev;
-  T* __restrict__ un = S.next;
+  const Slot<T>& S = A.s[si];
+  const long long plane = (long long)nx * ny;
+  const T* __restrict__ c = S.cur;
+  const T* __restrict__ p = S.prev;
+  T* __restrict__ out = S.next;
   const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
-  T* __restrict__ hw = S.hist_w;
+  const bool xy_vox = ADJ && S.hist_r != nullptr && i >= A.fl[0] && i < A.fl[0] + A.un[0] &&
+                      j >= A.fl[1] && j < A.fl[1] + A.un[1];
+  T* __restrict__ hw = ADJ ? nullptr : S.hist_w;
+  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
   long long id = (long long)i + (long long)nx * j + plane * z0;
-  T cm = u[id - plane];
-  T c0 = u[id];
+  T cm = c[id - plane];
+  T c0 = c[id];
+  T cp = c[id + plane];
+  T pv = p[id];
   const T c2 = A.c2;
   for (int k = z0; k < z1; ++k, id += plane) {
-    const T cp = u[id + plane];
+    const T cpp = (k + 2 <= nz - 1) ? c[id + 2 * plane] : T(0);
+    const T pvn = (k + 1 < z1) ? p[id + plane] : T(0);
     T val;
-    if (xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
-      val = T(2) * c0 - up[id] + c2 * fem_lap(A, u, id, i, j, k, c0, cm, cp);
+    const bool fem = xy_fem && k >= A.fl[2] && k <= A.fh[2];
+    if (fem) {
+      val = T(2) * c0 - pv + c2 * fem_lap(A, c, id, i, j, k, c0, cm, cp);
       if (hw)
-        hw[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] = val;
+        hw[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
+            val;
     } else {
-      const T lap = (u[id - 1] - c0) + (u[id + 1] - c0) + (u[id - nx] - c0) + (u[id + nx] - c0) + (cm - c0) +
+      const T lap = (c[id - 1] - c0) + (c[id + 1] - c0) + (c[id - nx] - c0) + (c[id + nx] - c0) + (cm - c0) +
                     (cp - c0);
-      val = T(2) * c0 - up[id] + c2 * lap;
+      val = T(2) * c0 - pv + c2 * lap;
     }
-    un[id] = val;
+    out[id] = val;
+    if (ADJ && xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
+      const long long vid = (long long)(i - A.fl[0]) +
+                            (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
+      A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, c, i, j, k);
+    }
     cm = c0;
     c0 = cp;
+    cp = cpp;
+    pv = pvn;
   }
 }
 
-// Outer faces: Neumann, source and absorbing rows; trace record.
+// Outer faces: Neumann, source and absorbing rows; trace record.  A node on
+// a single face takes an inlined row; edge and corner nodes the generic one.
 template <typename T>
 __global__ void __launch_bounds__(128) fwd_shell_kernel(const __grid_constant__ StepArgs<T> A) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -345,70 +380,75 @@ __global__ void __launch_bounds__(128) fwd_shell_kernel(const __grid_constant__ 
   int i, j, k;
   shell_node<T, 1>(A, t - (long long)si * ns, i, j, k);
   const Slot<T>& S = A.s[si];
-  const T val = fwd_new<T, 3>(A, S, i, j, k);
-  S.next[lin(A, i, j, k)] = val;
-  if (S.obs_w) {
-    const int ax = S.obs_face >> 1;
-    const int c = ax == 0 ? i : (ax == 1 ? j : k);
-    const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
-    if (c == ((S.obs_face & 1) ? n - 1 : 0)) S.obs_w[face_index(S.obs_face, i, j, k, A.nx, A.ny)] = val;
-  }
-}
-
-// Nodes at least two nodes away from every face: the transposed row is the
-// forward stencil (the mass-weighted operator is symmetric there).
-template <typename T>
-__global__ void __launch_bounds__(kStepThreads) adj_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
-  const int tps = A.npb * A.nzc;
-  const int si = blockIdx.x / tps;
-  const int rem = blockIdx.x - si * tps;
-  const int zc = rem / A.npb;
-  const int pb = rem - zc * A.npb;
-  const int nx = A.nx;
-  const int bx = nx - 4, by = A.ny - 4;
-  const int q = pb * kStepThreads + threadIdx.x;
-  if (q >= bx * by) return;
-  const int jj = q / bx;
-  const int i = 2 + q - jj * bx;
-  const int j = 2 + jj;
-  const Slot<T>& S = A.s[si];
-  const long long plane = (long long)nx * A.ny;
-  const int z0 = 2 + zc * A.zchunk;
-  const int z1 = min(z0 + A.zchunk, A.nz - 2);
-  if (z0 >= z1) return;
-  const T* __restrict__ l1 = S.cur;
-  const T* __restrict__ l2 = S.prev;
-  T* __restrict__ ln = S.next;
-  const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
-  const bool xy_vox = S.hist_r != nullptr && i >= A.fl[0] && i < A.fl[0] + A.un[0] && j >= A.fl[1] &&
-                      j < A.fl[1] + A.un[1];
-  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
-  long long id = (long long)i + (long long)nx * j + plane * z0;
-  T cm = l1[id - plane];
-  T c0 = l1[id];
-  const T c2 = A.c2;
-  for (int k = z0; k < z1; ++k, id += plane) {
-    const T cp = l1[id + plane];
-    T val;
-    if (xy_fem && k >= A.fl[2] && k <= A.fh[2]) {
-      val = T(2) * c0 - l2[id] + c2 * fem_lap(A, l1, id, i, j, k, c0, cm, cp);
+  const int fall = face_bits(i, j, k, A.nx, A.ny, A.nz);
+  const long long id = lin(A, i, j, k);
+  T val;
+  if (__popc(fall) == 1) {
+    const int f = __ffs(fall) - 1;
+    const int ax = f >> 1;
+    const int step = (f & 1) ? -1 : 1;  // inward
+    const long long sa = axis_stride(A, ax);
+    const T* __restrict__ u = S.cur;
+    const T* __restrict__ up = S.prev;
+    if (S.mask_f & fall) {
+      // Eq. (eq:abs2) with the new value of the inward neighbour b1
+      const long long id1 = id + step * sa;
+      const T n1 = T(2) * u[id1] - up[id1] +
+                   A.c2 * interior_lap(A, u, id1, i + (ax == 0 ? step : 0), j + (ax == 1 ? step : 0),
+                                       k + (ax == 2 ? step : 0));
+      val = A.r * u[id] + (u[id1] - A.r * n1);
     } else {
-      const T lap = (l1[id - 1] - c0) + (l1[id + 1] - c0) + (l1[id - nx] - c0) + (l1[id + nx] - c0) +
-                    (cm - c0) + (cp - c0);
-      val = T(2) * c0 - l2[id] + c2 * lap;
+      // mirror ghost along the face normal, plus the source flux
+      const T cc = u[id];
+      T lap = T(2) * (u[id + step * sa] - cc);
+#pragma unroll
+      for (int a2 = 0; a2 < 3; ++a2) {
+        if (a2 == ax) continue;
+        const long long s2 = axis_stride(A, a2);
+        lap += (u[id - s2] - cc) + (u[id + s2] - cc);
+      }
+      val = T(2) * cc - up[id] + A.c2 * lap;
+      if (S.src_face == f) val += S.srcval;
     }
-    ln[id] = val;
-    if (xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
-      const long long vid = (long long)(i - A.fl[0]) +
-                            (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
-      A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, l1, i, j, k);
-    }
-    cm = c0;
-    c0 = cp;
+  } else {
+    val = fwd_new<T, 3>(A, S, i, j, k);
   }
+  S.next[id] = val;
+  if (S.obs_w && ((fall >> S.obs_face) & 1)) S.obs_w[face_index(S.obs_face, i, j, k, A.nx, A.ny)] = val;
 }
 
-// Nodes within one node of a face: gather of the transposed rows.
+// lambda^j at a node on the single face f whose in-face coordinates are at
+// least two nodes from the other faces (no transposed absorbing coupling
+// reaches it).
+template <typename T>
+__device__ __forceinline__ T adj_face_interior(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k,
+                                               int f) {
+  const T* __restrict__ l1 = S.cur;
+  const long long id = lin(A, i, j, k);
+  const int ax = f >> 1;
+  const int step = (f & 1) ? -1 : 1;
+  const long long sa = axis_stride(A, ax);
+  const bool abc = (S.mask_f >> f) & 1;
+  T rhs = abc ? A.r * l1[id] : (T(2) - T(6) * A.c2) * l1[id];
+  rhs += A.c2 *
+         row_coef(A, i + (ax == 0 ? step : 0), j + (ax == 1 ? step : 0), k + (ax == 2 ? step : 0), ax, -step) *
+         l1[id + step * sa];
+  if (!abc) {
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2) {
+      if (a2 == ax) continue;
+      const long long s2 = axis_stride(A, a2);
+      rhs += A.c2 * (l1[id - s2] + l1[id + s2]);
+    }
+  }
+  if (!((S.mask_c >> f) & 1)) rhs -= S.prev[id];
+  if (S.obs_r && S.obs_face == f) rhs += S.obs_r[face_index(f, i, j, k, A.nx, A.ny)];
+  return rhs;
+}
+
+// Nodes within one node of a face.  Inlined rows for the two common cases
+// (on one face, or one node inside one face, away from edges); the generic
+// transposed gather for the rest.
 template <typename T>
 __global__ void __launch_bounds__(128) adj_shell_kernel(const __grid_constant__ StepArgs<T> A) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -418,7 +458,56 @@ __global__ void __launch_bounds__(128) adj_shell_kernel(const __grid_constant__ 
   int i, j, k;
   shell_node<T, 2>(A, t - (long long)si * ns, i, j, k);
   const Slot<T>& S = A.s[si];
-  S.next[lin(A, i, j, k)] = adj_new<T, 3>(A, S, i, j, k);
+  const int cc[3] = {i, j, k};
+  const int nn[3] = {A.nx, A.ny, A.nz};
+  int n0 = 0, n1 = 0, a0 = 0, a1 = 0;
+  bool fast = nn[0] >= 4 && nn[1] >= 4 && nn[2] >= 4;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int d = min(cc[ax], nn[ax] - 1 - cc[ax]);
+    if (d == 0) {
+      ++n0;
+      a0 = ax;
+    } else if (d == 1) {
+      ++n1;
+      a1 = ax;
+    }
+  }
+  const long long id = lin(A, i, j, k);
+  T val;
+  if (fast && n0 == 1 && n1 == 0) {
+    val = adj_face_interior(A, S, i, j, k, 2 * a0 + (cc[a0] == 0 ? 0 : 1));
+  } else if (fast && n0 == 0 && n1 == 1) {
+    // one node inside face f; b is the face node next to it
+    const int f = 2 * a1 + (cc[a1] == 1 ? 0 : 1);
+    const int bs = (f & 1) ? 1 : -1;  // from m towards b
+    const T* __restrict__ l1 = S.cur;
+    T rhs = (T(2) + A.c2 * row_diag(A, i, j, k)) * l1[id];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+      for (int tt = 0; tt < 2; ++tt) {
+        const int s = tt ? 1 : -1;
+        const long long nid = id + s * axis_stride(A, ax);
+        if (ax == a1 && s == bs) {
+          rhs += ((S.mask_f >> f) & 1) ? l1[nid] : T(2) * A.c2 * l1[nid];
+        } else {
+          rhs += A.c2 *
+                 row_coef(A, i + (ax == 0 ? s : 0), j + (ax == 1 ? s : 0), k + (ax == 2 ? s : 0), ax, -s) *
+                 l1[nid];
+        }
+      }
+    }
+    rhs -= S.prev[id];
+    if ((S.mask_e >> f) & 1) {
+      rhs -= A.r * adj_face_interior(A, S, i + (a1 == 0 ? bs : 0), j + (a1 == 1 ? bs : 0),
+                                     k + (a1 == 2 ? bs : 0), f);
+    }
+    val = rhs;
+  } else {
+    val = adj_new<T, 3>(A, S, i, j, k);
+  }
+  S.next[id] = val;
   pair_if_voxel(A, S, si, i, j, k);
 }
 
@@ -489,7 +578,7 @@ __global__ void extract_owned_kernel(const __grid_constant__ StepArgs<T> A, cons
 template <typename T>
 void launch_forward(const StepArgs<T>& a, cudaStream_t st) {
   const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
-  if (grid) fwd_bulk_kernel<T><<<grid, kStepThreads, 0, st>>>(a);
+  if (grid) bulk_kernel<T, 1, false><<<grid, kTileX * kTileY, 0, st>>>(a);
   const long long n = a.nshell * a.nslots;
   fwd_shell_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
 }
@@ -497,7 +586,7 @@ void launch_forward(const StepArgs<T>& a, cudaStream_t st) {
 template <typename T>
 void launch_adjoint(const StepArgs<T>& a, cudaStream_t st) {
   const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
-  if (grid) adj_bulk_kernel<T><<<grid, kStepThreads, 0, st>>>(a);
+  if (grid) bulk_kernel<T, 2, true><<<grid, kTileX * kTileY, 0, st>>>(a);
   const long long n = a.nshell * a.nslots;
   adj_shell_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
 }
