@@ -89,6 +89,8 @@ struct hyb_mesh {
   long long launches = 0;
   long long bytes = 0;
   cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
+  cudaStream_t aux = nullptr;  // runs the boundary-shell kernel of each step
+  cudaEvent_t ev_bulk = nullptr, ev_shell = nullptr;
   SweepGraph graphs[3];
 };
 
@@ -236,22 +238,15 @@ int mask_at(const hyb_mesh* m, const hyb_source& s, int k, double dt) {
   return mask;
 }
 
-// Launch geometry of one step: the interior box (nodes TH .. n-1-TH on every
-// axis) goes to the z-marching interior kernel, the rest of the lattice (the
-// boundary shell of thickness TH) to the shell kernel.
-void step_geometry(const hyb_mesh* m, int nslots, int TH, int* npb, int* ntx, int* zchunk, int* nzc,
-                   long long* nshell) {
-  const long long bx = std::max(m->n[0] - 2 * TH, 0);
-  const long long by = std::max(m->n[1] - 2 * TH, 0);
-  const long long bz = std::max(m->n[2] - 2 * TH, 0);
-  *nshell = m->N - bx * by * bz;
-  if (bx == 0 || by == 0 || bz == 0) {
-    *npb = 0;
-    *ntx = 1;
-    *zchunk = 1;
-    *nzc = 0;
-    return;
-  }
+// Launch geometry of one step: the interior kernel covers nodes 1 .. n-2 on
+// every axis in 32 x 8 tiles and z chunks; the edge kernel the nodes within
+// one node of two faces.  Lattices with fewer than 5 nodes on an axis use a
+// single generic kernel instead.
+void step_geometry(const hyb_mesh* m, int nslots, int* npb, int* ntx, int* zchunk, int* nzc, int* small,
+                   int* nedge) {
+  *small = (m->n[0] < 5 || m->n[1] < 5 || m->n[2] < 5) ? 1 : 0;
+  *nedge = *small ? 0 : 1 + (m->n[0] - 4 + 7) / 8 + (m->n[1] - 4 + 7) / 8 + (m->n[2] - 4 + 7) / 8;
+  const long long bx = m->n[0] - 2, by = m->n[1] - 2, bz = m->n[2] - 2;
   *ntx = (int)((bx + kTileX - 1) / kTileX);
   const int nty = (int)((by + kTileY - 1) / kTileY);
   *npb = *ntx * nty;
@@ -266,8 +261,37 @@ void step_geometry(const hyb_mesh* m, int nslots, int TH, int* npb, int* ntx, in
   *nzc = (int)((bz + z - 1) / z);
 }
 
+// One time level on two streams: the interior kernel on `st`, the edge
+// kernel on the mesh's aux stream.  Each waits for both kernels of the
+// previous level (fork/join through two events), so they overlap with each
+// other but not across levels.  begin_steps/join_steps bracket a run of
+// levels; other work on `st` must come after join_steps.
+hyb_status begin_steps(hyb_mesh* m, cudaStream_t st) {
+  HYB_CU(cudaEventRecord(m->ev_bulk, st));
+  HYB_CU(cudaEventRecord(m->ev_shell, st));
+  return HYB_OK;
+}
+
+template <class Bulk, class Shell>
+hyb_status step_pair(hyb_mesh* m, cudaStream_t st, Bulk bulk, Shell shell) {
+  HYB_CU(cudaStreamWaitEvent(m->aux, m->ev_bulk, 0));
+  HYB_CU(cudaStreamWaitEvent(st, m->ev_shell, 0));
+  bulk(st);
+  HYB_LAUNCHED(m);
+  HYB_CU(cudaEventRecord(m->ev_bulk, st));
+  shell(m->aux);
+  HYB_LAUNCHED(m);
+  HYB_CU(cudaEventRecord(m->ev_shell, m->aux));
+  return HYB_OK;
+}
+
+hyb_status join_steps(hyb_mesh* m, cudaStream_t st) {
+  HYB_CU(cudaStreamWaitEvent(st, m->ev_shell, 0));
+  return HYB_OK;
+}
+
 template <typename T>
-void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots, int TH) {
+void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   std::memset(&A, 0, sizeof(A));
   A.nx = m->n[0];
   A.ny = m->n[1];
@@ -286,7 +310,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots, int TH)
   const double h = m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
   A.r = (T)((h - dt) / (h + dt));
-  step_geometry(m, nslots, TH, &A.npb, &A.ntx, &A.zchunk, &A.nzc, &A.nshell);
+  step_geometry(m, nslots, &A.npb, &A.ntx, &A.zchunk, &A.nzc, &A.small, &A.nedge);
   A.nslots = nslots;
 }
 
@@ -338,7 +362,7 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
     }
   }
   StepArgs<T> A;
-  base_args(m, A, dt, nsrc, 1);
+  base_args(m, A, dt, nsrc);
   if (m->fem) {
     launch_set_coef<T>(A, (T*)m->W.p, a, m->d.a_max, (int*)m->flag.p, m->st);
     HYB_LAUNCHED(m);
@@ -352,8 +376,10 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
     T* hist = (T*)m->hist.p;
     if (keep && !ckpt && m->nown > 0) HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->nown * sizeof(T), st));
     const size_t lvl = (size_t)nsrc * m->nown;
+    HYB_TRY(begin_steps(m, st));
     for (int k = 0; k < nsteps; ++k) {
       if (keep && ckpt && m->nown > 0 && k > 0 && k % C == 0) {
+        HYB_TRY(join_steps(m, st));
         const size_t seg = (size_t)(k / C);
         for (int s = 0; s < nsrc; ++s) {
           char* base = (char*)m->ckpt.p + ((seg * nsrc + s) * 2) * fb;
@@ -361,12 +387,14 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
           HYB_CU(cudaMemcpyAsync(base + fb, field_buf<T>(m, m->U, nsrc, s, k - 1), fb, cudaMemcpyDeviceToDevice,
                                  st));
         }
+        HYB_TRY(begin_steps(m, st));
       }
       T* hl = (keep && !ckpt && m->nown > 0 && k + 1 <= nsteps - 1) ? hist + (size_t)(k + 1) * lvl : nullptr;
       forward_slots<T>(m, A, src, nsrc, nsteps, dt, k, trace, hl);
-      launch_forward<T>(A, st);
-      HYB_LAUNCHED(m);
+      HYB_TRY(step_pair(m, st, [&](cudaStream_t q) { launch_forward_bulk<T>(A, q); },
+                        [&](cudaStream_t q) { launch_forward_shell<T>(A, q); }));
     }
+    HYB_TRY(join_steps(m, st));
     return HYB_OK;
   };
   HYB_TRY(run_sweep(m, m->graphs[keep ? 0 : 1], make_key(m, keep ? 0 : 1, trace, 0, nsteps, nsrc, dt, src), body));
@@ -422,10 +450,10 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   const bool ckpt = C > 0;
   HYB_TRY(ensure(m, m->L, 3 * (size_t)nsrc * fb));
   HYB_TRY(ensure(m, m->G, (size_t)nsrc * m->nu * sizeof(double)));
-  StepArgs<T> A;   // adjoint steps (boundary shell of thickness 2)
-  base_args(m, A, dt, nsrc, 2);
-  StepArgs<T> F;   // recomputed forward steps (shell of thickness 1)
-  base_args(m, F, dt, nsrc, 1);
+  StepArgs<T> A;   // adjoint steps
+  base_args(m, A, dt, nsrc);
+  StepArgs<T> F;   // recomputed forward steps
+  base_args(m, F, dt, nsrc);
   auto body = [&](cudaStream_t st) -> hyb_status {
     if (!accumulate) HYB_CU(cudaMemsetAsync(m->G.p, 0, (size_t)nsrc * m->nu * sizeof(double), st));
     for (int s = 0; s < nsrc; ++s) {
@@ -435,24 +463,33 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
     T* hist = (T*)m->hist.p;
     const size_t lvl = (size_t)nsrc * m->nown;
     const bool pairing = m->nu > 0 && m->nown > 0;
+    auto adj_step = [&](int j, const T* hl) -> hyb_status {
+      adjoint_slots<T>(m, A, cot, j, hl);
+      return step_pair(m, st, [&](cudaStream_t q) { launch_adjoint_bulk<T>(A, q); },
+                       [&](cudaStream_t q) { launch_adjoint_shell<T>(A, q); });
+    };
+    auto fwd_step = [&](int k, T* hl) -> hyb_status {
+      forward_slots<T>(m, F, m->src, nsrc, nsteps, dt, k, nullptr, hl);
+      return step_pair(m, st, [&](cudaStream_t q) { launch_forward_bulk<T>(F, q); },
+                       [&](cudaStream_t q) { launch_forward_shell<T>(F, q); });
+    };
+    HYB_TRY(begin_steps(m, st));
     if (!ckpt) {
       for (int j = nsteps; j >= 1; --j) {
         const T* hl = (pairing && j <= nsteps - 1) ? hist + (size_t)j * lvl : nullptr;
-        adjoint_slots<T>(m, A, cot, j, hl);
-        launch_adjoint<T>(A, st);
-        HYB_LAUNCHED(m);
+        HYB_TRY(adj_step(j, hl));
       }
+      HYB_TRY(join_steps(m, st));
       if (pairing) HYB_TRY(pair_first<T>(m, A, hist, st));
       return HYB_OK;
     }
-    adjoint_slots<T>(m, A, cot, nsteps, nullptr);
-    launch_adjoint<T>(A, st);
-    HYB_LAUNCHED(m);
+    HYB_TRY(adj_step(nsteps, nullptr));
     const int nseg = (nsteps + C - 1) / C;
     for (int seg = nseg - 1; seg >= 0; --seg) {
       const int kb = seg * C;
       const int ke = std::min((seg + 1) * C, nsteps) - 1;
       if (pairing) {
+        HYB_TRY(join_steps(m, st));
         for (int s = 0; s < nsrc; ++s) {
           T* u0 = field_buf<T>(m, m->U, nsrc, s, kb);
           T* um = field_buf<T>(m, m->U, nsrc, s, kb - 1);
@@ -467,18 +504,13 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
           launch_extract_owned<T>(F, u0, hist + (size_t)s * m->nown, st);
           HYB_LAUNCHED(m);
         }
-        for (int k = kb; k < ke; ++k) {
-          forward_slots<T>(m, F, m->src, nsrc, nsteps, dt, k, nullptr, hist + (size_t)(k + 1 - kb) * lvl);
-          launch_forward<T>(F, st);
-          HYB_LAUNCHED(m);
-        }
+        HYB_TRY(begin_steps(m, st));
+        for (int k = kb; k < ke; ++k) HYB_TRY(fwd_step(k, hist + (size_t)(k + 1 - kb) * lvl));
       }
-      for (int j = ke; j >= std::max(kb, 1); --j) {
-        adjoint_slots<T>(m, A, cot, j, pairing ? hist + (size_t)(j - kb) * lvl : nullptr);
-        launch_adjoint<T>(A, st);
-        HYB_LAUNCHED(m);
-      }
+      for (int j = ke; j >= std::max(kb, 1); --j)
+        HYB_TRY(adj_step(j, pairing ? hist + (size_t)(j - kb) * lvl : nullptr));
     }
+    HYB_TRY(join_steps(m, st));
     if (pairing) HYB_TRY(pair_first<T>(m, A, hist, st));
     return HYB_OK;
   };
@@ -704,10 +736,12 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   }
   if (st == HYB_OK && cudaMemsetAsync(m->flag.p, 0, sizeof(int), m->st) != cudaSuccess)
     st = fail(HYB_ERR_CUDA, "cudaMemsetAsync failed");
-  if (st == HYB_OK && cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess) {
+  if (st == HYB_OK && (cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&m->ev_bulk, cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&m->ev_shell, cudaEventDisableTiming) != cudaSuccess)) {
     cudaGetLastError();
-    m->cap = nullptr;
-    st = fail(HYB_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+    st = fail(HYB_ERR_CUDA, "stream or event creation failed");
   }
   if (st != HYB_OK) {
     hyb_mesh_destroy(m);
@@ -734,6 +768,7 @@ hyb_status hyb_mesh_query(const hyb_mesh* m, hyb_mesh_info* o) {
 hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   if (!m) return HYB_OK;
   cudaStreamSynchronize(m->st);
+  if (m->aux) cudaStreamSynchronize(m->aux);
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
                     &m->g, &m->atrial, &m->cot, &m->trace};
   for (DevBuf* b : bufs) release(*b);
@@ -741,6 +776,9 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   for (SweepGraph& g : m->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (m->cap) cudaStreamDestroy(m->cap);
+  if (m->aux) cudaStreamDestroy(m->aux);
+  if (m->ev_bulk) cudaEventDestroy(m->ev_bulk);
+  if (m->ev_shell) cudaEventDestroy(m->ev_shell);
   delete m;
   return HYB_OK;
 }

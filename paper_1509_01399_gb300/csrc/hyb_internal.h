@@ -49,18 +49,24 @@ struct StepArgs {
   int npb;           // interior kernel: thread blocks per plane of the interior box
   int ntx;           // interior kernel: tiles along x
   int zchunk, nzc;   // interior kernel: planes per block, blocks along z
-  long long nshell;  // boundary-shell kernel: nodes per slot
+  int small;         // some axis has < 5 nodes: one generic kernel per level
+  int nedge;         // edge kernel: 128-thread tiles per slot
   int nslots;
   Slot<T> s[kMaxSlots];
 };
 
-// One time level: interior kernel + boundary-shell kernel (2 launches).
-// The interior/shell split must match shell thickness 1 (forward) and 2
-// (adjoint): see step_geometry().
+// One time level = an interior kernel and an edge kernel, which read the
+// same inputs and write disjoint nodes (they may run concurrently).  On
+// lattices with fewer than 5 nodes on an axis the "bulk" launcher runs one
+// generic kernel over every node and the "shell" launcher does nothing.
 template <typename T>
-void launch_forward(const StepArgs<T>& a, cudaStream_t st);
+void launch_forward_bulk(const StepArgs<T>& a, cudaStream_t st);
 template <typename T>
-void launch_adjoint(const StepArgs<T>& a, cudaStream_t st);
+void launch_forward_shell(const StepArgs<T>& a, cudaStream_t st);
+template <typename T>
+void launch_adjoint_bulk(const StepArgs<T>& a, cudaStream_t st);
+template <typename T>
+void launch_adjoint_shell(const StepArgs<T>& a, cudaStream_t st);
 // G[c] += voxel pairing of (u^0 in hist box, lambda^1) for one slot.
 template <typename T>
 void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t st);

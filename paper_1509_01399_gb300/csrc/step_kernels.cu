@@ -1,9 +1,10 @@
 // Time-step kernels of the hybrid FEM/FDM scheme.
 //
-// One launch advances every slot (source / problem) by one time level.  A
-// thread owns one (x, y) column of the lattice and marches a chunk of z
-// planes, keeping u at z-1, z, z+1 in registers; x/y neighbours come through
-// L1.  Three row kinds share the launch:
+// One time level of every slot (source / problem) is an interior launch
+// (all nodes but those within one node of two faces) and a small edge
+// launch, which read the same inputs and write disjoint nodes.  An interior
+// thread owns one (x, y) column and marches a chunk of z planes, keeping u
+// at z-1, z, z+1 in registers; x/y neighbours come through L1.  Row kinds:
 //  * FDM rows, Eq. (fdmschemeforward): u^{k+1} = 2u^k - u^{k-1} + tau^2 Delta_h u^k,
 //  * FEM rows on the FEM-owned nodes, Eq. (fem) with lumped mass: on the
 //    Kuhn-cut voxels the row is a 7-point stencil whose axis-edge weight is
@@ -11,15 +12,17 @@
 //    the voxel's diagonal corners) or a_c / 6,
 //  * boundary rows: Neumann mirror ghosts, the plane-wave flux of Eq. (f),
 //    and the absorbing rows of Eq. (eq:abs2), which use the new value of the
-//    inward neighbour; a boundary thread recomputes that value itself, so no
-//    intra-step synchronisation is needed.
+//    inward neighbour: the thread of that neighbour writes the face node, and
+//    edge/corner threads recompute the values they need, so no intra-step
+//    synchronisation is needed.
 // Both schemes write the same field, so the omega_o / omega_diamond copies
 // of Algorithm 1 need no data movement.
 //
 // The adjoint kernel is the exact transpose of the forward step (the
 // discrete form of Eq. (adjoint1)).  Away from the outer boundary the
 // mass-weighted operator is symmetric, so the transposed row is the forward
-// stencil; within one node of the boundary each node gathers the transposed
+// stencil; next to a face the transposed face row (closed form) and its
+// coupling are added, and near edges each node gathers the transposed
 // coefficients of its neighbours' rows (mirror factors, absorbing rows) and
 // solves the transposed absorbing coupling by recomputing the outer values.
 // The same launch accumulates, per unknown voxel and in FP64, the sum over
@@ -187,6 +190,43 @@ __device__ __noinline__ T adj_rhs(const StepArgs<T>& A, const Slot<T>& S, int i,
   return rhs;
 }
 
+// Inlined copy of adj_rhs (below).
+// Right-hand side of the transposed step at node m:
+// (B_j^T lambda^{j+1})_m - (C_{j+1}^T lambda^{j+2})_m + c^j_m.
+template <typename T>
+__device__ __forceinline__ T adj_rhs_inl(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k) {
+  const T* __restrict__ l1 = S.cur;
+  const long long id = lin(A, i, j, k);
+  const int fbm = face_bits(i, j, k, A.nx, A.ny, A.nz);
+  T rhs;
+  if (fbm & S.mask_f) rhs = A.r * l1[id];
+  else rhs = (T(2) + A.c2 * row_diag(A, i, j, k)) * l1[id];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int s = t ? 1 : -1;
+      const int ni = i + (ax == 0 ? s : 0);
+      const int nj = j + (ax == 1 ? s : 0);
+      const int nk = k + (ax == 2 ? s : 0);
+      if (ni < 0 || ni >= A.nx || nj < 0 || nj >= A.ny || nk < 0 || nk >= A.nz) continue;
+      const long long nid = lin(A, ni, nj, nk);
+      const int fbn = face_bits(ni, nj, nk, A.nx, A.ny, A.nz) & S.mask_f;
+      if (fbn) {
+        // absorbing row of the neighbour couples to m only when m is its
+        // inward neighbour across the face on side s of axis ax
+        const int f = 2 * ax + (s > 0 ? 1 : 0);
+        if (fbn & (1 << f)) rhs += l1[nid] / T(__popc(fbn));
+      } else {
+        rhs += A.c2 * row_coef(A, ni, nj, nk, ax, -s) * l1[nid];
+      }
+    }
+  }
+  if (!(fbm & S.mask_c)) rhs -= S.prev[id];
+  if (S.obs_r && ((fbm >> S.obs_face) & 1)) rhs += S.obs_r[face_index(S.obs_face, i, j, k, A.nx, A.ny)];
+  return rhs;
+}
+
 // lambda^j at node m: solve E_{j-1}^T lambda^j = rhs, where E couples an
 // absorbing node b to its inward neighbours with r / L_b.
 template <typename T, int D>
@@ -237,42 +277,20 @@ __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restric
   return d3 / T(3) + d6 / T(6);
 }
 
-// Node t of the boundary shell of thickness TH (every node with a coordinate
-// closer than TH to a face), enumerated as whole z planes, then whole y rows
-// of the remaining planes, then the x ends of the remaining rows.
-template <typename T, int TH>
-__device__ __forceinline__ void shell_node(const StepArgs<T>& A, long long t, int& i, int& j, int& k) {
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int ix = max(nx - 2 * TH, 0), iy = max(ny - 2 * TH, 0), iz = max(nz - 2 * TH, 0);
-  const long long plane = (long long)nx * ny;
-  const long long na = (long long)(nz - iz) * plane;
-  if (t < na) {
-    const int p = (int)(t / plane);
-    const long long r = t - (long long)p * plane;
-    k = p < TH ? p : p + iz;
-    j = (int)(r / nx);
-    i = (int)(r - (long long)j * nx);
-    return;
-  }
-  t -= na;
-  const long long rowsz = (long long)(ny - iy) * nx;
-  const long long nb = (long long)iz * rowsz;
-  if (t < nb) {
-    const int pk = (int)(t / rowsz);
-    const long long r = t - (long long)pk * rowsz;
-    k = TH + pk;
-    const int row = (int)(r / nx);
-    j = row < TH ? row : row + iy;
-    i = (int)(r - (long long)row * nx);
-    return;
-  }
-  t -= nb;
-  const int w = nx - ix;
-  const long long idx = t / w;
-  const int c = (int)(t - idx * w);
-  k = TH + (int)(idx / iy);
-  j = TH + (int)(idx % iy);
-  i = c < TH ? c : c + ix;
+// Laplacian part of a non-absorbing row (inlined form of row_lap).
+template <typename T>
+__device__ __forceinline__ T row_lap_inl(const StepArgs<T>& A, const T* __restrict__ u, int i, int j, int k) {
+  const long long id = lin(A, i, j, k);
+  const long long sz = (long long)A.nx * A.ny;
+  const T c = u[id];
+  if (fem_owned(A, i, j, k)) return fem_lap(A, u, id, i, j, k, c, u[id - sz], u[id + sz]);
+  const T xm = i > 0 ? u[id - 1] : u[id + 1];
+  const T xp = i < A.nx - 1 ? u[id + 1] : u[id - 1];
+  const T ym = j > 0 ? u[id - A.nx] : u[id + A.nx];
+  const T yp = j < A.ny - 1 ? u[id + A.nx] : u[id - A.nx];
+  const T zm = k > 0 ? u[id - sz] : u[id + sz];
+  const T zp = k < A.nz - 1 ? u[id + sz] : u[id - sz];
+  return (xm - c) + (xp - c) + (ym - c) + (yp - c) + (zm - c) + (zp - c);
 }
 
 template <typename T>
@@ -288,28 +306,143 @@ __device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T
   A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, S.cur, i, j, k);
 }
 
-// Laplacian part of the row of a node that lies on no face (all six
-// neighbours exist, no mirror): FEM stencil or 7-point FDM.
-template <typename T>
-__device__ __forceinline__ T interior_lap(const StepArgs<T>& A, const T* __restrict__ u, long long id, int i,
-                                          int j, int k) {
-  const long long pl = (long long)A.nx * A.ny;
-  const T c = u[id];
-  if (fem_owned(A, i, j, k)) return fem_lap(A, u, id, i, j, k, c, u[id - pl], u[id + pl]);
-  return (u[id - 1] - c) + (u[id + 1] - c) + (u[id - A.nx] - c) + (u[id + A.nx] - c) + (u[id - pl] - c) +
-         (u[id + pl] - c);
-}
-
 template <typename T>
 __device__ __forceinline__ long long axis_stride(const StepArgs<T>& A, int ax) {
   return ax == 0 ? 1LL : (ax == 1 ? (long long)A.nx : (long long)A.nx * A.ny);
 }
 
-// Interior kernel shared by the forward (TH = 1) and adjoint (TH = 2)
-// steps: 32 x 8 thread tiles of the interior box, each thread marching a
-// chunk of z planes with u at z-1, z, z+1 in registers and the next plane
-// and the previous-level value loaded one iteration ahead.
-template <typename T, int TH, bool ADJ>
+// The "edge set" (lattices with >= 5 nodes per axis): every node whose
+// coordinate is near a face (0, 1, n-2 or n-1) on at least two axes.  It is
+// cut into tiles of 128 threads: tile 0 is the 4 x 4 x 4 corner block
+// (threads 0..63), the other tiles are 8 consecutive positions of one of
+// the 12 edge bars (4 x 4 near coordinates x 8).  Within a tile every
+// absorbing coupling stays inside the tile.  Returns false for idle threads;
+// q[] holds the near index (0..3 -> 0, 1, n-2, n-1) per axis (-1: mid) and
+// nf the number of axes on which the node is on a face.
+template <typename T>
+__device__ __forceinline__ bool edge_tile_node(const StepArgs<T>& A, int blk, int t, int& i, int& j, int& k,
+                                               int q[3], int& nf) {
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  auto nr = [](int qq, int n) { return qq < 2 ? qq : n - 4 + qq; };
+  int pos = 0, bar = -1;
+  if (blk == 0) {
+    if (t >= 64) return false;
+    q[0] = t & 3;
+    q[1] = (t >> 2) & 3;
+    q[2] = t >> 4;
+  } else {
+    blk -= 1;
+    const int bz = (nz - 4 + 7) / 8, by = (ny - 4 + 7) / 8;
+    const int lo = t & 3, hi = (t >> 2) & 3;
+    if (blk < bz) {
+      bar = 2;
+      pos = blk * 8 + (t >> 4);
+      if (pos >= nz - 4) return false;
+      q[0] = lo;
+      q[1] = hi;
+      q[2] = -1;
+    } else if (blk < bz + by) {
+      bar = 1;
+      pos = (blk - bz) * 8 + (t >> 4);
+      if (pos >= ny - 4) return false;
+      q[0] = lo;
+      q[1] = -1;
+      q[2] = hi;
+    } else {
+      bar = 0;
+      pos = (blk - bz - by) * 8 + (t >> 4);
+      if (pos >= nx - 4) return false;
+      q[0] = -1;
+      q[1] = lo;
+      q[2] = hi;
+    }
+  }
+  i = q[0] < 0 ? 2 + pos : nr(q[0], nx);
+  j = q[1] < 0 ? 2 + pos : nr(q[1], ny);
+  k = q[2] < 0 ? 2 + pos : nr(q[2], nz);
+  nf = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) nf += (q[a] == 0 || q[a] == 3) ? 1 : 0;
+  (void)bar;
+  return true;
+}
+
+// Thread index, inside the same tile, of the node with near index qn on
+// axis ax (the other coordinates unchanged).
+__device__ __forceinline__ int edge_tile_peer(int t, int blk, const int q[3], int ax, int qn) {
+  if (blk == 0) {
+    const int sh = 2 * ax;
+    return (t & ~(3 << sh)) | (qn << sh);
+  }
+  // bar tiles: bits 0-1 = first near axis, bits 2-3 = second near axis
+  int first = -1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (q[a] >= 0) {
+      first = a;
+      break;
+    }
+  const int sh = (ax == first) ? 0 : 2;
+  return (t & ~(3 << sh)) | (qn << sh);
+}
+
+// Value of a face node b on the single face f, given the inward neighbour
+// m = b1: u^k_b, u^k_m and the new u^{k+1}_m.  Absorbing: Eq. (eq:abs2);
+// otherwise the mirror-ghost row with the source flux.  b's in-face
+// neighbours exist (its in-face coordinates are at least 2 from the edges).
+template <typename T>
+__device__ __forceinline__ T fwd_face_value(const StepArgs<T>& A, const Slot<T>& S, long long idb, int f, T ub,
+                                            T um, T nm) {
+  if ((S.mask_f >> f) & 1) return A.r * ub + (um - A.r * nm);
+  const int ax = f >> 1;
+  const T* __restrict__ u = S.cur;
+  T lap = T(2) * (um - ub);
+#pragma unroll
+  for (int a2 = 0; a2 < 3; ++a2) {
+    if (a2 == ax) continue;
+    const long long s2 = axis_stride(A, a2);
+    lap += (u[idb - s2] - ub) + (u[idb + s2] - ub);
+  }
+  T v = T(2) * ub - S.prev[idb] + A.c2 * lap;
+  if (S.src_face == f) v += S.srcval;
+  return v;
+}
+
+// lambda^j at a face node b on the single face f whose in-face coordinates
+// are at least 2 from the edges (no transposed absorbing coupling reaches
+// it), given lambda^{j+1} at b and at its inward neighbour m, and the
+// coefficient of m's row on b.
+template <typename T>
+__device__ __forceinline__ T adj_face_value(const StepArgs<T>& A, const Slot<T>& S, long long idb, int f, int i,
+                                            int j, int k, T lb, T lm, T coef_mb) {
+  const bool abc = (S.mask_f >> f) & 1;
+  T rhs = abc ? A.r * lb : (T(2) - T(6) * A.c2) * lb;
+  rhs += A.c2 * coef_mb * lm;
+  if (!abc) {
+    const int ax = f >> 1;
+    const T* __restrict__ l1 = S.cur;
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2) {
+      if (a2 == ax) continue;
+      const long long s2 = axis_stride(A, a2);
+      rhs += A.c2 * (l1[idb - s2] + l1[idb + s2]);
+    }
+  }
+  if (!((S.mask_c >> f) & 1)) rhs -= S.prev[idb];
+  if (S.obs_r && S.obs_face == f) rhs += S.obs_r[face_index(f, i, j, k, A.nx, A.ny)];
+  return rhs;
+}
+
+// Interior kernel of one time level (lattices with >= 5 nodes per axis),
+// forward (ADJ = false) or transposed (ADJ = true).  32 x 8 thread tiles of
+// the nodes 1 .. n-2, each thread marching a chunk of z planes with u at
+// z-1, z, z+1 in registers and the next plane and the previous level loaded
+// one iteration ahead.  A node one step inside exactly one face also
+// produces the face node next to it (the forward needs its new value; the
+// transposed face row has a closed form) and applies the transposed
+// boundary couplings to itself.  Nodes within one node of two faces are
+// left to the edge kernel.
+template <typename T, bool ADJ>
 __global__ void __launch_bounds__(kTileX * kTileY) bulk_kernel(const __grid_constant__ StepArgs<T> A) {
   const int tps = A.npb * A.nzc;
   const int si = blockIdx.x / tps;
@@ -319,16 +452,20 @@ __global__ void __launch_bounds__(kTileX * kTileY) bulk_kernel(const __grid_cons
   const int tyy = rem / A.ntx;
   const int txx = rem - tyy * A.ntx;
   const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int i = TH + txx * kTileX + (threadIdx.x % kTileX);
-  const int j = TH + tyy * kTileY + (threadIdx.x / kTileX);
-  if (i > nx - 1 - TH || j > ny - 1 - TH) return;
-  const int z0 = TH + zc * A.zchunk;
-  const int z1 = min(z0 + A.zchunk, nz - TH);
+  const int i = 1 + txx * kTileX + (threadIdx.x % kTileX);
+  const int j = 1 + tyy * kTileY + (threadIdx.x / kTileX);
+  if (i > nx - 2 || j > ny - 2) return;
+  const int dxs = (i == 1) ? -1 : (i == nx - 2 ? 1 : 0);  // direction to a near face
+  const int dys = (j == 1) ? -1 : (j == ny - 2 ? 1 : 0);
+  const int nxy = (dxs != 0) + (dys != 0);
+  if (nxy >= 2) return;  // the column runs along an edge: edge kernel
+  const int z0 = 1 + zc * A.zchunk;
+  const int z1 = min(z0 + A.zchunk, nz - 1);
   if (z0 >= z1) return;
   const Slot<T>& S = A.s[si];
   const long long plane = (long long)nx * ny;
+  const int pl = (int)plane;
   const T* __restrict__ c = S.cur;
-  const T* __restrict__ p = S.prev;
   T* __restrict__ out = S.next;
   const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
   const bool xy_vox = ADJ && S.hist_r != nullptr && i >= A.fl[0] && i < A.fl[0] + A.un[0] &&
@@ -336,178 +473,196 @@ __global__ void __launch_bounds__(kTileX * kTileY) bulk_kernel(const __grid_cons
   T* __restrict__ hw = ADJ ? nullptr : S.hist_w;
   const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
   long long id = (long long)i + (long long)nx * j + plane * z0;
-  T cm = c[id - plane];
-  T c0 = c[id];
-  T cp = c[id + plane];
-  T pv = p[id];
+  const T* __restrict__ cq = c + id;
+  const T* __restrict__ pq = S.prev + id;
+  T* __restrict__ oq = out + id;
+  T cm = cq[-pl];
+  T c0 = cq[0];
+  T cp = cq[pl];
+  T pv = pq[0];
   const T c2 = A.c2;
-  for (int k = z0; k < z1; ++k, id += plane) {
-    const T cpp = (k + 2 <= nz - 1) ? c[id + 2 * plane] : T(0);
-    const T pvn = (k + 1 < z1) ? p[id + plane] : T(0);
-    T val;
-    const bool fem = xy_fem && k >= A.fl[2] && k <= A.fh[2];
-    if (fem) {
-      val = T(2) * c0 - pv + c2 * fem_lap(A, c, id, i, j, k, c0, cm, cp);
-      if (hw)
+  for (int k = z0; k < z1; ++k) {
+    const T cpp = (k + 2 <= nz - 1) ? cq[2 * pl] : T(0);
+    const T pvn = (k + 1 < z1) ? pq[pl] : T(0);
+    const int dzs = (k == 1) ? -1 : (k == nz - 2 ? 1 : 0);
+    const int cnt = nxy + (dzs != 0);
+    if (cnt <= 1) {
+      T val;
+      const bool fem = xy_fem && k >= A.fl[2] && k <= A.fh[2];
+      if (fem) {
+        val = T(2) * c0 - pv + c2 * fem_lap(A, c, id, i, j, k, c0, cm, cp);
+      } else {
+        const T lap = (cq[-1] - c0) + (cq[1] - c0) + (cq[-nx] - c0) + (cq[nx] - c0) + (cm - c0) + (cp - c0);
+        val = T(2) * c0 - pv + c2 * lap;
+      }
+      if (cnt == 1) {
+        // the face node b next to this node, on face f of axis ax
+        const int ax = dxs ? 0 : (dys ? 1 : 2);
+        const int sd = dxs ? dxs : (dys ? dys : dzs);
+        const int f = 2 * ax + (sd > 0 ? 1 : 0);
+        const long long db = sd * axis_stride(A, ax);
+        const T xb = ax == 2 ? (sd < 0 ? cm : cp) : cq[db];
+        const int bi = i + (ax == 0 ? sd : 0), bj = j + (ax == 1 ? sd : 0), bk = k + (ax == 2 ? sd : 0);
+        if constexpr (!ADJ) {
+          const T vb = fwd_face_value(A, S, id + db, f, xb, c0, val);
+          out[id + db] = vb;
+          if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, bk, nx, ny)] = vb;
+        } else {
+          const T coef_mb = row_coef(A, i, j, k, ax, sd);
+          const T lb = adj_face_value(A, S, id + db, f, bi, bj, bk, xb, c0, coef_mb);
+          // the face row's transposed coefficient on this node replaces the
+          // symmetric one the stencil used
+          val += (((S.mask_f >> f) & 1) ? xb : T(2) * c2 * xb) - c2 * coef_mb * xb;
+          if ((S.mask_e >> f) & 1) val -= A.r * lb;
+          out[id + db] = lb;
+        }
+      }
+      oq[0] = val;
+      if (!ADJ && hw && fem)
         hw[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
             val;
-    } else {
-      const T lap = (c[id - 1] - c0) + (c[id + 1] - c0) + (c[id - nx] - c0) + (c[id + nx] - c0) + (cm - c0) +
-                    (cp - c0);
-      val = T(2) * c0 - pv + c2 * lap;
-    }
-    out[id] = val;
-    if (ADJ && xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
-      const long long vid = (long long)(i - A.fl[0]) +
-                            (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
-      A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, c, i, j, k);
+      if (ADJ && xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
+        const long long vid = (long long)(i - A.fl[0]) +
+                              (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
+        A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, c, i, j, k);
+      }
     }
     cm = c0;
     c0 = cp;
     cp = cpp;
     pv = pvn;
+    cq += pl;
+    pq += pl;
+    oq += pl;
+    id += pl;
   }
 }
 
-// Outer faces: Neumann, source and absorbing rows; trace record.  A node on
-// a single face takes an inlined row; edge and corner nodes the generic one.
+// Edge set of the forward step.  Levels by the number of faces a node lies
+// on: nodes on no face take their interior row, then face, edge and corner
+// nodes; an absorbing row (Eq. (eq:abs2)) reads the new values of its
+// inward neighbours, one level down in the same tile, from shared memory.
 template <typename T>
-__global__ void __launch_bounds__(128) fwd_shell_kernel(const __grid_constant__ StepArgs<T> A) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long ns = A.nshell;
-  if (t >= ns * A.nslots) return;
-  const int si = (int)(t / ns);
-  int i, j, k;
-  shell_node<T, 1>(A, t - (long long)si * ns, i, j, k);
+__global__ void __launch_bounds__(128) fwd_edge_kernel(const __grid_constant__ StepArgs<T> A) {
+  __shared__ T nv[128];
+  const int si = blockIdx.x / A.nedge;
+  const int blk = blockIdx.x - si * A.nedge;
+  const int t = threadIdx.x;
   const Slot<T>& S = A.s[si];
-  const int fall = face_bits(i, j, k, A.nx, A.ny, A.nz);
-  const long long id = lin(A, i, j, k);
-  T val;
-  if (__popc(fall) == 1) {
-    const int f = __ffs(fall) - 1;
-    const int ax = f >> 1;
-    const int step = (f & 1) ? -1 : 1;  // inward
-    const long long sa = axis_stride(A, ax);
-    const T* __restrict__ u = S.cur;
-    const T* __restrict__ up = S.prev;
-    if (S.mask_f & fall) {
-      // Eq. (eq:abs2) with the new value of the inward neighbour b1
-      const long long id1 = id + step * sa;
-      const T n1 = T(2) * u[id1] - up[id1] +
-                   A.c2 * interior_lap(A, u, id1, i + (ax == 0 ? step : 0), j + (ax == 1 ? step : 0),
-                                       k + (ax == 2 ? step : 0));
-      val = A.r * u[id] + (u[id1] - A.r * n1);
-    } else {
-      // mirror ghost along the face normal, plus the source flux
-      const T cc = u[id];
-      T lap = T(2) * (u[id + step * sa] - cc);
-#pragma unroll
-      for (int a2 = 0; a2 < 3; ++a2) {
-        if (a2 == ax) continue;
-        const long long s2 = axis_stride(A, a2);
-        lap += (u[id - s2] - cc) + (u[id + s2] - cc);
-      }
-      val = T(2) * cc - up[id] + A.c2 * lap;
-      if (S.src_face == f) val += S.srcval;
-    }
-  } else {
-    val = fwd_new<T, 3>(A, S, i, j, k);
+  int i = 0, j = 0, k = 0, nf = -1, q[3];
+  const bool valid = edge_tile_node(A, blk, t, i, j, k, q, nf);
+  const long long id = valid ? lin(A, i, j, k) : 0;
+  const int fall = valid ? face_bits(i, j, k, A.nx, A.ny, A.nz) : 0;
+  const int fb = fall & S.mask_f;
+  T plain = T(0);  // the non-absorbing row, from level-k data only
+  if (valid && !fb) {
+    plain = T(2) * S.cur[id] - S.prev[id] + A.c2 * row_lap_inl(A, S.cur, i, j, k);
+    if (S.src_face >= 0 && ((fall >> S.src_face) & 1)) plain += S.srcval;
   }
+  nv[t] = plain;
+  __syncthreads();
+  for (int level = 1; level <= 3; ++level) {
+    T v = T(0);
+    const bool mine = valid && fb && __popc(fall) == level;
+    if (mine) {
+      T acc = T(0);
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const int fa = (fb >> (2 * ax)) & 3;
+        if (!fa) continue;
+        const int step = (fa & 1) ? 1 : -1;  // inward
+        const long long id1 = id + step * (ax == 0 ? 1LL : (ax == 1 ? (long long)A.nx : (long long)A.nx * A.ny));
+        const int t1 = edge_tile_peer(t, blk, q, ax, (fa & 1) ? 1 : 2);
+        acc += S.cur[id1] - A.r * nv[t1];
+      }
+      v = A.r * S.cur[id] + acc / T(__popc(fb));
+    }
+    __syncthreads();
+    if (mine) nv[t] = v;
+    __syncthreads();
+  }
+  if (!valid) return;
+  const T val = nv[t];
   S.next[id] = val;
   if (S.obs_w && ((fall >> S.obs_face) & 1)) S.obs_w[face_index(S.obs_face, i, j, k, A.nx, A.ny)] = val;
+  if (S.hist_w && fem_owned(A, i, j, k))
+    S.hist_w[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
+        val;
 }
 
-// lambda^j at a node on the single face f whose in-face coordinates are at
-// least two nodes from the other faces (no transposed absorbing coupling
-// reaches it).
+// Edge set of the transposed step: every thread gathers its transposed row
+// in parallel, then the transposed absorbing couplings (E^T) are resolved
+// from the nodes on the most faces inwards, through shared memory.
 template <typename T>
-__device__ __forceinline__ T adj_face_interior(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k,
-                                               int f) {
-  const T* __restrict__ l1 = S.cur;
-  const long long id = lin(A, i, j, k);
-  const int ax = f >> 1;
-  const int step = (f & 1) ? -1 : 1;
-  const long long sa = axis_stride(A, ax);
-  const bool abc = (S.mask_f >> f) & 1;
-  T rhs = abc ? A.r * l1[id] : (T(2) - T(6) * A.c2) * l1[id];
-  rhs += A.c2 *
-         row_coef(A, i + (ax == 0 ? step : 0), j + (ax == 1 ? step : 0), k + (ax == 2 ? step : 0), ax, -step) *
-         l1[id + step * sa];
-  if (!abc) {
-#pragma unroll
-    for (int a2 = 0; a2 < 3; ++a2) {
-      if (a2 == ax) continue;
-      const long long s2 = axis_stride(A, a2);
-      rhs += A.c2 * (l1[id - s2] + l1[id + s2]);
-    }
-  }
-  if (!((S.mask_c >> f) & 1)) rhs -= S.prev[id];
-  if (S.obs_r && S.obs_face == f) rhs += S.obs_r[face_index(f, i, j, k, A.nx, A.ny)];
-  return rhs;
-}
-
-// Nodes within one node of a face.  Inlined rows for the two common cases
-// (on one face, or one node inside one face, away from edges); the generic
-// transposed gather for the rest.
-template <typename T>
-__global__ void __launch_bounds__(128) adj_shell_kernel(const __grid_constant__ StepArgs<T> A) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long ns = A.nshell;
-  if (t >= ns * A.nslots) return;
-  const int si = (int)(t / ns);
-  int i, j, k;
-  shell_node<T, 2>(A, t - (long long)si * ns, i, j, k);
+__global__ void __launch_bounds__(128) adj_edge_kernel(const __grid_constant__ StepArgs<T> A) {
+  __shared__ T lam[128];
+  const int si = blockIdx.x / A.nedge;
+  const int blk = blockIdx.x - si * A.nedge;
+  const int t = threadIdx.x;
   const Slot<T>& S = A.s[si];
-  const int cc[3] = {i, j, k};
-  const int nn[3] = {A.nx, A.ny, A.nz};
-  int n0 = 0, n1 = 0, a0 = 0, a1 = 0;
-  bool fast = nn[0] >= 4 && nn[1] >= 4 && nn[2] >= 4;
+  int i = 0, j = 0, k = 0, nf = -1, q[3];
+  const bool valid = edge_tile_node(A, blk, t, i, j, k, q, nf);
+  lam[t] = valid ? adj_rhs_inl(A, S, i, j, k) : T(0);
+  __syncthreads();
+  for (int level = 2; level >= 0; --level) {
+    T v = T(0);
+    const bool mine = valid && nf == level;
+    if (mine) {
+      v = lam[t];
 #pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const int d = min(cc[ax], nn[ax] - 1 - cc[ax]);
-    if (d == 0) {
-      ++n0;
-      a0 = ax;
-    } else if (d == 1) {
-      ++n1;
-      a1 = ax;
-    }
-  }
-  const long long id = lin(A, i, j, k);
-  T val;
-  if (fast && n0 == 1 && n1 == 0) {
-    val = adj_face_interior(A, S, i, j, k, 2 * a0 + (cc[a0] == 0 ? 0 : 1));
-  } else if (fast && n0 == 0 && n1 == 1) {
-    // one node inside face f; b is the face node next to it
-    const int f = 2 * a1 + (cc[a1] == 1 ? 0 : 1);
-    const int bs = (f & 1) ? 1 : -1;  // from m towards b
-    const T* __restrict__ l1 = S.cur;
-    T rhs = (T(2) + A.c2 * row_diag(A, i, j, k)) * l1[id];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-#pragma unroll
-      for (int tt = 0; tt < 2; ++tt) {
-        const int s = tt ? 1 : -1;
-        const long long nid = id + s * axis_stride(A, ax);
-        if (ax == a1 && s == bs) {
-          rhs += ((S.mask_f >> f) & 1) ? l1[nid] : T(2) * A.c2 * l1[nid];
-        } else {
-          rhs += A.c2 *
-                 row_coef(A, i + (ax == 0 ? s : 0), j + (ax == 1 ? s : 0), k + (ax == 2 ? s : 0), ax, -s) *
-                 l1[nid];
-        }
+      for (int ax = 0; ax < 3; ++ax) {
+        if (q[ax] != 1 && q[ax] != 2) continue;  // not one node inside a face on this axis
+        const int s = q[ax] == 1 ? -1 : 1;
+        const int bi = i + (ax == 0 ? s : 0), bj = j + (ax == 1 ? s : 0), bk = k + (ax == 2 ? s : 0);
+        const int f = 2 * ax + (s > 0 ? 1 : 0);
+        const int fbb = face_bits(bi, bj, bk, A.nx, A.ny, A.nz) & S.mask_e;
+        if (!(fbb & (1 << f))) continue;
+        v -= (A.r / T(__popc(fbb))) * lam[edge_tile_peer(t, blk, q, ax, q[ax] == 1 ? 0 : 3)];
       }
     }
-    rhs -= S.prev[id];
-    if ((S.mask_e >> f) & 1) {
-      rhs -= A.r * adj_face_interior(A, S, i + (a1 == 0 ? bs : 0), j + (a1 == 1 ? bs : 0),
-                                     k + (a1 == 2 ? bs : 0), f);
-    }
-    val = rhs;
-  } else {
-    val = adj_new<T, 3>(A, S, i, j, k);
+    __syncthreads();
+    if (mine) lam[t] = v;
+    __syncthreads();
   }
+  if (!valid) return;
+  S.next[lin(A, i, j, k)] = lam[t];
+  pair_if_voxel(A, S, si, i, j, k);
+}
+
+// Lattices with fewer than 5 nodes on some axis: every node by the generic
+// rows (forward and transposed).
+template <typename T>
+__global__ void __launch_bounds__(128) fwd_all_kernel(const __grid_constant__ StepArgs<T> A) {
+  const long long n = (long long)A.nx * A.ny * A.nz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * A.nslots) return;
+  const int si = (int)(t / n);
+  const long long id = t - (long long)si * n;
+  const int i = (int)(id % A.nx);
+  const int j = (int)((id / A.nx) % A.ny);
+  const int k = (int)(id / ((long long)A.nx * A.ny));
+  const Slot<T>& S = A.s[si];
+  const T val = fwd_new<T, 3>(A, S, i, j, k);
   S.next[id] = val;
+  if (S.obs_w && ((face_bits(i, j, k, A.nx, A.ny, A.nz) >> S.obs_face) & 1))
+    S.obs_w[face_index(S.obs_face, i, j, k, A.nx, A.ny)] = val;
+  if (S.hist_w && fem_owned(A, i, j, k))
+    S.hist_w[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
+        val;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) adj_all_kernel(const __grid_constant__ StepArgs<T> A) {
+  const long long n = (long long)A.nx * A.ny * A.nz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * A.nslots) return;
+  const int si = (int)(t / n);
+  const long long id = t - (long long)si * n;
+  const int i = (int)(id % A.nx);
+  const int j = (int)((id / A.nx) % A.ny);
+  const int k = (int)(id / ((long long)A.nx * A.ny));
+  const Slot<T>& S = A.s[si];
+  S.next[id] = adj_new<T, 3>(A, S, i, j, k);
   pair_if_voxel(A, S, si, i, j, k);
 }
 
@@ -576,19 +731,37 @@ __global__ void extract_owned_kernel(const __grid_constant__ StepArgs<T> A, cons
 }  // namespace
 
 template <typename T>
-void launch_forward(const StepArgs<T>& a, cudaStream_t st) {
+void launch_forward_bulk(const StepArgs<T>& a, cudaStream_t st) {
+  if (a.small) {
+    const long long n = (long long)a.nx * a.ny * a.nz * a.nslots;
+    fwd_all_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+    return;
+  }
   const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
-  if (grid) bulk_kernel<T, 1, false><<<grid, kTileX * kTileY, 0, st>>>(a);
-  const long long n = a.nshell * a.nslots;
-  fwd_shell_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+  if (grid) bulk_kernel<T, false><<<grid, kTileX * kTileY, 0, st>>>(a);
 }
 
 template <typename T>
-void launch_adjoint(const StepArgs<T>& a, cudaStream_t st) {
+void launch_forward_shell(const StepArgs<T>& a, cudaStream_t st) {
+  if (a.small) return;
+  fwd_edge_kernel<T><<<(unsigned)(a.nedge * a.nslots), 128, 0, st>>>(a);
+}
+
+template <typename T>
+void launch_adjoint_bulk(const StepArgs<T>& a, cudaStream_t st) {
+  if (a.small) {
+    const long long n = (long long)a.nx * a.ny * a.nz * a.nslots;
+    adj_all_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+    return;
+  }
   const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
-  if (grid) bulk_kernel<T, 2, true><<<grid, kTileX * kTileY, 0, st>>>(a);
-  const long long n = a.nshell * a.nslots;
-  adj_shell_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+  if (grid) bulk_kernel<T, true><<<grid, kTileX * kTileY, 0, st>>>(a);
+}
+
+template <typename T>
+void launch_adjoint_shell(const StepArgs<T>& a, cudaStream_t st) {
+  if (a.small) return;
+  adj_edge_kernel<T><<<(unsigned)(a.nedge * a.nslots), 128, 0, st>>>(a);
 }
 
 template <typename T>
@@ -615,8 +788,10 @@ void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStre
 }
 
 #define HYB_INSTANTIATE(T)                                                                       \
-  template void launch_forward<T>(const StepArgs<T>&, cudaStream_t);                             \
-  template void launch_adjoint<T>(const StepArgs<T>&, cudaStream_t);                             \
+  template void launch_forward_bulk<T>(const StepArgs<T>&, cudaStream_t);                        \
+  template void launch_forward_shell<T>(const StepArgs<T>&, cudaStream_t);                       \
+  template void launch_adjoint_bulk<T>(const StepArgs<T>&, cudaStream_t);                        \
+  template void launch_adjoint_shell<T>(const StepArgs<T>&, cudaStream_t);                       \
   template void launch_pair<T>(const StepArgs<T>&, const T*, const T*, cudaStream_t);            \
   template void launch_set_coef<T>(const StepArgs<T>&, T*, const double*, double, int*,         \
                                    cudaStream_t);                                                \
