@@ -91,6 +91,27 @@ def kuhn_tets(origin_nodes: np.ndarray):
     return out
 
 
+def refine_voxels(tet_nodes, tet_unknown, refine, n_lattice):
+    """Refine the marked voxels once by bisection.  The refinement edge of a
+    Kuhn tetrahedron v0 v1 v2 v3 (v0, v3 the voxel's diagonal corners) is the
+    diagonal v0 v3, shared by the six tetrahedra of the voxel and by no other
+    voxel; bisecting it at the voxel centre c replaces each tetrahedron by
+    (v0, v1, v2, c) and (c, v1, v2, v3).  The mesh stays conforming.  Centre
+    nodes get the ids n_lattice, n_lattice + 1, ... in unknown-voxel order."""
+    cid = np.full(refine.size, -1, dtype=np.int64)
+    cid[refine] = n_lattice + np.arange(int(refine.sum()))
+    keep = (tet_unknown < 0) | ~refine[np.maximum(tet_unknown, 0)]
+    par = ~keep
+    pn = tet_nodes[par]
+    pu = tet_unknown[par]
+    c = cid[pu]
+    ch1 = np.stack([pn[:, 0], pn[:, 1], pn[:, 2], c], axis=1)
+    ch2 = np.stack([c, pn[:, 1], pn[:, 2], pn[:, 3]], axis=1)
+    nodes = np.concatenate([tet_nodes[keep], ch1, ch2], axis=0)
+    unk = np.concatenate([tet_unknown[keep], pu, pu])
+    return nodes, unk, cid
+
+
 @dataclass
 class Phase:
     """Boundary state of one time step: the set of absorbing faces and the
@@ -104,7 +125,9 @@ class Phase:
 class Problem:
     """Lattice, FEM block, node classes and assembled operators."""
 
-    def __init__(self, n, h, fem_lo=None, fem_hi=None, bc=(BC_ABC,) * 6, origin=(0.0, 0.0, 0.0)):
+    def __init__(self, n, h, fem_lo=None, fem_hi=None, bc=(BC_ABC,) * 6, origin=(0.0, 0.0, 0.0), refine=None):
+        """refine: optional boolean per unknown voxel (x fastest); each marked
+        voxel is refined once by bisection (see `refine_voxels`)."""
         self.n = tuple(int(v) for v in n)
         if min(self.n) < 3:
             raise ValueError("every axis needs at least 3 nodes")
@@ -144,10 +167,24 @@ class Problem:
             rel = vox[unk] - (lo + 1)
             uid[unk] = rel[:, 0] + ud[0] * (rel[:, 1] + ud[1] * rel[:, 2])
             tets = kuhn_tets(vox)  # (V, 6, 4, 3)
-            self.tet_nodes = self.node_id(tets.reshape(-1, 3)).reshape(-1, 4)
-            self.tet_unknown = np.repeat(uid, 6)
-            X = self.h * tets.reshape(-1, 4, 3).astype(np.float64)
-            self.tet_vol, self.tet_grads = p1_element(X)
+            tet_nodes = self.node_id(tets.reshape(-1, 3)).reshape(-1, 4)
+            tet_unknown = np.repeat(uid, 6)
+            X_all = self.h * self.I.astype(np.float64)
+            self.NC = 0
+            self.center_of_unknown = np.full(self.n_unknown, -1, dtype=np.int64)
+            if refine is not None and self.n_unknown:
+                refine = np.asarray(refine, dtype=bool).ravel()
+                if refine.size != self.n_unknown:
+                    raise ValueError("refine mask must have one entry per unknown voxel")
+                tet_nodes, tet_unknown, centres = refine_voxels(tet_nodes, tet_unknown, refine, self.N)
+                self.NC = int(refine.sum())
+                self.center_of_unknown[np.flatnonzero(refine)] = self.N + np.arange(self.NC)
+                rel_ids = np.flatnonzero(refine)
+                cvox = np.stack([rel_ids % ud[0], (rel_ids // ud[0]) % ud[1], rel_ids // (ud[0] * ud[1])], axis=1)
+                X_all = np.concatenate([X_all, self.h * (cvox + lo + 1 + 0.5)], axis=0)
+            self.tet_nodes = tet_nodes
+            self.tet_unknown = tet_unknown
+            self.tet_vol, self.tet_grads = p1_element(X_all[tet_nodes])
             self.voxel_volume = self.h ** 3
         else:
             self.owned = np.zeros(self.N, dtype=bool)
@@ -156,9 +193,17 @@ class Problem:
             self.unknown_dims = (0, 0, 0)
             self.n_unknown = 0
             self.voxel_volume = self.h ** 3
+            self.NC = 0
+        # state vectors hold the lattice nodes, then the refinement centres
+        self.NT = self.N + self.NC
+        pad = np.zeros(self.NC, dtype=bool)
+        self.owned = np.concatenate([self.owned, np.ones(self.NC, dtype=bool)])
+        self.omega_o = np.concatenate([self.omega_o, pad])
+        self.omega_diamond = np.concatenate([self.omega_diamond, pad])
+        self.on_face = [np.concatenate([f, pad]) for f in self.on_face]
         self.fdm_owned = ~self.owned
         self.owned_nodes = np.flatnonzero(self.owned)
-        self.owned_pos = np.full(self.N, -1, dtype=np.int64)
+        self.owned_pos = np.full(self.NT, -1, dtype=np.int64)
         self.owned_pos[self.owned_nodes] = np.arange(self.owned_nodes.size)
         self.D = self._fdm_laplacian()
         self._phase_cache = {}
@@ -212,7 +257,7 @@ class Problem:
             cols.append(ids)
             vals.append(np.full(self.N, -2 * inv_h2))
         return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                             shape=(self.N, self.N))
+                             shape=(self.NT, self.NT))
 
     def tet_coefficient(self, a_unknown):
         """a_K per tetrahedron: the voxel's value on unknown voxels, 1 on the
@@ -226,20 +271,20 @@ class Problem:
     def assemble(self, a_unknown):
         """Global stiffness K(a) and lumped mass M^L over the FEM block."""
         if not self.has_fem:
-            return sp.csr_matrix((self.N, self.N)), np.zeros(self.N)
+            return sp.csr_matrix((self.NT, self.NT)), np.zeros(self.NT)
         Kloc = element_stiffness(self.tet_vol, self.tet_grads, self.tet_coefficient(a_unknown))
         r = np.repeat(self.tet_nodes, 4, axis=1).ravel()
         c = np.tile(self.tet_nodes, (1, 4)).ravel()
-        K = sp.csr_matrix((Kloc.ravel(), (r, c)), shape=(self.N, self.N))
+        K = sp.csr_matrix((Kloc.ravel(), (r, c)), shape=(self.NT, self.NT))
         ML = np.bincount(self.tet_nodes.ravel(), weights=np.repeat(self.tet_vol / 4.0, 4),
-                         minlength=self.N)
+                         minlength=self.NT)
         return K, ML
 
     def space_operator(self, a_unknown):
         """L such that a non-absorbing row reads u^{k+1} = 2u^k - u^{k-1} - tau^2 (L u^k)_i:
         -Delta_h on FDM-owned rows, (M^L)^{-1} K on FEM-owned rows."""
         K, ML = self.assemble(a_unknown)
-        inv_ml = np.zeros(self.N)
+        inv_ml = np.zeros(self.NT)
         inv_ml[self.owned] = 1.0 / ML[self.owned]
         Lfe = sp.diags(inv_ml) @ K
         Lfd = -self.D
@@ -264,7 +309,7 @@ class Problem:
         key = tuple(abc_faces)
         if key in self._phase_cache:
             return self._phase_cache[key]
-        level = np.zeros(self.N, dtype=np.int64)
+        level = np.zeros(self.NT, dtype=np.int64)
         for f in abc_faces:
             level += self.on_face[f]
         pairs = []
@@ -282,7 +327,7 @@ class Problem:
         level, pairs = self.abc_structure(phase.abc_faces)
         r = (self.h - dt) / (self.h + dt)
         nonabc = (level == 0).astype(float)
-        I = sp.identity(self.N, format="csr")
+        I = sp.identity(self.NT, format="csr")
         Dn = sp.diags(nonabc)
         B = Dn @ (2.0 * I - dt * dt * Lop)
         E = Dn @ I
@@ -302,7 +347,7 @@ class Problem:
         rr, cc = np.concatenate(rb), np.concatenate(cb)
         B = (B + sp.csr_matrix((np.concatenate(vb), (rr, cc)), shape=B.shape)).tocsr()
         E = (E + sp.csr_matrix((np.concatenate(ve), (rr, cc)), shape=E.shape)).tocsr()
-        s = np.zeros(self.N)
+        s = np.zeros(self.NT)
         if phase.src_face >= 0:
             m = self.on_face[phase.src_face] & (level == 0)
             s[m] = dt * dt * 2.0 * phase.p / self.h
@@ -323,8 +368,8 @@ class Problem:
         own = self.owned
         obs = self.face_nodes(src.face) if src is not None else np.zeros(0, dtype=np.int64)
         if init is None:
-            u_fd = np.zeros(self.N)
-            u_fd_prev = np.zeros(self.N)
+            u_fd = np.zeros(self.NT)
+            u_fd_prev = np.zeros(self.NT)
         else:
             u_fd = np.array(init[0], dtype=np.float64)
             u_fd_prev = np.array(init[1], dtype=np.float64)
@@ -341,13 +386,13 @@ class Problem:
             # 1. FDM rows at omega_+ and omega_o (non-absorbing rows)
             rows = self.fdm_owned & (level == 0)
             lap = self.D @ u_fd
-            new_fd = np.zeros(self.N)
+            new_fd = np.zeros(self.NT)
             new_fd[rows] = 2.0 * u_fd[rows] - u_fd_prev[rows] + tau2 * lap[rows]
             if ph.src_face >= 0:
                 m = rows & self.on_face[ph.src_face]
                 new_fd[m] += tau2 * 2.0 * ph.p / h
             # 2. FEM rows at omega_* and omega_diamond, Eq. (fem)
-            new_fe = np.zeros(self.N)
+            new_fe = np.zeros(self.NT)
             if self.has_fem:
                 Ku = K @ u_fe
                 new_fe[own] = 2.0 * u_fe[own] - u_fe_prev[own] - tau2 * Ku[own] / ML[own]
@@ -362,7 +407,7 @@ class Problem:
                         continue
                     bb, bb1 = b[sel], b1[sel]
                     if acc is None:
-                        acc = np.zeros(self.N)
+                        acc = np.zeros(self.NT)
                     acc[bb] += u_fd[bb1] - r * new_fd[bb1]
                 if acc is not None:
                     m = level == L
@@ -425,8 +470,8 @@ class Problem:
         E_k u^{k+1} = B_k u^k - C_k u^{k-1} + s_k (+ f_k); returns the trace."""
         cache, seq = self.operators(a_unknown, src, nsteps, dt)
         obs = self.face_nodes(src.face)
-        u = np.zeros(self.N) if init is None else np.array(init[0], dtype=np.float64)
-        up = np.zeros(self.N) if init is None else np.array(init[1], dtype=np.float64)
+        u = np.zeros(self.NT) if init is None else np.array(init[0], dtype=np.float64)
+        up = np.zeros(self.NT) if init is None else np.array(init[1], dtype=np.float64)
         trace = np.zeros((nsteps + 1, obs.size))
         trace[0] = u[obs]
         strict = {key: self._strict_part(E) for key, (E, _, _, _) in cache.items()}
@@ -450,8 +495,8 @@ class Problem:
         cache, seq = self.operators(a_unknown, src, nsteps, dt)
         K, ML = self.assemble(a_unknown)
         obs = self.face_nodes(src.face)
-        lam1 = np.zeros(self.N)
-        lam2 = np.zeros(self.N)
+        lam1 = np.zeros(self.NT)
+        lam2 = np.zeros(self.NT)
         Gacc = np.zeros(self.n_unknown)
         lams = [None] * (nsteps + 2) if keep_lambdas else None
         tr = {key: (self._strict_part(E, transpose=True), B.T.tocsr(), C.T.tocsr())
@@ -580,4 +625,5 @@ def cg_step(prob: Problem, a, sources, nsteps, dt, obs_traces, state: dict, gamm
 
 
 def problem_from_workload(w) -> Problem:
-    return Problem(w.n, w.h, w.fem_lo, w.fem_hi, w.bc, w.origin)
+    refine = getattr(w, "refine", None)
+    return Problem(w.n, w.h, w.fem_lo, w.fem_hi, w.bc, w.origin, refine=refine)

@@ -64,6 +64,7 @@ class Workload:
     precision: str = "fp64"  # "fp64" or "fp32"
     ckpt_every: int = 0
     extra: dict = field(default_factory=dict)
+    refine: Optional[np.ndarray] = None  # bool per unknown voxel: refined once
 
     @property
     def unknown_dims(self) -> Tuple[int, int, int]:
@@ -179,6 +180,31 @@ def add_noise(trace: np.ndarray, level: float, seed: int = 1) -> np.ndarray:
     return t + level * np.abs(t).max() * rng.standard_normal(t.shape)
 
 
+def dilate(mask3: np.ndarray, r: int = 1) -> np.ndarray:
+    """Cubic (Chebyshev) dilation of a boolean (z, y, x) voxel mask by r voxels."""
+    out = mask3.copy()
+    nz, ny, nx = mask3.shape
+    for dz in range(-r, r + 1):
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                src = mask3[max(0, -dz):nz - max(0, dz), max(0, -dy):ny - max(0, dy), max(0, -dx):nx - max(0, dx)]
+                out[max(0, dz):nz - max(0, -dz), max(0, dy):ny - max(0, -dy), max(0, dx):nx - max(0, -dx)] |= src
+    return out
+
+
+def refine_around(sigma: np.ndarray, ud, r: int = 1) -> np.ndarray:
+    """Refinement mask: the voxels with sigma > 0 dilated by r voxels."""
+    m = (np.asarray(sigma).reshape(ud[2], ud[1], ud[0]) > 0)
+    return dilate(m, r).ravel()
+
+
+def refined_dt(h: float, a_max: float, safety: float = 0.9) -> float:
+    """Time step for meshes with voxels refined once: 2 / sqrt(32 a_max / h^2)
+    scaled by a safety factor (32 / h^2 bounds the rows of the once-bisected
+    Kuhn voxels, 12 / h^2 those of the lattice)."""
+    return safety * 2.0 * h / math.sqrt(32.0 * a_max)
+
+
 def structured_dt(h: float, a_max: float, safety: float = 0.9) -> float:
     """Time step from the CFL bound tau <= h / sqrt(3 a) (Eq. (CFL)) scaled by
     a safety factor."""
@@ -209,9 +235,11 @@ def inverse_129(nsteps: int = 1500) -> Workload:
     lo, hi = central_half(129)
     rng = np.random.Generator(np.random.PCG64(2))
     sigma = random_box_inclusions(lo, hi, 3, (3, 6), (0.5, 2.0), rng)
+    ud = unknown_dims(lo, hi)
     return Workload("inverse_129", n, h, origin, lo, hi, ALL_ABC, [Source(FACE_ZP, 40.0)],
-                    nsteps, structured_dt(h, 5.0), 5.0, sigma, "fp32",
-                    extra=dict(cg_iters=20, gamma=0.01, a0=1.0, noise=0.03, noise_seed=1))
+                    nsteps, refined_dt(h, 5.0), 5.0, sigma, "fp32",
+                    extra=dict(cg_iters=20, gamma=0.01, a0=1.0, noise=0.03, noise_seed=1),
+                    refine=refine_around(sigma, ud, 1))
 
 
 def autograd_97(nsteps: int = 1200) -> Workload:
@@ -226,7 +254,7 @@ def autograd_97(nsteps: int = 1200) -> Workload:
                     nsteps, structured_dt(h, 4.0), 4.0, sigma, "fp64", ckpt_every=50)
 
 
-def serving_request(i: int, sizes=(33, 65, 97, 129)) -> Workload:
+def serving_request(i: int, sizes=(33, 65, 97, 129), nsteps: Optional[int] = None) -> Workload:
     """Request i of the serving stream: grid drawn from `sizes`, FEM block =
     central half, 2-4 random cubic inclusions with sigma ~ U[0.2, 2], step
     count linear in the grid size (400 at 33^3 .. 1500 at 129^3), FP32."""
@@ -241,7 +269,8 @@ def serving_request(i: int, sizes=(33, 65, 97, 129)) -> Workload:
     side_hi = min(side_hi, max(2, (ud[0] - 4) // 3))
     side_lo = min(side_lo, side_hi)
     sigma = random_box_inclusions(lo, hi, count, (side_lo, side_hi), (0.2, 2.0), rng)
-    nsteps = int(round(400 + (N - 33) * (1500 - 400) / (129 - 33)))
+    if nsteps is None:
+        nsteps = int(round(400 + (N - 33) * (1500 - 400) / (129 - 33)))
     return Workload(f"serve_{i}", n, h, origin, lo, hi, ALL_ABC, [Source(FACE_ZP, 40.0)],
                     nsteps, structured_dt(h, 3.0), 3.0, sigma, "fp32")
 
@@ -261,7 +290,7 @@ def large_257(nsteps: int = 3000, n_src: int = 6) -> Workload:
 
 def small_problem(n=9, fem=(2, 6), nsteps=60, bc=ALL_ABC, src_face=FACE_ZP, omega=12.0,
                   sigma_seed=0, sigma_scale=1.0, a_max=4.0, courant=0.5, cubic=True,
-                  name="small") -> Workload:
+                  name="small", refine_frac=0.0, refine_seed=5) -> Workload:
     """Tiny problem for unit and parity tests: n^3 (or n = (nx, ny, nz))
     lattice with spacing 1 / (n - 1) on [-1/2, 1/2]^3-ish, FEM block nodes
     fem[0]..fem[1] on every axis, random sigma in [0, sigma_scale) on the
@@ -279,9 +308,16 @@ def small_problem(n=9, fem=(2, 6), nsteps=60, bc=ALL_ABC, src_face=FACE_ZP, omeg
         ud = unknown_dims(lo, hi)
         rng = np.random.Generator(np.random.PCG64(sigma_seed))
         sigma = sigma_scale * rng.random(ud[0] * ud[1] * ud[2])
-    dt = courant * h / math.sqrt(3.0 * a_max)
+    refine = None
+    if refine_frac > 0 and sigma.size:
+        rng = np.random.Generator(np.random.PCG64(refine_seed))
+        refine = rng.random(sigma.size) < refine_frac
+        dt = courant * 2.0 * h / math.sqrt(32.0 * a_max)
+    else:
+        dt = courant * h / math.sqrt(3.0 * a_max)
     srcs = [] if src_face is None else [Source(src_face, omega)]
-    return Workload(name, n, h, origin, lo, hi, tuple(bc), srcs, nsteps, dt, a_max, sigma, "fp64")
+    return Workload(name, n, h, origin, lo, hi, tuple(bc), srcs, nsteps, dt, a_max, sigma, "fp64",
+                    refine=refine)
 
 
 def random_cotangent(n_src, nsteps, n_obs, seed=7) -> np.ndarray:
