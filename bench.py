@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--nsteps", type=int, default=1500, help="time steps of the workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-steps", type=int, default=30)
+    p.add_argument("--serve-requests", type=int, default=512, help="requests of the serving stream (0: skip)")
+    p.add_argument("--serve-workers", type=int, default=8)
     p.add_argument("--workload", default="inverse_129", choices=["inverse_129", "large_257"])
     p.add_argument("--sources", type=int, default=0, help="with --sweeps-only: use the first K sources")
     p.add_argument("--sweeps-only", type=int, default=0,
@@ -208,6 +210,47 @@ def oracle_sample(w, sample_steps):
     P.adjoint(a, src, sample_steps, w.dt, cot, res["hist"])
     el = time.perf_counter() - t0
     return 2.0 * w.n_nodes * sample_steps / el / 1e9, el
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args, dev):
+    """Serving stream: FP32 forward + adjoint + gradient solves on lattices
+    drawn from {33, 65, 97, 129}^3 (FEM block = central half, 2-4 inclusions,
+    400-1500 steps by size).  Capacity is measured with requests arriving
+    back to back; the stream then arrives as a Poisson process at 80% of it.
+    Beside it, the FP64 path with one request at a time."""
+    import numpy as np
+    import synth
+    from paper_1509_01399_gb300.serve import Request, ServingEngine, latency_stats, poisson_arrivals
+    R = args.serve_requests
+    eng = ServingEngine(workers=args.serve_workers, device=str(dev))
+    sizes = (33, 65, 97, 129)
+    warm = []
+    for N in sizes:  # pools and sweep graphs of every class, outside timing
+        i = next(i for i in range(1000) if synth.serving_request(i).n[0] == N)
+        warm += [Request(-1 - len(warm), synth.serving_request(i), 0.0) for _ in range(3)]
+    eng.run(warm)
+    cap_n = min(R, 128)
+    cap = eng.run([Request(i, synth.serving_request(i), 0.0) for i in range(cap_n)])
+    mu = latency_stats(cap)["solves_per_s"]
+    lam = 0.8 * mu
+    arr = poisson_arrivals(R, lam, seed=3)
+    res = eng.run([Request(i, synth.serving_request(i), float(arr[i])) for i in range(R)])
+    st = latency_stats(res)
+    eng.close()
+    # FP64 path, one request at a time, on a sample of the same stream
+    n64 = min(R, 16)
+    e64 = ServingEngine(workers=1, precision="fp64", device=str(dev))
+    e64.run([Request(-1, synth.serving_request(i), 0.0) for i in range(2)])
+    r64 = e64.run([Request(i, synth.serving_request(i), 0.0) for i in range(n64)])
+    e64.close()
+    lat64 = np.array([r.finish - r.start for r in r64])
+    return {"requests": R, "workers": args.serve_workers, "capacity_solves_per_s": mu, "rate_per_s": lam,
+            "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_ms": st["mean_ms"], "dtype": "f32",
+            "fp64_one_at_a_time": {"sample": n64, "solves_per_s": float(n64 / lat64.sum()),
+                                   "p50_ms": float(np.percentile(lat64, 50) * 1e3),
+                                   "p99_ms": float(np.percentile(lat64, 99) * 1e3)}}
 
 
 # ---------------------------------------------------------------- reference
@@ -371,12 +414,16 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "cg": {"J_first": reps[0].J, "J_last": reps[-1].J, "gnorm_last": reps[-1].gnorm}}
+    m.close()
+    del obs, obs_dev, a_dev, trace, cot
+    torch.cuda.empty_cache()
+    if args.serve_requests > 0:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, el = oracle_sample(w, args.cpu_sample_steps)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "%d forward + %d adjoint steps of the 129^3 workload (%.1f s)"
                                           % (args.cpu_sample_steps, args.cpu_sample_steps, el)}
-    m.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

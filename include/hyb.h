@@ -76,7 +76,15 @@ typedef struct {
                           fields every C steps and the adjoint recomputes each
                           segment */
   double a_max;        /* upper admissible bound of a (Eq. (admpar)); sets
-                          dt_max = h / sqrt(3 a_max) (Eq. (CFL)) */
+                          dt_max = h / sqrt(3 a_max) (Eq. (CFL)) on unrefined
+                          meshes */
+  const uint8_t* refine_mask; /* HOST, one byte per unknown voxel (NULL: none):
+                          non-zero marks a voxel refined once by bisection (the
+                          local refinement of K_h, Sec. 7.1): its six Kuhn
+                          tetrahedra are bisected along their refinement edge,
+                          the voxel diagonal, at a new centre node.  Marked
+                          voxels need every corner at least 2 nodes from the
+                          outer faces. */
 } hyb_mesh_desc;
 
 typedef struct {
@@ -85,10 +93,14 @@ typedef struct {
   int64_t n_fem_owned;     /* FEM-owned nodes */
   int32_t unknown_dims[3];
   int32_t obs_stride;      /* padded length of one trace row */
-  double dt_max;           /* CFL bound for a <= a_max */
+  double dt_max;           /* stability bound for a <= a_max: h / sqrt(3 a_max)
+                              (Eq. (CFL)), lowered by a row-sum bound of the
+                              refined rows when voxels are refined */
   double voxel_volume;     /* h^3 */
   int64_t device_bytes;    /* device memory currently held by the mesh */
   int64_t launches;        /* kernels launched by this mesh so far */
+  int64_t n_centres;       /* centre nodes of refined voxels */
+  int64_t n_sparse_rows;   /* rows updated in sparse form (refined region) */
 } hyb_mesh_info;
 
 /* Plane-wave source of Eq. (f): a Neumann flux d_n u = amp sin(omega t) on
@@ -196,7 +208,9 @@ hyb_status hyb_cg_step(hyb_mesh* mesh, double* a, const void* u_obs, const hyb_s
 
 /* Copy a field of source `isrc` (HYB_FIELD_*: u^N or u^{N-1} of the last
    forward, lambda^1 of the last adjoint) into `out` (device field[n_nodes],
-   x fastest). */
+   x fastest; lattice nodes only).  The adjoint is kept in the mass-scaled
+   form lambda_i h^3 / M^L_i on FEM-owned rows, which equals lambda except at
+   corners of refined voxels. */
 hyb_status hyb_get_field(hyb_mesh* mesh, int32_t which, int32_t isrc, void* out);
 
 /* Allocation-free data misfit.  The paper has no counterpart: this exists

@@ -9,6 +9,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "hyb_internal.h"
 
@@ -88,6 +90,11 @@ struct hyb_mesh {
   hyb_source src[kMaxSlots];
   long long launches = 0;
   long long bytes = 0;
+  // refined region
+  int nc = 0, nr = 0, nrl = 0, nnz = 0;
+  double dt_max = 0.0;
+  DevBuf rrow, rptr, rcol, rval, cptr, cunk, cw, rmask, refvox, refvox_id, k9;
+  DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
   cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
   cudaStream_t aux = nullptr;  // runs the boundary-shell kernel of each step
   cudaEvent_t ev_bulk = nullptr, ev_shell = nullptr;
@@ -159,7 +166,7 @@ SweepKey make_key(const hyb_mesh* m, int kind, const void* io, int accumulate, i
     k.omega[i] = src[i].omega;
     k.amp[i] = src[i].amp;
   }
-  const void* b[8] = {m->U.p, m->L.p, m->hist.p, m->ckpt.p, m->G.p, m->W.p, nullptr, nullptr};
+  const void* b[8] = {m->U.p, m->L.p, m->hist.p, m->ckpt.p, m->G.p, m->W.p, m->CU.p, m->CL.p};
   for (int i = 0; i < 8; ++i) k.bufs[i] = b[i];
   return k;
 }
@@ -250,7 +257,7 @@ void step_geometry(const hyb_mesh* m, int nslots, int* npb, int* ntx, int* zchun
   *ntx = (int)((bx + kTileX - 1) / kTileX);
   const int nty = (int)((by + kTileY - 1) / kTileY);
   *npb = *ntx * nty;
-  const long long target = 152LL * 8;  // resident blocks wanted on 152 SMs
+  const long long target = 152LL * 16;  // blocks wanted: 16 per SM on 152 SMs
   const long long per_z = (long long)(*npb) * nslots;
   long long want = (target + per_z - 1) / per_z;
   if (want < 1) want = 1;
@@ -273,7 +280,7 @@ hyb_status begin_steps(hyb_mesh* m, cudaStream_t st) {
 }
 
 template <class Bulk, class Shell>
-hyb_status step_pair(hyb_mesh* m, cudaStream_t st, Bulk bulk, Shell shell) {
+hyb_status step_pair(hyb_mesh* m, cudaStream_t st, Bulk bulk, Shell shell, int shell_kernels = 1) {
   HYB_CU(cudaStreamWaitEvent(m->aux, m->ev_bulk, 0));
   HYB_CU(cudaStreamWaitEvent(st, m->ev_shell, 0));
   bulk(st);
@@ -281,12 +288,219 @@ hyb_status step_pair(hyb_mesh* m, cudaStream_t st, Bulk bulk, Shell shell) {
   HYB_CU(cudaEventRecord(m->ev_bulk, st));
   shell(m->aux);
   HYB_LAUNCHED(m);
+  m->launches += shell_kernels - 1;
   HYB_CU(cudaEventRecord(m->ev_shell, m->aux));
   return HYB_OK;
 }
 
 hyb_status join_steps(hyb_mesh* m, cudaStream_t st) {
   HYB_CU(cudaStreamWaitEvent(st, m->ev_shell, 0));
+  return HYB_OK;
+}
+
+// P1 element of a tetrahedron (vertex coordinates X[4][3]): volume and
+// stiffness K_ij = |K| grad phi_i . grad phi_j (Sec. 7.2), a = 1.
+void p1_tet(const double X[4][3], double* vol, double K[4][4]) {
+  double J[3][3];
+  for (int c = 0; c < 3; ++c)
+    for (int r = 0; r < 3; ++r) J[r][c] = X[c + 1][r] - X[0][r];
+  const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  double inv[3][3];  // inverse of J: row i = grad of the barycentric function of vertex i + 1
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  double g[4][3];
+  for (int d = 0; d < 3; ++d) {
+    g[1][d] = inv[0][d];
+    g[2][d] = inv[1][d];
+    g[3][d] = inv[2][d];
+    g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+  }
+  *vol = std::fabs(det) / 6.0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) K[i][j] = *vol * (g[i][0] * g[j][0] + g[i][1] * g[j][1] + g[i][2] * g[j][2]);
+}
+
+// Stiffness (a = 1) and lumped masses of the unit voxel cut into its six
+// Kuhn tetrahedra (8 corners, id a + 2b + 4c) and of the voxel refined once
+// (each tetrahedron bisected along the diagonal at the centre, id 8).
+void unit_voxel_matrices(double K8[64], double m8[8], double K9[81], double m9[9]) {
+  for (int i = 0; i < 64; ++i) K8[i] = 0.0;
+  for (int i = 0; i < 81; ++i) K9[i] = 0.0;
+  for (int i = 0; i < 8; ++i) m8[i] = 0.0;
+  for (int i = 0; i < 9; ++i) m9[i] = 0.0;
+  double P[9][3];
+  for (int c = 0; c < 8; ++c) {
+    P[c][0] = c & 1;
+    P[c][1] = (c >> 1) & 1;
+    P[c][2] = c >> 2;
+  }
+  P[8][0] = P[8][1] = P[8][2] = 0.5;
+  const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (const auto& pm : perms) {
+    int v[4] = {0, 0, 0, 7};
+    v[1] = 1 << pm[0];
+    v[2] = v[1] | (1 << pm[1]);
+    const int tets[3][4] = {{v[0], v[1], v[2], v[3]}, {v[0], v[1], v[2], 8}, {8, v[1], v[2], v[3]}};
+    for (int t = 0; t < 3; ++t) {
+      double X[4][3], vol, K[4][4];
+      for (int q = 0; q < 4; ++q)
+        for (int d = 0; d < 3; ++d) X[q][d] = P[tets[t][q]][d];
+      p1_tet(X, &vol, K);
+      for (int a = 0; a < 4; ++a) {
+        const int ia = tets[t][a];
+        if (t == 0) m8[ia] += vol / 4.0;
+        else m9[ia] += vol / 4.0;
+        for (int b = 0; b < 4; ++b) {
+          if (t == 0) K8[ia * 8 + tets[t][b]] += K[a][b];
+          else K9[ia * 9 + tets[t][b]] += K[a][b];
+        }
+      }
+    }
+  }
+}
+
+template <typename V>
+hyb_status upload(hyb_mesh* m, DevBuf& b, const std::vector<V>& host) {
+  HYB_TRY(ensure(m, b, host.size() * sizeof(V)));
+  if (!host.empty()) HYB_CU(cudaMemcpy(b.p, host.data(), host.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return HYB_OK;
+}
+
+// Sparse rows of the refined region: the lattice nodes touching a refined
+// voxel (their rows see the twelve children of each refined voxel around
+// them) and the centre nodes.  Each entry keeps its per-voxel contributions
+// W = -K_loc / M_i (unit voxel), so the values follow the coefficient.
+hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
+  const long long nu = m->nu;
+  std::vector<int> cid(nu, -1);
+  std::vector<unsigned char> refv(nu, 0);
+  std::vector<int> refid;
+  for (long long u = 0; u < nu; ++u) {
+    if (!mask[u]) continue;
+    const int x = (int)(u % m->un[0]), y = (int)((u / m->un[0]) % m->un[1]), z = (int)(u / ((long long)m->un[0] * m->un[1]));
+    const int o[3] = {m->fl[0] + x, m->fl[1] + y, m->fl[2] + z};
+    for (int d = 0; d < 3; ++d)
+      if (o[d] < 2 || o[d] + 1 > m->n[d] - 3)
+        return fail(HYB_ERR_ARG, "refined voxel %lld: its corners must be at least 2 nodes from the faces", u);
+    cid[u] = (int)refid.size();
+    refv[u] = 1;
+    refid.push_back((int)u);
+  }
+  m->nc = (int)refid.size();
+  if (m->nc == 0) return HYB_OK;
+  double K8[64], m8[8], K9[81], m9[9];
+  unit_voxel_matrices(K8, m8, K9, m9);
+  const long long N = m->N;
+  auto lid = [&](int i, int j, int k) { return (long long)i + (long long)m->n[0] * (j + (long long)m->n[1] * k); };
+  auto unk_of = [&](int i, int j, int k) -> long long {  // voxel with origin (i,j,k)
+    const int x = i - m->fl[0], y = j - m->fl[1], z = k - m->fl[2];
+    if (x < 0 || y < 0 || z < 0 || x >= m->un[0] || y >= m->un[1] || z >= m->un[2]) return -1;
+    return x + (long long)m->un[0] * (y + (long long)m->un[1] * z);
+  };
+  // lattice rows: corners of refined voxels, in lattice order
+  std::vector<long long> rows;
+  std::vector<unsigned char> rmask((size_t)m->nown, 0);
+  for (int u : refid) {
+    const int x = u % m->un[0], y = (u / m->un[0]) % m->un[1], z = u / (m->un[0] * m->un[1]);
+    for (int c = 0; c < 8; ++c) {
+      const int i = m->fl[0] + x + (c & 1), j = m->fl[1] + y + ((c >> 1) & 1), k = m->fl[2] + z + (c >> 2);
+      const long long b = (long long)(i - m->fl[0]) + (long long)m->fn[0] * ((j - m->fl[1]) + (long long)m->fn[1] * (k - m->fl[2]));
+      if (!rmask[b]) {
+        rmask[b] = 1;
+        rows.push_back(lid(i, j, k));
+      }
+    }
+  }
+  std::sort(rows.begin(), rows.end());
+  m->nrl = (int)rows.size();
+  m->nr = m->nrl + m->nc;
+  std::vector<int> rptr(1, 0), rcol, cptr(1, 0), cunk;
+  std::vector<double> cw;
+  double bound = 0.0;  // largest row-sum (Gershgorin) bound of M^{-1} K at a = 1, unit spacing
+  auto emit_row = [&](std::vector<std::pair<long long, std::pair<int, double>>>& ent, double M) {
+    std::sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    double absum = 0.0, sum = 0.0;
+    size_t q = 0;
+    while (q < ent.size()) {
+      const long long col = ent[q].first;
+      double wsum = 0.0;
+      while (q < ent.size() && ent[q].first == col) {
+        cunk.push_back(ent[q].second.first);
+        cw.push_back(-ent[q].second.second / M);
+        wsum += -ent[q].second.second / M;
+        ++q;
+      }
+      rcol.push_back((int)col);
+      cptr.push_back((int)cunk.size());
+      absum += std::fabs(wsum);
+      sum += wsum;
+    }
+    rptr.push_back((int)rcol.size());
+    bound = std::max(bound, std::fabs(sum) + absum);
+  };
+  for (long long p : rows) {
+    const int i = (int)(p % m->n[0]), j = (int)((p / m->n[0]) % m->n[1]), k = (int)(p / ((long long)m->n[0] * m->n[1]));
+    std::vector<std::pair<long long, std::pair<int, double>>> ent;
+    double M = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+      const int oi = i - a, oj = j - b, ok = k - d;  // voxel origin; this node is its corner c
+      const long long u = unk_of(oi, oj, ok);
+      const bool ref = u >= 0 && refv[u];
+      if (ref) {
+        M += m9[c];
+        for (int q = 0; q < 9; ++q) {
+          if (q == c || std::fabs(K9[c * 9 + q]) < 1e-14) continue;
+          const long long col = q < 8 ? lid(oi + (q & 1), oj + ((q >> 1) & 1), ok + (q >> 2)) : N + cid[u];
+          ent.push_back({col, {(int)u, K9[c * 9 + q]}});
+        }
+      } else {
+        M += m8[c];
+        for (int q = 0; q < 8; ++q) {
+          if (q == c || std::fabs(K8[c * 8 + q]) < 1e-14) continue;
+          ent.push_back({lid(oi + (q & 1), oj + ((q >> 1) & 1), ok + (q >> 2)), {(int)u, K8[c * 8 + q]}});
+        }
+      }
+    }
+    emit_row(ent, M);
+  }
+  for (int u : refid) {  // centre rows
+    const int x = u % m->un[0], y = (u / m->un[0]) % m->un[1], z = u / (m->un[0] * m->un[1]);
+    const int oi = m->fl[0] + x, oj = m->fl[1] + y, ok = m->fl[2] + z;
+    std::vector<std::pair<long long, std::pair<int, double>>> ent;
+    for (int q = 0; q < 8; ++q) {
+      if (std::fabs(K9[8 * 9 + q]) < 1e-14) continue;
+      ent.push_back({lid(oi + (q & 1), oj + ((q >> 1) & 1), ok + (q >> 2)), {u, K9[8 * 9 + q]}});
+    }
+    emit_row(ent, m9[8]);
+  }
+  m->nnz = (int)rcol.size();
+  // stability: the refined rows' bound at a = a_max, against h / sqrt(3 a_max)
+  const double h = m->d.h;
+  const double lam = std::max(12.0, bound) * m->d.a_max / (h * h);
+  m->dt_max = std::min(m->dt_max, 2.0 / std::sqrt(lam));
+  std::vector<int> rrow(rows.begin(), rows.end());
+  std::vector<double> k9(K9, K9 + 81);
+  HYB_TRY(upload(m, m->rrow, rrow));
+  HYB_TRY(upload(m, m->rptr, rptr));
+  HYB_TRY(upload(m, m->rcol, rcol));
+  HYB_TRY(upload(m, m->cptr, cptr));
+  HYB_TRY(upload(m, m->cunk, cunk));
+  HYB_TRY(upload(m, m->cw, cw));
+  HYB_TRY(upload(m, m->rmask, rmask));
+  HYB_TRY(upload(m, m->refvox, refv));
+  HYB_TRY(upload(m, m->refvox_id, refid));
+  HYB_TRY(upload(m, m->k9, k9));
+  HYB_TRY(ensure(m, m->rval, (size_t)m->nnz * esize(m)));
   return HYB_OK;
 }
 
@@ -312,6 +526,27 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.r = (T)((h - dt) / (h + dt));
   step_geometry(m, nslots, &A.npb, &A.ntx, &A.zchunk, &A.nzc, &A.small, &A.nedge);
   A.nslots = nslots;
+  A.nlat = m->N;
+  if (m->nc > 0) {
+    A.nr = m->nr;
+    A.nrl = m->nrl;
+    A.nref = m->nc;
+    A.rrow = (const int*)m->rrow.p;
+    A.rptr = (const int*)m->rptr.p;
+    A.rcol = (const int*)m->rcol.p;
+    A.rval = (const T*)m->rval.p;
+    A.rmask = (const unsigned char*)m->rmask.p;
+    A.refvox = (const unsigned char*)m->refvox.p;
+    A.refvox_id = (const int*)m->refvox_id.p;
+    A.k9 = (const double*)m->k9.p;
+  }
+}
+
+template <typename T>
+T* centre_buf(const hyb_mesh* m, const DevBuf& b, int nsrc, int s, int level) {
+  if (m->nc == 0) return nullptr;
+  const int r = ((level % 3) + 3) % 3;
+  return (T*)b.p + ((size_t)r * nsrc + s) * (size_t)m->nc;
 }
 
 template <typename T>
@@ -323,7 +558,7 @@ T* field_buf(const hyb_mesh* m, const DevBuf& b, int nsrc, int s, int level) {
 // Fill the forward slots of step k (u^k -> u^{k+1}).
 template <typename T>
 void forward_slots(const hyb_mesh* m, StepArgs<T>& A, const hyb_source* src, int nsrc, int nsteps,
-                   double dt, int k, T* trace, T* hist_level) {
+                   double dt, int k, T* trace, T* hist_level, T* chist_level) {
   for (int s = 0; s < nsrc; ++s) {
     Slot<T>& S = A.s[s];
     S.cur = field_buf<T>(m, m->U, nsrc, s, k);
@@ -333,6 +568,11 @@ void forward_slots(const hyb_mesh* m, StepArgs<T>& A, const hyb_source* src, int
     S.obs_r = nullptr;
     S.hist_w = hist_level ? hist_level + (size_t)s * m->nown : nullptr;
     S.hist_r = nullptr;
+    S.ccur = centre_buf<T>(m, m->CU, nsrc, s, k);
+    S.cprev = centre_buf<T>(m, m->CU, nsrc, s, k - 1);
+    S.cnext = centre_buf<T>(m, m->CU, nsrc, s, k + 1);
+    S.chist_w = (hist_level && m->nc) ? chist_level + (size_t)s * m->nc : nullptr;
+    S.chist_r = nullptr;
     int mask, f;
     double p;
     phase_of(m, src[s], k, dt, &mask, &f, &p);
@@ -351,14 +591,19 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
   const size_t fb = (size_t)m->N * sizeof(T);
   const int C = m->d.ckpt_every;
   const bool ckpt = C > 0;
+  const size_t cb = (size_t)m->nc * sizeof(T);  // centre values of one level
   HYB_TRY(ensure(m, m->U, 3 * (size_t)nsrc * fb));
+  HYB_TRY(ensure(m, m->CU, 3 * (size_t)nsrc * cb));
   if (keep && m->nown > 0) {
     if (!ckpt) {
       HYB_TRY(ensure(m, m->hist, (size_t)nsteps * nsrc * m->nown * sizeof(T)));
+      HYB_TRY(ensure(m, m->chist, (size_t)nsteps * nsrc * cb));
     } else {
       const size_t nseg = ((size_t)nsteps + C - 1) / C;
       HYB_TRY(ensure(m, m->ckpt, nseg * 2 * (size_t)nsrc * fb));
+      HYB_TRY(ensure(m, m->cckpt, nseg * 2 * (size_t)nsrc * cb));
       HYB_TRY(ensure(m, m->hist, (size_t)C * nsrc * m->nown * sizeof(T)));
+      HYB_TRY(ensure(m, m->chist, (size_t)C * nsrc * cb));
     }
   }
   StepArgs<T> A;
@@ -367,15 +612,30 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
     launch_set_coef<T>(A, (T*)m->W.p, a, m->d.a_max, (int*)m->flag.p, m->st);
     HYB_LAUNCHED(m);
   }
+  if (m->nc > 0) {
+    launch_set_sparse<T>((const int*)m->cptr.p, (const int*)m->cunk.p, (const double*)m->cw.p, a, (T*)m->rval.p,
+                         m->nnz, m->st);
+    HYB_LAUNCHED(m);
+  }
+  const int nshell = 1;  // edge kernel per level (its trailing blocks run the refined rows)
   auto body = [&](cudaStream_t st) -> hyb_status {
     for (int s = 0; s < nsrc; ++s) {
       HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, 0), 0, fb, st));
       HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, -1), 0, fb, st));
+      if (m->nc) {
+        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CU, nsrc, s, 0), 0, cb, st));
+        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CU, nsrc, s, -1), 0, cb, st));
+      }
     }
     if (trace) HYB_CU(cudaMemsetAsync(trace, 0, (size_t)nsrc * (nsteps + 1) * m->obs_stride * sizeof(T), st));
     T* hist = (T*)m->hist.p;
-    if (keep && !ckpt && m->nown > 0) HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->nown * sizeof(T), st));
+    T* chist = (T*)m->chist.p;
+    if (keep && !ckpt && m->nown > 0) {
+      HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->nown * sizeof(T), st));
+      if (m->nc) HYB_CU(cudaMemsetAsync(chist, 0, (size_t)nsrc * cb, st));
+    }
     const size_t lvl = (size_t)nsrc * m->nown;
+    const size_t clvl = (size_t)nsrc * m->nc;
     HYB_TRY(begin_steps(m, st));
     for (int k = 0; k < nsteps; ++k) {
       if (keep && ckpt && m->nown > 0 && k > 0 && k % C == 0) {
@@ -386,13 +646,21 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
           HYB_CU(cudaMemcpyAsync(base, field_buf<T>(m, m->U, nsrc, s, k), fb, cudaMemcpyDeviceToDevice, st));
           HYB_CU(cudaMemcpyAsync(base + fb, field_buf<T>(m, m->U, nsrc, s, k - 1), fb, cudaMemcpyDeviceToDevice,
                                  st));
+          if (m->nc) {
+            char* cbase = (char*)m->cckpt.p + ((seg * nsrc + s) * 2) * cb;
+            HYB_CU(cudaMemcpyAsync(cbase, centre_buf<T>(m, m->CU, nsrc, s, k), cb, cudaMemcpyDeviceToDevice, st));
+            HYB_CU(cudaMemcpyAsync(cbase + cb, centre_buf<T>(m, m->CU, nsrc, s, k - 1), cb,
+                                   cudaMemcpyDeviceToDevice, st));
+          }
         }
         HYB_TRY(begin_steps(m, st));
       }
-      T* hl = (keep && !ckpt && m->nown > 0 && k + 1 <= nsteps - 1) ? hist + (size_t)(k + 1) * lvl : nullptr;
-      forward_slots<T>(m, A, src, nsrc, nsteps, dt, k, trace, hl);
+      const bool hk = keep && !ckpt && m->nown > 0 && k + 1 <= nsteps - 1;
+      T* hl = hk ? hist + (size_t)(k + 1) * lvl : nullptr;
+      T* chl = hk ? chist + (size_t)(k + 1) * clvl : nullptr;
+      forward_slots<T>(m, A, src, nsrc, nsteps, dt, k, trace, hl, chl);
       HYB_TRY(step_pair(m, st, [&](cudaStream_t q) { launch_forward_bulk<T>(A, q); },
-                        [&](cudaStream_t q) { launch_forward_shell<T>(A, q); }));
+                        [&](cudaStream_t q) { launch_forward_shell<T>(A, q); }, nshell));
     }
     HYB_TRY(join_steps(m, st));
     return HYB_OK;
@@ -409,7 +677,8 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
 }
 
 template <typename T>
-void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const T* hist_level) {
+void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const T* hist_level,
+                   const T* chist_level) {
   const int nsrc = m->nsrc, nsteps = m->nsteps;
   for (int s = 0; s < nsrc; ++s) {
     Slot<T>& S = A.s[s];
@@ -417,9 +686,14 @@ void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const
     S.prev = field_buf<T>(m, m->L, nsrc, s, j + 2);
     S.next = field_buf<T>(m, m->L, nsrc, s, j);
     S.obs_w = nullptr;
-    S.obs_r = cot + ((size_t)s * (nsteps + 1) + j) * (size_t)m->obs_stride;
+    S.obs_r = cot ? cot + ((size_t)s * (nsteps + 1) + j) * (size_t)m->obs_stride : nullptr;
     S.hist_w = nullptr;
     S.hist_r = hist_level ? hist_level + (size_t)s * m->nown : nullptr;
+    S.ccur = centre_buf<T>(m, m->CL, nsrc, s, j + 1);
+    S.cprev = centre_buf<T>(m, m->CL, nsrc, s, j + 2);
+    S.cnext = centre_buf<T>(m, m->CL, nsrc, s, j);
+    S.chist_w = nullptr;
+    S.chist_r = (hist_level && m->nc) ? chist_level + (size_t)s * m->nc : nullptr;
     S.srcval = T(0);
     S.src_face = -1;
     S.mask_f = mask_at(m, m->src[s], j, m->dt);
@@ -429,12 +703,18 @@ void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const
   }
 }
 
+// Gradient pairing of level 0: (u^0, lambda^1) on every unknown voxel.
 template <typename T>
-hyb_status pair_first(hyb_mesh* m, StepArgs<T>& A, const T* level0, cudaStream_t st) {
+hyb_status pair_first(hyb_mesh* m, StepArgs<T>& A, const T* level0, const T* clevel0, cudaStream_t st) {
   for (int s = 0; s < m->nsrc; ++s) {
     StepArgs<T> B = A;
     B.G = (double*)m->G.p + (size_t)s * m->nu;
     launch_pair<T>(B, level0 + (size_t)s * m->nown, field_buf<T>(m, m->L, m->nsrc, s, 1), st);
+    HYB_LAUNCHED(m);
+  }
+  if (m->nc > 0) {
+    adjoint_slots<T>(m, A, nullptr, 0, level0, clevel0);  // cur = lambda^1, hist = u^0
+    launch_refined_pair<T>(A, st);
     HYB_LAUNCHED(m);
   }
   return HYB_OK;
@@ -448,8 +728,11 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   const size_t fb = (size_t)m->N * sizeof(T);
   const int C = m->d.ckpt_every;
   const bool ckpt = C > 0;
+  const size_t cb = (size_t)m->nc * sizeof(T);
   HYB_TRY(ensure(m, m->L, 3 * (size_t)nsrc * fb));
+  HYB_TRY(ensure(m, m->CL, 3 * (size_t)nsrc * cb));
   HYB_TRY(ensure(m, m->G, (size_t)nsrc * m->nu * sizeof(double)));
+  const int nshell = 1;
   StepArgs<T> A;   // adjoint steps
   base_args(m, A, dt, nsrc);
   StepArgs<T> F;   // recomputed forward steps
@@ -459,31 +742,37 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
     for (int s = 0; s < nsrc; ++s) {
       HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, nsteps + 1), 0, fb, st));
       HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, nsteps + 2), 0, fb, st));
+      if (m->nc) {
+        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CL, nsrc, s, nsteps + 1), 0, cb, st));
+        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CL, nsrc, s, nsteps + 2), 0, cb, st));
+      }
     }
     T* hist = (T*)m->hist.p;
+    T* chist = (T*)m->chist.p;
     const size_t lvl = (size_t)nsrc * m->nown;
+    const size_t clvl = (size_t)nsrc * m->nc;
     const bool pairing = m->nu > 0 && m->nown > 0;
-    auto adj_step = [&](int j, const T* hl) -> hyb_status {
-      adjoint_slots<T>(m, A, cot, j, hl);
+    auto adj_step = [&](int j, const T* hl, const T* chl) -> hyb_status {
+      adjoint_slots<T>(m, A, cot, j, hl, chl);
       return step_pair(m, st, [&](cudaStream_t q) { launch_adjoint_bulk<T>(A, q); },
-                       [&](cudaStream_t q) { launch_adjoint_shell<T>(A, q); });
+                       [&](cudaStream_t q) { launch_adjoint_shell<T>(A, q); }, nshell);
     };
-    auto fwd_step = [&](int k, T* hl) -> hyb_status {
-      forward_slots<T>(m, F, m->src, nsrc, nsteps, dt, k, nullptr, hl);
+    auto fwd_step = [&](int k, T* hl, T* chl) -> hyb_status {
+      forward_slots<T>(m, F, m->src, nsrc, nsteps, dt, k, nullptr, hl, chl);
       return step_pair(m, st, [&](cudaStream_t q) { launch_forward_bulk<T>(F, q); },
-                       [&](cudaStream_t q) { launch_forward_shell<T>(F, q); });
+                       [&](cudaStream_t q) { launch_forward_shell<T>(F, q); }, nshell);
     };
     HYB_TRY(begin_steps(m, st));
     if (!ckpt) {
       for (int j = nsteps; j >= 1; --j) {
-        const T* hl = (pairing && j <= nsteps - 1) ? hist + (size_t)j * lvl : nullptr;
-        HYB_TRY(adj_step(j, hl));
+        const bool pj = pairing && j <= nsteps - 1;
+        HYB_TRY(adj_step(j, pj ? hist + (size_t)j * lvl : nullptr, pj ? chist + (size_t)j * clvl : nullptr));
       }
       HYB_TRY(join_steps(m, st));
-      if (pairing) HYB_TRY(pair_first<T>(m, A, hist, st));
+      if (pairing) HYB_TRY(pair_first<T>(m, A, hist, chist, st));
       return HYB_OK;
     }
-    HYB_TRY(adj_step(nsteps, nullptr));
+    HYB_TRY(adj_step(nsteps, nullptr, nullptr));
     const int nseg = (nsteps + C - 1) / C;
     for (int seg = nseg - 1; seg >= 0; --seg) {
       const int kb = seg * C;
@@ -493,25 +782,39 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
         for (int s = 0; s < nsrc; ++s) {
           T* u0 = field_buf<T>(m, m->U, nsrc, s, kb);
           T* um = field_buf<T>(m, m->U, nsrc, s, kb - 1);
+          T* c0 = centre_buf<T>(m, m->CU, nsrc, s, kb);
+          T* cm = centre_buf<T>(m, m->CU, nsrc, s, kb - 1);
           if (seg == 0) {
             HYB_CU(cudaMemsetAsync(u0, 0, fb, st));
             HYB_CU(cudaMemsetAsync(um, 0, fb, st));
+            if (m->nc) {
+              HYB_CU(cudaMemsetAsync(c0, 0, cb, st));
+              HYB_CU(cudaMemsetAsync(cm, 0, cb, st));
+            }
           } else {
             const char* base = (const char*)m->ckpt.p + (((size_t)seg * nsrc + s) * 2) * fb;
             HYB_CU(cudaMemcpyAsync(u0, base, fb, cudaMemcpyDeviceToDevice, st));
             HYB_CU(cudaMemcpyAsync(um, base + fb, fb, cudaMemcpyDeviceToDevice, st));
+            if (m->nc) {
+              const char* cbase = (const char*)m->cckpt.p + (((size_t)seg * nsrc + s) * 2) * cb;
+              HYB_CU(cudaMemcpyAsync(c0, cbase, cb, cudaMemcpyDeviceToDevice, st));
+              HYB_CU(cudaMemcpyAsync(cm, cbase + cb, cb, cudaMemcpyDeviceToDevice, st));
+            }
           }
           launch_extract_owned<T>(F, u0, hist + (size_t)s * m->nown, st);
           HYB_LAUNCHED(m);
+          if (m->nc) HYB_CU(cudaMemcpyAsync(chist + (size_t)s * m->nc, c0, cb, cudaMemcpyDeviceToDevice, st));
         }
         HYB_TRY(begin_steps(m, st));
-        for (int k = kb; k < ke; ++k) HYB_TRY(fwd_step(k, hist + (size_t)(k + 1 - kb) * lvl));
+        for (int k = kb; k < ke; ++k)
+          HYB_TRY(fwd_step(k, hist + (size_t)(k + 1 - kb) * lvl, chist + (size_t)(k + 1 - kb) * clvl));
       }
       for (int j = ke; j >= std::max(kb, 1); --j)
-        HYB_TRY(adj_step(j, pairing ? hist + (size_t)(j - kb) * lvl : nullptr));
+        HYB_TRY(adj_step(j, pairing ? hist + (size_t)(j - kb) * lvl : nullptr,
+                         pairing ? chist + (size_t)(j - kb) * clvl : nullptr));
     }
     HYB_TRY(join_steps(m, st));
-    if (pairing) HYB_TRY(pair_first<T>(m, A, hist, st));
+    if (pairing) HYB_TRY(pair_first<T>(m, A, hist, chist, st));
     return HYB_OK;
   };
   HYB_TRY(run_sweep(m, m->graphs[2], make_key(m, 2, cot, accumulate, nsteps, nsrc, dt, m->src), body));
@@ -665,9 +968,9 @@ hyb_status check_sources(const hyb_mesh* m, const hyb_source* src, int nsrc) {
 hyb_status check_time(const hyb_mesh* m, int nsteps, double dt) {
   if (nsteps < 1) return fail(HYB_ERR_ARG, "nsteps must be >= 1");
   if (!(dt > 0.0)) return fail(HYB_ERR_ARG, "dt must be > 0");
-  const double dt_max = m->d.h / std::sqrt(3.0 * m->d.a_max);
+  const double dt_max = m->dt_max;
   if (dt > dt_max * (1.0 + 1e-12))
-    return fail(HYB_ERR_CFL, "dt = %.17g exceeds the CFL bound h / sqrt(3 a_max) = %.17g", dt, dt_max);
+    return fail(HYB_ERR_CFL, "dt = %.17g exceeds the stability bound dt_max = %.17g", dt, dt_max);
   return HYB_OK;
 }
 
@@ -726,6 +1029,7 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   m->obs_stride = std::max(d->n[0] * d->n[1], std::max(d->n[0] * d->n[2], d->n[1] * d->n[2]));
   for (int f = 0; f < 6; ++f)
     if (d->bc[f] == HYB_BC_ABC) m->abc_mask |= 1 << f;
+  m->dt_max = d->h / std::sqrt(3.0 * d->a_max);
   hyb_status st = HYB_OK;
   if (fem) st = ensure(m, m->W, 3 * (size_t)m->wsz * esize(m));
   if (st == HYB_OK) st = ensure(m, m->flag, sizeof(int));
@@ -743,6 +1047,10 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
     cudaGetLastError();
     st = fail(HYB_ERR_CUDA, "stream or event creation failed");
   }
+  if (st == HYB_OK && d->refine_mask && fem && m->nu > 0) {
+    if (d->n[0] < 5 || d->n[1] < 5 || d->n[2] < 5) st = fail(HYB_ERR_ARG, "refinement needs >= 5 nodes per axis");
+    else st = build_refined(m, d->refine_mask);
+  }
   if (st != HYB_OK) {
     hyb_mesh_destroy(m);
     return st;
@@ -758,7 +1066,9 @@ hyb_status hyb_mesh_query(const hyb_mesh* m, hyb_mesh_info* o) {
   o->n_fem_owned = m->nown;
   for (int a = 0; a < 3; ++a) o->unknown_dims[a] = m->un[a];
   o->obs_stride = m->obs_stride;
-  o->dt_max = m->d.h / std::sqrt(3.0 * m->d.a_max);
+  o->dt_max = m->dt_max;
+  o->n_centres = m->nc;
+  o->n_sparse_rows = m->nr;
   o->voxel_volume = m->d.h * m->d.h * m->d.h;
   o->device_bytes = m->bytes;
   o->launches = m->launches;
@@ -770,7 +1080,9 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   cudaStreamSynchronize(m->st);
   if (m->aux) cudaStreamSynchronize(m->aux);
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
-                    &m->g, &m->atrial, &m->cot, &m->trace};
+                    &m->g, &m->atrial, &m->cot, &m->trace, &m->rrow, &m->rptr, &m->rcol, &m->rval,
+                    &m->cptr, &m->cunk, &m->cw, &m->rmask, &m->refvox, &m->refvox_id, &m->k9,
+                    &m->CU, &m->CL, &m->chist, &m->cckpt};
   for (DevBuf* b : bufs) release(*b);
   if (m->hscal) cudaFreeHost(m->hscal);
   for (SweepGraph& g : m->graphs)
@@ -904,11 +1216,13 @@ hyb_status hyb_misfit_noalloc(const void* trace, const void* u_obs, int32_t prec
 
 hyb_status hyb_sync(hyb_mesh* m) {
   if (!m) return fail(HYB_ERR_ARG, "null mesh");
+  // stream-ordered copies only: other streams (other meshes) keep running
+  int* flag = (int*)(m->hscal + 15);
+  HYB_CU(cudaMemcpyAsync(flag, m->flag.p, sizeof(int), cudaMemcpyDeviceToHost, m->st));
   HYB_CU(cudaStreamSynchronize(m->st));
-  int flag = 0;
-  HYB_CU(cudaMemcpy(&flag, m->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
-  if (flag) {
-    HYB_CU(cudaMemset(m->flag.p, 0, sizeof(int)));
+  if (*flag) {
+    HYB_CU(cudaMemsetAsync(m->flag.p, 0, sizeof(int), m->st));
+    HYB_CU(cudaStreamSynchronize(m->st));
     return fail(HYB_ERR_CFL, "a coefficient value exceeded a_max (or was not finite)");
   }
   return HYB_OK;

@@ -32,6 +32,11 @@ struct Slot {
   int mask_c;        // adjoint: absorbing faces of C_{j+1}
   int src_face;      // forward: face carrying the source flux, or -1
   int obs_face;      // face recorded in the trace / receiving the cotangent
+  const T* ccur;     // centre nodes of refined voxels, levels as cur/prev/next
+  const T* cprev;
+  T* cnext;
+  T* chist_w;        // forward: centre values of u^{k+1} for the gradient (or nullptr)
+  const T* chist_r;  // adjoint: centre values of u^j (or nullptr)
 };
 
 template <typename T>
@@ -52,6 +57,18 @@ struct StepArgs {
   int small;         // some axis has < 5 nodes: one generic kernel per level
   int nedge;         // edge kernel: 128-thread tiles per slot
   int nslots;
+  // refined region (nr == 0: nothing refined).  Sparse rows: the nrl
+  // lattice nodes touching a refined voxel, then the nref centre nodes.
+  int nr, nrl, nref;
+  long long nlat;             // lattice nodes (column ids >= nlat are centres)
+  const int* rrow;            // lattice id of each lattice sparse row
+  const int* rptr;            // CSR row pointers [nr + 1]
+  const int* rcol;            // column: lattice id, or nlat + centre index
+  const T* rval;              // weight W_ij of the off-diagonal entries
+  const unsigned char* rmask; // FEM-owned box: 1 = node updated by a sparse row
+  const unsigned char* refvox;// unknown voxels: 1 = refined
+  const int* refvox_id;       // unknown id of each refined voxel (centre order)
+  const double* k9;           // 9 x 9 stiffness of a refined unit voxel, a = 1
   Slot<T> s[kMaxSlots];
 };
 
@@ -75,6 +92,17 @@ void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t
 template <typename T>
 void launch_set_coef(const StepArgs<T>& a, T* W, const double* acoef, double a_max, int* flag,
                      cudaStream_t st);
+// (The sparse rows of the refined region, identical for the forward and the
+// mass-scaled adjoint, and the adjoint's gradient pairing of refined voxels
+// run in trailing blocks of the edge launch of each level.)
+// Gradient pairing of refined voxels for level 0 (u^0 from the history
+// slots `hist`/`chist`, lambda^1 as the slots' cur/ccur).
+template <typename T>
+void launch_refined_pair(const StepArgs<T>& a, cudaStream_t st);
+// rval[e] = sum over the contributions of entry e of a(unk) * w (a = 1 for unk < 0).
+template <typename T>
+void launch_set_sparse(const int* cptr, const int* cunk, const double* cw, const double* acoef, T* rval, int nnz,
+                       cudaStream_t st);
 // Copy the FEM-owned box of a lattice field into a history slot.
 template <typename T>
 void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStream_t st);

@@ -303,6 +303,7 @@ __device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T
   const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
   const long long vid = (long long)(i - A.fl[0]) +
                         (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
+  if (A.refvox && A.refvox[vid]) return;
   A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, S.cur, i, j, k);
 }
 
@@ -517,14 +518,17 @@ __global__ void __launch_bounds__(kTileX * kTileY) bulk_kernel(const __grid_cons
           out[id + db] = lb;
         }
       }
-      oq[0] = val;
-      if (!ADJ && hw && fem)
-        hw[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
-            val;
+      const long long bidx =
+          fem ? (long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))
+              : 0;
+      if (!(fem && A.rmask && A.rmask[bidx])) {  // sparse rows are written by the refined kernel
+        oq[0] = val;
+        if (!ADJ && hw && fem) hw[bidx] = val;
+      }
       if (ADJ && xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
         const long long vid = (long long)(i - A.fl[0]) +
                               (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
-        A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, c, i, j, k);
+        if (!(A.refvox && A.refvox[vid])) A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, c, i, j, k);
       }
     }
     cm = c0;
@@ -542,9 +546,16 @@ __global__ void __launch_bounds__(kTileX * kTileY) bulk_kernel(const __grid_cons
 // on: nodes on no face take their interior row, then face, edge and corner
 // nodes; an absorbing row (Eq. (eq:abs2)) reads the new values of its
 // inward neighbours, one level down in the same tile, from shared memory.
+template <typename T, bool ADJ>
+__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t);
+
 template <typename T>
 __global__ void __launch_bounds__(128) fwd_edge_kernel(const __grid_constant__ StepArgs<T> A) {
   __shared__ T nv[128];
+  if ((long long)blockIdx.x >= (long long)A.nedge * A.nslots) {  // trailing blocks: refined rows
+    refined_rows<T, false>(A, ((long long)blockIdx.x - (long long)A.nedge * A.nslots) * 128 + threadIdx.x);
+    return;
+  }
   const int si = blockIdx.x / A.nedge;
   const int blk = blockIdx.x - si * A.nedge;
   const int t = threadIdx.x;
@@ -596,6 +607,10 @@ __global__ void __launch_bounds__(128) fwd_edge_kernel(const __grid_constant__ S
 template <typename T>
 __global__ void __launch_bounds__(128) adj_edge_kernel(const __grid_constant__ StepArgs<T> A) {
   __shared__ T lam[128];
+  if ((long long)blockIdx.x >= (long long)A.nedge * A.nslots) {  // trailing blocks: refined rows and voxels
+    refined_rows<T, true>(A, ((long long)blockIdx.x - (long long)A.nedge * A.nslots) * 128 + threadIdx.x);
+    return;
+  }
   const int si = blockIdx.x / A.nedge;
   const int blk = blockIdx.x - si * A.nedge;
   const int t = threadIdx.x;
@@ -676,7 +691,117 @@ __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __re
   const long long r = t / A.un[0];
   const int y = (int)(r % A.un[1]);
   const int z = (int)(r / A.un[1]);
+  if (A.refvox && A.refvox[t]) return;
   grad[t] += (double)voxel_pair(A, hist, lam, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z);
+}
+
+// Pairing of a refined voxel: u^T K9 lambda over its 8 corners and centre,
+// K9 the stiffness of the refined unit voxel (a = 1); the host scales the
+// sum like the structured pairing.
+template <typename T>
+__device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* __restrict__ hb,
+                                          const T* __restrict__ chb, const T* __restrict__ lam,
+                                          const T* __restrict__ clam) {
+  const int uid = A.refvox_id[v];
+  const int x = uid % A.un[0], y = (uid / A.un[0]) % A.un[1], z = uid / (A.un[0] * A.un[1]);
+  const int i = A.fl[0] + x, j = A.fl[1] + y, k = A.fl[2] + z;
+  const long long hy = A.fn[0], hz = (long long)A.fn[0] * A.fn[1];
+  const long long h0 = (long long)x + hy * y + hz * z;
+  const long long l0 = lin(A, i, j, k);
+  const long long ly = A.nx, lz = (long long)A.nx * A.ny;
+  T u[9], l[9];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+    u[c] = hb[h0 + a + b * hy + d * hz];
+    l[c] = lam[l0 + a + b * ly + d * lz];
+  }
+  u[8] = chb[v];
+  l[8] = clam[v];
+  T acc = T(0);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    T row = T(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) row += (T)A.k9[p * 9 + q] * l[q];
+    acc += u[p] * row;
+  }
+  return acc;
+}
+
+// Refined region of one time level (run by the trailing blocks of the edge
+// launch).  Threads [0, nr): the sparse rows,
+// u^{k+1}_i = 2 u^k_i - u^{k-1}_i + tau^2/h^2 sum_j W_ij (u^k_j - u^k_i),
+// lattice rows into the field, centre rows into the centre array (the
+// adjoint runs the same rows on the mass-scaled lambda).  Adjoint threads
+// [nr, nr + nref): gradient pairing of the refined voxels.
+template <typename T, bool ADJ>
+__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t) {
+  // per slot: 4 lanes per sparse row, then (adjoint) one thread per refined
+  // voxel, padded to a multiple of 4 so row lane groups stay warp aligned
+  const int per = 4 * A.nr + (ADJ ? ((A.nref + 3) & ~3) : 0);
+  if (t >= (long long)per * A.nslots) return;
+  const int si = (int)(t / per);
+  const int r4 = (int)(t - (long long)si * per);
+  const Slot<T>& S = A.s[si];
+  if (r4 < 4 * A.nr) {
+    const int r = r4 >> 2, lane = r4 & 3;
+    const bool lat = r < A.nrl;
+    const long long self = lat ? (long long)A.rrow[r] : 0;
+    const T ui = lat ? S.cur[self] : S.ccur[r - A.nrl];
+    T acc = T(0);
+    for (int e = A.rptr[r] + lane; e < A.rptr[r + 1]; e += 4) {
+      const int cidx = A.rcol[e];
+      const T uj = cidx < A.nlat ? S.cur[cidx] : S.ccur[cidx - A.nlat];
+      acc += A.rval[e] * (uj - ui);
+    }
+    const unsigned grp = 0xFu << (threadIdx.x & 28);
+    acc += __shfl_xor_sync(grp, acc, 1);
+    acc += __shfl_xor_sync(grp, acc, 2);
+    if (lane) return;
+    const T pi = lat ? S.prev[self] : S.cprev[r - A.nrl];
+    const T val = T(2) * ui - pi + A.c2 * acc;
+    if (lat) {
+      S.next[self] = val;
+      if (!ADJ && S.hist_w) {
+        const int i = (int)(self % A.nx), j = (int)((self / A.nx) % A.ny), k = (int)(self / ((long long)A.nx * A.ny));
+        S.hist_w[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
+            val;
+      }
+    } else {
+      S.cnext[r - A.nrl] = val;
+      if (!ADJ && S.chist_w) S.chist_w[r - A.nrl] = val;
+    }
+    return;
+  }
+  if constexpr (ADJ) {
+    const int v = r4 - 4 * A.nr;
+    if (!S.hist_r || v >= A.nref) return;
+    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+    A.G[(long long)si * nv + A.refvox_id[v]] += (double)refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur);
+  }
+}
+
+template <typename T>
+__global__ void refined_pair_kernel(const __grid_constant__ StepArgs<T> A) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)A.nref * A.nslots) return;
+  const int si = (int)(t / A.nref);
+  const int v = (int)(t - (long long)si * A.nref);
+  const Slot<T>& S = A.s[si];
+  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+  A.G[(long long)si * nv + A.refvox_id[v]] += (double)refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur);
+}
+
+template <typename T>
+__global__ void set_sparse_kernel(const int* __restrict__ cptr, const int* __restrict__ cunk,
+                                  const double* __restrict__ cw, const double* __restrict__ a, T* __restrict__ rval,
+                                  int nnz) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  double v = 0.0;
+  for (int q = cptr[e]; q < cptr[e + 1]; ++q) v += (cunk[q] >= 0 ? a[cunk[q]] : 1.0) * cw[q];
+  rval[e] = (T)v;
 }
 
 template <typename T>
@@ -742,9 +867,15 @@ void launch_forward_bulk(const StepArgs<T>& a, cudaStream_t st) {
 }
 
 template <typename T>
+unsigned refined_blocks(const StepArgs<T>& a, bool adjoint) {
+  const long long n = (long long)(4 * a.nr + (adjoint ? ((a.nref + 3) & ~3) : 0)) * a.nslots;
+  return (unsigned)((n + 127) / 128);
+}
+
+template <typename T>
 void launch_forward_shell(const StepArgs<T>& a, cudaStream_t st) {
   if (a.small) return;
-  fwd_edge_kernel<T><<<(unsigned)(a.nedge * a.nslots), 128, 0, st>>>(a);
+  fwd_edge_kernel<T><<<(unsigned)(a.nedge * a.nslots) + refined_blocks(a, false), 128, 0, st>>>(a);
 }
 
 template <typename T>
@@ -761,7 +892,21 @@ void launch_adjoint_bulk(const StepArgs<T>& a, cudaStream_t st) {
 template <typename T>
 void launch_adjoint_shell(const StepArgs<T>& a, cudaStream_t st) {
   if (a.small) return;
-  adj_edge_kernel<T><<<(unsigned)(a.nedge * a.nslots), 128, 0, st>>>(a);
+  adj_edge_kernel<T><<<(unsigned)(a.nedge * a.nslots) + refined_blocks(a, true), 128, 0, st>>>(a);
+}
+
+template <typename T>
+void launch_refined_pair(const StepArgs<T>& a, cudaStream_t st) {
+  const long long n = (long long)a.nref * a.nslots;
+  if (n == 0) return;
+  refined_pair_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+}
+
+template <typename T>
+void launch_set_sparse(const int* cptr, const int* cunk, const double* cw, const double* acoef, T* rval, int nnz,
+                       cudaStream_t st) {
+  if (nnz == 0) return;
+  set_sparse_kernel<T><<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(cptr, cunk, cw, acoef, rval, nnz);
 }
 
 template <typename T>
@@ -795,7 +940,10 @@ void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStre
   template void launch_pair<T>(const StepArgs<T>&, const T*, const T*, cudaStream_t);            \
   template void launch_set_coef<T>(const StepArgs<T>&, T*, const double*, double, int*,         \
                                    cudaStream_t);                                                \
-  template void launch_extract_owned<T>(const StepArgs<T>&, const T*, T*, cudaStream_t);
+  template void launch_extract_owned<T>(const StepArgs<T>&, const T*, T*, cudaStream_t);              \
+  template void launch_refined_pair<T>(const StepArgs<T>&, cudaStream_t);                        \
+  template void launch_set_sparse<T>(const int*, const int*, const double*, const double*, T*, int, \
+                                     cudaStream_t);
 
 HYB_INSTANTIATE(float)
 HYB_INSTANTIATE(double)

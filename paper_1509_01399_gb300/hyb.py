@@ -34,13 +34,15 @@ class HybError(RuntimeError):
 class hyb_mesh_desc(ctypes.Structure):
     _fields_ = [("n", c_int32 * 3), ("h", c_double), ("origin", c_double * 3),
                 ("fem_lo", c_int32 * 3), ("fem_hi", c_int32 * 3), ("bc", c_int32 * 6),
-                ("precision", c_int32), ("ckpt_every", c_int32), ("a_max", c_double)]
+                ("precision", c_int32), ("ckpt_every", c_int32), ("a_max", c_double),
+                ("refine_mask", c_void_p)]
 
 
 class hyb_mesh_info(ctypes.Structure):
     _fields_ = [("n_nodes", c_int64), ("n_unknown", c_int64), ("n_fem_owned", c_int64),
                 ("unknown_dims", c_int32 * 3), ("obs_stride", c_int32), ("dt_max", c_double),
-                ("voxel_volume", c_double), ("device_bytes", c_int64), ("launches", c_int64)]
+                ("voxel_volume", c_double), ("device_bytes", c_int64), ("launches", c_int64),
+                ("n_centres", c_int64), ("n_sparse_rows", c_int64)]
 
 
 class hyb_source(ctypes.Structure):
@@ -191,7 +193,7 @@ class HybMesh:
     arrays.  precision: "fp64" or "fp32" (FP32 fields, FP64 gradient/CG)."""
 
     def __init__(self, n, h, fem_lo=None, fem_hi=None, bc=(1,) * 6, precision="fp64", ckpt_every=0,
-                 a_max=4.0, origin=(0.0, 0.0, 0.0), device="cuda", stream=None):
+                 a_max=4.0, origin=(0.0, 0.0, 0.0), device="cuda", stream=None, refine=None):
         import torch
 
         self.torch = torch
@@ -208,6 +210,11 @@ class HybMesh:
         d.precision = HYB_FP64 if precision == "fp64" else HYB_FP32
         d.ckpt_every = int(ckpt_every)
         d.a_max = float(a_max)
+        self._refine = None
+        if refine is not None:
+            import numpy as _np
+            self._refine = _np.ascontiguousarray(_np.asarray(refine).astype(_np.uint8).ravel())
+            d.refine_mask = self._refine.ctypes.data
         self.desc = d
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         with torch.cuda.device(self.device):
@@ -224,6 +231,7 @@ class HybMesh:
 
     @classmethod
     def from_workload(cls, w, precision=None, ckpt_every=None, **kw):
+        kw.setdefault("refine", getattr(w, "refine", None))
         return cls(w.n, w.h, w.fem_lo, w.fem_hi, w.bc, precision or w.precision,
                    w.ckpt_every if ckpt_every is None else ckpt_every, w.a_max, w.origin, **kw)
 

@@ -50,7 +50,7 @@ def test_binding_mirrors_the_abi(lib):
         assert n in hyb.EXPORTED and callable(getattr(hyb, n))
     # struct sizes agree with the C layout (natural alignment)
     assert ctypes.sizeof(hyb.hyb_source) == 24
-    assert ctypes.sizeof(hyb.hyb_mesh_desc) == 4 * 3 + 4 + 8 + 24 + 12 + 12 + 24 + 4 + 4 + 8
+    assert ctypes.sizeof(hyb.hyb_mesh_desc) == 4 * 3 + 4 + 8 + 24 + 12 + 12 + 24 + 4 + 4 + 8 + 8
     assert hyb.hyb_last_error() == ""
 
 

@@ -57,13 +57,18 @@ def run_oracle(w, a, a_obs, srcs=None):
         c = ro["trace"] - oo
         res["J"] += 0.5 * float(np.sum(c[1:] ** 2))
         res["trace"].append(ro["trace"])
-        res["u"].append(ro["u"])
+        res["u"].append(ro["u"][: P.N])  # lattice nodes (centre nodes of refined voxels follow)
         if P.n_unknown:
             gi, lam1 = P.adjoint(a, src, w.nsteps, w.dt, c, ro["hist"], return_lambda=True)
             res["g"] += gi
         else:
             _, lam1 = P.adjoint(a, src, w.nsteps, w.dt, c, np.zeros((w.nsteps, 0)), return_lambda=True)
-        res["lam1"].append(lam1)
+        # the library keeps lambda scaled by h^3 / M^L on FEM-owned rows (it
+        # differs from lambda only at corners of refined voxels)
+        _, ML = P.assemble(a)
+        scale = np.ones(P.NT)
+        scale[P.owned] = P.h ** 3 / ML[P.owned]
+        res["lam1"].append((lam1 * scale)[: P.N])
     return res
 
 
@@ -92,6 +97,11 @@ CASES = {
     "thin_fem": lambda: synth.small_problem(n=12, fem=(4, 6), nsteps=40, omega=12.0),
     "wide_tiles": lambda: synth.small_problem(n=(37, 21, 19), fem=((5, 4, 4), (30, 16, 15)), nsteps=45,
                                               omega=15.0, courant=0.9, sigma_scale=2.0),
+    "refined": lambda: synth.small_problem(n=11, fem=(2, 8), nsteps=60, omega=12.0, courant=0.8,
+                                           refine_frac=0.4),
+    "refined_neumann_ragged": lambda: synth.small_problem(n=(12, 11, 13), fem=((2, 2, 2), (9, 8, 10)), nsteps=60,
+                                                          omega=12.0, courant=0.8, refine_frac=0.5,
+                                                          bc=(0, 1, 0, 1, 1, 1)),
 }
 
 
@@ -150,8 +160,9 @@ def test_batched_sources_equal_single_runs(H):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_checkpoint_recompute_equals_stored_history(H, precision):
-    w = synth.small_problem(n=12, fem=(3, 8), nsteps=103, omega=12.0, courant=0.8)
+@pytest.mark.parametrize("refine", [0.0, 0.4])
+def test_checkpoint_recompute_equals_stored_history(H, precision, refine):
+    w = synth.small_problem(n=12, fem=(2, 9), nsteps=103, omega=12.0, courant=0.8, refine_frac=refine)
     P = oracle.problem_from_workload(w)
     a_obs = 1.0 + np.random.default_rng(5).random(P.n_unknown)
     a = w.a_true()
@@ -226,6 +237,25 @@ def test_full_size_129_first_steps(H, precision, steps):
         t = ora["trace"][0]
         assert rel_l2(gpu["trace"][0, :, : t.shape[1]], t) <= TOL32_TRACE
         assert rel_l2(gpu["g"], ora["g"]) <= TOL32_GRAD
+
+
+def test_refined_mesh_reports_its_stability_bound(H):
+    """Refined voxels lower dt_max below h / sqrt(3 a_max); a refined voxel
+    too close to the outer faces is rejected."""
+    w = synth.small_problem(n=11, fem=(2, 8), nsteps=10, omega=12.0, refine_frac=0.4)
+    m = H.HybMesh.from_workload(w)
+    info = m.query()
+    assert info.n_centres == int(w.refine.sum()) and info.n_sparse_rows > info.n_centres
+    assert info.dt_max < w.h / np.sqrt(3 * w.a_max)
+    with pytest.raises(H.HybError) as e:
+        m.forward(w.a_true(), w.sources, 5, 1.01 * info.dt_max)
+    assert e.value.status == H.HYB_ERR_CFL
+    w2 = synth.small_problem(n=9, fem=(0, 8), nsteps=10)  # unknown voxel 0 has a corner 1 node from the faces
+    w2.refine = np.zeros(w2.n_unknown, dtype=bool)
+    w2.refine[0] = True
+    with pytest.raises(H.HybError) as e:
+        H.HybMesh.from_workload(w2)
+    assert e.value.status == H.HYB_ERR_ARG
 
 
 def test_argument_and_state_errors(H):
