@@ -96,8 +96,8 @@ struct hyb_mesh {
   DevBuf rrow, rptr, rcol, rval, cptr, cunk, cw, rmask, refvox, refvox_id, k9;
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
   cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
-  cudaStream_t aux = nullptr;  // runs the boundary-shell kernel of each step
-  cudaEvent_t ev_bulk = nullptr, ev_shell = nullptr;
+  int nsm = 0;                 // SMs of the device
+  int bps = 0;                 // resident step-kernel blocks per SM
   SweepGraph graphs[3];
 };
 
@@ -245,10 +245,13 @@ int mask_at(const hyb_mesh* m, const hyb_source& s, int k, double dt) {
   return mask;
 }
 
-// Launch geometry of one step: the interior kernel covers nodes 1 .. n-2 on
-// every axis in 32 x 8 tiles and z chunks; the edge kernel the nodes within
-// one node of two faces.  Lattices with fewer than 5 nodes on an axis use a
-// single generic kernel instead.
+// Launch geometry of one step: the interior blocks cover nodes 1 .. n-2 on
+// every axis in 32 x 8 tiles and z chunks, sized so that the launch fills
+// the SMs kStepWaves times at the step kernel's occupancy; the edge tiles
+// cover the nodes within one node of two faces.  Lattices with fewer than 5
+// nodes on an axis use a single generic kernel instead.
+constexpr int kStepWaves = 4;
+
 void step_geometry(const hyb_mesh* m, int nslots, int* npb, int* ntx, int* zchunk, int* nzc, int* small,
                    int* nedge) {
   *small = (m->n[0] < 5 || m->n[1] < 5 || m->n[2] < 5) ? 1 : 0;
@@ -257,7 +260,7 @@ void step_geometry(const hyb_mesh* m, int nslots, int* npb, int* ntx, int* zchun
   *ntx = (int)((bx + kTileX - 1) / kTileX);
   const int nty = (int)((by + kTileY - 1) / kTileY);
   *npb = *ntx * nty;
-  const long long target = 152LL * 16;  // blocks wanted: 16 per SM on 152 SMs
+  const long long target = (long long)std::max(m->nsm, 1) * std::max(m->bps, 1) * kStepWaves;
   const long long per_z = (long long)(*npb) * nslots;
   long long want = (target + per_z - 1) / per_z;
   if (want < 1) want = 1;
@@ -268,33 +271,11 @@ void step_geometry(const hyb_mesh* m, int nslots, int* npb, int* ntx, int* zchun
   *nzc = (int)((bz + z - 1) / z);
 }
 
-// One time level on two streams: the interior kernel on `st`, the edge
-// kernel on the mesh's aux stream.  Each waits for both kernels of the
-// previous level (fork/join through two events), so they overlap with each
-// other but not across levels.  begin_steps/join_steps bracket a run of
-// levels; other work on `st` must come after join_steps.
-hyb_status begin_steps(hyb_mesh* m, cudaStream_t st) {
-  HYB_CU(cudaEventRecord(m->ev_bulk, st));
-  HYB_CU(cudaEventRecord(m->ev_shell, st));
-  return HYB_OK;
-}
-
-template <class Bulk, class Shell>
-hyb_status step_pair(hyb_mesh* m, cudaStream_t st, Bulk bulk, Shell shell, int shell_kernels = 1) {
-  HYB_CU(cudaStreamWaitEvent(m->aux, m->ev_bulk, 0));
-  HYB_CU(cudaStreamWaitEvent(st, m->ev_shell, 0));
-  bulk(st);
+// One time level: a single launch on `st`.
+template <class Launch>
+hyb_status step_launch(hyb_mesh* m, cudaStream_t st, Launch launch) {
+  launch(st);
   HYB_LAUNCHED(m);
-  HYB_CU(cudaEventRecord(m->ev_bulk, st));
-  shell(m->aux);
-  HYB_LAUNCHED(m);
-  m->launches += shell_kernels - 1;
-  HYB_CU(cudaEventRecord(m->ev_shell, m->aux));
-  return HYB_OK;
-}
-
-hyb_status join_steps(hyb_mesh* m, cudaStream_t st) {
-  HYB_CU(cudaStreamWaitEvent(st, m->ev_shell, 0));
   return HYB_OK;
 }
 
@@ -617,7 +598,6 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
                          m->nnz, m->st);
     HYB_LAUNCHED(m);
   }
-  const int nshell = 1;  // edge kernel per level (its trailing blocks run the refined rows)
   auto body = [&](cudaStream_t st) -> hyb_status {
     for (int s = 0; s < nsrc; ++s) {
       HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, 0), 0, fb, st));
@@ -636,10 +616,8 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
     }
     const size_t lvl = (size_t)nsrc * m->nown;
     const size_t clvl = (size_t)nsrc * m->nc;
-    HYB_TRY(begin_steps(m, st));
     for (int k = 0; k < nsteps; ++k) {
       if (keep && ckpt && m->nown > 0 && k > 0 && k % C == 0) {
-        HYB_TRY(join_steps(m, st));
         const size_t seg = (size_t)(k / C);
         for (int s = 0; s < nsrc; ++s) {
           char* base = (char*)m->ckpt.p + ((seg * nsrc + s) * 2) * fb;
@@ -653,16 +631,13 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
                                    cudaMemcpyDeviceToDevice, st));
           }
         }
-        HYB_TRY(begin_steps(m, st));
       }
       const bool hk = keep && !ckpt && m->nown > 0 && k + 1 <= nsteps - 1;
       T* hl = hk ? hist + (size_t)(k + 1) * lvl : nullptr;
       T* chl = hk ? chist + (size_t)(k + 1) * clvl : nullptr;
       forward_slots<T>(m, A, src, nsrc, nsteps, dt, k, trace, hl, chl);
-      HYB_TRY(step_pair(m, st, [&](cudaStream_t q) { launch_forward_bulk<T>(A, q); },
-                        [&](cudaStream_t q) { launch_forward_shell<T>(A, q); }, nshell));
+      HYB_TRY(step_launch(m, st, [&](cudaStream_t q) { launch_forward_step<T>(A, q); }));
     }
-    HYB_TRY(join_steps(m, st));
     return HYB_OK;
   };
   HYB_TRY(run_sweep(m, m->graphs[keep ? 0 : 1], make_key(m, keep ? 0 : 1, trace, 0, nsteps, nsrc, dt, src), body));
@@ -732,7 +707,6 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   HYB_TRY(ensure(m, m->L, 3 * (size_t)nsrc * fb));
   HYB_TRY(ensure(m, m->CL, 3 * (size_t)nsrc * cb));
   HYB_TRY(ensure(m, m->G, (size_t)nsrc * m->nu * sizeof(double)));
-  const int nshell = 1;
   StepArgs<T> A;   // adjoint steps
   base_args(m, A, dt, nsrc);
   StepArgs<T> F;   // recomputed forward steps
@@ -754,21 +728,17 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
     const bool pairing = m->nu > 0 && m->nown > 0;
     auto adj_step = [&](int j, const T* hl, const T* chl) -> hyb_status {
       adjoint_slots<T>(m, A, cot, j, hl, chl);
-      return step_pair(m, st, [&](cudaStream_t q) { launch_adjoint_bulk<T>(A, q); },
-                       [&](cudaStream_t q) { launch_adjoint_shell<T>(A, q); }, nshell);
+      return step_launch(m, st, [&](cudaStream_t q) { launch_adjoint_step<T>(A, q); });
     };
     auto fwd_step = [&](int k, T* hl, T* chl) -> hyb_status {
       forward_slots<T>(m, F, m->src, nsrc, nsteps, dt, k, nullptr, hl, chl);
-      return step_pair(m, st, [&](cudaStream_t q) { launch_forward_bulk<T>(F, q); },
-                       [&](cudaStream_t q) { launch_forward_shell<T>(F, q); }, nshell);
+      return step_launch(m, st, [&](cudaStream_t q) { launch_forward_step<T>(F, q); });
     };
-    HYB_TRY(begin_steps(m, st));
     if (!ckpt) {
       for (int j = nsteps; j >= 1; --j) {
         const bool pj = pairing && j <= nsteps - 1;
         HYB_TRY(adj_step(j, pj ? hist + (size_t)j * lvl : nullptr, pj ? chist + (size_t)j * clvl : nullptr));
       }
-      HYB_TRY(join_steps(m, st));
       if (pairing) HYB_TRY(pair_first<T>(m, A, hist, chist, st));
       return HYB_OK;
     }
@@ -778,7 +748,6 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
       const int kb = seg * C;
       const int ke = std::min((seg + 1) * C, nsteps) - 1;
       if (pairing) {
-        HYB_TRY(join_steps(m, st));
         for (int s = 0; s < nsrc; ++s) {
           T* u0 = field_buf<T>(m, m->U, nsrc, s, kb);
           T* um = field_buf<T>(m, m->U, nsrc, s, kb - 1);
@@ -805,7 +774,6 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
           HYB_LAUNCHED(m);
           if (m->nc) HYB_CU(cudaMemcpyAsync(chist + (size_t)s * m->nc, c0, cb, cudaMemcpyDeviceToDevice, st));
         }
-        HYB_TRY(begin_steps(m, st));
         for (int k = kb; k < ke; ++k)
           HYB_TRY(fwd_step(k, hist + (size_t)(k + 1 - kb) * lvl, chist + (size_t)(k + 1 - kb) * clvl));
       }
@@ -813,7 +781,6 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
         HYB_TRY(adj_step(j, pairing ? hist + (size_t)(j - kb) * lvl : nullptr,
                          pairing ? chist + (size_t)(j - kb) * clvl : nullptr));
     }
-    HYB_TRY(join_steps(m, st));
     if (pairing) HYB_TRY(pair_first<T>(m, A, hist, chist, st));
     return HYB_OK;
   };
@@ -1040,12 +1007,19 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   }
   if (st == HYB_OK && cudaMemsetAsync(m->flag.p, 0, sizeof(int), m->st) != cudaSuccess)
     st = fail(HYB_ERR_CUDA, "cudaMemsetAsync failed");
-  if (st == HYB_OK && (cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
-                        cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking) != cudaSuccess ||
-                        cudaEventCreateWithFlags(&m->ev_bulk, cudaEventDisableTiming) != cudaSuccess ||
-                        cudaEventCreateWithFlags(&m->ev_shell, cudaEventDisableTiming) != cudaSuccess)) {
+  if (st == HYB_OK && cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
-    st = fail(HYB_ERR_CUDA, "stream or event creation failed");
+    st = fail(HYB_ERR_CUDA, "stream creation failed");
+  }
+  if (st == HYB_OK) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      st = fail(HYB_ERR_CUDA, "device query failed");
+    } else {
+      m->bps = std::min(step_blocks_per_sm(d->precision, 0), step_blocks_per_sm(d->precision, 1));
+    }
   }
   if (st == HYB_OK && d->refine_mask && fem && m->nu > 0) {
     if (d->n[0] < 5 || d->n[1] < 5 || d->n[2] < 5) st = fail(HYB_ERR_ARG, "refinement needs >= 5 nodes per axis");
@@ -1078,7 +1052,6 @@ hyb_status hyb_mesh_query(const hyb_mesh* m, hyb_mesh_info* o) {
 hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   if (!m) return HYB_OK;
   cudaStreamSynchronize(m->st);
-  if (m->aux) cudaStreamSynchronize(m->aux);
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
                     &m->g, &m->atrial, &m->cot, &m->trace, &m->rrow, &m->rptr, &m->rcol, &m->rval,
                     &m->cptr, &m->cunk, &m->cw, &m->rmask, &m->refvox, &m->refvox_id, &m->k9,
@@ -1088,9 +1061,6 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   for (SweepGraph& g : m->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (m->cap) cudaStreamDestroy(m->cap);
-  if (m->aux) cudaStreamDestroy(m->aux);
-  if (m->ev_bulk) cudaEventDestroy(m->ev_bulk);
-  if (m->ev_shell) cudaEventDestroy(m->ev_shell);
   delete m;
   return HYB_OK;
 }

@@ -10,9 +10,9 @@
 namespace hyb {
 
 constexpr int kMaxSlots = 16;   // problems advanced by one step launch
-constexpr int kStepThreads = 256;
-constexpr int kTileX = 32;       // interior kernel thread tile (x)
-constexpr int kTileY = 8;        // interior kernel thread tile (y)
+constexpr int kStepBlock = 256;  // threads per block of the step kernel
+constexpr int kTileX = 32;       // interior thread tile (x): one warp per tile row
+constexpr int kTileY = 8;        // interior thread tile (y)
 constexpr int kReduceBlocks = 512;
 constexpr int kReduceThreads = 256;
 
@@ -51,11 +51,12 @@ struct StepArgs {
   int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
   T c2;              // tau^2 / h^2
   T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
-  int npb;           // interior kernel: thread blocks per plane of the interior box
-  int ntx;           // interior kernel: tiles along x
-  int zchunk, nzc;   // interior kernel: planes per block, blocks along z
+  int npb;           // interior: thread blocks per plane of the interior box
+  int ntx;           // interior: tiles along x
+  int zchunk, nzc;   // interior: planes per block, blocks along z
   int small;         // some axis has < 5 nodes: one generic kernel per level
-  int nedge;         // edge kernel: 128-thread tiles per slot
+  int nedge;         // edge tiles (128 nodes) per slot
+  int nhe, nhr;      // step kernel: leading blocks of edge tiles, then of refined rows
   int nslots;
   // refined region (nr == 0: nothing refined).  Sparse rows: the nrl
   // lattice nodes touching a refined voxel, then the nref centre nodes.
@@ -72,18 +73,15 @@ struct StepArgs {
   Slot<T> s[kMaxSlots];
 };
 
-// One time level = an interior kernel and an edge kernel, which read the
-// same inputs and write disjoint nodes (they may run concurrently).  On
-// lattices with fewer than 5 nodes on an axis the "bulk" launcher runs one
-// generic kernel over every node and the "shell" launcher does nothing.
+// One time level of every slot: one launch of the step kernel (edge tiles,
+// refined rows and interior blocks), or on lattices with fewer than 5 nodes
+// on an axis one generic kernel over every node.
 template <typename T>
-void launch_forward_bulk(const StepArgs<T>& a, cudaStream_t st);
+void launch_forward_step(const StepArgs<T>& a, cudaStream_t st);
 template <typename T>
-void launch_forward_shell(const StepArgs<T>& a, cudaStream_t st);
-template <typename T>
-void launch_adjoint_bulk(const StepArgs<T>& a, cudaStream_t st);
-template <typename T>
-void launch_adjoint_shell(const StepArgs<T>& a, cudaStream_t st);
+void launch_adjoint_step(const StepArgs<T>& a, cudaStream_t st);
+// Resident blocks per SM of the step kernel (for grid sizing), at least 1.
+int step_blocks_per_sm(int precision, int adjoint);
 // G[c] += voxel pairing of (u^0 in hist box, lambda^1) for one slot.
 template <typename T>
 void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t st);
@@ -94,7 +92,7 @@ void launch_set_coef(const StepArgs<T>& a, T* W, const double* acoef, double a_m
                      cudaStream_t st);
 // (The sparse rows of the refined region, identical for the forward and the
 // mass-scaled adjoint, and the adjoint's gradient pairing of refined voxels
-// run in trailing blocks of the edge launch of each level.)
+// run in blocks of the step kernel.)
 // Gradient pairing of refined voxels for level 0 (u^0 from the history
 // slots `hist`/`chist`, lambda^1 as the slots' cur/ccur).
 template <typename T>

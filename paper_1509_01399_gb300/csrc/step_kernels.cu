@@ -1,10 +1,13 @@
 // Time-step kernels of the hybrid FEM/FDM scheme.
 //
-// One time level of every slot (source / problem) is an interior launch
-// (all nodes but those within one node of two faces) and a small edge
-// launch, which read the same inputs and write disjoint nodes.  An interior
-// thread owns one (x, y) column and marches a chunk of z planes, keeping u
-// at z-1, z, z+1 in registers; x/y neighbours come through L1.  Row kinds:
+// One time level of every slot (source / problem) is one launch of
+// step_kernel: its leading blocks run the edge tiles (nodes within one node
+// of two faces) and the refined sparse rows, the rest the interior (all
+// other nodes).  All blocks read levels k and k-1 and write disjoint nodes of
+// level k+1.  An interior thread owns one (x, y) column of a 32 x 8 tile (one
+// warp per tile row) and marches a chunk of z planes, keeping u at z-1, z,
+// z+1 in registers, taking x/y neighbours through L1 and prefetching several
+// planes ahead.  Row kinds:
 //  * FDM rows, Eq. (fdmschemeforward): u^{k+1} = 2u^k - u^{k-1} + tau^2 Delta_h u^k,
 //  * FEM rows on the FEM-owned nodes, Eq. (fem) with lumped mass: on the
 //    Kuhn-cut voxels the row is a 7-point stencil whose axis-edge weight is
@@ -14,11 +17,11 @@
 //    and the absorbing rows of Eq. (eq:abs2), which use the new value of the
 //    inward neighbour: the thread of that neighbour writes the face node, and
 //    edge/corner threads recompute the values they need, so no intra-step
-//    synchronisation is needed.
+//    synchronisation between blocks is needed.
 // Both schemes write the same field, so the omega_o / omega_diamond copies
 // of Algorithm 1 need no data movement.
 //
-// The adjoint kernel is the exact transpose of the forward step (the
+// The transposed step is the exact transpose of the forward step (the
 // discrete form of Eq. (adjoint1)).  Away from the outer boundary the
 // mass-weighted operator is symmetric, so the transposed row is the forward
 // stencil; next to a face the transposed face row (closed form) and its
@@ -251,7 +254,21 @@ __device__ __noinline__ T adj_new(const StepArgs<T>& A, const Slot<T>& S, int i,
   return v;
 }
 
-// sum over the 12 axis edges of voxel (i,j,k) of w_e (u_p - u_q)(l_p - l_q)
+// Sum over the 12 axis edges of a voxel of w_e (u_p - u_q)(l_p - l_q), corner
+// c = a + 2b + 4d at offset (a, b, d); w_e = 1/3 on the edges at the
+// voxel's diagonal corners 0 and 7, 1/6 on the others.
+template <typename T>
+__device__ __forceinline__ T pair_sum(const T u[8], const T l[8]) {
+  const T d3 = (u[1] - u[0]) * (l[1] - l[0]) + (u[7] - u[6]) * (l[7] - l[6]) +
+               (u[2] - u[0]) * (l[2] - l[0]) + (u[7] - u[5]) * (l[7] - l[5]) +
+               (u[4] - u[0]) * (l[4] - l[0]) + (u[7] - u[3]) * (l[7] - l[3]);
+  const T d6 = (u[3] - u[2]) * (l[3] - l[2]) + (u[5] - u[4]) * (l[5] - l[4]) +
+               (u[3] - u[1]) * (l[3] - l[1]) + (u[6] - u[4]) * (l[6] - l[4]) +
+               (u[5] - u[1]) * (l[5] - l[1]) + (u[6] - u[2]) * (l[6] - l[2]);
+  return d3 / T(3) + d6 / T(6);
+}
+
+// pair_sum of voxel (i,j,k): u from the FEM-owned box hb, lambda from the lattice
 template <typename T>
 __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restrict__ hb,
                                         const T* __restrict__ lam, int i, int j, int k) {
@@ -268,13 +285,13 @@ __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restric
     u[c] = hb[h0 + a + b * hy + d * hz];
     l[c] = lam[l0 + a + b * ly + d * lz];
   }
-  const T d3 = (u[1] - u[0]) * (l[1] - l[0]) + (u[7] - u[6]) * (l[7] - l[6]) +
-               (u[2] - u[0]) * (l[2] - l[0]) + (u[7] - u[5]) * (l[7] - l[5]) +
-               (u[4] - u[0]) * (l[4] - l[0]) + (u[7] - u[3]) * (l[7] - l[3]);
-  const T d6 = (u[3] - u[2]) * (l[3] - l[2]) + (u[5] - u[4]) * (l[5] - l[4]) +
-               (u[3] - u[1]) * (l[3] - l[1]) + (u[6] - u[4]) * (l[6] - l[4]) +
-               (u[5] - u[1]) * (l[5] - l[1]) + (u[6] - u[2]) * (l[6] - l[2]);
-  return d3 / T(3) + d6 / T(6);
+  return pair_sum(u, l);
+}
+
+// Laplacian part (without 1/h^2) of a 7-point row with unit weights.
+template <typename T>
+__device__ __forceinline__ T lap7(T xm, T xp, T ym, T yp, T zm, T zp, T c) {
+  return (xm - c) + (xp - c) + (ym - c) + (yp - c) + (zm - c) + (zp - c);
 }
 
 // Laplacian part of a non-absorbing row (inlined form of row_lap).
@@ -290,7 +307,7 @@ __device__ __forceinline__ T row_lap_inl(const StepArgs<T>& A, const T* __restri
   const T yp = j < A.ny - 1 ? u[id + A.nx] : u[id - A.nx];
   const T zm = k > 0 ? u[id - sz] : u[id + sz];
   const T zp = k < A.nz - 1 ? u[id + sz] : u[id - sz];
-  return (xm - c) + (xp - c) + (ym - c) + (yp - c) + (zm - c) + (zp - c);
+  return lap7(xm, xp, ym, yp, zm, zp, c);
 }
 
 template <typename T>
@@ -387,181 +404,400 @@ __device__ __forceinline__ int edge_tile_peer(int t, int blk, const int q[3], in
   return (t & ~(3 << sh)) | (qn << sh);
 }
 
-// Value of a face node b on the single face f, given the inward neighbour
-// m = b1: u^k_b, u^k_m and the new u^{k+1}_m.  Absorbing: Eq. (eq:abs2);
-// otherwise the mirror-ghost row with the source flux.  b's in-face
-// neighbours exist (its in-face coordinates are at least 2 from the edges).
+// Value of a face node b on the single face f, from u^k at b (ub), at its
+// inward neighbour m (um), the new value at m (nm), b's four in-face
+// neighbours (first the lower of the two other axes, each as (minus, plus))
+// and u^{k-1} at b.  Absorbing: Eq. (eq:abs2); otherwise the mirror-ghost
+// row with the source flux.
 template <typename T>
-__device__ __forceinline__ T fwd_face_value(const StepArgs<T>& A, const Slot<T>& S, long long idb, int f, T ub,
-                                            T um, T nm) {
+__device__ __forceinline__ T fwd_face_row(const StepArgs<T>& A, const Slot<T>& S, int f, T ub, T um, T nm, T n1m,
+                                          T n1p, T n2m, T n2p, T pb) {
   if ((S.mask_f >> f) & 1) return A.r * ub + (um - A.r * nm);
-  const int ax = f >> 1;
-  const T* __restrict__ u = S.cur;
   T lap = T(2) * (um - ub);
-#pragma unroll
-  for (int a2 = 0; a2 < 3; ++a2) {
-    if (a2 == ax) continue;
-    const long long s2 = axis_stride(A, a2);
-    lap += (u[idb - s2] - ub) + (u[idb + s2] - ub);
-  }
-  T v = T(2) * ub - S.prev[idb] + A.c2 * lap;
+  lap += (n1m - ub) + (n1p - ub);
+  lap += (n2m - ub) + (n2p - ub);
+  T v = T(2) * ub - pb + A.c2 * lap;
   if (S.src_face == f) v += S.srcval;
   return v;
 }
 
 // lambda^j at a face node b on the single face f whose in-face coordinates
 // are at least 2 from the edges (no transposed absorbing coupling reaches
-// it), given lambda^{j+1} at b and at its inward neighbour m, and the
-// coefficient of m's row on b.
+// it), from lambda^{j+1} at b and at its inward neighbour m, the coefficient
+// of m's row on b, b's four in-face neighbours (as in fwd_face_row) and
+// lambda^{j+2} at b.
 template <typename T>
-__device__ __forceinline__ T adj_face_value(const StepArgs<T>& A, const Slot<T>& S, long long idb, int f, int i,
-                                            int j, int k, T lb, T lm, T coef_mb) {
+__device__ __forceinline__ T adj_face_row(const StepArgs<T>& A, const Slot<T>& S, int f, int bi, int bj, int bk,
+                                          T lb, T lm, T coef_mb, T n1m, T n1p, T n2m, T n2p, T pb) {
   const bool abc = (S.mask_f >> f) & 1;
   T rhs = abc ? A.r * lb : (T(2) - T(6) * A.c2) * lb;
   rhs += A.c2 * coef_mb * lm;
   if (!abc) {
-    const int ax = f >> 1;
-    const T* __restrict__ l1 = S.cur;
-#pragma unroll
-    for (int a2 = 0; a2 < 3; ++a2) {
-      if (a2 == ax) continue;
-      const long long s2 = axis_stride(A, a2);
-      rhs += A.c2 * (l1[idb - s2] + l1[idb + s2]);
-    }
+    rhs += A.c2 * (n1m + n1p);
+    rhs += A.c2 * (n2m + n2p);
   }
-  if (!((S.mask_c >> f) & 1)) rhs -= S.prev[idb];
-  if (S.obs_r && S.obs_face == f) rhs += S.obs_r[face_index(f, i, j, k, A.nx, A.ny)];
+  if (!((S.mask_c >> f) & 1)) rhs -= pb;
+  if (S.obs_r && S.obs_face == f) rhs += S.obs_r[face_index(f, bi, bj, bk, A.nx, A.ny)];
   return rhs;
 }
 
-// Interior kernel of one time level (lattices with >= 5 nodes per axis),
-// forward (ADJ = false) or transposed (ADJ = true).  32 x 8 thread tiles of
-// the nodes 1 .. n-2, each thread marching a chunk of z planes with u at
-// z-1, z, z+1 in registers and the next plane and the previous level loaded
-// one iteration ahead.  A node one step inside exactly one face also
-// produces the face node next to it (the forward needs its new value; the
-// transposed face row has a closed form) and applies the transposed
-// boundary couplings to itself.  Nodes within one node of two faces are
-// left to the edge kernel.
+// Position of an interior thread.
+struct Col {
+  int si, i, j;
+  int dxs, dys;   // -1 / +1: one node inside the low / high face of x, y; 0: not
+  bool xy_fem;    // (i, j) inside the FEM-owned range
+  bool xy_vox;    // (i, j) is the x-y origin of an unknown voxel and the step pairs
+};
+
+// Node (i, j, k) of the interior by the general rows, reading level data from
+// global memory (u^k at z-1, z, z+1 and u^{k-1} given): any node, including
+// those one node inside a z face.  A node one step inside exactly one face
+// also produces the face node next to it (the forward needs its new value;
+// the transposed face row has a closed form) and applies the transposed
+// boundary couplings to itself.  Nodes within one node of two faces belong
+// to the edge tiles.
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(kTileX * kTileY) bulk_kernel(const __grid_constant__ StepArgs<T> A) {
+__device__ __noinline__ void general_node(const StepArgs<T>& A, const Slot<T>& S, const Col& C, int k, T cm, T c0,
+                                             T cp, T pv) {
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int i = C.i, j = C.j;
+  const int dzs = (k == 1) ? -1 : (k == nz - 2 ? 1 : 0);
+  const int cnt = (C.dxs != 0) + (C.dys != 0) + (dzs != 0);
+  if (cnt > 1) return;
+  const long long id = lin(A, i, j, k);
+  const T* __restrict__ cq = S.cur + id;
+  const T c2 = A.c2;
+  T val;
+  const bool fem = C.xy_fem && k >= A.fl[2] && k <= A.fh[2];
+  if (fem) {
+    val = T(2) * c0 - pv + c2 * fem_lap(A, S.cur, id, i, j, k, c0, cm, cp);
+  } else {
+    val = T(2) * c0 - pv + c2 * lap7(cq[-1], cq[1], cq[-nx], cq[nx], cm, cp, c0);
+  }
+  if (cnt == 1) {
+    const int ax = C.dxs ? 0 : (C.dys ? 1 : 2);
+    const int sd = C.dxs ? C.dxs : (C.dys ? C.dys : dzs);
+    const int f = 2 * ax + (sd > 0 ? 1 : 0);
+    const long long db = sd * axis_stride(A, ax);
+    const long long idb = id + db;
+    const T xb = ax == 2 ? (sd < 0 ? cm : cp) : cq[db];
+    const long long s1 = axis_stride(A, ax == 0 ? 1 : 0);
+    const long long s2 = axis_stride(A, ax == 2 ? 1 : 2);
+    const T* __restrict__ u = S.cur;
+    const int bi = i + (ax == 0 ? sd : 0), bj = j + (ax == 1 ? sd : 0), bk = k + (ax == 2 ? sd : 0);
+    if constexpr (!ADJ) {
+      const T vb = fwd_face_row(A, S, f, xb, c0, val, u[idb - s1], u[idb + s1], u[idb - s2], u[idb + s2], S.prev[idb]);
+      S.next[idb] = vb;
+      if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, bk, nx, ny)] = vb;
+    } else {
+      const T coef_mb = row_coef(A, i, j, k, ax, sd);
+      const T lb = adj_face_row(A, S, f, bi, bj, bk, xb, c0, coef_mb, u[idb - s1], u[idb + s1], u[idb - s2],
+                                u[idb + s2], S.prev[idb]);
+      // the face row's transposed coefficient on this node replaces the
+      // symmetric one the stencil used
+      val += (((S.mask_f >> f) & 1) ? xb : T(2) * c2 * xb) - c2 * coef_mb * xb;
+      if ((S.mask_e >> f) & 1) val -= A.r * lb;
+      S.next[idb] = lb;
+    }
+  }
+  const long long bidx =
+      fem ? (long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2])) : 0;
+  if (!(fem && A.rmask && A.rmask[bidx])) {  // sparse rows are written by the refined rows
+    S.next[id] = val;
+    if (!ADJ && S.hist_w && fem) S.hist_w[bidx] = val;
+  }
+  if (ADJ && C.xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
+    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+    const long long vid =
+        (long long)(i - A.fl[0]) + (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
+    if (!(A.refvox && A.refvox[vid]))
+      atomicAdd(A.G + (long long)C.si * nv + vid, (double)voxel_pair(A, S.hist_r, S.cur, i, j, k));
+  }
+}
+
+// ---- shared-memory pipeline of the interior blocks ----
+// A block stages, plane by plane and kPipe<T>::D planes ahead of its z march,
+// with cp.async: u^k on the tile and a one-node halo (34 x 10), u^{k-1} on
+// the same box, and on tiles that meet the FEM block the three edge-weight
+// arrays (33 x 9, one node below the tile in x and y) and, for the
+// transposed step, the stored u of the FEM-owned box (33 x 9, one node
+// above).  Each plane lives in a ring of stages indexed by plane modulo the
+// ring size.
+constexpr int kBoxX = kTileX + 2, kBoxY = kTileY + 2, kBox = kBoxX * kBoxY;
+constexpr int kHBoxX = kTileX + 1, kHBoxY = kTileY + 1, kHBox = kHBoxX * kHBoxY;
+
+template <typename T>
+struct kPipe {
+  static constexpr int pow2(int n) { return n <= 1 ? 1 : 2 * pow2((n + 1) / 2); }
+  static constexpr int D = 2;             // levels in flight
+  static constexpr int SC = pow2(D + 3);  // u^k stages (planes k-1 .. k+1+D)
+  static constexpr int SP = pow2(D + 1);  // u^{k-1} stages (k .. k+D)
+  static constexpr int SW = pow2(D + 2);  // edge-weight stages (k-1 .. k+D)
+  static constexpr int SH = pow2(D + 2);  // stored-u stages (k .. k+1+D)
+  static constexpr int elems = SC * kBox + SP * kBox + SW * 3 * kHBox + SH * kHBox;
+  static constexpr size_t bytes = sizeof(T) * (size_t)elems;
+};
+
+template <typename T>
+__device__ __forceinline__ void cp_async(T* dst, const T* src) {
+#if defined(__CUDA_ARCH__)
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+#else
+  *dst = *src;
+#endif
+}
+
+__device__ __forceinline__ void cp_commit() {
+#if defined(__CUDA_ARCH__)
+  asm volatile("cp.async.commit_group;" ::: "memory");
+#endif
+}
+
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+#if defined(__CUDA_ARCH__)
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+#endif
+}
+
+// Interior part of one time level (lattices with >= 5 nodes per axis):
+// 32 x 8 thread tiles of the nodes 1 .. n-2, one warp per tile row, each
+// block marching a chunk of z planes through the shared-memory pipeline.
+// Nodes one step inside an x or y face also produce the face node; planes
+// one step inside a z face take the general rows from global memory.
+template <typename T, bool ADJ>
+__device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* sm) {
+  static_assert(kTileX == 32, "one warp per tile row");
+  static_assert(kTileX * kTileY == kStepBlock, "one thread per tile column");
+  using P = kPipe<T>;
+  constexpr int D = P::D;
   const int tps = A.npb * A.nzc;
-  const int si = blockIdx.x / tps;
-  int rem = blockIdx.x - si * tps;
+  Col C;
+  C.si = b / tps;
+  int rem = b - C.si * tps;
   const int zc = rem / A.npb;
   rem -= zc * A.npb;
   const int tyy = rem / A.ntx;
   const int txx = rem - tyy * A.ntx;
   const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int i = 1 + txx * kTileX + (threadIdx.x % kTileX);
-  const int j = 1 + tyy * kTileY + (threadIdx.x / kTileX);
-  if (i > nx - 2 || j > ny - 2) return;
-  const int dxs = (i == 1) ? -1 : (i == nx - 2 ? 1 : 0);  // direction to a near face
-  const int dys = (j == 1) ? -1 : (j == ny - 2 ? 1 : 0);
-  const int nxy = (dxs != 0) + (dys != 0);
-  if (nxy >= 2) return;  // the column runs along an edge: edge kernel
+  const int pl = nx * ny;
   const int z0 = 1 + zc * A.zchunk;
   const int z1 = min(z0 + A.zchunk, nz - 1);
-  if (z0 >= z1) return;
-  const Slot<T>& S = A.s[si];
-  const long long plane = (long long)nx * ny;
-  const int pl = (int)plane;
-  const T* __restrict__ c = S.cur;
-  T* __restrict__ out = S.next;
-  const bool xy_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
-  const bool xy_vox = ADJ && S.hist_r != nullptr && i >= A.fl[0] && i < A.fl[0] + A.un[0] &&
-                      j >= A.fl[1] && j < A.fl[1] + A.un[1];
-  T* __restrict__ hw = ADJ ? nullptr : S.hist_w;
-  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
-  long long id = (long long)i + (long long)nx * j + plane * z0;
-  const T* __restrict__ cq = c + id;
-  const T* __restrict__ pq = S.prev + id;
-  T* __restrict__ oq = out + id;
-  T cm = cq[-pl];
-  T c0 = cq[0];
-  T cp = cq[pl];
-  T pv = pq[0];
+  if (z0 >= z1) return;  // whole block
+  const int t = (int)threadIdx.x;
+  const int tx = t & 31, ty = t >> 5;
+  const int i0 = 1 + txx * kTileX, j0 = 1 + tyy * kTileY;
+  C.i = i0 + tx;
+  C.j = j0 + ty;
+  C.dxs = (C.i == 1) ? -1 : (C.i == nx - 2 ? 1 : 0);
+  C.dys = (C.j == 1) ? -1 : (C.j == ny - 2 ? 1 : 0);
+  const bool active = C.i <= nx - 2 && C.j <= ny - 2 && !(C.dxs != 0 && C.dys != 0);
+  const Slot<T>& S = A.s[C.si];
+  const bool has_fem = A.fl[0] <= A.fh[0];
+  C.xy_fem = has_fem && C.i >= A.fl[0] && C.i <= A.fh[0] && C.j >= A.fl[1] && C.j <= A.fh[1];
+  const bool pairing = ADJ && S.hist_r != nullptr;
+  C.xy_vox = pairing && C.i >= A.fl[0] && C.i < A.fl[0] + A.un[0] && C.j >= A.fl[1] && C.j < A.fl[1] + A.un[1];
+  // the tile meets the FEM-owned block in x-y (block-uniform)
+  const bool fem_tile = has_fem && i0 <= A.fh[0] && i0 + kTileX - 1 >= A.fl[0] && j0 <= A.fh[1] &&
+                        j0 + kTileY - 1 >= A.fl[1];
+  const bool hist_tile = pairing && fem_tile;
+
+  T* CR = sm;
+  T* PR = CR + P::SC * kBox;
+  T* WR = PR + P::SP * kBox;
+  T* HR = WR + P::SW * 3 * kHBox;
+
+  // copy slots of this thread (offsets within a plane; -1: no copy)
+  int go[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int e = t + kStepBlock * s;
+    const int r = e / kBoxX, c = e - r * kBoxX;
+    const int gi = i0 - 1 + c, gj = j0 - 1 + r;
+    go[s] = (e < kBox && gi <= nx - 1 && gj <= ny - 1) ? gj * nx + gi : -1;
+  }
+  int wo[4] = {-1, -1, -1, -1}, ho[2] = {-1, -1};
+  int wz = 0, hz = 0;
+  if (fem_tile) {
+    wz = A.wn[0] * A.wn[1];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int e = t + kStepBlock * s;
+      const int a = e / kHBox;
+      const int q = e - a * kHBox;
+      const int r = q / kHBoxX, c = q - r * kHBoxX;
+      const int wi = i0 - 1 + c - A.wl[0], wj = j0 - 1 + r - A.wl[1];
+      if (e < 3 * kHBox && wi >= 0 && wi < A.wn[0] && wj >= 0 && wj < A.wn[1])
+        wo[s] = a * (int)A.wsz + wj * A.wn[0] + wi;
+    }
+  }
+  if (hist_tile) {
+    hz = A.fn[0] * A.fn[1];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int e = t + kStepBlock * s;
+      const int r = e / kHBoxX, c = e - r * kHBoxX;
+      const int hi = i0 + c - A.fl[0], hj = j0 + r - A.fl[1];
+      if (e < kHBox && hi >= 0 && hi < A.fn[0] && hj >= 0 && hj < A.fn[1]) ho[s] = hj * A.fn[0] + hi;
+    }
+  }
+  const int wlo = A.wl[2], whi = A.wl[2] + A.wn[2] - 1;
+  const int hlo = A.fl[2], hhi = A.fh[2];
+  const T* __restrict__ gcur = S.cur;
+  const T* __restrict__ gprev = S.prev;
+  const T* __restrict__ ghist = S.hist_r;
+  // copy of plane q of each staged array into its ring stage (q & (S - 1))
+  auto copy_c = [&](int q) {
+    if (q > z1) return;
+    T* dst = CR + (q & (P::SC - 1)) * kBox + t;
+    const T* src = gcur + (long long)q * pl;
+    if (go[0] >= 0) cp_async(dst, src + go[0]);
+    if (go[1] >= 0) cp_async(dst + kStepBlock, src + go[1]);
+  };
+  auto copy_p = [&](int q) {
+    if (q > z1 - 1) return;
+    T* dst = PR + (q & (P::SP - 1)) * kBox + t;
+    const T* src = gprev + (long long)q * pl;
+    if (go[0] >= 0) cp_async(dst, src + go[0]);
+    if (go[1] >= 0) cp_async(dst + kStepBlock, src + go[1]);
+  };
+  auto copy_w = [&](int q) {
+    if (q < wlo || q > whi) return;
+    T* dst = WR + (q & (P::SW - 1)) * 3 * kHBox + t;
+    const T* src = A.W + (long long)(q - wlo) * wz;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (wo[s] >= 0) cp_async(dst + kStepBlock * s, src + wo[s]);
+  };
+  auto copy_h = [&](int q) {
+    if (q < hlo || q > hhi) return;
+    T* dst = HR + (q & (P::SH - 1)) * kHBox + t;
+    const T* src = ghist + (long long)(q - hlo) * hz;
+    if (ho[0] >= 0) cp_async(dst, src + ho[0]);
+    if (ho[1] >= 0) cp_async(dst + kStepBlock, src + ho[1]);
+  };
+  // prologue: the planes of levels z0 .. z0 + D - 1, one group per level
+  copy_c(z0 - 1);
+  copy_c(z0);
+  if (fem_tile) copy_w(z0 - 1);
+  if (hist_tile) copy_h(z0);
+  for (int g = 0; g < D; ++g) {
+    copy_c(z0 + 1 + g);
+    copy_p(z0 + g);
+    if (fem_tile) copy_w(z0 + g);
+    if (hist_tile) copy_h(z0 + 1 + g);
+    cp_commit();
+  }
   const T c2 = A.c2;
-  for (int k = z0; k < z1; ++k) {
-    const T cpp = (k + 2 <= nz - 1) ? cq[2 * pl] : T(0);
-    const T pvn = (k + 1 < z1) ? pq[pl] : T(0);
-    const int dzs = (k == 1) ? -1 : (k == nz - 2 ? 1 : 0);
-    const int cnt = nxy + (dzs != 0);
-    if (cnt <= 1) {
-      T val;
-      const bool fem = xy_fem && k >= A.fl[2] && k <= A.fh[2];
-      if (fem) {
-        val = T(2) * c0 - pv + c2 * fem_lap(A, c, id, i, j, k, c0, cm, cp);
+  const int o = (ty + 1) * kBoxX + (tx + 1);    // this node in a u box
+  const int ow = (ty + 1) * kHBoxX + (tx + 1);  // this node in an edge-weight box
+  const int oh = ty * kHBoxX + tx;              // this node in a stored-u box
+  const int rlo = A.fl[2], rhi = A.fh[2];
+  T* __restrict__ gnext = S.next;
+  long long id = (long long)C.i + (long long)nx * C.j + (long long)pl * z0;
+  for (int k = z0; k < z1; ++k, id += pl) {
+    cp_wait<D - 1>();
+    __syncthreads();
+    // planes of level k + D (their stages were last read at level k - 1)
+    copy_c(k + 1 + D);
+    copy_p(k + D);
+    if (fem_tile) copy_w(k + D);
+    if (hist_tile) copy_h(k + 1 + D);
+    cp_commit();
+    if (!active) continue;
+    const T* C0 = CR + (k & (P::SC - 1)) * kBox + o;
+    const T* Cm = CR + ((k - 1) & (P::SC - 1)) * kBox + o;
+    const T* Cp = CR + ((k + 1) & (P::SC - 1)) * kBox + o;
+    const T* P0 = PR + (k & (P::SP - 1)) * kBox + o;
+    const T c0 = C0[0], cm = Cm[0], cp = Cp[0], pv = P0[0];
+    if (k == 1 || k == nz - 2) {  // block-uniform
+      general_node<T, ADJ>(A, S, C, k, cm, c0, cp, pv);
+      continue;
+    }
+    const T xm = C0[-1], xp = C0[1], ym = C0[-kBoxX], yp = C0[kBoxX];
+    const bool lf = C.xy_fem && k >= rlo && k <= rhi;
+    T wxm = T(1), wxp = T(1), wym = T(1), wyp = T(1);
+    T lap;
+    if (lf) {
+      const T* WX = WR + (k & (P::SW - 1)) * 3 * kHBox + ow;
+      const T* WY = WX + kHBox;
+      const T* WZ = WX + 2 * kHBox;
+      const T* WZm = WR + ((k - 1) & (P::SW - 1)) * 3 * kHBox + 2 * kHBox + ow;
+      wxm = WX[-1];
+      wxp = WX[0];
+      wym = WY[-kHBoxX];
+      wyp = WY[0];
+      lap = wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + WZ[0] * (cp - c0) +
+            WZm[0] * (cm - c0);
+    } else {
+      lap = lap7(xm, xp, ym, yp, cm, cp, c0);
+    }
+    T val = T(2) * c0 - pv + c2 * lap;
+    if (C.dxs != 0 || C.dys != 0) {  // the x or y face node next to this node
+      const int ax = C.dxs ? 0 : 1;
+      const int sd = C.dxs ? C.dxs : C.dys;
+      const int f = 2 * ax + (sd > 0 ? 1 : 0);
+      const int ob = ax == 0 ? sd : sd * kBoxX;  // b relative to this node in a u box
+      const int o1 = ax == 0 ? kBoxX : 1;        // the other in-plane axis in the box
+      const T ub = C0[ob];
+      // in-face neighbours: the other in-plane axis first, then z
+      const T n1m = C0[ob - o1], n1p = C0[ob + o1], n2m = Cm[ob], n2p = Cp[ob], pb = P0[ob];
+      const long long idb = id + (ax == 0 ? (long long)sd : (long long)sd * nx);
+      const int bi = C.i + (ax == 0 ? sd : 0), bj = C.j + (ax == 1 ? sd : 0);
+      if constexpr (!ADJ) {
+        const T vb = fwd_face_row(A, S, f, ub, c0, val, n1m, n1p, n2m, n2p, pb);
+        gnext[idb] = vb;
+        if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, k, nx, ny)] = vb;
       } else {
-        const T lap = (cq[-1] - c0) + (cq[1] - c0) + (cq[-nx] - c0) + (cq[nx] - c0) + (cm - c0) + (cp - c0);
-        val = T(2) * c0 - pv + c2 * lap;
-      }
-      if (cnt == 1) {
-        // the face node b next to this node, on face f of axis ax
-        const int ax = dxs ? 0 : (dys ? 1 : 2);
-        const int sd = dxs ? dxs : (dys ? dys : dzs);
-        const int f = 2 * ax + (sd > 0 ? 1 : 0);
-        const long long db = sd * axis_stride(A, ax);
-        const T xb = ax == 2 ? (sd < 0 ? cm : cp) : cq[db];
-        const int bi = i + (ax == 0 ? sd : 0), bj = j + (ax == 1 ? sd : 0), bk = k + (ax == 2 ? sd : 0);
-        if constexpr (!ADJ) {
-          const T vb = fwd_face_value(A, S, id + db, f, xb, c0, val);
-          out[id + db] = vb;
-          if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, bk, nx, ny)] = vb;
-        } else {
-          const T coef_mb = row_coef(A, i, j, k, ax, sd);
-          const T lb = adj_face_value(A, S, id + db, f, bi, bj, bk, xb, c0, coef_mb);
-          // the face row's transposed coefficient on this node replaces the
-          // symmetric one the stencil used
-          val += (((S.mask_f >> f) & 1) ? xb : T(2) * c2 * xb) - c2 * coef_mb * xb;
-          if ((S.mask_e >> f) & 1) val -= A.r * lb;
-          out[id + db] = lb;
-        }
-      }
-      const long long bidx =
-          fem ? (long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))
-              : 0;
-      if (!(fem && A.rmask && A.rmask[bidx])) {  // sparse rows are written by the refined kernel
-        oq[0] = val;
-        if (!ADJ && hw && fem) hw[bidx] = val;
-      }
-      if (ADJ && xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
-        const long long vid = (long long)(i - A.fl[0]) +
-                              (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
-        if (!(A.refvox && A.refvox[vid])) A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, c, i, j, k);
+        const T coef_mb = ax == 0 ? (sd > 0 ? wxp : wxm) : (sd > 0 ? wyp : wym);
+        const T lb = adj_face_row(A, S, f, bi, bj, k, ub, c0, coef_mb, n1m, n1p, n2m, n2p, pb);
+        val += (((S.mask_f >> f) & 1) ? ub : T(2) * c2 * ub) - c2 * coef_mb * ub;
+        if ((S.mask_e >> f) & 1) val -= A.r * lb;
+        gnext[idb] = lb;
       }
     }
-    cm = c0;
-    c0 = cp;
-    cp = cpp;
-    pv = pvn;
-    cq += pl;
-    pq += pl;
-    oq += pl;
-    id += pl;
+    if (!lf) {
+      gnext[id] = val;
+    } else {
+      const int bo = (C.i - A.fl[0]) + A.fn[0] * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]));
+      if (!(A.rmask && A.rmask[bo])) {  // sparse rows are written by the refined rows
+        gnext[id] = val;
+        if (!ADJ && S.hist_w) S.hist_w[bo] = val;
+      }
+      if constexpr (ADJ) {
+        if (C.xy_vox && k < A.fl[2] + A.un[2]) {
+          const T* H0 = HR + (k & (P::SH - 1)) * kHBox + oh;
+          const T* H1 = HR + ((k + 1) & (P::SH - 1)) * kHBox + oh;
+          const T u[8] = {H0[0], H0[1], H0[kHBoxX], H0[kHBoxX + 1], H1[0], H1[1], H1[kHBoxX], H1[kHBoxX + 1]};
+          const T l[8] = {c0, xp, yp, C0[kBoxX + 1], cp, Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
+          const int vz = A.un[0] * A.un[1];
+          const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
+          if (!(A.refvox && A.refvox[vid]))
+            atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
+        }
+      }
+    }
   }
+  cp_wait<0>();  // no copy outstanding when the block exits
 }
 
-// Edge set of the forward step.  Levels by the number of faces a node lies
-// on: nodes on no face take their interior row, then face, edge and corner
-// nodes; an absorbing row (Eq. (eq:abs2)) reads the new values of its
-// inward neighbours, one level down in the same tile, from shared memory.
 template <typename T, bool ADJ>
 __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t);
 
+// Edge tile of the forward step.  Levels by the number of faces a node lies
+// on: nodes on no face take their interior row, then face, edge and corner
+// nodes; an absorbing row (Eq. (eq:abs2)) reads the new values of its
+// inward neighbours, one level down in the same tile, from shared memory.
+// Every thread of the block calls it (it synchronises); nv holds 128 values.
 template <typename T>
-__global__ void __launch_bounds__(128) fwd_edge_kernel(const __grid_constant__ StepArgs<T> A) {
-  __shared__ T nv[128];
-  if ((long long)blockIdx.x >= (long long)A.nedge * A.nslots) {  // trailing blocks: refined rows
-    refined_rows<T, false>(A, ((long long)blockIdx.x - (long long)A.nedge * A.nslots) * 128 + threadIdx.x);
-    return;
-  }
-  const int si = blockIdx.x / A.nedge;
-  const int blk = blockIdx.x - si * A.nedge;
-  const int t = threadIdx.x;
+__device__ __forceinline__ void fwd_edge_tile(const StepArgs<T>& A, int si, int blk, int t, T* nv) {
   const Slot<T>& S = A.s[si];
   int i = 0, j = 0, k = 0, nf = -1, q[3];
-  const bool valid = edge_tile_node(A, blk, t, i, j, k, q, nf);
+  const bool valid = blk < A.nedge && edge_tile_node(A, blk, t, i, j, k, q, nf);
   const long long id = valid ? lin(A, i, j, k) : 0;
   const int fall = valid ? face_bits(i, j, k, A.nx, A.ny, A.nz) : 0;
   const int fb = fall & S.mask_f;
@@ -582,7 +818,7 @@ __global__ void __launch_bounds__(128) fwd_edge_kernel(const __grid_constant__ S
         const int fa = (fb >> (2 * ax)) & 3;
         if (!fa) continue;
         const int step = (fa & 1) ? 1 : -1;  // inward
-        const long long id1 = id + step * (ax == 0 ? 1LL : (ax == 1 ? (long long)A.nx : (long long)A.nx * A.ny));
+        const long long id1 = id + step * axis_stride(A, ax);
         const int t1 = edge_tile_peer(t, blk, q, ax, (fa & 1) ? 1 : 2);
         acc += S.cur[id1] - A.r * nv[t1];
       }
@@ -601,22 +837,14 @@ __global__ void __launch_bounds__(128) fwd_edge_kernel(const __grid_constant__ S
         val;
 }
 
-// Edge set of the transposed step: every thread gathers its transposed row
+// Edge tile of the transposed step: every thread gathers its transposed row
 // in parallel, then the transposed absorbing couplings (E^T) are resolved
 // from the nodes on the most faces inwards, through shared memory.
 template <typename T>
-__global__ void __launch_bounds__(128) adj_edge_kernel(const __grid_constant__ StepArgs<T> A) {
-  __shared__ T lam[128];
-  if ((long long)blockIdx.x >= (long long)A.nedge * A.nslots) {  // trailing blocks: refined rows and voxels
-    refined_rows<T, true>(A, ((long long)blockIdx.x - (long long)A.nedge * A.nslots) * 128 + threadIdx.x);
-    return;
-  }
-  const int si = blockIdx.x / A.nedge;
-  const int blk = blockIdx.x - si * A.nedge;
-  const int t = threadIdx.x;
+__device__ __forceinline__ void adj_edge_tile(const StepArgs<T>& A, int si, int blk, int t, T* lam) {
   const Slot<T>& S = A.s[si];
   int i = 0, j = 0, k = 0, nf = -1, q[3];
-  const bool valid = edge_tile_node(A, blk, t, i, j, k, q, nf);
+  const bool valid = blk < A.nedge && edge_tile_node(A, blk, t, i, j, k, q, nf);
   lam[t] = valid ? adj_rhs_inl(A, S, i, j, k) : T(0);
   __syncthreads();
   for (int level = 2; level >= 0; --level) {
@@ -642,6 +870,36 @@ __global__ void __launch_bounds__(128) adj_edge_kernel(const __grid_constant__ S
   if (!valid) return;
   S.next[lin(A, i, j, k)] = lam[t];
   pair_if_voxel(A, S, si, i, j, k);
+}
+
+// One time level of every slot in one launch of kStepBlock threads per
+// block: first the edge tiles (two 128-node tiles per block, so their short
+// dependent chains start early), then the refined sparse rows, then the
+// interior blocks.  All blocks read levels k, k-1 and write disjoint nodes
+// of level k+1.
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 4 : 3) step_kernel(const __grid_constant__ StepArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char hyb_smem[];  // kPipe<T>::bytes
+  T* sh = reinterpret_cast<T*>(hyb_smem);
+  int b = blockIdx.x;
+  if (b < A.nhe) {
+    const int ne2 = (A.nedge + 1) / 2;
+    const int si = b / ne2;
+    const int half = (int)(threadIdx.x >> 7);
+    const int blk = 2 * (b - si * ne2) + half;
+    const int t = (int)(threadIdx.x & 127);
+    if constexpr (ADJ)
+      adj_edge_tile<T>(A, si, blk, t, sh + 128 * half);
+    else
+      fwd_edge_tile<T>(A, si, blk, t, sh + 128 * half);
+    return;
+  }
+  b -= A.nhe;
+  if (b < A.nhr) {
+    refined_rows<T, ADJ>(A, (long long)b * kStepBlock + threadIdx.x);
+    return;
+  }
+  interior_block<T, ADJ>(A, b - A.nhr, sh);
 }
 
 // Lattices with fewer than 5 nodes on some axis: every node by the generic
@@ -856,43 +1114,54 @@ __global__ void extract_owned_kernel(const __grid_constant__ StepArgs<T> A, cons
 }  // namespace
 
 template <typename T>
-void launch_forward_bulk(const StepArgs<T>& a, cudaStream_t st) {
-  if (a.small) {
-    const long long n = (long long)a.nx * a.ny * a.nz * a.nslots;
-    fwd_all_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
-    return;
-  }
-  const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
-  if (grid) bulk_kernel<T, false><<<grid, kTileX * kTileY, 0, st>>>(a);
-}
-
-template <typename T>
 unsigned refined_blocks(const StepArgs<T>& a, bool adjoint) {
   const long long n = (long long)(4 * a.nr + (adjoint ? ((a.nref + 3) & ~3) : 0)) * a.nslots;
-  return (unsigned)((n + 127) / 128);
+  return (unsigned)((n + kStepBlock - 1) / kStepBlock);
 }
 
-template <typename T>
-void launch_forward_shell(const StepArgs<T>& a, cudaStream_t st) {
-  if (a.small) return;
-  fwd_edge_kernel<T><<<(unsigned)(a.nedge * a.nslots) + refined_blocks(a, false), 128, 0, st>>>(a);
-}
-
-template <typename T>
-void launch_adjoint_bulk(const StepArgs<T>& a, cudaStream_t st) {
+template <typename T, bool ADJ>
+void launch_step(const StepArgs<T>& a, cudaStream_t st) {
   if (a.small) {
     const long long n = (long long)a.nx * a.ny * a.nz * a.nslots;
-    adj_all_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+    if (ADJ)
+      adj_all_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+    else
+      fwd_all_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
     return;
   }
-  const unsigned grid = (unsigned)(a.npb * a.nzc * a.nslots);
-  if (grid) bulk_kernel<T, true><<<grid, kTileX * kTileY, 0, st>>>(a);
+  StepArgs<T> b = a;
+  b.nhe = ((a.nedge + 1) / 2) * a.nslots;
+  b.nhr = (int)refined_blocks(a, ADJ);
+  const long long grid = (long long)b.nhe + b.nhr + (long long)a.npb * a.nzc * a.nslots;
+  step_kernel<T, ADJ><<<(unsigned)grid, kStepBlock, kPipe<T>::bytes, st>>>(b);
 }
 
 template <typename T>
-void launch_adjoint_shell(const StepArgs<T>& a, cudaStream_t st) {
-  if (a.small) return;
-  adj_edge_kernel<T><<<(unsigned)(a.nedge * a.nslots) + refined_blocks(a, true), 128, 0, st>>>(a);
+void launch_forward_step(const StepArgs<T>& a, cudaStream_t st) {
+  launch_step<T, false>(a, st);
+}
+
+template <typename T>
+void launch_adjoint_step(const StepArgs<T>& a, cudaStream_t st) {
+  launch_step<T, true>(a, st);
+}
+
+template <typename T, bool ADJ>
+int step_occupancy() {
+  int n = 0;
+  if (cudaFuncSetAttribute(step_kernel<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipe<T>::bytes) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, ADJ>, kStepBlock, kPipe<T>::bytes) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+int step_blocks_per_sm(int precision, int adjoint) {
+  if (precision == HYB_FP32) return adjoint ? step_occupancy<float, true>() : step_occupancy<float, false>();
+  return adjoint ? step_occupancy<double, true>() : step_occupancy<double, false>();
 }
 
 template <typename T>
@@ -933,10 +1202,8 @@ void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStre
 }
 
 #define HYB_INSTANTIATE(T)                                                                       \
-  template void launch_forward_bulk<T>(const StepArgs<T>&, cudaStream_t);                        \
-  template void launch_forward_shell<T>(const StepArgs<T>&, cudaStream_t);                       \
-  template void launch_adjoint_bulk<T>(const StepArgs<T>&, cudaStream_t);                        \
-  template void launch_adjoint_shell<T>(const StepArgs<T>&, cudaStream_t);                       \
+  template void launch_forward_step<T>(const StepArgs<T>&, cudaStream_t);                        \
+  template void launch_adjoint_step<T>(const StepArgs<T>&, cudaStream_t);                        \
   template void launch_pair<T>(const StepArgs<T>&, const T*, const T*, cudaStream_t);            \
   template void launch_set_coef<T>(const StepArgs<T>&, T*, const double*, double, int*,         \
                                    cudaStream_t);                                                \
