@@ -74,10 +74,15 @@ struct hyb_mesh {
   hyb_mesh_desc d;
   cudaStream_t st = nullptr;
   int n[3] = {0, 0, 0};
-  long long N = 0;
+  long long N = 0;    // lattice nodes
+  int px = 0;         // row pitch of the lattice fields (multiple of 4)
+  long long Np = 0;   // entries of one lattice field (px ny nz)
   bool fem = false;
   int fl[3], fh[3], fn[3], wl[3], wn[3], un[3];
+  int wx0 = 0, wpx = 0;  // edge-weight arrays: x origin and row pitch (multiples of 4)
+  int hx0 = 0, hpx = 0;  // FEM-owned (history) box: x origin and row pitch (multiples of 4)
   long long wsz = 0, nu = 0, nown = 0;
+  long long hbox = 0;    // entries of one history box (hpx fn1 fn2)
   int obs_stride = 0;
   int abc_mask = 0;
   DevBuf W, G, flag, U, L, hist, ckpt, part, scal, g, atrial, cot, trace;
@@ -250,7 +255,7 @@ int mask_at(const hyb_mesh* m, const hyb_source& s, int k, double dt) {
 // the SMs kStepWaves times at the step kernel's occupancy; the edge tiles
 // cover the nodes within one node of two faces.  Lattices with fewer than 5
 // nodes on an axis use a single generic kernel instead.
-constexpr int kStepWaves = 4;
+constexpr int kStepWaves = 2;
 
 void step_geometry(const hyb_mesh* m, int nslots, int* npb, int* ntx, int* zchunk, int* nzc, int* small,
                    int* nedge) {
@@ -260,9 +265,11 @@ void step_geometry(const hyb_mesh* m, int nslots, int* npb, int* ntx, int* zchun
   *ntx = (int)((bx + kTileX - 1) / kTileX);
   const int nty = (int)((by + kTileY - 1) / kTileY);
   *npb = *ntx * nty;
+  // z chunks per tile: as many as fit kStepWaves full waves (rounded down,
+  // so that no wave is left part-filled)
   const long long target = (long long)std::max(m->nsm, 1) * std::max(m->bps, 1) * kStepWaves;
   const long long per_z = (long long)(*npb) * nslots;
-  long long want = (target + per_z - 1) / per_z;
+  long long want = target / per_z;
   if (want < 1) want = 1;
   long long z = (bz + want - 1) / want;
   z = std::max<long long>(z, 2);
@@ -380,8 +387,8 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   if (m->nc == 0) return HYB_OK;
   double K8[64], m8[8], K9[81], m9[9];
   unit_voxel_matrices(K8, m8, K9, m9);
-  const long long N = m->N;
-  auto lid = [&](int i, int j, int k) { return (long long)i + (long long)m->n[0] * (j + (long long)m->n[1] * k); };
+  const long long N = m->Np;  // centre columns follow the lattice field entries
+  auto lid = [&](int i, int j, int k) { return (long long)i + (long long)m->px * (j + (long long)m->n[1] * k); };
   auto unk_of = [&](int i, int j, int k) -> long long {  // voxel with origin (i,j,k)
     const int x = i - m->fl[0], y = j - m->fl[1], z = k - m->fl[2];
     if (x < 0 || y < 0 || z < 0 || x >= m->un[0] || y >= m->un[1] || z >= m->un[2]) return -1;
@@ -389,12 +396,12 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   };
   // lattice rows: corners of refined voxels, in lattice order
   std::vector<long long> rows;
-  std::vector<unsigned char> rmask((size_t)m->nown, 0);
+  std::vector<unsigned char> rmask((size_t)m->hbox, 0);
   for (int u : refid) {
     const int x = u % m->un[0], y = (u / m->un[0]) % m->un[1], z = u / (m->un[0] * m->un[1]);
     for (int c = 0; c < 8; ++c) {
       const int i = m->fl[0] + x + (c & 1), j = m->fl[1] + y + ((c >> 1) & 1), k = m->fl[2] + z + (c >> 2);
-      const long long b = (long long)(i - m->fl[0]) + (long long)m->fn[0] * ((j - m->fl[1]) + (long long)m->fn[1] * (k - m->fl[2]));
+      const long long b = (long long)(i - m->hx0) + (long long)m->hpx * ((j - m->fl[1]) + (long long)m->fn[1] * (k - m->fl[2]));
       if (!rmask[b]) {
         rmask[b] = 1;
         rows.push_back(lid(i, j, k));
@@ -429,7 +436,7 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
     bound = std::max(bound, std::fabs(sum) + absum);
   };
   for (long long p : rows) {
-    const int i = (int)(p % m->n[0]), j = (int)((p / m->n[0]) % m->n[1]), k = (int)(p / ((long long)m->n[0] * m->n[1]));
+    const int i = (int)(p % m->px), j = (int)((p / m->px) % m->n[1]), k = (int)(p / ((long long)m->px * m->n[1]));
     std::vector<std::pair<long long, std::pair<int, double>>> ent;
     double M = 0.0;
     for (int c = 0; c < 8; ++c) {
@@ -485,6 +492,62 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   return HYB_OK;
 }
 
+// Tiled tensor maps for the step kernel's bulk copies (cuTensorMapEncodeTiled
+// through the runtime's driver entry point, so the library does not link the
+// driver library directly).
+typedef CUresult (*TmapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TmapEncodeFn tmap_encoder() {
+  static const TmapEncodeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (TmapEncodeFn) nullptr;
+    }
+    return (TmapEncodeFn)p;
+  }();
+  return fn;
+}
+
+// 3-D map of d0 x d1 x d2 elements with row pitch p0 and plane pitch p1
+// (elements; 16-byte multiples), box b0 x b1 x 1.
+template <typename T>
+hyb_status encode_map(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t p0,
+                      uint64_t p1, uint32_t b0, uint32_t b1) {
+  const TmapEncodeFn enc = tmap_encoder();
+  if (!enc) return fail(HYB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {p0 * sizeof(T), p1 * sizeof(T)};
+  const cuuint32_t box[3] = {b0, b1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                         const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HYB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return HYB_OK;
+}
+
+// Maps of one sweep: the field buffer `field` (3 levels x nsrc slots), the
+// edge weights, and (transposed step with pairing) the history buffer of
+// `hist_levels` levels.
+template <typename T>
+hyb_status step_maps(const hyb_mesh* m, StepArgs<T>& A, const DevBuf& field, int nsrc, int hist_levels) {
+  HYB_TRY(encode_map<T>(&A.tmf, field.p, m->n[0], m->n[1], (uint64_t)m->n[2] * 3 * nsrc, m->px,
+                        (uint64_t)m->px * m->n[1], 36, kTileY + 2));
+  if (m->fem && m->wsz > 0)
+    HYB_TRY(encode_map<T>(&A.tmw, m->W.p, m->wpx, m->wn[1], 3ull * m->wn[2], m->wpx, (uint64_t)m->wpx * m->wn[1],
+                          36, kTileY + 1));
+  if (hist_levels > 0 && m->hbox > 0)
+    HYB_TRY(encode_map<T>(&A.tmh, m->hist.p, m->hpx, m->fn[1], (uint64_t)m->fn[2] * nsrc * hist_levels, m->hpx,
+                          (uint64_t)m->hpx * m->fn[1], 36, kTileY + 1));
+  return HYB_OK;
+}
+
 template <typename T>
 void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   std::memset(&A, 0, sizeof(A));
@@ -500,6 +563,12 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
     A.un[d] = m->un[d];
   }
   A.wsz = m->wsz;
+  A.px = m->px;
+  A.wx0 = m->wx0;
+  A.wpx = m->wpx;
+  A.hx0 = m->hx0;
+  A.hpx = m->hpx;
+  A.err = (int*)m->flag.p + 1;
   A.W = (const T*)m->W.p;
   A.G = (double*)m->G.p;
   const double h = m->d.h;
@@ -507,7 +576,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.r = (T)((h - dt) / (h + dt));
   step_geometry(m, nslots, &A.npb, &A.ntx, &A.zchunk, &A.nzc, &A.small, &A.nedge);
   A.nslots = nslots;
-  A.nlat = m->N;
+  A.nlat = m->Np;
   if (m->nc > 0) {
     A.nr = m->nr;
     A.nrl = m->nrl;
@@ -533,7 +602,7 @@ T* centre_buf(const hyb_mesh* m, const DevBuf& b, int nsrc, int s, int level) {
 template <typename T>
 T* field_buf(const hyb_mesh* m, const DevBuf& b, int nsrc, int s, int level) {
   const int r = ((level % 3) + 3) % 3;
-  return (T*)b.p + ((size_t)r * nsrc + s) * (size_t)m->N;
+  return (T*)b.p + ((size_t)r * nsrc + s) * (size_t)m->Np;
 }
 
 // Fill the forward slots of step k (u^k -> u^{k+1}).
@@ -547,7 +616,7 @@ void forward_slots(const hyb_mesh* m, StepArgs<T>& A, const hyb_source* src, int
     S.next = field_buf<T>(m, m->U, nsrc, s, k + 1);
     S.obs_w = trace ? trace + ((size_t)s * (nsteps + 1) + (k + 1)) * (size_t)m->obs_stride : nullptr;
     S.obs_r = nullptr;
-    S.hist_w = hist_level ? hist_level + (size_t)s * m->nown : nullptr;
+    S.hist_w = hist_level ? hist_level + (size_t)s * m->hbox : nullptr;
     S.hist_r = nullptr;
     S.ccur = centre_buf<T>(m, m->CU, nsrc, s, k);
     S.cprev = centre_buf<T>(m, m->CU, nsrc, s, k - 1);
@@ -561,6 +630,9 @@ void forward_slots(const hyb_mesh* m, StepArgs<T>& A, const hyb_source* src, int
     S.mask_e = 0;
     S.mask_c = 0;
     S.src_face = f;
+    S.zf_cur = (int)((S.cur - (const T*)m->U.p) / ((long long)m->px * m->n[1]));
+    S.zf_prev = (int)((S.prev - (const T*)m->U.p) / ((long long)m->px * m->n[1]));
+    S.zf_hist = 0;
     S.srcval = (T)(dt * dt * 2.0 * p / m->d.h);
     S.obs_face = src[s].face;
   }
@@ -569,7 +641,7 @@ void forward_slots(const hyb_mesh* m, StepArgs<T>& A, const hyb_source* src, int
 template <typename T>
 hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int nsrc, int nsteps,
                         double dt, T* trace, bool keep) {
-  const size_t fb = (size_t)m->N * sizeof(T);
+  const size_t fb = (size_t)m->Np * sizeof(T);
   const int C = m->d.ckpt_every;
   const bool ckpt = C > 0;
   const size_t cb = (size_t)m->nc * sizeof(T);  // centre values of one level
@@ -577,18 +649,19 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
   HYB_TRY(ensure(m, m->CU, 3 * (size_t)nsrc * cb));
   if (keep && m->nown > 0) {
     if (!ckpt) {
-      HYB_TRY(ensure(m, m->hist, (size_t)nsteps * nsrc * m->nown * sizeof(T)));
+      HYB_TRY(ensure(m, m->hist, (size_t)nsteps * nsrc * m->hbox * sizeof(T)));
       HYB_TRY(ensure(m, m->chist, (size_t)nsteps * nsrc * cb));
     } else {
       const size_t nseg = ((size_t)nsteps + C - 1) / C;
       HYB_TRY(ensure(m, m->ckpt, nseg * 2 * (size_t)nsrc * fb));
       HYB_TRY(ensure(m, m->cckpt, nseg * 2 * (size_t)nsrc * cb));
-      HYB_TRY(ensure(m, m->hist, (size_t)C * nsrc * m->nown * sizeof(T)));
+      HYB_TRY(ensure(m, m->hist, (size_t)C * nsrc * m->hbox * sizeof(T)));
       HYB_TRY(ensure(m, m->chist, (size_t)C * nsrc * cb));
     }
   }
   StepArgs<T> A;
   base_args(m, A, dt, nsrc);
+  HYB_TRY(step_maps<T>(m, A, m->U, nsrc, 0));
   if (m->fem) {
     launch_set_coef<T>(A, (T*)m->W.p, a, m->d.a_max, (int*)m->flag.p, m->st);
     HYB_LAUNCHED(m);
@@ -611,10 +684,10 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
     T* hist = (T*)m->hist.p;
     T* chist = (T*)m->chist.p;
     if (keep && !ckpt && m->nown > 0) {
-      HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->nown * sizeof(T), st));
+      HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->hbox * sizeof(T), st));
       if (m->nc) HYB_CU(cudaMemsetAsync(chist, 0, (size_t)nsrc * cb, st));
     }
-    const size_t lvl = (size_t)nsrc * m->nown;
+    const size_t lvl = (size_t)nsrc * m->hbox;
     const size_t clvl = (size_t)nsrc * m->nc;
     for (int k = 0; k < nsteps; ++k) {
       if (keep && ckpt && m->nown > 0 && k > 0 && k % C == 0) {
@@ -663,7 +736,7 @@ void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const
     S.obs_w = nullptr;
     S.obs_r = cot ? cot + ((size_t)s * (nsteps + 1) + j) * (size_t)m->obs_stride : nullptr;
     S.hist_w = nullptr;
-    S.hist_r = hist_level ? hist_level + (size_t)s * m->nown : nullptr;
+    S.hist_r = hist_level ? hist_level + (size_t)s * m->hbox : nullptr;
     S.ccur = centre_buf<T>(m, m->CL, nsrc, s, j + 1);
     S.cprev = centre_buf<T>(m, m->CL, nsrc, s, j + 2);
     S.cnext = centre_buf<T>(m, m->CL, nsrc, s, j);
@@ -671,6 +744,9 @@ void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const
     S.chist_r = (hist_level && m->nc) ? chist_level + (size_t)s * m->nc : nullptr;
     S.srcval = T(0);
     S.src_face = -1;
+    S.zf_cur = (int)((S.cur - (const T*)m->L.p) / ((long long)m->px * m->n[1]));
+    S.zf_prev = (int)((S.prev - (const T*)m->L.p) / ((long long)m->px * m->n[1]));
+    S.zf_hist = S.hist_r ? (int)((S.hist_r - (const T*)m->hist.p) / ((long long)m->hpx * m->fn[1])) : 0;
     S.mask_f = mask_at(m, m->src[s], j, m->dt);
     S.mask_e = mask_at(m, m->src[s], j - 1, m->dt);
     S.mask_c = mask_at(m, m->src[s], j + 1, m->dt);
@@ -684,7 +760,7 @@ hyb_status pair_first(hyb_mesh* m, StepArgs<T>& A, const T* level0, const T* cle
   for (int s = 0; s < m->nsrc; ++s) {
     StepArgs<T> B = A;
     B.G = (double*)m->G.p + (size_t)s * m->nu;
-    launch_pair<T>(B, level0 + (size_t)s * m->nown, field_buf<T>(m, m->L, m->nsrc, s, 1), st);
+    launch_pair<T>(B, level0 + (size_t)s * m->hbox, field_buf<T>(m, m->L, m->nsrc, s, 1), st);
     HYB_LAUNCHED(m);
   }
   if (m->nc > 0) {
@@ -700,7 +776,7 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   if (!m->have_fwd) return fail(HYB_ERR_STATE, "hyb_adjoint needs a preceding hyb_forward of this mesh");
   const int nsrc = m->nsrc, nsteps = m->nsteps;
   const double dt = m->dt;
-  const size_t fb = (size_t)m->N * sizeof(T);
+  const size_t fb = (size_t)m->Np * sizeof(T);
   const int C = m->d.ckpt_every;
   const bool ckpt = C > 0;
   const size_t cb = (size_t)m->nc * sizeof(T);
@@ -711,6 +787,8 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   base_args(m, A, dt, nsrc);
   StepArgs<T> F;   // recomputed forward steps
   base_args(m, F, dt, nsrc);
+  HYB_TRY(step_maps<T>(m, A, m->L, nsrc, ckpt ? C : nsteps));
+  HYB_TRY(step_maps<T>(m, F, m->U, nsrc, 0));
   auto body = [&](cudaStream_t st) -> hyb_status {
     if (!accumulate) HYB_CU(cudaMemsetAsync(m->G.p, 0, (size_t)nsrc * m->nu * sizeof(double), st));
     for (int s = 0; s < nsrc; ++s) {
@@ -723,7 +801,7 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
     }
     T* hist = (T*)m->hist.p;
     T* chist = (T*)m->chist.p;
-    const size_t lvl = (size_t)nsrc * m->nown;
+    const size_t lvl = (size_t)nsrc * m->hbox;
     const size_t clvl = (size_t)nsrc * m->nc;
     const bool pairing = m->nu > 0 && m->nown > 0;
     auto adj_step = [&](int j, const T* hl, const T* chl) -> hyb_status {
@@ -770,7 +848,7 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
               HYB_CU(cudaMemcpyAsync(cm, cbase + cb, cb, cudaMemcpyDeviceToDevice, st));
             }
           }
-          launch_extract_owned<T>(F, u0, hist + (size_t)s * m->nown, st);
+          launch_extract_owned<T>(F, u0, hist + (size_t)s * m->hbox, st);
           HYB_LAUNCHED(m);
           if (m->nc) HYB_CU(cudaMemcpyAsync(chist + (size_t)s * m->nc, c0, cb, cudaMemcpyDeviceToDevice, st));
         }
@@ -972,6 +1050,8 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   m->st = (cudaStream_t)stream;
   for (int a = 0; a < 3; ++a) m->n[a] = d->n[a];
   m->N = (long long)d->n[0] * d->n[1] * d->n[2];
+  m->px = (d->n[0] + 3) & ~3;
+  m->Np = (long long)m->px * d->n[1] * d->n[2];
   m->fem = fem;
   for (int a = 0; a < 3; ++a) {
     if (fem) {
@@ -990,22 +1070,29 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
       m->un[a] = 0;
     }
   }
-  m->wsz = (long long)m->wn[0] * m->wn[1] * m->wn[2];
+  if (fem) {
+    m->wx0 = m->wl[0] & ~3;
+    m->wpx = (m->wl[0] + m->wn[0] - m->wx0 + 3) & ~3;
+    m->hx0 = m->fl[0] & ~3;
+    m->hpx = (m->fh[0] + 1 - m->hx0 + 3) & ~3;
+  }
+  m->wsz = (long long)m->wpx * m->wn[1] * m->wn[2];
   m->nu = (long long)m->un[0] * m->un[1] * m->un[2];
   m->nown = (long long)m->fn[0] * m->fn[1] * m->fn[2];
+  m->hbox = (long long)m->hpx * m->fn[1] * m->fn[2];
   m->obs_stride = std::max(d->n[0] * d->n[1], std::max(d->n[0] * d->n[2], d->n[1] * d->n[2]));
   for (int f = 0; f < 6; ++f)
     if (d->bc[f] == HYB_BC_ABC) m->abc_mask |= 1 << f;
   m->dt_max = d->h / std::sqrt(3.0 * d->a_max);
   hyb_status st = HYB_OK;
   if (fem) st = ensure(m, m->W, 3 * (size_t)m->wsz * esize(m));
-  if (st == HYB_OK) st = ensure(m, m->flag, sizeof(int));
+  if (st == HYB_OK) st = ensure(m, m->flag, 2 * sizeof(int));
   if (st == HYB_OK && cudaMallocHost(&m->hscal, 16 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     m->hscal = nullptr;
     st = fail(HYB_ERR_OOM, "cudaMallocHost failed");
   }
-  if (st == HYB_OK && cudaMemsetAsync(m->flag.p, 0, sizeof(int), m->st) != cudaSuccess)
+  if (st == HYB_OK && cudaMemsetAsync(m->flag.p, 0, 2 * sizeof(int), m->st) != cudaSuccess)
     st = fail(HYB_ERR_CUDA, "cudaMemsetAsync failed");
   if (st == HYB_OK && cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -1126,7 +1213,7 @@ hyb_status hyb_cg_step(hyb_mesh* m, double* a, const void* u_obs, const hyb_sour
 hyb_status hyb_get_field(hyb_mesh* m, int32_t which, int32_t isrc, void* out) {
   if (!m || !out) return fail(HYB_ERR_ARG, "null argument");
   if (!m->have_run || isrc < 0 || isrc >= m->nsrc) return fail(HYB_ERR_STATE, "no such field");
-  const size_t fb = (size_t)m->N * esize(m);
+  const size_t fb = (size_t)m->Np * esize(m);
   const char* src = nullptr;
   const int r_u_last = ((m->nsteps % 3) + 3) % 3;
   const int r_u_prev = (((m->nsteps - 1) % 3) + 3) % 3;
@@ -1140,7 +1227,9 @@ hyb_status hyb_get_field(hyb_mesh* m, int32_t which, int32_t isrc, void* out) {
   } else {
     return fail(HYB_ERR_ARG, "bad field selector");
   }
-  HYB_CU(cudaMemcpyAsync(out, src, fb, cudaMemcpyDeviceToDevice, m->st));
+  const size_t es = esize(m);  // drop the row padding
+  HYB_CU(cudaMemcpy2DAsync(out, (size_t)m->n[0] * es, src, (size_t)m->px * es, (size_t)m->n[0] * es,
+                           (size_t)m->n[1] * m->n[2], cudaMemcpyDeviceToDevice, m->st));
   return HYB_OK;
 }
 
@@ -1187,13 +1276,15 @@ hyb_status hyb_misfit_noalloc(const void* trace, const void* u_obs, int32_t prec
 hyb_status hyb_sync(hyb_mesh* m) {
   if (!m) return fail(HYB_ERR_ARG, "null mesh");
   // stream-ordered copies only: other streams (other meshes) keep running
-  int* flag = (int*)(m->hscal + 15);
-  HYB_CU(cudaMemcpyAsync(flag, m->flag.p, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+  int* flag = (int*)(m->hscal + 14);
+  HYB_CU(cudaMemcpyAsync(flag, m->flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, m->st));
   HYB_CU(cudaStreamSynchronize(m->st));
-  if (*flag) {
-    HYB_CU(cudaMemsetAsync(m->flag.p, 0, sizeof(int), m->st));
+  if (flag[0] || flag[1]) {
+    const int f0 = flag[0];
+    HYB_CU(cudaMemsetAsync(m->flag.p, 0, 2 * sizeof(int), m->st));
     HYB_CU(cudaStreamSynchronize(m->st));
-    return fail(HYB_ERR_CFL, "a coefficient value exceeded a_max (or was not finite)");
+    if (f0) return fail(HYB_ERR_CFL, "a coefficient value exceeded a_max (or was not finite)");
+    return fail(HYB_ERR_CUDA, "a step kernel timed out waiting for its staged planes");
   }
   return HYB_OK;
 }

@@ -2,6 +2,7 @@
 // the step kernels and the host-side launchers.  Not part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -10,9 +11,9 @@
 namespace hyb {
 
 constexpr int kMaxSlots = 16;   // problems advanced by one step launch
-constexpr int kStepBlock = 256;  // threads per block of the step kernel
+constexpr int kStepBlock = 288;  // threads per block of the step kernel (9 warps)
 constexpr int kTileX = 32;       // interior thread tile (x): one warp per tile row
-constexpr int kTileY = 8;        // interior thread tile (y)
+constexpr int kTileY = 16;       // interior tile (y): two rows per consumer thread
 constexpr int kReduceBlocks = 512;
 constexpr int kReduceThreads = 256;
 
@@ -37,15 +38,29 @@ struct Slot {
   T* cnext;
   T* chist_w;        // forward: centre values of u^{k+1} for the gradient (or nullptr)
   const T* chist_r;  // adjoint: centre values of u^j (or nullptr)
+  int zf_cur, zf_prev;  // plane 0 of cur / prev in the field tensor map (tmf)
+  int zf_hist;          // plane 0 of hist_r's box in the history tensor map (tmh)
 };
 
+// Lattice fields are stored with a row pitch px >= nx (a multiple of 4, so
+// that rows start on 16-byte boundaries): node (i, j, k) of a field is
+// element i + px (j + ny k).  The edge-weight box and the FEM-owned box
+// (history) likewise start at an x origin that is a multiple of 4 (wx0,
+// hx0) and have row pitches wpx, hpx that are multiples of 4.
 template <typename T>
 struct StepArgs {
+  CUtensorMap tmf;   // field buffer (all levels and slots): {nx, ny, planes}, box 36 x (kTileY + 2) x 1
+  CUtensorMap tmw;   // edge weights: {wpx, wn1, 3 wn2}, box 36 x (kTileY + 1) x 1
+  CUtensorMap tmh;   // history: {hpx, fn1, fn2 x boxes}, box 36 x (kTileY + 1) x 1
+  int* err;          // [0]: set when a pipeline wait timed out
   int nx, ny, nz;
+  int px;            // row pitch of lattice fields
   int fl[3], fh[3];  // FEM-owned node range (inclusive); fl[0] > fh[0]: no FEM
   int fn[3];         // FEM-owned box dims (history layout)
   int wl[3], wn[3];  // edge-weight box: nodes fl-1 .. fh+1
-  long long wsz;     // entries per axis array of the edge-weight box
+  int wx0, wpx;      // x origin and row pitch of the edge-weight arrays
+  long long wsz;     // entries per axis array of the edge-weight box (wpx wn1 wn2)
+  int hx0, hpx;      // x origin and row pitch of the FEM-owned (history) box
   const T* W;        // [3][wsz]: weight of the edge (p, p + e_axis)
   double* G;         // FP64 gradient accumulator over unknown voxels (adjoint)
   int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
@@ -61,7 +76,7 @@ struct StepArgs {
   // refined region (nr == 0: nothing refined).  Sparse rows: the nrl
   // lattice nodes touching a refined voxel, then the nref centre nodes.
   int nr, nrl, nref;
-  long long nlat;             // lattice nodes (column ids >= nlat are centres)
+  long long nlat;             // lattice field entries (column ids >= nlat are centres)
   const int* rrow;            // lattice id of each lattice sparse row
   const int* rptr;            // CSR row pointers [nr + 1]
   const int* rcol;            // column: lattice id, or nlat + centre index

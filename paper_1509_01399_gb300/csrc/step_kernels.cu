@@ -31,6 +31,7 @@
 // The same launch accumulates, per unknown voxel and in FP64, the sum over
 // the voxel's 12 axis edges of w_e (u_p - u_q)(lambda_p - lambda_q) with
 // w_e = 1/3 or 1/6; the host scales it by -tau^2 / h^2 (Eq. (gradient1)).
+#include "async_copy.cuh"
 #include "hyb_internal.h"
 
 namespace hyb {
@@ -41,9 +42,16 @@ __device__ __forceinline__ int face_bits(int i, int j, int k, int nx, int ny, in
          (k == 0 ? 16 : 0) | (k == nz - 1 ? 32 : 0);
 }
 
+// field index of node (i, j, k)
 template <typename T>
 __device__ __forceinline__ long long lin(const StepArgs<T>& A, int i, int j, int k) {
-  return (long long)i + (long long)A.nx * ((long long)j + (long long)A.ny * k);
+  return (long long)i + (long long)A.px * ((long long)j + (long long)A.ny * k);
+}
+
+// index of node (i, j, k) in the FEM-owned (history) box
+template <typename T>
+__device__ __forceinline__ long long hidx(const StepArgs<T>& A, int i, int j, int k) {
+  return (long long)(i - A.hx0) + (long long)A.hpx * ((long long)(j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]));
 }
 
 template <typename T>
@@ -54,8 +62,8 @@ __device__ __forceinline__ bool fem_owned(const StepArgs<T>& A, int i, int j, in
 
 template <typename T>
 __device__ __forceinline__ long long widx(const StepArgs<T>& A, int i, int j, int k) {
-  return (long long)(i - A.wl[0]) +
-         (long long)A.wn[0] * ((long long)(j - A.wl[1]) + (long long)A.wn[1] * (k - A.wl[2]));
+  return (long long)(i - A.wx0) +
+         (long long)A.wpx * ((long long)(j - A.wl[1]) + (long long)A.wn[1] * (k - A.wl[2]));
 }
 
 // sum over the six axis edges of W_e (u_nb - u_c) at a FEM-owned node
@@ -66,10 +74,10 @@ __device__ __forceinline__ T fem_lap(const StepArgs<T>& A, const T* __restrict__
   const T* Wx = A.W;
   const T* Wy = A.W + A.wsz;
   const T* Wz = A.W + 2 * A.wsz;
-  const long long wy = A.wn[0];
-  const long long wz = (long long)A.wn[0] * A.wn[1];
-  return Wx[w] * (u[id + 1] - c) + Wx[w - 1] * (u[id - 1] - c) + Wy[w] * (u[id + A.nx] - c) +
-         Wy[w - wy] * (u[id - A.nx] - c) + Wz[w] * (zp - c) + Wz[w - wz] * (zm - c);
+  const long long wy = A.wpx;
+  const long long wz = (long long)A.wpx * A.wn[1];
+  return Wx[w] * (u[id + 1] - c) + Wx[w - 1] * (u[id - 1] - c) + Wy[w] * (u[id + A.px] - c) +
+         Wy[w - wy] * (u[id - A.px] - c) + Wz[w] * (zp - c) + Wz[w - wz] * (zm - c);
 }
 
 // Laplacian part (without 1/h^2) of a non-absorbing row at any node:
@@ -77,16 +85,16 @@ __device__ __forceinline__ T fem_lap(const StepArgs<T>& A, const T* __restrict__
 template <typename T>
 __device__ __noinline__ T row_lap(const StepArgs<T>& A, const T* __restrict__ u, int i, int j, int k) {
   const long long id = lin(A, i, j, k);
-  const long long sz = (long long)A.nx * A.ny;
+  const long long sz = (long long)A.px * A.ny;
   const T c = u[id];
   if (fem_owned(A, i, j, k)) return fem_lap(A, u, id, i, j, k, c, u[id - sz], u[id + sz]);
   T lap = T(0);
   if (i == 0) lap += T(2) * (u[id + 1] - c);
   else if (i == A.nx - 1) lap += T(2) * (u[id - 1] - c);
   else lap += (u[id - 1] - c) + (u[id + 1] - c);
-  if (j == 0) lap += T(2) * (u[id + A.nx] - c);
-  else if (j == A.ny - 1) lap += T(2) * (u[id - A.nx] - c);
-  else lap += (u[id - A.nx] - c) + (u[id + A.nx] - c);
+  if (j == 0) lap += T(2) * (u[id + A.px] - c);
+  else if (j == A.ny - 1) lap += T(2) * (u[id - A.px] - c);
+  else lap += (u[id - A.px] - c) + (u[id + A.px] - c);
   if (k == 0) lap += T(2) * (u[id + sz] - c);
   else if (k == A.nz - 1) lap += T(2) * (u[id - sz] - c);
   else lap += (u[id - sz] - c) + (u[id + sz] - c);
@@ -128,7 +136,7 @@ template <typename T>
 __device__ __forceinline__ T row_coef(const StepArgs<T>& A, int i, int j, int k, int ax, int s) {
   if (fem_owned(A, i, j, k)) {
     const long long w = widx(A, i, j, k);
-    const long long ws = ax == 0 ? 1 : (ax == 1 ? (long long)A.wn[0] : (long long)A.wn[0] * A.wn[1]);
+    const long long ws = ax == 0 ? 1 : (ax == 1 ? (long long)A.wpx : (long long)A.wpx * A.wn[1]);
     return A.W[ax * A.wsz + (s > 0 ? w : w - ws)];
   }
   const int c = ax == 0 ? i : (ax == 1 ? j : k);
@@ -141,8 +149,8 @@ template <typename T>
 __device__ __forceinline__ T row_diag(const StepArgs<T>& A, int i, int j, int k) {
   if (fem_owned(A, i, j, k)) {
     const long long w = widx(A, i, j, k);
-    const long long wy = A.wn[0];
-    const long long wz = (long long)A.wn[0] * A.wn[1];
+    const long long wy = A.wpx;
+    const long long wz = (long long)A.wpx * A.wn[1];
     const T* W = A.W;
     return -(W[w] + W[w - 1] + W[A.wsz + w] + W[A.wsz + w - wy] + W[2 * A.wsz + w] +
              W[2 * A.wsz + w - wz]);
@@ -272,11 +280,11 @@ __device__ __forceinline__ T pair_sum(const T u[8], const T l[8]) {
 template <typename T>
 __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restrict__ hb,
                                         const T* __restrict__ lam, int i, int j, int k) {
-  const long long hy = A.fn[0];
-  const long long hz = (long long)A.fn[0] * A.fn[1];
-  const long long h0 = (long long)(i - A.fl[0]) + hy * (j - A.fl[1]) + hz * (k - A.fl[2]);
-  const long long ly = A.nx;
-  const long long lz = (long long)A.nx * A.ny;
+  const long long hy = A.hpx;
+  const long long hz = (long long)A.hpx * A.fn[1];
+  const long long h0 = hidx(A, i, j, k);
+  const long long ly = A.px;
+  const long long lz = (long long)A.px * A.ny;
   const long long l0 = lin(A, i, j, k);
   T u[8], l[8];
 #pragma unroll
@@ -298,13 +306,13 @@ __device__ __forceinline__ T lap7(T xm, T xp, T ym, T yp, T zm, T zp, T c) {
 template <typename T>
 __device__ __forceinline__ T row_lap_inl(const StepArgs<T>& A, const T* __restrict__ u, int i, int j, int k) {
   const long long id = lin(A, i, j, k);
-  const long long sz = (long long)A.nx * A.ny;
+  const long long sz = (long long)A.px * A.ny;
   const T c = u[id];
   if (fem_owned(A, i, j, k)) return fem_lap(A, u, id, i, j, k, c, u[id - sz], u[id + sz]);
   const T xm = i > 0 ? u[id - 1] : u[id + 1];
   const T xp = i < A.nx - 1 ? u[id + 1] : u[id - 1];
-  const T ym = j > 0 ? u[id - A.nx] : u[id + A.nx];
-  const T yp = j < A.ny - 1 ? u[id + A.nx] : u[id - A.nx];
+  const T ym = j > 0 ? u[id - A.px] : u[id + A.px];
+  const T yp = j < A.ny - 1 ? u[id + A.px] : u[id - A.px];
   const T zm = k > 0 ? u[id - sz] : u[id + sz];
   const T zp = k < A.nz - 1 ? u[id + sz] : u[id - sz];
   return lap7(xm, xp, ym, yp, zm, zp, c);
@@ -326,7 +334,7 @@ __device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T
 
 template <typename T>
 __device__ __forceinline__ long long axis_stride(const StepArgs<T>& A, int ax) {
-  return ax == 0 ? 1LL : (ax == 1 ? (long long)A.nx : (long long)A.nx * A.ny);
+  return ax == 0 ? 1LL : (ax == 1 ? (long long)A.px : (long long)A.px * A.ny);
 }
 
 // The "edge set" (lattices with >= 5 nodes per axis): every node whose
@@ -472,7 +480,7 @@ __device__ __noinline__ void general_node(const StepArgs<T>& A, const Slot<T>& S
   if (fem) {
     val = T(2) * c0 - pv + c2 * fem_lap(A, S.cur, id, i, j, k, c0, cm, cp);
   } else {
-    val = T(2) * c0 - pv + c2 * lap7(cq[-1], cq[1], cq[-nx], cq[nx], cm, cp, c0);
+    val = T(2) * c0 - pv + c2 * lap7(cq[-1], cq[1], cq[-A.px], cq[A.px], cm, cp, c0);
   }
   if (cnt == 1) {
     const int ax = C.dxs ? 0 : (C.dys ? 1 : 2);
@@ -500,8 +508,7 @@ __device__ __noinline__ void general_node(const StepArgs<T>& A, const Slot<T>& S
       S.next[idb] = lb;
     }
   }
-  const long long bidx =
-      fem ? (long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2])) : 0;
+  const long long bidx = fem ? hidx(A, i, j, k) : 0;
   if (!(fem && A.rmask && A.rmask[bidx])) {  // sparse rows are written by the refined rows
     S.next[id] = val;
     if (!ADJ && S.hist_w && fem) S.hist_w[bidx] = val;
@@ -516,273 +523,302 @@ __device__ __noinline__ void general_node(const StepArgs<T>& A, const Slot<T>& S
 }
 
 // ---- shared-memory pipeline of the interior blocks ----
-// A block stages, plane by plane and kPipe<T>::D planes ahead of its z march,
-// with cp.async: u^k on the tile and a one-node halo (34 x 10), u^{k-1} on
-// the same box, and on tiles that meet the FEM block the three edge-weight
-// arrays (33 x 9, one node below the tile in x and y) and, for the
-// transposed step, the stored u of the FEM-owned box (33 x 9, one node
-// above).  Each plane lives in a ring of stages indexed by plane modulo the
-// ring size.
-constexpr int kBoxX = kTileX + 2, kBoxY = kTileY + 2, kBox = kBoxX * kBoxY;
-constexpr int kHBoxX = kTileX + 1, kHBoxY = kTileY + 1, kHBox = kHBoxX * kHBoxY;
+// A block stages, plane by plane and kPipe<T>::D levels ahead of its z
+// march, boxes that its producer warp loads with bulk tensor copies (TMA)
+// and that complete on one mbarrier per level: u^k on the tile and a
+// one-node halo (36 x 10 from x = i0 - 1: the box width is a multiple of 16
+// bytes), u^{k-1} on the same box, and on tiles that meet the FEM block the
+// three edge-weight arrays and, for the transposed step, the stored u of the
+// FEM-owned box (36 x 9).  Each plane lives in a ring of stages indexed by
+// the plane number modulo the (power-of-two) ring size.  The eight consumer
+// warps (the 32 x 8 tile) read only shared memory.
+constexpr int kBoxX = kTileX + 4, kBoxY = kTileY + 2, kBox = kBoxX * kBoxY;  // 36 x 18
+constexpr int kHBoxY = kTileY + 1, kHBox = kBoxX * kHBoxY;                    // 36 x 17
 
 template <typename T>
 struct kPipe {
   static constexpr int pow2(int n) { return n <= 1 ? 1 : 2 * pow2((n + 1) / 2); }
-  static constexpr int D = 2;             // levels in flight
+  static constexpr int round128(int elems) { return (int)(((elems * (int)sizeof(T) + 127) / 128) * 128 / sizeof(T)); }
+  static constexpr int D = sizeof(T) == 4 ? 2 : 1;  // levels in flight
   static constexpr int SC = pow2(D + 3);  // u^k stages (planes k-1 .. k+1+D)
   static constexpr int SP = pow2(D + 1);  // u^{k-1} stages (k .. k+D)
   static constexpr int SW = pow2(D + 2);  // edge-weight stages (k-1 .. k+D)
   static constexpr int SH = pow2(D + 2);  // stored-u stages (k .. k+1+D)
-  static constexpr int elems = SC * kBox + SP * kBox + SW * 3 * kHBox + SH * kHBox;
-  static constexpr size_t bytes = sizeof(T) * (size_t)elems;
+  static constexpr int NB = pow2(D + 1);  // level barriers
+  static constexpr int CS = round128(kBox);   // elements per u stage (128-byte aligned)
+  static constexpr int WS = round128(kHBox);  // elements per edge-weight array / stored-u stage
+  static constexpr int elems = SC * CS + SP * CS + SW * 3 * WS + SH * WS;
+  static constexpr size_t bytes = sizeof(T) * (size_t)elems + 8 * NB;
 };
 
+// Producer side of one interior block: which boxes exist, and their issue.
 template <typename T>
-__device__ __forceinline__ void cp_async(T* dst, const T* src) {
-#if defined(__CUDA_ARCH__)
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-#else
-  *dst = *src;
-#endif
-}
+struct Producer {
+  const StepArgs<T>* A;
+  const Slot<T>* S;
+  T *CR, *PR, *WR, *HR;
+  uint64_t* bars;
+  int z0, z1, xf, yf, xw, yw, xh, yh;
+  bool fem_tile, hist_tile;
+  // the planes first read at level g (the first level also reads planes
+  // g - 1 and g of u^k, g - 1 of the weights and g of the stored u)
+  __device__ __forceinline__ void issue(int g, bool first) const {
+    using P = kPipe<T>;
+    constexpr uint32_t kCBytes = (uint32_t)(kBox * sizeof(T));
+    constexpr uint32_t kWBytes = (uint32_t)(kHBox * sizeof(T));
+    uint64_t* bar = bars + ((g - z0) & (P::NB - 1));
+    const int wlo = A->wl[2], whi = A->wl[2] + A->wn[2] - 1, hlo = A->fl[2], hhi = A->fh[2];
+    const bool c_on = g + 1 <= z1;
+    const bool w_on = fem_tile && g >= wlo && g <= whi;
+    const bool wm_on = first && fem_tile && g - 1 >= wlo && g - 1 <= whi;
+    const bool h_on = hist_tile && g + 1 >= hlo && g + 1 <= hhi;
+    const bool h0_on = first && hist_tile && g >= hlo && g <= hhi;
+    const uint32_t bytes = kCBytes * ((c_on ? 1 : 0) + 1 + (first ? 2 : 0)) +
+                           kWBytes * (3 * ((w_on ? 1 : 0) + (wm_on ? 1 : 0)) + (h_on ? 1 : 0) + (h0_on ? 1 : 0));
+    mbar_arrive_expect_tx(bar, bytes);
+    if (first) {
+      tma_load_3d(CR + ((g - 1) & (P::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g - 1, bar);
+      tma_load_3d(CR + (g & (P::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g, bar);
+    }
+    if (c_on) tma_load_3d(CR + ((g + 1) & (P::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g + 1, bar);
+    tma_load_3d(PR + (g & (P::SP - 1)) * P::CS, &A->tmf, xf, yf, S->zf_prev + g, bar);
+    if (wm_on) weights(g - 1, bar);
+    if (w_on) weights(g, bar);
+    if (h0_on) tma_load_3d(HR + (g & (P::SH - 1)) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g - hlo), bar);
+    if (h_on) tma_load_3d(HR + ((g + 1) & (P::SH - 1)) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g + 1 - hlo), bar);
+  }
+  __device__ __forceinline__ void weights(int q, uint64_t* bar) const {
+    using P = kPipe<T>;
+    T* w = WR + (q & (P::SW - 1)) * 3 * P::WS;
+    const int zq = q - A->wl[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tma_load_3d(w + a * P::WS, &A->tmw, xw, yw, a * A->wn[2] + zq, bar);
+  }
+};
 
-__device__ __forceinline__ void cp_commit() {
-#if defined(__CUDA_ARCH__)
-  asm volatile("cp.async.commit_group;" ::: "memory");
-#endif
-}
-
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-#if defined(__CUDA_ARCH__)
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-#endif
-}
-
-// Interior part of one time level (lattices with >= 5 nodes per axis):
-// 32 x 8 thread tiles of the nodes 1 .. n-2, one warp per tile row, each
-// block marching a chunk of z planes through the shared-memory pipeline.
-// Nodes one step inside an x or y face also produce the face node; planes
-// one step inside a z face take the general rows from global memory.
-template <typename T, bool ADJ>
-__device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* sm) {
-  static_assert(kTileX == 32, "one warp per tile row");
-  static_assert(kTileX * kTileY == kStepBlock, "one thread per tile column");
+// One node (i, j, k) of an interior block from the staged planes: Ck, Cm, Cp
+// are this node in the u^k boxes of planes k, k-1, k+1, Pk in the u^{k-1}
+// box, Wk / Wm in the edge-weight arrays of planes k / k-1, Hk / Hp in the
+// stored-u boxes of planes k / k+1 (at the voxel origin).
+template <typename T, bool ADJ, bool FEMT, bool FACE>
+__device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T>& S, const Col& C, int k, int off,
+                                              const T* Ck, const T* Cm, const T* Cp, const T* Pk, const T* Wk,
+                                              const T* Wm, const T* Hk, const T* Hp) {
   using P = kPipe<T>;
-  constexpr int D = P::D;
-  const int tps = A.npb * A.nzc;
-  Col C;
-  C.si = b / tps;
-  int rem = b - C.si * tps;
-  const int zc = rem / A.npb;
-  rem -= zc * A.npb;
-  const int tyy = rem / A.ntx;
-  const int txx = rem - tyy * A.ntx;
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int pl = nx * ny;
-  const int z0 = 1 + zc * A.zchunk;
-  const int z1 = min(z0 + A.zchunk, nz - 1);
-  if (z0 >= z1) return;  // whole block
-  const int t = (int)threadIdx.x;
-  const int tx = t & 31, ty = t >> 5;
-  const int i0 = 1 + txx * kTileX, j0 = 1 + tyy * kTileY;
-  C.i = i0 + tx;
-  C.j = j0 + ty;
-  C.dxs = (C.i == 1) ? -1 : (C.i == nx - 2 ? 1 : 0);
-  C.dys = (C.j == 1) ? -1 : (C.j == ny - 2 ? 1 : 0);
-  const bool active = C.i <= nx - 2 && C.j <= ny - 2 && !(C.dxs != 0 && C.dys != 0);
-  const Slot<T>& S = A.s[C.si];
-  const bool has_fem = A.fl[0] <= A.fh[0];
-  C.xy_fem = has_fem && C.i >= A.fl[0] && C.i <= A.fh[0] && C.j >= A.fl[1] && C.j <= A.fh[1];
-  const bool pairing = ADJ && S.hist_r != nullptr;
-  C.xy_vox = pairing && C.i >= A.fl[0] && C.i < A.fl[0] + A.un[0] && C.j >= A.fl[1] && C.j < A.fl[1] + A.un[1];
-  // the tile meets the FEM-owned block in x-y (block-uniform)
-  const bool fem_tile = has_fem && i0 <= A.fh[0] && i0 + kTileX - 1 >= A.fl[0] && j0 <= A.fh[1] &&
-                        j0 + kTileY - 1 >= A.fl[1];
-  const bool hist_tile = pairing && fem_tile;
-
-  T* CR = sm;
-  T* PR = CR + P::SC * kBox;
-  T* WR = PR + P::SP * kBox;
-  T* HR = WR + P::SW * 3 * kHBox;
-
-  // copy slots of this thread (offsets within a plane; -1: no copy)
-  int go[2];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const int e = t + kStepBlock * s;
-    const int r = e / kBoxX, c = e - r * kBoxX;
-    const int gi = i0 - 1 + c, gj = j0 - 1 + r;
-    go[s] = (e < kBox && gi <= nx - 1 && gj <= ny - 1) ? gj * nx + gi : -1;
-  }
-  int wo[4] = {-1, -1, -1, -1}, ho[2] = {-1, -1};
-  int wz = 0, hz = 0;
-  if (fem_tile) {
-    wz = A.wn[0] * A.wn[1];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int e = t + kStepBlock * s;
-      const int a = e / kHBox;
-      const int q = e - a * kHBox;
-      const int r = q / kHBoxX, c = q - r * kHBoxX;
-      const int wi = i0 - 1 + c - A.wl[0], wj = j0 - 1 + r - A.wl[1];
-      if (e < 3 * kHBox && wi >= 0 && wi < A.wn[0] && wj >= 0 && wj < A.wn[1])
-        wo[s] = a * (int)A.wsz + wj * A.wn[0] + wi;
-    }
-  }
-  if (hist_tile) {
-    hz = A.fn[0] * A.fn[1];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int e = t + kStepBlock * s;
-      const int r = e / kHBoxX, c = e - r * kHBoxX;
-      const int hi = i0 + c - A.fl[0], hj = j0 + r - A.fl[1];
-      if (e < kHBox && hi >= 0 && hi < A.fn[0] && hj >= 0 && hj < A.fn[1]) ho[s] = hj * A.fn[0] + hi;
-    }
-  }
-  const int wlo = A.wl[2], whi = A.wl[2] + A.wn[2] - 1;
-  const int hlo = A.fl[2], hhi = A.fh[2];
-  const T* __restrict__ gcur = S.cur;
-  const T* __restrict__ gprev = S.prev;
-  const T* __restrict__ ghist = S.hist_r;
-  // copy of plane q of each staged array into its ring stage (q & (S - 1))
-  auto copy_c = [&](int q) {
-    if (q > z1) return;
-    T* dst = CR + (q & (P::SC - 1)) * kBox + t;
-    const T* src = gcur + (long long)q * pl;
-    if (go[0] >= 0) cp_async(dst, src + go[0]);
-    if (go[1] >= 0) cp_async(dst + kStepBlock, src + go[1]);
-  };
-  auto copy_p = [&](int q) {
-    if (q > z1 - 1) return;
-    T* dst = PR + (q & (P::SP - 1)) * kBox + t;
-    const T* src = gprev + (long long)q * pl;
-    if (go[0] >= 0) cp_async(dst, src + go[0]);
-    if (go[1] >= 0) cp_async(dst + kStepBlock, src + go[1]);
-  };
-  auto copy_w = [&](int q) {
-    if (q < wlo || q > whi) return;
-    T* dst = WR + (q & (P::SW - 1)) * 3 * kHBox + t;
-    const T* src = A.W + (long long)(q - wlo) * wz;
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (wo[s] >= 0) cp_async(dst + kStepBlock * s, src + wo[s]);
-  };
-  auto copy_h = [&](int q) {
-    if (q < hlo || q > hhi) return;
-    T* dst = HR + (q & (P::SH - 1)) * kHBox + t;
-    const T* src = ghist + (long long)(q - hlo) * hz;
-    if (ho[0] >= 0) cp_async(dst, src + ho[0]);
-    if (ho[1] >= 0) cp_async(dst + kStepBlock, src + ho[1]);
-  };
-  // prologue: the planes of levels z0 .. z0 + D - 1, one group per level
-  copy_c(z0 - 1);
-  copy_c(z0);
-  if (fem_tile) copy_w(z0 - 1);
-  if (hist_tile) copy_h(z0);
-  for (int g = 0; g < D; ++g) {
-    copy_c(z0 + 1 + g);
-    copy_p(z0 + g);
-    if (fem_tile) copy_w(z0 + g);
-    if (hist_tile) copy_h(z0 + 1 + g);
-    cp_commit();
-  }
   const T c2 = A.c2;
-  const int o = (ty + 1) * kBoxX + (tx + 1);    // this node in a u box
-  const int ow = (ty + 1) * kHBoxX + (tx + 1);  // this node in an edge-weight box
-  const int oh = ty * kHBoxX + tx;              // this node in a stored-u box
-  const int rlo = A.fl[2], rhi = A.fh[2];
+  const T c0 = Ck[0], cm = Cm[0], cp = Cp[0], pv = Pk[0];
+  const T xm = Ck[-1], xp = Ck[1], ym = Ck[-kBoxX], yp = Ck[kBoxX];
+  bool lf = false;
+  T wxm = T(1), wxp = T(1), wym = T(1), wyp = T(1);
+  T lap;
+  if constexpr (FEMT) lf = C.xy_fem && k >= A.fl[2] && k <= A.fh[2];
+  if (FEMT && lf) {
+    wxm = Wk[-1];
+    wxp = Wk[0];
+    wym = Wk[P::WS - kBoxX];
+    wyp = Wk[P::WS];
+    lap = wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + Wk[2 * P::WS] * (cp - c0) +
+          Wm[2 * P::WS] * (cm - c0);
+  } else {
+    lap = lap7(xm, xp, ym, yp, cm, cp, c0);
+  }
+  T val = T(2) * c0 - pv + c2 * lap;
   T* __restrict__ gnext = S.next;
-  long long id = (long long)C.i + (long long)nx * C.j + (long long)pl * z0;
-  for (int k = z0; k < z1; ++k, id += pl) {
-    cp_wait<D - 1>();
-    __syncthreads();
-    // planes of level k + D (their stages were last read at level k - 1)
-    copy_c(k + 1 + D);
-    copy_p(k + D);
-    if (fem_tile) copy_w(k + D);
-    if (hist_tile) copy_h(k + 1 + D);
-    cp_commit();
-    if (!active) continue;
-    const T* C0 = CR + (k & (P::SC - 1)) * kBox + o;
-    const T* Cm = CR + ((k - 1) & (P::SC - 1)) * kBox + o;
-    const T* Cp = CR + ((k + 1) & (P::SC - 1)) * kBox + o;
-    const T* P0 = PR + (k & (P::SP - 1)) * kBox + o;
-    const T c0 = C0[0], cm = Cm[0], cp = Cp[0], pv = P0[0];
-    if (k == 1 || k == nz - 2) {  // block-uniform
-      general_node<T, ADJ>(A, S, C, k, cm, c0, cp, pv);
-      continue;
-    }
-    const T xm = C0[-1], xp = C0[1], ym = C0[-kBoxX], yp = C0[kBoxX];
-    const bool lf = C.xy_fem && k >= rlo && k <= rhi;
-    T wxm = T(1), wxp = T(1), wym = T(1), wyp = T(1);
-    T lap;
-    if (lf) {
-      const T* WX = WR + (k & (P::SW - 1)) * 3 * kHBox + ow;
-      const T* WY = WX + kHBox;
-      const T* WZ = WX + 2 * kHBox;
-      const T* WZm = WR + ((k - 1) & (P::SW - 1)) * 3 * kHBox + 2 * kHBox + ow;
-      wxm = WX[-1];
-      wxp = WX[0];
-      wym = WY[-kHBoxX];
-      wyp = WY[0];
-      lap = wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + WZ[0] * (cp - c0) +
-            WZm[0] * (cm - c0);
-    } else {
-      lap = lap7(xm, xp, ym, yp, cm, cp, c0);
-    }
-    T val = T(2) * c0 - pv + c2 * lap;
+  if constexpr (FACE) {
     if (C.dxs != 0 || C.dys != 0) {  // the x or y face node next to this node
       const int ax = C.dxs ? 0 : 1;
       const int sd = C.dxs ? C.dxs : C.dys;
       const int f = 2 * ax + (sd > 0 ? 1 : 0);
       const int ob = ax == 0 ? sd : sd * kBoxX;  // b relative to this node in a u box
       const int o1 = ax == 0 ? kBoxX : 1;        // the other in-plane axis in the box
-      const T ub = C0[ob];
+      const T ub = Ck[ob];
       // in-face neighbours: the other in-plane axis first, then z
-      const T n1m = C0[ob - o1], n1p = C0[ob + o1], n2m = Cm[ob], n2p = Cp[ob], pb = P0[ob];
-      const long long idb = id + (ax == 0 ? (long long)sd : (long long)sd * nx);
+      const T n1m = Ck[ob - o1], n1p = Ck[ob + o1], n2m = Cm[ob], n2p = Cp[ob], pb = Pk[ob];
+      const int offb = off + (ax == 0 ? sd : sd * A.px);
       const int bi = C.i + (ax == 0 ? sd : 0), bj = C.j + (ax == 1 ? sd : 0);
       if constexpr (!ADJ) {
         const T vb = fwd_face_row(A, S, f, ub, c0, val, n1m, n1p, n2m, n2p, pb);
-        gnext[idb] = vb;
-        if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, k, nx, ny)] = vb;
+        gnext[offb] = vb;
+        if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, k, A.nx, A.ny)] = vb;
       } else {
         const T coef_mb = ax == 0 ? (sd > 0 ? wxp : wxm) : (sd > 0 ? wyp : wym);
         const T lb = adj_face_row(A, S, f, bi, bj, k, ub, c0, coef_mb, n1m, n1p, n2m, n2p, pb);
         val += (((S.mask_f >> f) & 1) ? ub : T(2) * c2 * ub) - c2 * coef_mb * ub;
         if ((S.mask_e >> f) & 1) val -= A.r * lb;
-        gnext[idb] = lb;
-      }
-    }
-    if (!lf) {
-      gnext[id] = val;
-    } else {
-      const int bo = (C.i - A.fl[0]) + A.fn[0] * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]));
-      if (!(A.rmask && A.rmask[bo])) {  // sparse rows are written by the refined rows
-        gnext[id] = val;
-        if (!ADJ && S.hist_w) S.hist_w[bo] = val;
-      }
-      if constexpr (ADJ) {
-        if (C.xy_vox && k < A.fl[2] + A.un[2]) {
-          const T* H0 = HR + (k & (P::SH - 1)) * kHBox + oh;
-          const T* H1 = HR + ((k + 1) & (P::SH - 1)) * kHBox + oh;
-          const T u[8] = {H0[0], H0[1], H0[kHBoxX], H0[kHBoxX + 1], H1[0], H1[1], H1[kHBoxX], H1[kHBoxX + 1]};
-          const T l[8] = {c0, xp, yp, C0[kBoxX + 1], cp, Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
-          const int vz = A.un[0] * A.un[1];
-          const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
-          if (!(A.refvox && A.refvox[vid]))
-            atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
-        }
+        gnext[offb] = lb;
       }
     }
   }
-  cp_wait<0>();  // no copy outstanding when the block exits
+  if (!(FEMT && lf)) {
+    gnext[off] = val;
+    return;
+  }
+  const int bo = (C.i - A.hx0) + A.hpx * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]));
+  if (!(A.rmask && A.rmask[bo])) {  // sparse rows are written by the refined rows
+    gnext[off] = val;
+    if (!ADJ && S.hist_w) S.hist_w[bo] = val;
+  }
+  if constexpr (ADJ) {
+    if (C.xy_vox && k < A.fl[2] + A.un[2]) {
+      const T u[8] = {Hk[0], Hk[1], Hk[kBoxX], Hk[kBoxX + 1], Hp[0], Hp[1], Hp[kBoxX], Hp[kBoxX + 1]};
+      const T l[8] = {c0, xp, yp, Ck[kBoxX + 1], cp, Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
+      const int vz = A.un[0] * A.un[1];
+      const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
+      if (!(A.refvox && A.refvox[vid]))
+        atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
+    }
+  }
+}
+
+// Consumer loop of an interior block, specialised by whether the tile meets
+// the FEM block (FEMT) and whether it holds nodes one step inside an x or y
+// face (FACE).  Each consumer thread owns two tile rows (ty and ty + 8).
+template <typename T, bool ADJ, bool FEMT, bool FACE>
+__device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot<T>& S, const Col (&C)[2],
+                                                const Producer<T>& pr, const bool (&active)[2], int z0, int z1) {
+  using P = kPipe<T>;
+  constexpr int D = P::D;
+  constexpr int kProd = kTileX * kTileY / 2;  // the producer thread
+  const int t = (int)threadIdx.x;
+  const int tx = t & 31, ty = t >> 5;
+  const int nz = A.nz;
+  const int pl = A.px * A.ny;
+  const int o0 = (ty + 1) * kBoxX + (tx + 1);       // row 0 in a u box / edge-weight array
+  const int o1 = o0 + (kTileY / 2) * kBoxX;          // row 1
+  const int h0 = ty * kBoxX + (tx + 1);              // row 0 in a stored-u box
+  const int h1 = h0 + (kTileY / 2) * kBoxX;
+  const long long budget = 1LL << 29;                // cycles a level may wait for its planes (~0.25 s)
+  bool ok = true;
+  int off0 = C[0].i + A.px * C[0].j + pl * z0;       // field offsets of the two nodes
+  int off1 = off0 + (kTileY / 2) * A.px;
+  for (int k = z0; k < z1; ++k, off0 += pl, off1 += pl) {
+    // the producer thread waits for level k's planes; the barrier then
+    // releases the consumers (and orders the staged data before their reads)
+    if (t == kProd && ok &&
+        !mbar_wait(pr.bars + ((k - z0) & (P::NB - 1)), (uint32_t)(((k - z0) / P::NB) & 1), budget, A.err)) {
+      ok = false;
+      atomicExch(A.err, 1);
+    }
+    __syncthreads();  // every thread is done with level k - 1: its stages may be refilled
+    if (t >= kProd) {  // producer warp
+      if (t == kProd && k + D < z1) {
+        fence_proxy_async();
+        pr.issue(k + D, false);
+      }
+      continue;
+    }
+    const T* Ck = pr.CR + (k & (P::SC - 1)) * P::CS;
+    const T* Cm = pr.CR + ((k - 1) & (P::SC - 1)) * P::CS;
+    const T* Cp = pr.CR + ((k + 1) & (P::SC - 1)) * P::CS;
+    const T* Pk = pr.PR + (k & (P::SP - 1)) * P::CS;
+    if (k == 1 || k == nz - 2) {  // block-uniform: the general rows, from global memory
+      if (active[0]) general_node<T, ADJ>(A, S, C[0], k, Cm[o0], Ck[o0], Cp[o0], Pk[o0]);
+      if (active[1]) general_node<T, ADJ>(A, S, C[1], k, Cm[o1], Ck[o1], Cp[o1], Pk[o1]);
+      continue;
+    }
+    const T* Wk = nullptr;
+    const T* Wm = nullptr;
+    const T* Hk = nullptr;
+    const T* Hp = nullptr;
+    if constexpr (FEMT) {
+      Wk = pr.WR + (k & (P::SW - 1)) * 3 * P::WS;
+      Wm = pr.WR + ((k - 1) & (P::SW - 1)) * 3 * P::WS;
+      Hk = pr.HR + (k & (P::SH - 1)) * P::WS;
+      Hp = pr.HR + ((k + 1) & (P::SH - 1)) * P::WS;
+    }
+    if (active[0])
+      interior_node<T, ADJ, FEMT, FACE>(A, S, C[0], k, off0, Ck + o0, Cm + o0, Cp + o0, Pk + o0, Wk + o0, Wm + o0,
+                                        Hk + h0, Hp + h0);
+    if (active[1])
+      interior_node<T, ADJ, FEMT, FACE>(A, S, C[1], k, off1, Ck + o1, Cm + o1, Cp + o1, Pk + o1, Wk + o1, Wm + o1,
+                                        Hk + h1, Hp + h1);
+  }
+}
+
+// Interior part of one time level (lattices with >= 5 nodes per axis):
+// 32 x 16 tiles of the nodes 1 .. n-2 and z chunks, one block per (tile,
+// chunk): eight consumer warps (two tile rows per thread) and a producer
+// warp.  Nodes one step inside an x or y face also produce the face node;
+// planes one step inside a z face take the general rows from global memory.
+template <typename T, bool ADJ>
+__device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* sm) {
+  static_assert(kTileX == 32, "one warp per tile row");
+  static_assert(kTileX * kTileY / 2 + 32 == kStepBlock, "eight consumer warps (two rows each) and a producer warp");
+  using P = kPipe<T>;
+  constexpr int D = P::D;
+  const int tps = A.npb * A.nzc;
+  const int si = b / tps;
+  int rem = b - si * tps;
+  const int zc = rem / A.npb;
+  rem -= zc * A.npb;
+  const int tyy = rem / A.ntx;
+  const int txx = rem - tyy * A.ntx;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int z0 = 1 + zc * A.zchunk;
+  const int z1 = min(z0 + A.zchunk, nz - 1);
+  if (z0 >= z1) return;  // whole block
+  const int t = (int)threadIdx.x;
+  const int tx = t & 31, ty = t >> 5;
+  const int i0 = 1 + txx * kTileX, j0 = 1 + tyy * kTileY;
+  const Slot<T>& S = A.s[si];
+  const bool has_fem = A.fl[0] <= A.fh[0];
+  const bool pairing = ADJ && S.hist_r != nullptr;
+  Col C[2];
+  bool active[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    C[r].si = si;
+    C[r].i = i0 + tx;
+    C[r].j = j0 + ty + r * (kTileY / 2);
+    C[r].dxs = (C[r].i == 1) ? -1 : (C[r].i == nx - 2 ? 1 : 0);
+    C[r].dys = (C[r].j == 1) ? -1 : (C[r].j == ny - 2 ? 1 : 0);
+    active[r] = t < kTileX * kTileY / 2 && C[r].i <= nx - 2 && C[r].j <= ny - 2 && !(C[r].dxs != 0 && C[r].dys != 0);
+    C[r].xy_fem = has_fem && C[r].i >= A.fl[0] && C[r].i <= A.fh[0] && C[r].j >= A.fl[1] && C[r].j <= A.fh[1];
+    C[r].xy_vox = pairing && C[r].i >= A.fl[0] && C[r].i < A.fl[0] + A.un[0] && C[r].j >= A.fl[1] &&
+                  C[r].j < A.fl[1] + A.un[1];
+  }
+  // block-uniform tile kinds
+  const bool fem_tile = has_fem && i0 <= A.fh[0] && i0 + kTileX - 1 >= A.fl[0] && j0 <= A.fh[1] &&
+                        j0 + kTileY - 1 >= A.fl[1];
+  const bool face_tile = i0 == 1 || i0 + kTileX - 1 >= nx - 2 || j0 == 1 || j0 + kTileY - 1 >= ny - 2;
+  Producer<T> pr;
+  pr.A = &A;
+  pr.S = &S;
+  pr.CR = sm;
+  pr.PR = pr.CR + P::SC * P::CS;
+  pr.WR = pr.PR + P::SP * P::CS;
+  pr.HR = pr.WR + P::SW * 3 * P::WS;
+  pr.bars = reinterpret_cast<uint64_t*>(pr.HR + P::SH * P::WS);
+  pr.z0 = z0;
+  pr.z1 = z1;
+  pr.xf = i0 - 1;  // multiples of 4: 16-byte aligned box origins
+  pr.yf = j0 - 1;
+  pr.xw = i0 - 1 - A.wx0;
+  pr.yw = j0 - 1 - A.wl[1];
+  pr.xh = i0 - 1 - A.hx0;
+  pr.yh = j0 - A.fl[1];
+  pr.fem_tile = fem_tile;
+  pr.hist_tile = pairing && fem_tile;
+  const int tp = kTileX * kTileY / 2;  // the producer thread
+  if (t == tp) {
+    for (int q = 0; q < P::NB; ++q) mbar_init(pr.bars + q, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (t == tp) {
+    for (int g = 0; g < D && z0 + g < z1; ++g) pr.issue(z0 + g, g == 0);
+  }
+  if (fem_tile) {
+    if (face_tile)
+      interior_levels<T, ADJ, true, true>(A, S, C, pr, active, z0, z1);
+    else
+      interior_levels<T, ADJ, true, false>(A, S, C, pr, active, z0, z1);
+  } else {
+    if (face_tile)
+      interior_levels<T, ADJ, false, true>(A, S, C, pr, active, z0, z1);
+    else
+      interior_levels<T, ADJ, false, false>(A, S, C, pr, active, z0, z1);
+  }
 }
 
 template <typename T, bool ADJ>
@@ -832,9 +868,7 @@ __device__ __forceinline__ void fwd_edge_tile(const StepArgs<T>& A, int si, int 
   const T val = nv[t];
   S.next[id] = val;
   if (S.obs_w && ((fall >> S.obs_face) & 1)) S.obs_w[face_index(S.obs_face, i, j, k, A.nx, A.ny)] = val;
-  if (S.hist_w && fem_owned(A, i, j, k))
-    S.hist_w[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
-        val;
+  if (S.hist_w && fem_owned(A, i, j, k)) S.hist_w[hidx(A, i, j, k)] = val;
 }
 
 // Edge tile of the transposed step: every thread gathers its transposed row
@@ -878,15 +912,15 @@ __device__ __forceinline__ void adj_edge_tile(const StepArgs<T>& A, int si, int 
 // interior blocks.  All blocks read levels k, k-1 and write disjoint nodes
 // of level k+1.
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 4 : 3) step_kernel(const __grid_constant__ StepArgs<T> A) {
-  extern __shared__ __align__(16) unsigned char hyb_smem[];  // kPipe<T>::bytes
+__global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kernel(const __grid_constant__ StepArgs<T> A) {
+  extern __shared__ __align__(128) unsigned char hyb_smem[];  // kPipe<T>::bytes
   T* sh = reinterpret_cast<T*>(hyb_smem);
   int b = blockIdx.x;
-  if (b < A.nhe) {
+  if (b < A.nhe) {  // two 128-node tiles; the last warp takes part in the barriers only
     const int ne2 = (A.nedge + 1) / 2;
     const int si = b / ne2;
     const int half = (int)(threadIdx.x >> 7);
-    const int blk = 2 * (b - si * ne2) + half;
+    const int blk = half < 2 ? 2 * (b - si * ne2) + half : A.nedge;
     const int t = (int)(threadIdx.x & 127);
     if constexpr (ADJ)
       adj_edge_tile<T>(A, si, blk, t, sh + 128 * half);
@@ -910,18 +944,17 @@ __global__ void __launch_bounds__(128) fwd_all_kernel(const __grid_constant__ St
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * A.nslots) return;
   const int si = (int)(t / n);
-  const long long id = t - (long long)si * n;
-  const int i = (int)(id % A.nx);
-  const int j = (int)((id / A.nx) % A.ny);
-  const int k = (int)(id / ((long long)A.nx * A.ny));
+  const long long q = t - (long long)si * n;
+  const int i = (int)(q % A.nx);
+  const int j = (int)((q / A.nx) % A.ny);
+  const int k = (int)(q / ((long long)A.nx * A.ny));
+  const long long id = lin(A, i, j, k);
   const Slot<T>& S = A.s[si];
   const T val = fwd_new<T, 3>(A, S, i, j, k);
   S.next[id] = val;
   if (S.obs_w && ((face_bits(i, j, k, A.nx, A.ny, A.nz) >> S.obs_face) & 1))
     S.obs_w[face_index(S.obs_face, i, j, k, A.nx, A.ny)] = val;
-  if (S.hist_w && fem_owned(A, i, j, k))
-    S.hist_w[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
-        val;
+  if (S.hist_w && fem_owned(A, i, j, k)) S.hist_w[hidx(A, i, j, k)] = val;
 }
 
 template <typename T>
@@ -930,12 +963,12 @@ __global__ void __launch_bounds__(128) adj_all_kernel(const __grid_constant__ St
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * A.nslots) return;
   const int si = (int)(t / n);
-  const long long id = t - (long long)si * n;
-  const int i = (int)(id % A.nx);
-  const int j = (int)((id / A.nx) % A.ny);
-  const int k = (int)(id / ((long long)A.nx * A.ny));
+  const long long q = t - (long long)si * n;
+  const int i = (int)(q % A.nx);
+  const int j = (int)((q / A.nx) % A.ny);
+  const int k = (int)(q / ((long long)A.nx * A.ny));
   const Slot<T>& S = A.s[si];
-  S.next[id] = adj_new<T, 3>(A, S, i, j, k);
+  S.next[lin(A, i, j, k)] = adj_new<T, 3>(A, S, i, j, k);
   pair_if_voxel(A, S, si, i, j, k);
 }
 
@@ -963,10 +996,10 @@ __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* 
   const int uid = A.refvox_id[v];
   const int x = uid % A.un[0], y = (uid / A.un[0]) % A.un[1], z = uid / (A.un[0] * A.un[1]);
   const int i = A.fl[0] + x, j = A.fl[1] + y, k = A.fl[2] + z;
-  const long long hy = A.fn[0], hz = (long long)A.fn[0] * A.fn[1];
-  const long long h0 = (long long)x + hy * y + hz * z;
+  const long long hy = A.hpx, hz = (long long)A.hpx * A.fn[1];
+  const long long h0 = hidx(A, i, j, k);
   const long long l0 = lin(A, i, j, k);
-  const long long ly = A.nx, lz = (long long)A.nx * A.ny;
+  const long long ly = A.px, lz = (long long)A.px * A.ny;
   T u[9], l[9];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -1022,9 +1055,8 @@ __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t) 
     if (lat) {
       S.next[self] = val;
       if (!ADJ && S.hist_w) {
-        const int i = (int)(self % A.nx), j = (int)((self / A.nx) % A.ny), k = (int)(self / ((long long)A.nx * A.ny));
-        S.hist_w[(long long)(i - A.fl[0]) + (long long)A.fn[0] * ((j - A.fl[1]) + (long long)A.fn[1] * (k - A.fl[2]))] =
-            val;
+        const int i = (int)(self % A.px), j = (int)((self / A.px) % A.ny), k = (int)(self / ((long long)A.px * A.ny));
+        S.hist_w[hidx(A, i, j, k)] = val;
       }
     } else {
       S.cnext[r - A.nrl] = val;
@@ -1072,11 +1104,12 @@ __global__ void set_coef_kernel(const __grid_constant__ StepArgs<T> A, T* __rest
     if (!(v <= a_max * (1.0 + 1e-12)) || !(v == v)) atomicExch(flag, 1);
   }
   if (t >= A.wsz) return;
-  const int p[3] = {A.wl[0] + (int)(t % A.wn[0]), A.wl[1] + (int)((t / A.wn[0]) % A.wn[1]),
-                    A.wl[2] + (int)(t / ((long long)A.wn[0] * A.wn[1]))};
+  const int p[3] = {A.wx0 + (int)(t % A.wpx), A.wl[1] + (int)((t / A.wpx) % A.wn[1]),
+                    A.wl[2] + (int)(t / ((long long)A.wpx * A.wn[1]))};
+  const bool in_box = p[0] >= A.wl[0] && p[0] <= A.wl[0] + A.wn[0] - 1;  // else row padding
   for (int ax = 0; ax < 3; ++ax) {
     double w = 0.0;
-    if (p[ax] + 1 <= A.wl[ax] + A.wn[ax] - 1) {
+    if (in_box && p[ax] + 1 <= A.wl[ax] + A.wn[ax] - 1) {
       const int P = ax == 0 ? 1 : 0;
       const int Q = ax == 2 ? 1 : 2;
       for (int bp = 0; bp < 2; ++bp) {
@@ -1108,7 +1141,7 @@ __global__ void extract_owned_kernel(const __grid_constant__ StepArgs<T> A, cons
   const long long r = t / A.fn[0];
   const int y = (int)(r % A.fn[1]);
   const int z = (int)(r / A.fn[1]);
-  box[t] = f[lin(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z)];
+  box[hidx(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z)] = f[lin(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z)];
 }
 
 }  // namespace

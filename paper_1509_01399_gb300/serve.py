@@ -61,9 +61,9 @@ def class_key(w, precision) -> tuple:
 def estimate_bytes(w, precision) -> int:
     """Device bytes one pooled mesh of this class holds after a solve."""
     es = 8 if precision == "fp64" else 4
-    N = w.n[0] * w.n[1] * w.n[2]
+    N = ((w.n[0] + 3) // 4 * 4) * w.n[1] * w.n[2]  # rows padded to a multiple of 4
     fn = [w.fem_hi[d] - w.fem_lo[d] - 1 for d in range(3)]
-    nown = fn[0] * fn[1] * fn[2]
+    nown = (fn[0] + 6) * fn[1] * fn[2]  # history box rows padded and aligned
     un = [max(0, v - 1) for v in fn]
     nu = un[0] * un[1] * un[2]
     wsz = (fn[0] + 2) * (fn[1] + 2) * (fn[2] + 2)
