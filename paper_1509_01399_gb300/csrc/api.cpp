@@ -98,7 +98,7 @@ struct hyb_mesh {
   // refined region
   int nc = 0, nr = 0, nrl = 0, nnz = 0;
   double dt_max = 0.0;
-  DevBuf rrow, rptr, rcol, rval, cptr, cunk, cw, rmask, refvox, refvox_id, k9;
+  DevBuf rrow, rptr, rcol, rval, cptr, cunk, cw, rmask, rzr, refvox, refvox_id, k9;
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
   cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
   int nsm = 0;                 // SMs of the device
@@ -477,7 +477,8 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   const double lam = std::max(12.0, bound) * m->d.a_max / (h * h);
   m->dt_max = std::min(m->dt_max, 2.0 / std::sqrt(lam));
   std::vector<int> rrow(rows.begin(), rows.end());
-  std::vector<double> k9(K9, K9 + 81);
+  std::vector<double> k9(81);  // the kernels accumulate six times the pairing (see kGradPairScale)
+  for (int q = 0; q < 81; ++q) k9[q] = 6.0 * K9[q];
   HYB_TRY(upload(m, m->rrow, rrow));
   HYB_TRY(upload(m, m->rptr, rptr));
   HYB_TRY(upload(m, m->rcol, rcol));
@@ -485,6 +486,22 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   HYB_TRY(upload(m, m->cunk, cunk));
   HYB_TRY(upload(m, m->cw, cw));
   HYB_TRY(upload(m, m->rmask, rmask));
+  // z range of the sparse-row nodes of each FEM-owned column
+  std::vector<int> rzr((size_t)2 * m->fn[0] * m->fn[1]);
+  for (size_t c = 0; c < rzr.size() / 2; ++c) {
+    rzr[2 * c] = 1 << 30;
+    rzr[2 * c + 1] = -1;
+  }
+  for (int k = 0; k < m->fn[2]; ++k)
+    for (int j = 0; j < m->fn[1]; ++j)
+      for (int i = 0; i < m->fn[0]; ++i) {
+        const int x = m->fl[0] + i;
+        if (!rmask[(size_t)(x - m->hx0) + (size_t)m->hpx * (j + (size_t)m->fn[1] * k)]) continue;
+        const size_t c = (size_t)i + (size_t)m->fn[0] * j;
+        rzr[2 * c] = std::min(rzr[2 * c], m->fl[2] + k);
+        rzr[2 * c + 1] = std::max(rzr[2 * c + 1], m->fl[2] + k);
+      }
+  HYB_TRY(upload(m, m->rzr, rzr));
   HYB_TRY(upload(m, m->refvox, refv));
   HYB_TRY(upload(m, m->refvox_id, refid));
   HYB_TRY(upload(m, m->k9, k9));
@@ -586,6 +603,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
     A.rcol = (const int*)m->rcol.p;
     A.rval = (const T*)m->rval.p;
     A.rmask = (const unsigned char*)m->rmask.p;
+    A.rzr = (const int*)m->rzr.p;
     A.refvox = (const unsigned char*)m->refvox.p;
     A.refvox_id = (const int*)m->refvox_id.p;
     A.k9 = (const double*)m->k9.p;
@@ -928,7 +946,7 @@ hyb_status cg_impl(hyb_mesh* m, double* a, const T* obs, const hyb_source* src, 
   double Jd = 0.0;
   HYB_TRY(misfit_impl<T>(m, tr, obs, P->weights, &Jd, (T*)m->cot.p));
   HYB_TRY(adjoint_impl<T>(m, (const T*)m->cot.p, 0));
-  launch_grad_finalize((const double*)m->G.p, nsrc, a, -dt * dt / (m->d.h * m->d.h), P->gamma, vol, P->a0,
+  launch_grad_finalize((const double*)m->G.p, nsrc, a, -dt * dt / (m->d.h * m->d.h) / kGradPairScale, P->gamma, vol, P->a0,
                        g, nu, m->st);
   HYB_LAUNCHED(m);
   launch_cg_norms(g, a, P->a0, nu, part, m->st);
@@ -1141,7 +1159,7 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   cudaStreamSynchronize(m->st);
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
                     &m->g, &m->atrial, &m->cot, &m->trace, &m->rrow, &m->rptr, &m->rcol, &m->rval,
-                    &m->cptr, &m->cunk, &m->cw, &m->rmask, &m->refvox, &m->refvox_id, &m->k9,
+                    &m->cptr, &m->cunk, &m->cw, &m->rmask, &m->rzr, &m->refvox, &m->refvox_id, &m->k9,
                     &m->CU, &m->CL, &m->chist, &m->cckpt};
   for (DevBuf* b : bufs) release(*b);
   if (m->hscal) cudaFreeHost(m->hscal);
@@ -1181,7 +1199,7 @@ hyb_status hyb_gradient(hyb_mesh* m, const double* a, double gamma, double a0, d
   if (!m->have_adj) return fail(HYB_ERR_STATE, "hyb_gradient needs a preceding hyb_adjoint");
   if (m->nu == 0) return HYB_OK;
   const double h = m->d.h;
-  launch_grad_finalize((const double*)m->G.p, m->nsrc, a, -m->dt * m->dt / (h * h), gamma, h * h * h, a0,
+  launch_grad_finalize((const double*)m->G.p, m->nsrc, a, -m->dt * m->dt / (h * h) / kGradPairScale, gamma, h * h * h, a0,
                        g_out, m->nu, m->st);
   HYB_LAUNCHED(m);
   return HYB_OK;

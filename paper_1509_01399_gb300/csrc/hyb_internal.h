@@ -15,6 +15,9 @@ constexpr int kStepBlock = 288;  // threads per block of the step kernel (9 warp
 constexpr int kTileX = 32;       // interior thread tile (x): one warp per tile row
 constexpr int kTileY = 16;       // interior tile (y): two rows per consumer thread
 constexpr int kReduceBlocks = 512;
+// The step kernels accumulate kGradPairScale times the voxel pairing of
+// Eq. (gradient1) (integer edge weights 2 and 1 instead of 1/3 and 1/6).
+constexpr double kGradPairScale = 6.0;
 constexpr int kReduceThreads = 256;
 
 // One problem (one source of one mesh) inside a step launch.
@@ -82,6 +85,8 @@ struct StepArgs {
   const int* rcol;            // column: lattice id, or nlat + centre index
   const T* rval;              // weight W_ij of the off-diagonal entries
   const unsigned char* rmask; // FEM-owned box: 1 = node updated by a sparse row
+  const int* rzr;             // per FEM-owned column (i - fl0) + fn0 (j - fl1): [kmin, kmax] of its
+                              // sparse-row nodes (kmin > kmax: none); refined voxels lie inside
   const unsigned char* refvox;// unknown voxels: 1 = refined
   const int* refvox_id;       // unknown id of each refined voxel (centre order)
   const double* k9;           // 9 x 9 stiffness of a refined unit voxel, a = 1

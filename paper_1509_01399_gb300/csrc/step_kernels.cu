@@ -262,9 +262,11 @@ __device__ __noinline__ T adj_new(const StepArgs<T>& A, const Slot<T>& S, int i,
   return v;
 }
 
-// Sum over the 12 axis edges of a voxel of w_e (u_p - u_q)(l_p - l_q), corner
-// c = a + 2b + 4d at offset (a, b, d); w_e = 1/3 on the edges at the
-// voxel's diagonal corners 0 and 7, 1/6 on the others.
+// Six times the sum over the 12 axis edges of a voxel of
+// w_e (u_p - u_q)(l_p - l_q), corner c = a + 2b + 4d at offset (a, b, d);
+// w_e = 1/3 on the edges at the voxel's diagonal corners 0 and 7, 1/6 on the
+// others.  (The factor 6 keeps divisions out of the kernels; the host scale
+// of the gradient divides it out.)
 template <typename T>
 __device__ __forceinline__ T pair_sum(const T u[8], const T l[8]) {
   const T d3 = (u[1] - u[0]) * (l[1] - l[0]) + (u[7] - u[6]) * (l[7] - l[6]) +
@@ -273,7 +275,7 @@ __device__ __forceinline__ T pair_sum(const T u[8], const T l[8]) {
   const T d6 = (u[3] - u[2]) * (l[3] - l[2]) + (u[5] - u[4]) * (l[5] - l[4]) +
                (u[3] - u[1]) * (l[3] - l[1]) + (u[6] - u[4]) * (l[6] - l[4]) +
                (u[5] - u[1]) * (l[5] - l[1]) + (u[6] - u[2]) * (l[6] - l[2]);
-  return d3 / T(3) + d6 / T(6);
+  return T(2) * d3 + d6;
 }
 
 // pair_sum of voxel (i,j,k): u from the FEM-owned box hb, lambda from the lattice
@@ -455,6 +457,7 @@ struct Col {
   int dxs, dys;   // -1 / +1: one node inside the low / high face of x, y; 0: not
   bool xy_fem;    // (i, j) inside the FEM-owned range
   bool xy_vox;    // (i, j) is the x-y origin of an unknown voxel and the step pairs
+  int rz0, rz1;   // z range of the column's sparse-row nodes (rz0 > rz1: none)
 };
 
 // Node (i, j, k) of the interior by the general rows, reading level data from
@@ -654,7 +657,8 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     return;
   }
   const int bo = (C.i - A.hx0) + A.hpx * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]));
-  if (!(A.rmask && A.rmask[bo])) {  // sparse rows are written by the refined rows
+  const bool rz = k >= C.rz0 && k <= C.rz1;  // the column has sparse-row nodes here
+  if (!(rz && A.rmask[bo])) {  // sparse rows are written by the refined rows
     gnext[off] = val;
     if (!ADJ && S.hist_w) S.hist_w[bo] = val;
   }
@@ -664,7 +668,7 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
       const T l[8] = {c0, xp, yp, Ck[kBoxX + 1], cp, Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
       const int vz = A.un[0] * A.un[1];
       const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
-      if (!(A.refvox && A.refvox[vid]))
+      if (!(rz && A.refvox[vid]))
         atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
     }
   }
@@ -776,6 +780,13 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
     C[r].xy_fem = has_fem && C[r].i >= A.fl[0] && C[r].i <= A.fh[0] && C[r].j >= A.fl[1] && C[r].j <= A.fh[1];
     C[r].xy_vox = pairing && C[r].i >= A.fl[0] && C[r].i < A.fl[0] + A.un[0] && C[r].j >= A.fl[1] &&
                   C[r].j < A.fl[1] + A.un[1];
+    C[r].rz0 = 1;
+    C[r].rz1 = 0;
+    if (A.rzr && C[r].xy_fem) {
+      const int c = (C[r].i - A.fl[0]) + A.fn[0] * (C[r].j - A.fl[1]);
+      C[r].rz0 = A.rzr[2 * c];
+      C[r].rz1 = A.rzr[2 * c + 1];
+    }
   }
   // block-uniform tile kinds
   const bool fem_tile = has_fem && i0 <= A.fh[0] && i0 + kTileX - 1 >= A.fl[0] && j0 <= A.fh[1] &&
