@@ -635,18 +635,35 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
       const int ob = ax == 0 ? sd : sd * kBoxX;  // b relative to this node in a u box
       const int o1 = ax == 0 ? kBoxX : 1;        // the other in-plane axis in the box
       const T ub = Ck[ob];
-      // in-face neighbours: the other in-plane axis first, then z
-      const T n1m = Ck[ob - o1], n1p = Ck[ob + o1], n2m = Cm[ob], n2p = Cp[ob], pb = Pk[ob];
+      const bool abc = (S.mask_f >> f) & 1;
       const int offb = off + (ax == 0 ? sd : sd * A.px);
       const int bi = C.i + (ax == 0 ? sd : 0), bj = C.j + (ax == 1 ? sd : 0);
+      // (as fwd_face_row / adj_face_row; the in-face neighbours, the other
+      // in-plane axis first, then z, are read only for non-absorbing faces)
       if constexpr (!ADJ) {
-        const T vb = fwd_face_row(A, S, f, ub, c0, val, n1m, n1p, n2m, n2p, pb);
+        T vb;
+        if (abc) {
+          vb = A.r * ub + (c0 - A.r * val);
+        } else {
+          T lb = T(2) * (c0 - ub);
+          lb += (Ck[ob - o1] - ub) + (Ck[ob + o1] - ub);
+          lb += (Cm[ob] - ub) + (Cp[ob] - ub);
+          vb = T(2) * ub - Pk[ob] + c2 * lb;
+          if (S.src_face == f) vb += S.srcval;
+        }
         gnext[offb] = vb;
         if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, k, A.nx, A.ny)] = vb;
       } else {
         const T coef_mb = ax == 0 ? (sd > 0 ? wxp : wxm) : (sd > 0 ? wyp : wym);
-        const T lb = adj_face_row(A, S, f, bi, bj, k, ub, c0, coef_mb, n1m, n1p, n2m, n2p, pb);
-        val += (((S.mask_f >> f) & 1) ? ub : T(2) * c2 * ub) - c2 * coef_mb * ub;
+        T lb = abc ? A.r * ub : (T(2) - T(6) * c2) * ub;
+        lb += c2 * coef_mb * c0;
+        if (!abc) {
+          lb += c2 * (Ck[ob - o1] + Ck[ob + o1]);
+          lb += c2 * (Cm[ob] + Cp[ob]);
+        }
+        if (!((S.mask_c >> f) & 1)) lb -= Pk[ob];
+        if (S.obs_r && S.obs_face == f) lb += S.obs_r[face_index(f, bi, bj, k, A.nx, A.ny)];
+        val += (abc ? ub : T(2) * c2 * ub) - c2 * coef_mb * ub;
         if ((S.mask_e >> f) & 1) val -= A.r * lb;
         gnext[offb] = lb;
       }
