@@ -366,10 +366,10 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     fwd_ms = e0.elapsed_time(e1) / nsteps
     adj_ms = e1b.elapsed_time(e2) / nsteps
-    dom = "adj_kernel<float>" if adj_ms >= fwd_ms else "fwd_kernel<float>"
+    dom = "step_kernel<float,adjoint>" if adj_ms >= fwd_ms else "step_kernel<float,forward>"
     dom_ms, dom_b = (adj_ms, adj_b) if adj_ms >= fwd_ms else (fwd_ms, fwd_b)
     achieved = dom_b / (dom_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(dom.split("<")[0])
+    traffic = recorded_traffic(dom)
 
     # end to end through the public API with host buffers
     obs_host = torch.from_numpy(obs_np.astype(np.float32)).pin_memory()
