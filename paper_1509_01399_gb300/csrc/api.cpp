@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <array>
 #include <utility>
 #include <vector>
 
@@ -101,6 +102,10 @@ struct hyb_mesh {
   DevBuf rrow, rptr, rcol, rval, cptr, cunk, cw, rmask, rzr, refvox, refvox_id, k9;
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
   cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
+  // interior work items of the forward / transposed step per slot count; built
+  // once and kept (captured sweep graphs refer to them)
+  DevBuf items[2][kMaxSlots + 1];
+  int nitems[2][kMaxSlots + 1] = {};
   int nsm = 0;                 // SMs of the device
   int bps = 0;                 // resident step-kernel blocks per SM
   SweepGraph graphs[3];
@@ -250,32 +255,77 @@ int mask_at(const hyb_mesh* m, const hyb_source& s, int k, double dt) {
   return mask;
 }
 
-// Launch geometry of one step: the interior blocks cover nodes 1 .. n-2 on
-// every axis in 32 x 8 tiles and z chunks, sized so that the launch fills
-// the SMs kStepWaves times at the step kernel's occupancy; the edge tiles
-// cover the nodes within one node of two faces.  Lattices with fewer than 5
-// nodes on an axis use a single generic kernel instead.
-constexpr int kStepWaves = 2;
-
-void step_geometry(const hyb_mesh* m, int nslots, int* npb, int* ntx, int* zchunk, int* nzc, int* small,
-                   int* nedge) {
+// Launch geometry of one step: the interior covers nodes 1 .. n-2 on every
+// axis in 32 x 16 tiles; the edge tiles cover the nodes within one node of
+// two faces.  Lattices with fewer than 5 nodes on an axis use a single
+// generic kernel instead.
+void step_geometry(const hyb_mesh* m, int* npb, int* ntx, int* small, int* nedge) {
   *small = (m->n[0] < 5 || m->n[1] < 5 || m->n[2] < 5) ? 1 : 0;
   *nedge = *small ? 0 : 1 + (m->n[0] - 4 + 7) / 8 + (m->n[1] - 4 + 7) / 8 + (m->n[2] - 4 + 7) / 8;
-  const long long bx = m->n[0] - 2, by = m->n[1] - 2, bz = m->n[2] - 2;
-  *ntx = (int)((bx + kTileX - 1) / kTileX);
-  const int nty = (int)((by + kTileY - 1) / kTileY);
+  *ntx = (m->n[0] - 2 + kTileX - 1) / kTileX;
+  const int nty = (m->n[1] - 2 + kTileY - 1) / kTileY;
   *npb = *ntx * nty;
-  // z chunks per tile: as many as fit kStepWaves full waves (rounded down,
-  // so that no wave is left part-filled)
-  const long long target = (long long)std::max(m->nsm, 1) * std::max(m->bps, 1) * kStepWaves;
-  const long long per_z = (long long)(*npb) * nslots;
-  long long want = target / per_z;
-  if (want < 1) want = 1;
-  long long z = (bz + want - 1) / want;
-  z = std::max<long long>(z, 2);
-  z = std::min<long long>(z, bz);
-  *zchunk = (int)z;
-  *nzc = (int)((bz + z - 1) / z);
+}
+
+// Waves of resident interior blocks the work items are cut for: one when
+// each resident block would get few tile levels (a block's first level waits
+// for its planes, so long items pay off), three when there is much work
+// (blocks of uneven speed then even out within each SM).
+constexpr int kStepWavesFew = 1, kStepWavesMany = 3;
+constexpr double kManyLevelsPerBlock = 40.0;
+
+// Interior work items of one step launch, one per block: (slot, tile, z0,
+// z1).  Each tile's z range 1 .. n-2 is cut into pieces of about equal
+// estimated cost, so that the items fill the chosen number of waves of the
+// kernel's resident blocks evenly.  Relative cost of one tile level (measured per
+// level with cycle counters): 1 for a plain tile, 1.6 for a tile next to an
+// x or y face, plus 0.7 (forward) or 1.0 (transposed step with the gradient
+// pairing) on planes where the tile holds FEM-owned nodes.
+std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
+  const int nx = m->n[0], ny = m->n[1], nz = m->n[2];
+  const int ntx = (nx - 2 + kTileX - 1) / kTileX, nty = (ny - 2 + kTileY - 1) / kTileY;
+  struct Tile {
+    int si, tile;
+    double base, extra;
+  };
+  std::vector<Tile> tiles;
+  double total = 0.0;
+  const int zf0 = m->fl[2], zf1 = m->fh[2];
+  const int fem_levels = m->fem ? std::max(0, std::min(zf1, nz - 2) - std::max(zf0, 1) + 1) : 0;
+  for (int si = 0; si < nslots; ++si)
+    for (int ty = 0; ty < nty; ++ty)
+      for (int tx = 0; tx < ntx; ++tx) {
+        const int i0 = 1 + tx * kTileX, j0 = 1 + ty * kTileY;
+        const bool face = i0 == 1 || i0 + kTileX - 1 >= nx - 2 || j0 == 1 || j0 + kTileY - 1 >= ny - 2;
+        const bool femt = m->fem && i0 <= m->fh[0] && i0 + kTileX - 1 >= m->fl[0] && j0 <= m->fh[1] &&
+                          j0 + kTileY - 1 >= m->fl[1];
+        const Tile t{si, ty * ntx + tx, face ? 1.6 : 1.0, femt ? (adjoint ? 1.0 : 0.7) : 0.0};
+        tiles.push_back(t);
+        total += t.base * (nz - 2) + t.extra * fem_levels;
+      }
+  const double resident = (double)std::max(m->nsm, 1) * std::max(m->bps, 1);
+  const double levels_per_block = (double)tiles.size() * (nz - 2) / resident;
+  const double cap = resident * (levels_per_block > kManyLevelsPerBlock ? kStepWavesMany : kStepWavesFew);
+  const double target = total / cap;
+  std::vector<std::pair<double, std::array<int, 4>>> items;
+  for (const Tile& t : tiles) {
+    double acc = 0.0;
+    int z0 = 1;
+    for (int k = 1; k <= nz - 2; ++k) {
+      acc += t.base + ((k >= zf0 && k <= zf1) ? t.extra : 0.0);
+      if (acc >= target || k == nz - 2) {
+        items.push_back({acc, {t.si, t.tile, z0, k + 1}});
+        z0 = k + 1;
+        acc = 0.0;
+      }
+    }
+  }
+  // costliest first: with more items than resident blocks they start early
+  std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<int> out;
+  out.reserve(items.size() * 4);
+  for (const auto& it : items) out.insert(out.end(), it.second.begin(), it.second.end());
+  return out;
 }
 
 // One time level: a single launch on `st`.
@@ -565,6 +615,23 @@ hyb_status step_maps(const hyb_mesh* m, StepArgs<T>& A, const DevBuf& field, int
   return HYB_OK;
 }
 
+// Work items of the step launches with `nslots` slots (built and uploaded the
+// first time this slot count is used, outside any captured sweep).
+template <typename T>
+hyb_status step_items(hyb_mesh* m, StepArgs<T>& A, int nslots, bool adjoint) {
+  if (A.small) return HYB_OK;
+  const int d = adjoint ? 1 : 0;
+  DevBuf& buf = m->items[d][nslots];
+  if (!buf.p) {
+    const std::vector<int> host = build_items(m, nslots, adjoint);
+    HYB_TRY(upload(m, buf, host));
+    m->nitems[d][nslots] = (int)(host.size() / 4);
+  }
+  A.items = (const int*)buf.p;
+  A.nitems = m->nitems[d][nslots];
+  return HYB_OK;
+}
+
 template <typename T>
 void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   std::memset(&A, 0, sizeof(A));
@@ -591,7 +658,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   const double h = m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
   A.r = (T)((h - dt) / (h + dt));
-  step_geometry(m, nslots, &A.npb, &A.ntx, &A.zchunk, &A.nzc, &A.small, &A.nedge);
+  step_geometry(m, &A.npb, &A.ntx, &A.small, &A.nedge);
   A.nslots = nslots;
   A.nlat = m->Np;
   if (m->nc > 0) {
@@ -680,6 +747,7 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
   StepArgs<T> A;
   base_args(m, A, dt, nsrc);
   HYB_TRY(step_maps<T>(m, A, m->U, nsrc, 0));
+  HYB_TRY(step_items<T>(m, A, nsrc, false));
   if (m->fem) {
     launch_set_coef<T>(A, (T*)m->W.p, a, m->d.a_max, (int*)m->flag.p, m->st);
     HYB_LAUNCHED(m);
@@ -807,6 +875,8 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   base_args(m, F, dt, nsrc);
   HYB_TRY(step_maps<T>(m, A, m->L, nsrc, ckpt ? C : nsteps));
   HYB_TRY(step_maps<T>(m, F, m->U, nsrc, 0));
+  HYB_TRY(step_items<T>(m, A, nsrc, true));
+  HYB_TRY(step_items<T>(m, F, nsrc, false));
   auto body = [&](cudaStream_t st) -> hyb_status {
     if (!accumulate) HYB_CU(cudaMemsetAsync(m->G.p, 0, (size_t)nsrc * m->nu * sizeof(double), st));
     for (int s = 0; s < nsrc; ++s) {
@@ -1162,6 +1232,8 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
                     &m->cptr, &m->cunk, &m->cw, &m->rmask, &m->rzr, &m->refvox, &m->refvox_id, &m->k9,
                     &m->CU, &m->CL, &m->chist, &m->cckpt};
   for (DevBuf* b : bufs) release(*b);
+  for (auto& dir : m->items)
+    for (DevBuf& b : dir) release(b);
   if (m->hscal) cudaFreeHost(m->hscal);
   for (SweepGraph& g : m->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);

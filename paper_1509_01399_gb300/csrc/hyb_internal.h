@@ -69,9 +69,10 @@ struct StepArgs {
   int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
   T c2;              // tau^2 / h^2
   T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
-  int npb;           // interior: thread blocks per plane of the interior box
+  int npb;           // interior: tiles per plane of the interior box
   int ntx;           // interior: tiles along x
-  int zchunk, nzc;   // interior: planes per block, blocks along z
+  const int* items;  // interior work items, one per block: (slot, tile, z0, z1)
+  int nitems;
   int small;         // some axis has < 5 nodes: one generic kernel per level
   int nedge;         // edge tiles (128 nodes) per slot
   int nhe, nhr;      // step kernel: leading blocks of edge tiles, then of refined rows

@@ -757,9 +757,9 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
 }
 
 // Interior part of one time level (lattices with >= 5 nodes per axis):
-// 32 x 16 tiles of the nodes 1 .. n-2 and z chunks, one block per (tile,
-// chunk): eight consumer warps (two tile rows per thread) and a producer
-// warp.  Nodes one step inside an x or y face also produce the face node;
+// 32 x 16 tiles of the nodes 1 .. n-2 and z ranges, one block per work item
+// (slot, tile, z range; the host balances the items by cost): eight
+// consumer warps (two tile rows per thread) and a producer warp.  Nodes one step inside an x or y face also produce the face node;
 // planes one step inside a z face take the general rows from global memory.
 template <typename T, bool ADJ>
 __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* sm) {
@@ -767,16 +767,12 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   static_assert(kTileX * kTileY / 2 + 32 == kStepBlock, "eight consumer warps (two rows each) and a producer warp");
   using P = kPipe<T>;
   constexpr int D = P::D;
-  const int tps = A.npb * A.nzc;
-  const int si = b / tps;
-  int rem = b - si * tps;
-  const int zc = rem / A.npb;
-  rem -= zc * A.npb;
-  const int tyy = rem / A.ntx;
-  const int txx = rem - tyy * A.ntx;
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int z0 = 1 + zc * A.zchunk;
-  const int z1 = min(z0 + A.zchunk, nz - 1);
+  const int* item = A.items + 4 * b;  // (slot, tile, z0, z1)
+  const int si = item[0];
+  const int tyy = item[1] / A.ntx;
+  const int txx = item[1] - tyy * A.ntx;
+  const int z0 = item[2], z1 = item[3];
+  const int nx = A.nx, ny = A.ny;
   if (z0 >= z1) return;  // whole block
   const int t = (int)threadIdx.x;
   const int tx = t & 31, ty = t >> 5;
@@ -1193,7 +1189,7 @@ void launch_step(const StepArgs<T>& a, cudaStream_t st) {
   StepArgs<T> b = a;
   b.nhe = ((a.nedge + 1) / 2) * a.nslots;
   b.nhr = (int)refined_blocks(a, ADJ);
-  const long long grid = (long long)b.nhe + b.nhr + (long long)a.npb * a.nzc * a.nslots;
+  const long long grid = (long long)b.nhe + b.nhr + a.nitems;
   step_kernel<T, ADJ><<<(unsigned)grid, kStepBlock, kPipe<T>::bytes, st>>>(b);
 }
 
