@@ -64,4 +64,10 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Programmatic dependent launch: let the next launch in the stream start its
+// blocks now (they wait in pdl_wait), and wait for the previous launch's
+// completion and memory before touching what it wrote or read.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace hyb

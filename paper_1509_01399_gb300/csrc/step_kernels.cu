@@ -828,6 +828,7 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
     for (int q = 0; q < P::NB; ++q) mbar_init(pr.bars + q, 1);
     mbar_init_fence();
   }
+  pdl_wait();  // the previous level is complete: its output may be read, its input overwritten
   __syncthreads();
   if (t == tp) {
     for (int g = 0; g < D && z0 + g < z1; ++g) pr.issue(z0 + g, g == 0);
@@ -939,8 +940,10 @@ template <typename T, bool ADJ>
 __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kernel(const __grid_constant__ StepArgs<T> A) {
   extern __shared__ __align__(128) unsigned char hyb_smem[];  // kPipe<T>::bytes
   T* sh = reinterpret_cast<T*>(hyb_smem);
+  pdl_trigger();  // the next level's launch may start its blocks
   int b = blockIdx.x;
   if (b < A.nhe) {  // two 128-node tiles; the last warp takes part in the barriers only
+    pdl_wait();     // the previous level is complete
     const int ne2 = (A.nedge + 1) / 2;
     const int si = b / ne2;
     const int half = (int)(threadIdx.x >> 7);
@@ -954,6 +957,7 @@ __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kerne
   }
   b -= A.nhe;
   if (b < A.nhr) {
+    pdl_wait();
     refined_rows<T, ADJ>(A, (long long)b * kStepBlock + threadIdx.x);
     return;
   }
@@ -1190,7 +1194,19 @@ void launch_step(const StepArgs<T>& a, cudaStream_t st) {
   b.nhe = ((a.nedge + 1) / 2) * a.nslots;
   b.nhr = (int)refined_blocks(a, ADJ);
   const long long grid = (long long)b.nhe + b.nhr + a.nitems;
-  step_kernel<T, ADJ><<<(unsigned)grid, kStepBlock, kPipe<T>::bytes, st>>>(b);
+  // programmatic dependent launch: this level's blocks may start while the
+  // previous step launch drains (they wait for it before touching its data)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kStepBlock);
+  cfg.dynamicSmemBytes = kPipe<T>::bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, step_kernel<T, ADJ>, b);
 }
 
 template <typename T>
