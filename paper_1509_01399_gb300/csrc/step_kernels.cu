@@ -2,12 +2,15 @@
 //
 // One time level of every slot (source / problem) is one launch of
 // step_kernel: its leading blocks run the edge tiles (nodes within one node
-// of two faces) and the refined sparse rows, the rest the interior (all
-// other nodes).  All blocks read levels k and k-1 and write disjoint nodes of
-// level k+1.  An interior thread owns one (x, y) column of a 32 x 8 tile (one
-// warp per tile row) and marches a chunk of z planes, keeping u at z-1, z,
-// z+1 in registers, taking x/y neighbours through L1 and prefetching several
-// planes ahead.  Row kinds:
+// of two faces) and the refined sparse rows, the other blocks the interior
+// (all other nodes), one work item (slot, 32 x 16 tile, z range) each.  All
+// blocks read levels k and k-1 and write disjoint nodes of level k+1.  An
+// interior block's producer warp stages the planes it needs (u^k with a
+// one-node halo, u^{k-1}, FEM edge weights, stored history) into shared
+// memory with bulk tensor copies two levels ahead; its eight consumer warps
+// (two tile rows per thread) march the z range reading only shared memory.
+// Consecutive launches overlap through programmatic dependent launch.
+// Row kinds:
 //  * FDM rows, Eq. (fdmschemeforward): u^{k+1} = 2u^k - u^{k-1} + tau^2 Delta_h u^k,
 //  * FEM rows on the FEM-owned nodes, Eq. (fem) with lumped mass: on the
 //    Kuhn-cut voxels the row is a 7-point stencil whose axis-edge weight is
@@ -30,7 +33,8 @@
 // solves the transposed absorbing coupling by recomputing the outer values.
 // The same launch accumulates, per unknown voxel and in FP64, the sum over
 // the voxel's 12 axis edges of w_e (u_p - u_q)(lambda_p - lambda_q) with
-// w_e = 1/3 or 1/6; the host scales it by -tau^2 / h^2 (Eq. (gradient1)).
+// w_e = 2 or 1 (six times the edge weights 1/3 and 1/6); the host scales it
+// by -tau^2 / (6 h^2) (Eq. (gradient1)).
 #include "async_copy.cuh"
 #include "hyb_internal.h"
 
