@@ -273,6 +273,7 @@ void step_geometry(const hyb_mesh* m, int* npb, int* ntx, int* small, int* nedge
 // (blocks of uneven speed then even out within each SM).
 constexpr int kStepWavesFew = 1, kStepWavesMany = 3;
 constexpr double kManyLevelsPerBlock = 40.0;
+constexpr double kZFaceLevelCost = 10.0;
 
 // Interior work items of one step launch, one per block: (slot, tile, z0,
 // z1).  Each tile's z range 1 .. n-2 is cut into pieces of about equal
@@ -280,7 +281,9 @@ constexpr double kManyLevelsPerBlock = 40.0;
 // kernel's resident blocks evenly.  Relative cost of one tile level (measured per
 // level with cycle counters): 1 for a plain tile, 1.6 for a tile next to an
 // x or y face, plus 0.7 (forward) or 1.0 (transposed step with the gradient
-// pairing) on planes where the tile holds FEM-owned nodes.
+// pairing) on planes where the tile holds FEM-owned nodes, plus
+// kZFaceLevelCost on the two planes next to the z faces (general rows read
+// from global memory).
 std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
   const int nx = m->n[0], ny = m->n[1], nz = m->n[2];
   const int ntx = (nx - 2 + kTileX - 1) / kTileX, nty = (ny - 2 + kTileY - 1) / kTileY;
@@ -301,7 +304,7 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
                           j0 + kTileY - 1 >= m->fl[1];
         const Tile t{si, ty * ntx + tx, face ? 1.6 : 1.0, femt ? (adjoint ? 1.0 : 0.7) : 0.0};
         tiles.push_back(t);
-        total += t.base * (nz - 2) + t.extra * fem_levels;
+        total += t.base * (nz - 2) + t.extra * fem_levels + 2 * kZFaceLevelCost;
       }
   const double resident = (double)std::max(m->nsm, 1) * std::max(m->bps, 1);
   const double levels_per_block = (double)tiles.size() * (nz - 2) / resident;
@@ -312,7 +315,7 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
     double acc = 0.0;
     int z0 = 1;
     for (int k = 1; k <= nz - 2; ++k) {
-      acc += t.base + ((k >= zf0 && k <= zf1) ? t.extra : 0.0);
+      acc += t.base + ((k >= zf0 && k <= zf1) ? t.extra : 0.0) + ((k == 1 || k == nz - 2) ? kZFaceLevelCost : 0.0);
       if (acc >= target || k == nz - 2) {
         items.push_back({acc, {t.si, t.tile, z0, k + 1}});
         z0 = k + 1;
