@@ -273,7 +273,7 @@ void step_geometry(const hyb_mesh* m, int* npb, int* ntx, int* small, int* nedge
 // (blocks of uneven speed then even out within each SM).
 constexpr int kStepWavesFew = 1, kStepWavesMany = 3;
 constexpr double kManyLevelsPerBlock = 40.0;
-constexpr double kZFaceLevelCost = 10.0;
+constexpr double kZFaceLevelCost = 0.5;
 
 // Interior work items of one step launch, one per block: (slot, tile, z0,
 // z1).  Each tile's z range 1 .. n-2 is cut into pieces of about equal
@@ -282,8 +282,8 @@ constexpr double kZFaceLevelCost = 10.0;
 // level with cycle counters): 1 for a plain tile, 1.6 for a tile next to an
 // x or y face, plus 0.7 (forward) or 1.0 (transposed step with the gradient
 // pairing) on planes where the tile holds FEM-owned nodes, plus
-// kZFaceLevelCost on the two planes next to the z faces (general rows read
-// from global memory).
+// kZFaceLevelCost on the two planes next to the z faces (they also produce
+// the face plane).
 std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
   const int nx = m->n[0], ny = m->n[1], nz = m->n[2];
   const int ntx = (nx - 2 + kTileX - 1) / kTileX, nty = (ny - 2 + kTileY - 1) / kTileY;

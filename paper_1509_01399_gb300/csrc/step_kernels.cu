@@ -418,43 +418,6 @@ __device__ __forceinline__ int edge_tile_peer(int t, int blk, const int q[3], in
   return (t & ~(3 << sh)) | (qn << sh);
 }
 
-// Value of a face node b on the single face f, from u^k at b (ub), at its
-// inward neighbour m (um), the new value at m (nm), b's four in-face
-// neighbours (first the lower of the two other axes, each as (minus, plus))
-// and u^{k-1} at b.  Absorbing: Eq. (eq:abs2); otherwise the mirror-ghost
-// row with the source flux.
-template <typename T>
-__device__ __forceinline__ T fwd_face_row(const StepArgs<T>& A, const Slot<T>& S, int f, T ub, T um, T nm, T n1m,
-                                          T n1p, T n2m, T n2p, T pb) {
-  if ((S.mask_f >> f) & 1) return A.r * ub + (um - A.r * nm);
-  T lap = T(2) * (um - ub);
-  lap += (n1m - ub) + (n1p - ub);
-  lap += (n2m - ub) + (n2p - ub);
-  T v = T(2) * ub - pb + A.c2 * lap;
-  if (S.src_face == f) v += S.srcval;
-  return v;
-}
-
-// lambda^j at a face node b on the single face f whose in-face coordinates
-// are at least 2 from the edges (no transposed absorbing coupling reaches
-// it), from lambda^{j+1} at b and at its inward neighbour m, the coefficient
-// of m's row on b, b's four in-face neighbours (as in fwd_face_row) and
-// lambda^{j+2} at b.
-template <typename T>
-__device__ __forceinline__ T adj_face_row(const StepArgs<T>& A, const Slot<T>& S, int f, int bi, int bj, int bk,
-                                          T lb, T lm, T coef_mb, T n1m, T n1p, T n2m, T n2p, T pb) {
-  const bool abc = (S.mask_f >> f) & 1;
-  T rhs = abc ? A.r * lb : (T(2) - T(6) * A.c2) * lb;
-  rhs += A.c2 * coef_mb * lm;
-  if (!abc) {
-    rhs += A.c2 * (n1m + n1p);
-    rhs += A.c2 * (n2m + n2p);
-  }
-  if (!((S.mask_c >> f) & 1)) rhs -= pb;
-  if (S.obs_r && S.obs_face == f) rhs += S.obs_r[face_index(f, bi, bj, bk, A.nx, A.ny)];
-  return rhs;
-}
-
 // Position of an interior thread.
 struct Col {
   int si, i, j;
@@ -463,71 +426,6 @@ struct Col {
   bool xy_vox;    // (i, j) is the x-y origin of an unknown voxel and the step pairs
   int rz0, rz1;   // z range of the column's sparse-row nodes (rz0 > rz1: none)
 };
-
-// Node (i, j, k) of the interior by the general rows, reading level data from
-// global memory (u^k at z-1, z, z+1 and u^{k-1} given): any node, including
-// those one node inside a z face.  A node one step inside exactly one face
-// also produces the face node next to it (the forward needs its new value;
-// the transposed face row has a closed form) and applies the transposed
-// boundary couplings to itself.  Nodes within one node of two faces belong
-// to the edge tiles.
-template <typename T, bool ADJ>
-__device__ __noinline__ void general_node(const StepArgs<T>& A, const Slot<T>& S, const Col& C, int k, T cm, T c0,
-                                             T cp, T pv) {
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int i = C.i, j = C.j;
-  const int dzs = (k == 1) ? -1 : (k == nz - 2 ? 1 : 0);
-  const int cnt = (C.dxs != 0) + (C.dys != 0) + (dzs != 0);
-  if (cnt > 1) return;
-  const long long id = lin(A, i, j, k);
-  const T* __restrict__ cq = S.cur + id;
-  const T c2 = A.c2;
-  T val;
-  const bool fem = C.xy_fem && k >= A.fl[2] && k <= A.fh[2];
-  if (fem) {
-    val = T(2) * c0 - pv + c2 * fem_lap(A, S.cur, id, i, j, k, c0, cm, cp);
-  } else {
-    val = T(2) * c0 - pv + c2 * lap7(cq[-1], cq[1], cq[-A.px], cq[A.px], cm, cp, c0);
-  }
-  if (cnt == 1) {
-    const int ax = C.dxs ? 0 : (C.dys ? 1 : 2);
-    const int sd = C.dxs ? C.dxs : (C.dys ? C.dys : dzs);
-    const int f = 2 * ax + (sd > 0 ? 1 : 0);
-    const long long db = sd * axis_stride(A, ax);
-    const long long idb = id + db;
-    const T xb = ax == 2 ? (sd < 0 ? cm : cp) : cq[db];
-    const long long s1 = axis_stride(A, ax == 0 ? 1 : 0);
-    const long long s2 = axis_stride(A, ax == 2 ? 1 : 2);
-    const T* __restrict__ u = S.cur;
-    const int bi = i + (ax == 0 ? sd : 0), bj = j + (ax == 1 ? sd : 0), bk = k + (ax == 2 ? sd : 0);
-    if constexpr (!ADJ) {
-      const T vb = fwd_face_row(A, S, f, xb, c0, val, u[idb - s1], u[idb + s1], u[idb - s2], u[idb + s2], S.prev[idb]);
-      S.next[idb] = vb;
-      if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, bk, nx, ny)] = vb;
-    } else {
-      const T coef_mb = row_coef(A, i, j, k, ax, sd);
-      const T lb = adj_face_row(A, S, f, bi, bj, bk, xb, c0, coef_mb, u[idb - s1], u[idb + s1], u[idb - s2],
-                                u[idb + s2], S.prev[idb]);
-      // the face row's transposed coefficient on this node replaces the
-      // symmetric one the stencil used
-      val += (((S.mask_f >> f) & 1) ? xb : T(2) * c2 * xb) - c2 * coef_mb * xb;
-      if ((S.mask_e >> f) & 1) val -= A.r * lb;
-      S.next[idb] = lb;
-    }
-  }
-  const long long bidx = fem ? hidx(A, i, j, k) : 0;
-  if (!(fem && A.rmask && A.rmask[bidx])) {  // sparse rows are written by the refined rows
-    S.next[id] = val;
-    if (!ADJ && S.hist_w && fem) S.hist_w[bidx] = val;
-  }
-  if (ADJ && C.xy_vox && k >= A.fl[2] && k < A.fl[2] + A.un[2]) {
-    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
-    const long long vid =
-        (long long)(i - A.fl[0]) + (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
-    if (!(A.refvox && A.refvox[vid]))
-      atomicAdd(A.G + (long long)C.si * nv + vid, (double)voxel_pair(A, S.hist_r, S.cur, i, j, k));
-  }
-}
 
 // ---- shared-memory pipeline of the interior blocks ----
 // A block stages, plane by plane and kPipe<T>::D levels ahead of its z
@@ -609,9 +507,10 @@ struct Producer {
 // stored-u boxes of planes k / k+1 (at the voxel origin).
 template <typename T, bool ADJ, bool FEMT, bool FACE>
 __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T>& S, const Col& C, int k, int off,
-                                              const T* Ck, const T* Cm, const T* Cp, const T* Pk, const T* Wk,
-                                              const T* Wm, const T* Hk, const T* Hp) {
+                                              int dzs, const T* Ck, const T* Cm, const T* Cp, const T* Pk,
+                                              const T* Wk, const T* Wm, const T* Hk, const T* Hp) {
   using P = kPipe<T>;
+  if (dzs != 0 && (C.dxs != 0 || C.dys != 0)) return;  // near two faces: edge tiles
   const T c2 = A.c2;
   const T c0 = Ck[0], cm = Cm[0], cp = Cp[0], pv = Pk[0];
   const T xm = Ck[-1], xp = Ck[1], ym = Ck[-kBoxX], yp = Ck[kBoxX];
@@ -619,18 +518,54 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
   T wxm = T(1), wxp = T(1), wym = T(1), wyp = T(1);
   T lap;
   if constexpr (FEMT) lf = C.xy_fem && k >= A.fl[2] && k <= A.fh[2];
+  T wzm = T(1), wzp = T(1);
   if (FEMT && lf) {
     wxm = Wk[-1];
     wxp = Wk[0];
     wym = Wk[P::WS - kBoxX];
     wyp = Wk[P::WS];
-    lap = wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + Wk[2 * P::WS] * (cp - c0) +
-          Wm[2 * P::WS] * (cm - c0);
+    wzp = Wk[2 * P::WS];
+    wzm = Wm[2 * P::WS];
+    lap = wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + wzp * (cp - c0) + wzm * (cm - c0);
   } else {
     lap = lap7(xm, xp, ym, yp, cm, cp, c0);
   }
   T val = T(2) * c0 - pv + c2 * lap;
   T* __restrict__ gnext = S.next;
+  if (dzs != 0) {  // the z face node next to this node (the rows of the x / y faces below)
+    const int f = dzs > 0 ? 5 : 4;
+    const T* Cb = dzs > 0 ? Cp : Cm;  // b and its in-face neighbours in the staged plane k +- 1
+    const T ub = Cb[0];
+    const bool abc = (S.mask_f >> f) & 1;
+    const int offb = off + dzs * A.px * A.ny;
+    if constexpr (!ADJ) {
+      T vb;
+      if (abc) {
+        vb = A.r * ub + (c0 - A.r * val);
+      } else {
+        T lb = T(2) * (c0 - ub);
+        lb += (Cb[-1] - ub) + (Cb[1] - ub);
+        lb += (Cb[-kBoxX] - ub) + (Cb[kBoxX] - ub);
+        vb = T(2) * ub - S.prev[offb] + c2 * lb;  // (u^{k-1} of the face plane is not staged)
+        if (S.src_face == f) vb += S.srcval;
+      }
+      gnext[offb] = vb;
+      if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, C.i, C.j, k + dzs, A.nx, A.ny)] = vb;
+    } else {
+      const T coef_mb = dzs > 0 ? wzp : wzm;
+      T lb = abc ? A.r * ub : (T(2) - T(6) * c2) * ub;
+      lb += c2 * coef_mb * c0;
+      if (!abc) {
+        lb += c2 * (Cb[-1] + Cb[1]);
+        lb += c2 * (Cb[-kBoxX] + Cb[kBoxX]);
+      }
+      if (!((S.mask_c >> f) & 1)) lb -= S.prev[offb];
+      if (S.obs_r && S.obs_face == f) lb += S.obs_r[face_index(f, C.i, C.j, k + dzs, A.nx, A.ny)];
+      val += (abc ? ub : T(2) * c2 * ub) - c2 * coef_mb * ub;
+      if ((S.mask_e >> f) & 1) val -= A.r * lb;
+      gnext[offb] = lb;
+    }
+  }
   if constexpr (FACE) {
     if (C.dxs != 0 || C.dys != 0) {  // the x or y face node next to this node
       const int ax = C.dxs ? 0 : 1;
@@ -642,8 +577,12 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
       const bool abc = (S.mask_f >> f) & 1;
       const int offb = off + (ax == 0 ? sd : sd * A.px);
       const int bi = C.i + (ax == 0 ? sd : 0), bj = C.j + (ax == 1 ? sd : 0);
-      // (as fwd_face_row / adj_face_row; the in-face neighbours, the other
-      // in-plane axis first, then z, are read only for non-absorbing faces)
+      // Forward: the absorbing row of Eq. (eq:abs2) from u^k at b and m and
+      // the new value at m, or the mirror-ghost row with the source flux.
+      // Transposed: b's row in closed form (no transposed absorbing coupling
+      // reaches it), from lambda^{j+1} at b and m, the coefficient of m's row
+      // on b and lambda^{j+2} at b.  The in-face neighbours (the other
+      // in-plane axis first, then z) are read only for non-absorbing faces.
       if constexpr (!ADJ) {
         T vb;
         if (abc) {
@@ -736,11 +675,8 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     const T* Cm = pr.CR + ((k - 1) & (P::SC - 1)) * P::CS;
     const T* Cp = pr.CR + ((k + 1) & (P::SC - 1)) * P::CS;
     const T* Pk = pr.PR + (k & (P::SP - 1)) * P::CS;
-    if (k == 1 || k == nz - 2) {  // block-uniform: the general rows, from global memory
-      if (active[0]) general_node<T, ADJ>(A, S, C[0], k, Cm[o0], Ck[o0], Cp[o0], Pk[o0]);
-      if (active[1]) general_node<T, ADJ>(A, S, C[1], k, Cm[o1], Ck[o1], Cp[o1], Pk[o1]);
-      continue;
-    }
+    // planes one step inside a z face also produce the face plane (block-uniform)
+    const int dzs = k == 1 ? -1 : (k == nz - 2 ? 1 : 0);
     const T* Wk = nullptr;
     const T* Wm = nullptr;
     const T* Hk = nullptr;
@@ -752,11 +688,11 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
       Hp = pr.HR + ((k + 1) & (P::SH - 1)) * P::WS;
     }
     if (active[0])
-      interior_node<T, ADJ, FEMT, FACE>(A, S, C[0], k, off0, Ck + o0, Cm + o0, Cp + o0, Pk + o0, Wk + o0, Wm + o0,
-                                        Hk + h0, Hp + h0);
+      interior_node<T, ADJ, FEMT, FACE>(A, S, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0, Pk + o0,
+                                        Wk + o0, Wm + o0, Hk + h0, Hp + h0);
     if (active[1])
-      interior_node<T, ADJ, FEMT, FACE>(A, S, C[1], k, off1, Ck + o1, Cm + o1, Cp + o1, Pk + o1, Wk + o1, Wm + o1,
-                                        Hk + h1, Hp + h1);
+      interior_node<T, ADJ, FEMT, FACE>(A, S, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1, Pk + o1,
+                                        Wk + o1, Wm + o1, Hk + h1, Hp + h1);
   }
 }
 
