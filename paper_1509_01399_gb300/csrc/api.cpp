@@ -662,6 +662,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.G = (double*)m->G.p;
   const double h = m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
+  A.cd = (T)(2.0 - 6.0 * (dt * dt / (h * h)));
   A.r = (T)((h - dt) / (h + dt));
   step_geometry(m, &A.npb, &A.ntx, &A.small, &A.nedge);
   A.nslots = nslots;

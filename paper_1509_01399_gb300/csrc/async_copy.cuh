@@ -33,6 +33,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+// Arrive on the barrier (release: this thread's earlier accesses, and those
+// ordered before them by a warp barrier, happen before the phase completes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Wait for the phase with the given parity of the barrier to complete, for
 // at most `budget` clock cycles, giving up early once *abort is nonzero
 // (another block timed out).  Returns false on timeout or abort.  Each try

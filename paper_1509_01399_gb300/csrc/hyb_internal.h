@@ -68,6 +68,7 @@ struct StepArgs {
   double* G;         // FP64 gradient accumulator over unknown voxels (adjoint)
   int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
   T c2;              // tau^2 / h^2
+  T cd;              // 2 - 6 c2: diagonal of a lattice row with unit weights
   T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
   int npb;           // interior: tiles per plane of the interior box
   int ntx;           // interior: tiles along x

@@ -429,14 +429,17 @@ struct Col {
 
 // ---- shared-memory pipeline of the interior blocks ----
 // A block stages, plane by plane and kPipe<T>::D levels ahead of its z
-// march, boxes that its producer warp loads with bulk tensor copies (TMA)
-// and that complete on one mbarrier per level: u^k on the tile and a
-// one-node halo (36 x 10 from x = i0 - 1: the box width is a multiple of 16
-// bytes), u^{k-1} on the same box, and on tiles that meet the FEM block the
-// three edge-weight arrays and, for the transposed step, the stored u of the
-// FEM-owned box (36 x 9).  Each plane lives in a ring of stages indexed by
-// the plane number modulo the (power-of-two) ring size.  The eight consumer
-// warps (the 32 x 8 tile) read only shared memory.
+// march, boxes that its producer warp loads with bulk tensor copies (TMA):
+// u^k on the tile and a one-node halo (36 x 18 from x = i0 - 1: the box
+// width is a multiple of 16 bytes), u^{k-1} on the same box, and on tiles
+// that meet the FEM block the three edge-weight arrays and, for the
+// transposed step, the stored u of the FEM-owned box (36 x 17).  Each plane
+// lives in a ring of stages indexed by the plane number modulo the
+// (power-of-two) ring size.  The copies of a level complete on its "full"
+// mbarrier; each of the eight consumer warps (the 32 x 16 tile, two rows per
+// thread) waits on it, reads only shared memory and arrives on the level's
+// "empty" mbarrier, on which the producer waits before it overwrites the
+// level's stages.  The consumer warps thus run up to D levels apart.
 constexpr int kBoxX = kTileX + 4, kBoxY = kTileY + 2, kBox = kBoxX * kBoxY;  // 36 x 18
 constexpr int kHBoxY = kTileY + 1, kHBox = kBoxX * kHBoxY;                    // 36 x 17
 
@@ -449,11 +452,11 @@ struct kPipe {
   static constexpr int SP = pow2(D + 1);  // u^{k-1} stages (k .. k+D)
   static constexpr int SW = pow2(D + 2);  // edge-weight stages (k-1 .. k+D)
   static constexpr int SH = pow2(D + 2);  // stored-u stages (k .. k+1+D)
-  static constexpr int NB = pow2(D + 1);  // level barriers
+  static constexpr int NB = pow2(D + 1);  // level barriers (of each kind)
   static constexpr int CS = round128(kBox);   // elements per u stage (128-byte aligned)
   static constexpr int WS = round128(kHBox);  // elements per edge-weight array / stored-u stage
   static constexpr int elems = SC * CS + SP * CS + SW * 3 * WS + SH * WS;
-  static constexpr size_t bytes = sizeof(T) * (size_t)elems + 8 * NB;
+  static constexpr size_t bytes = sizeof(T) * (size_t)elems + 16 * NB;
 };
 
 // Producer side of one interior block: which boxes exist, and their issue.
@@ -462,7 +465,8 @@ struct Producer {
   const StepArgs<T>* A;
   const Slot<T>* S;
   T *CR, *PR, *WR, *HR;
-  uint64_t* bars;
+  uint64_t* full;   // [NB]: the planes of a level have landed (one arrival: the producer, plus bytes)
+  uint64_t* empty;  // [NB]: the consumer warps are done with a level (eight arrivals)
   int z0, z1, xf, yf, xw, yw, xh, yh;
   bool fem_tile, hist_tile;
   // the planes first read at level g (the first level also reads planes
@@ -471,7 +475,7 @@ struct Producer {
     using P = kPipe<T>;
     constexpr uint32_t kCBytes = (uint32_t)(kBox * sizeof(T));
     constexpr uint32_t kWBytes = (uint32_t)(kHBox * sizeof(T));
-    uint64_t* bar = bars + ((g - z0) & (P::NB - 1));
+    uint64_t* bar = full + ((g - z0) & (P::NB - 1));
     const int wlo = A->wl[2], whi = A->wl[2] + A->wn[2] - 1, hlo = A->fl[2], hhi = A->fh[2];
     const bool c_on = g + 1 <= z1;
     const bool w_on = fem_tile && g >= wlo && g <= whi;
@@ -504,21 +508,25 @@ struct Producer {
 // One node (i, j, k) of an interior block from the staged planes: Ck, Cm, Cp
 // are this node in the u^k boxes of planes k, k-1, k+1, Pk in the u^{k-1}
 // box, Wk / Wm in the edge-weight arrays of planes k / k-1, Hk / Hp in the
-// stored-u boxes of planes k / k+1 (at the voxel origin).
-template <typename T, bool ADJ, bool FEMT, bool FACE>
-__device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T>& S, const Col& C, int k, int off,
-                                              int dzs, const T* Ck, const T* Cm, const T* Cp, const T* Pk,
-                                              const T* Wk, const T* Wm, const T* Hk, const T* Hp) {
+// stored-u boxes of planes k / k+1 (at the voxel origin).  ZF: the plane is
+// one step inside a z face (dzs = -1 / +1: the low / high one) and the node
+// also produces the face node next to it.  Tiles without FACE hold no node
+// one step inside an x or y face.
+template <typename T, bool ADJ, bool FEMT, bool FACE, bool ZF>
+__device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T>& S, T* __restrict__ gnext,
+                                              const Col& C, int k, int off, int dzs, const T* Ck, const T* Cm,
+                                              const T* Cp, const T* Pk, const T* Wk, const T* Wm, const T* Hk,
+                                              const T* Hp) {
   using P = kPipe<T>;
-  if (dzs != 0 && (C.dxs != 0 || C.dys != 0)) return;  // near two faces: edge tiles
+  if (ZF && FACE && (C.dxs != 0 || C.dys != 0)) return;  // near two faces: edge tiles
   const T c2 = A.c2;
   const T c0 = Ck[0], cm = Cm[0], cp = Cp[0], pv = Pk[0];
   const T xm = Ck[-1], xp = Ck[1], ym = Ck[-kBoxX], yp = Ck[kBoxX];
   bool lf = false;
   T wxm = T(1), wxp = T(1), wym = T(1), wyp = T(1);
-  T lap;
   if constexpr (FEMT) lf = C.xy_fem && k >= A.fl[2] && k <= A.fh[2];
   T wzm = T(1), wzp = T(1);
+  T val;
   if (FEMT && lf) {
     wxm = Wk[-1];
     wxp = Wk[0];
@@ -526,13 +534,15 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     wyp = Wk[P::WS];
     wzp = Wk[2 * P::WS];
     wzm = Wm[2 * P::WS];
-    lap = wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + wzp * (cp - c0) + wzm * (cm - c0);
-  } else {
-    lap = lap7(xm, xp, ym, yp, cm, cp, c0);
+    const T lap =
+        wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + wzp * (cp - c0) + wzm * (cm - c0);
+    val = T(2) * c0 - pv + c2 * lap;
+  } else if constexpr (sizeof(T) == 4) {  // unit weights: the neighbour sum, and (2 - 6 c2) u^k - u^{k-1}
+    val = c2 * (((xm + xp) + (ym + yp)) + (cm + cp)) + (A.cd * c0 - pv);
+  } else {  // FP64 keeps the differences (less rounding over long runs)
+    val = T(2) * c0 - pv + c2 * lap7(xm, xp, ym, yp, cm, cp, c0);
   }
-  T val = T(2) * c0 - pv + c2 * lap;
-  T* __restrict__ gnext = S.next;
-  if (dzs != 0) {  // the z face node next to this node (the rows of the x / y faces below)
+  if constexpr (ZF) {  // the z face node next to this node (the rows of the x / y faces below)
     const int f = dzs > 0 ? 5 : 4;
     const T* Cb = dzs > 0 ? Cp : Cm;  // b and its in-face neighbours in the staged plane k +- 1
     const T ub = Cb[0];
@@ -644,6 +654,32 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   constexpr int D = P::D;
   constexpr int kProd = kTileX * kTileY / 2;  // the producer thread
   const int t = (int)threadIdx.x;
+  const long long budget = 1LL << 29;         // cycles a wait may take (~0.25 s)
+  if (t >= kProd) {
+    // Producer: the planes first read at level g overwrite stages last read
+    // at level g - D - 1 (the edge-weight and stored-u rings are the
+    // shortest), so they are issued once every consumer warp is done with it.
+    if (t != kProd) return;
+    int g = z0 + D;
+    for (; g < z1; ++g) {
+      const int q = g - D - 1 - z0;
+      if (q >= 0 && !mbar_wait(pr.empty + (q & (P::NB - 1)), (uint32_t)((q / P::NB) & 1), budget, A.err)) {
+        atomicExch(A.err, 1);
+        break;
+      }
+      fence_proxy_async();
+      pr.issue(g, false);
+    }
+    // let no copy be in flight when the block exits (the consumers may have
+    // given up): wait for the last issued levels, ignoring the abort flag
+    const int no_abort = 0;
+    const int issued = min(g, z1) - z0;
+    for (int q = max(0, issued - P::NB); q < issued; ++q)
+      mbar_wait(pr.full + (q & (P::NB - 1)), (uint32_t)((q / P::NB) & 1), budget, &no_abort);
+    return;
+  }
+  // Consumers: each warp waits for level k's planes, computes its nodes and
+  // releases the level; warps run up to D levels apart.
   const int tx = t & 31, ty = t >> 5;
   const int nz = A.nz;
   const int pl = A.px * A.ny;
@@ -651,32 +687,21 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   const int o1 = o0 + (kTileY / 2) * kBoxX;          // row 1
   const int h0 = ty * kBoxX + (tx + 1);              // row 0 in a stored-u box
   const int h1 = h0 + (kTileY / 2) * kBoxX;
-  const long long budget = 1LL << 29;                // cycles a level may wait for its planes (~0.25 s)
-  bool ok = true;
+  const bool act0 = !FACE || active[0], act1 = !FACE || active[1];  // every row of a tile off the faces is active
+  T* __restrict__ gnext = S.next;
   int off0 = C[0].i + A.px * C[0].j + pl * z0;       // field offsets of the two nodes
   int off1 = off0 + (kTileY / 2) * A.px;
   for (int k = z0; k < z1; ++k, off0 += pl, off1 += pl) {
-    // the producer thread waits for level k's planes; the barrier then
-    // releases the consumers (and orders the staged data before their reads)
-    if (t == kProd && ok &&
-        !mbar_wait(pr.bars + ((k - z0) & (P::NB - 1)), (uint32_t)(((k - z0) / P::NB) & 1), budget, A.err)) {
-      ok = false;
-      atomicExch(A.err, 1);
-    }
-    __syncthreads();  // every thread is done with level k - 1: its stages may be refilled
-    if (t >= kProd) {  // producer warp
-      if (t == kProd && k + D < z1) {
-        fence_proxy_async();
-        pr.issue(k + D, false);
-      }
-      continue;
+    const int q = k - z0;
+    const bool ok = mbar_wait(pr.full + (q & (P::NB - 1)), (uint32_t)((q / P::NB) & 1), budget, A.err);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (tx == 0) atomicExch(A.err, 1);
+      return;
     }
     const T* Ck = pr.CR + (k & (P::SC - 1)) * P::CS;
     const T* Cm = pr.CR + ((k - 1) & (P::SC - 1)) * P::CS;
     const T* Cp = pr.CR + ((k + 1) & (P::SC - 1)) * P::CS;
     const T* Pk = pr.PR + (k & (P::SP - 1)) * P::CS;
-    // planes one step inside a z face also produce the face plane (block-uniform)
-    const int dzs = k == 1 ? -1 : (k == nz - 2 ? 1 : 0);
     const T* Wk = nullptr;
     const T* Wm = nullptr;
     const T* Hk = nullptr;
@@ -687,20 +712,33 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
       Hk = pr.HR + (k & (P::SH - 1)) * P::WS;
       Hp = pr.HR + ((k + 1) & (P::SH - 1)) * P::WS;
     }
-    if (active[0])
-      interior_node<T, ADJ, FEMT, FACE>(A, S, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0, Pk + o0,
-                                        Wk + o0, Wm + o0, Hk + h0, Hp + h0);
-    if (active[1])
-      interior_node<T, ADJ, FEMT, FACE>(A, S, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1, Pk + o1,
-                                        Wk + o1, Wm + o1, Hk + h1, Hp + h1);
+    // planes one step inside a z face also produce the face plane (block-uniform)
+    const int dzs = k == 1 ? -1 : (k == nz - 2 ? 1 : 0);
+    if (dzs != 0) {
+      if (act0)
+        interior_node<T, ADJ, FEMT, FACE, true>(A, S, gnext, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0,
+                                                Pk + o0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
+      if (act1)
+        interior_node<T, ADJ, FEMT, FACE, true>(A, S, gnext, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1,
+                                                Pk + o1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
+    } else {
+      if (act0)
+        interior_node<T, ADJ, FEMT, FACE, false>(A, S, gnext, C[0], k, off0, 0, Ck + o0, Cm + o0, Cp + o0,
+                                                 Pk + o0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
+      if (act1)
+        interior_node<T, ADJ, FEMT, FACE, false>(A, S, gnext, C[1], k, off1, 0, Ck + o1, Cm + o1, Cp + o1,
+                                                 Pk + o1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
+    }
+    __syncwarp();  // the warp's reads of level k's stages are done
+    if (tx == 0) mbar_arrive(pr.empty + (q & (P::NB - 1)));
   }
 }
 
 // Interior part of one time level (lattices with >= 5 nodes per axis):
 // 32 x 16 tiles of the nodes 1 .. n-2 and z ranges, one block per work item
 // (slot, tile, z range; the host balances the items by cost): eight
-// consumer warps (two tile rows per thread) and a producer warp.  Nodes one step inside an x or y face also produce the face node;
-// planes one step inside a z face take the general rows from global memory.
+// consumer warps (two tile rows per thread) and a producer warp.  Nodes one
+// step inside a face also produce the face node next to them.
 template <typename T, bool ADJ>
 __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* sm) {
   static_assert(kTileX == 32, "one warp per tile row");
@@ -752,7 +790,8 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   pr.PR = pr.CR + P::SC * P::CS;
   pr.WR = pr.PR + P::SP * P::CS;
   pr.HR = pr.WR + P::SW * 3 * P::WS;
-  pr.bars = reinterpret_cast<uint64_t*>(pr.HR + P::SH * P::WS);
+  pr.full = reinterpret_cast<uint64_t*>(pr.HR + P::SH * P::WS);
+  pr.empty = pr.full + P::NB;
   pr.z0 = z0;
   pr.z1 = z1;
   pr.xf = i0 - 1;  // multiples of 4: 16-byte aligned box origins
@@ -765,7 +804,10 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   pr.hist_tile = pairing && fem_tile;
   const int tp = kTileX * kTileY / 2;  // the producer thread
   if (t == tp) {
-    for (int q = 0; q < P::NB; ++q) mbar_init(pr.bars + q, 1);
+    for (int q = 0; q < P::NB; ++q) {
+      mbar_init(pr.full + q, 1);
+      mbar_init(pr.empty + q, kTileX * kTileY / 2 / 32);
+    }
     mbar_init_fence();
   }
   pdl_wait();  // the previous level is complete: its output may be read, its input overwritten
