@@ -456,11 +456,28 @@ struct kPipe {
   static constexpr int CS = round128(kBox);   // elements per u stage (128-byte aligned)
   static constexpr int WS = round128(kHBox);  // elements per edge-weight array / stored-u stage
   static constexpr int elems = SC * CS + SP * CS + SW * 3 * WS + SH * WS;
-  static constexpr size_t bytes = sizeof(T) * (size_t)elems + 16 * NB;
+  // Tiles off the FEM block stage only u^k and u^{k-1}: they spend the same
+  // shared memory on deeper rings, DP levels ahead.
+  static constexpr int deep(int d) { return (pow2(d + 4) + pow2(d + 2)) * CS <= elems ? deep(d + 1) : d; }
+  static constexpr int DP = deep(D);
+  static constexpr int NBX = pow2(DP + 1) > NB ? pow2(DP + 1) : NB;  // barrier pairs allocated
+  static constexpr size_t bytes = sizeof(T) * (size_t)elems + 16 * NBX;
+};
+
+// Ring sizes of a tile: on the FEM block (all four rings, D levels ahead) or
+// off it (DEEP: u^k and u^{k-1} only, DP levels ahead).
+template <typename T, bool DEEP>
+struct Ring {
+  using P = kPipe<T>;
+  static constexpr int D = DEEP ? P::DP : P::D;
+  static constexpr int SC = P::pow2(D + 3);
+  static constexpr int SP = P::pow2(D + 1);
+  static constexpr int NB = P::pow2(D + 1);
+  static_assert(DEEP ? (SC + SP) * P::CS <= P::elems : (SC == P::SC && SP == P::SP && NB == P::NB), "ring sizes");
 };
 
 // Producer side of one interior block: which boxes exist, and their issue.
-template <typename T>
+template <typename T, bool DEEP>
 struct Producer {
   const StepArgs<T>* A;
   const Slot<T>* S;
@@ -473,28 +490,54 @@ struct Producer {
   // g - 1 and g of u^k, g - 1 of the weights and g of the stored u)
   __device__ __forceinline__ void issue(int g, bool first) const {
     using P = kPipe<T>;
+    using R = Ring<T, DEEP>;
     constexpr uint32_t kCBytes = (uint32_t)(kBox * sizeof(T));
     constexpr uint32_t kWBytes = (uint32_t)(kHBox * sizeof(T));
-    uint64_t* bar = full + ((g - z0) & (P::NB - 1));
+    uint64_t* bar = full + ((g - z0) & (R::NB - 1));
     const int wlo = A->wl[2], whi = A->wl[2] + A->wn[2] - 1, hlo = A->fl[2], hhi = A->fh[2];
     const bool c_on = g + 1 <= z1;
-    const bool w_on = fem_tile && g >= wlo && g <= whi;
-    const bool wm_on = first && fem_tile && g - 1 >= wlo && g - 1 <= whi;
-    const bool h_on = hist_tile && g + 1 >= hlo && g + 1 <= hhi;
-    const bool h0_on = first && hist_tile && g >= hlo && g <= hhi;
+    const bool w_on = !DEEP && fem_tile && g >= wlo && g <= whi;
+    const bool wm_on = !DEEP && first && fem_tile && g - 1 >= wlo && g - 1 <= whi;
+    const bool h_on = !DEEP && hist_tile && g + 1 >= hlo && g + 1 <= hhi;
+    const bool h0_on = !DEEP && first && hist_tile && g >= hlo && g <= hhi;
     const uint32_t bytes = kCBytes * ((c_on ? 1 : 0) + 1 + (first ? 2 : 0)) +
                            kWBytes * (3 * ((w_on ? 1 : 0) + (wm_on ? 1 : 0)) + (h_on ? 1 : 0) + (h0_on ? 1 : 0));
     mbar_arrive_expect_tx(bar, bytes);
     if (first) {
-      tma_load_3d(CR + ((g - 1) & (P::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g - 1, bar);
-      tma_load_3d(CR + (g & (P::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g, bar);
+      tma_load_3d(CR + ((g - 1) & (R::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g - 1, bar);
+      tma_load_3d(CR + (g & (R::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g, bar);
     }
-    if (c_on) tma_load_3d(CR + ((g + 1) & (P::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g + 1, bar);
-    tma_load_3d(PR + (g & (P::SP - 1)) * P::CS, &A->tmf, xf, yf, S->zf_prev + g, bar);
+    if (c_on) tma_load_3d(CR + ((g + 1) & (R::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g + 1, bar);
+    tma_load_3d(PR + (g & (R::SP - 1)) * P::CS, &A->tmf, xf, yf, S->zf_prev + g, bar);
     if (wm_on) weights(g - 1, bar);
     if (w_on) weights(g, bar);
     if (h0_on) tma_load_3d(HR + (g & (P::SH - 1)) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g - hlo), bar);
     if (h_on) tma_load_3d(HR + ((g + 1) & (P::SH - 1)) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g + 1 - hlo), bar);
+  }
+  // stages and barriers in the block's shared memory, box origins of the
+  // tile (i0 - 1, j0 - 1: multiples of 4 in x, so 16-byte aligned)
+  __device__ __forceinline__ void setup(const StepArgs<T>& a, const Slot<T>& s, T* sm, uint64_t* bars, int zlo,
+                                        int zhi, int i0, int j0, bool hist) {
+    using P = kPipe<T>;
+    using R = Ring<T, DEEP>;
+    A = &a;
+    S = &s;
+    CR = sm;
+    PR = CR + R::SC * P::CS;
+    WR = DEEP ? nullptr : PR + P::SP * P::CS;
+    HR = DEEP ? nullptr : WR + P::SW * 3 * P::WS;
+    full = bars;
+    empty = bars + P::NBX;
+    z0 = zlo;
+    z1 = zhi;
+    xf = i0 - 1;
+    yf = j0 - 1;
+    xw = i0 - 1 - a.wx0;
+    yw = j0 - 1 - a.wl[1];
+    xh = i0 - 1 - a.hx0;
+    yh = j0 - a.fl[1];
+    fem_tile = !DEEP;
+    hist_tile = !DEEP && hist;
   }
   __device__ __forceinline__ void weights(int q, uint64_t* bar) const {
     using P = kPipe<T>;
@@ -644,14 +687,99 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
   }
 }
 
+// The x face column of a tile whose lanes would otherwise diverge: lanes 1
+// .. 16 of the producer warp, one tile row each, compute the node m one step
+// inside the face (off the FEM block: unit weights) and the face node b next
+// to it, so that the consumer warps skip m.  Planes and rows next to another
+// face belong to the edge tiles.  The rows are those of interior_node.
+struct XFace {
+  bool on;   // the tile uses the face lanes
+  int mi;    // x of the nodes m (1 or nx - 2)
+  int sd;    // -1 / +1: the low / high x face
+  int i0, j0;
+};
+constexpr unsigned kFaceLanes = 0x1fffeu;  // lanes 1 .. 16 of the producer warp
+
+template <typename T, bool ADJ, bool DEEP>
+__device__ __forceinline__ void xface_levels(const StepArgs<T>& A, const Slot<T>& S, const Producer<T, DEEP>& pr,
+                                             const XFace& X, int z0, int z1, long long budget) {
+  using P = kPipe<T>;
+  using R = Ring<T, DEEP>;
+  const int r = (int)threadIdx.x - (kTileX * kTileY / 2 + 1);  // tile row 0 .. 15
+  const int j = X.j0 + r;
+  const bool row_on = j >= 2 && j <= A.ny - 3;
+  const int f = X.sd > 0 ? 1 : 0;
+  const int sd = X.sd;
+  const int o = (r + 1) * kBoxX + (X.mi - X.i0 + 1);  // m in a u box
+  const T c2 = A.c2;
+  const bool abc = (S.mask_f >> f) & 1;
+  T* __restrict__ gnext = S.next;
+  const int pl = A.px * A.ny;
+  int off = X.mi + A.px * j + pl * z0;
+  for (int k = z0; k < z1; ++k, off += pl) {
+    const int q = k - z0;
+    const bool ok = mbar_wait(pr.full + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), budget, A.err);
+    if (!__all_sync(kFaceLanes, ok)) {
+      if (r == 0) atomicExch(A.err, 1);
+      return;
+    }
+    if (row_on && k >= 2 && k <= A.nz - 3) {
+      const T* Ck = pr.CR + (k & (R::SC - 1)) * P::CS + o;
+      const T* Cm = pr.CR + ((k - 1) & (R::SC - 1)) * P::CS + o;
+      const T* Cp = pr.CR + ((k + 1) & (R::SC - 1)) * P::CS + o;
+      const T* Pk = pr.PR + (k & (R::SP - 1)) * P::CS + o;
+      const T c0 = Ck[0], xm = Ck[-1], xp = Ck[1], ym = Ck[-kBoxX], yp = Ck[kBoxX];
+      const T cm = Cm[0], cp = Cp[0], pv = Pk[0];
+      T val;
+      if constexpr (sizeof(T) == 4)
+        val = c2 * (((xm + xp) + (ym + yp)) + (cm + cp)) + (A.cd * c0 - pv);
+      else
+        val = T(2) * c0 - pv + c2 * lap7(xm, xp, ym, yp, cm, cp, c0);
+      const T ub = Ck[sd];
+      const int offb = off + sd;
+      if constexpr (!ADJ) {
+        T vb;
+        if (abc) {
+          vb = A.r * ub + (c0 - A.r * val);
+        } else {
+          T lb = T(2) * (c0 - ub);
+          lb += (Ck[sd - kBoxX] - ub) + (Ck[sd + kBoxX] - ub);
+          lb += (Cm[sd] - ub) + (Cp[sd] - ub);
+          vb = T(2) * ub - Pk[sd] + c2 * lb;
+          if (S.src_face == f) vb += S.srcval;
+        }
+        gnext[offb] = vb;
+        if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, X.mi + sd, j, k, A.nx, A.ny)] = vb;
+      } else {
+        T lb = abc ? A.r * ub : (T(2) - T(6) * c2) * ub;
+        lb += c2 * c0;
+        if (!abc) {
+          lb += c2 * (Ck[sd - kBoxX] + Ck[sd + kBoxX]);
+          lb += c2 * (Cm[sd] + Cp[sd]);
+        }
+        if (!((S.mask_c >> f) & 1)) lb -= Pk[sd];
+        if (S.obs_r && S.obs_face == f) lb += S.obs_r[face_index(f, X.mi + sd, j, k, A.nx, A.ny)];
+        val += (abc ? ub : T(2) * c2 * ub) - c2 * ub;
+        if ((S.mask_e >> f) & 1) val -= A.r * lb;
+        gnext[offb] = lb;
+      }
+      gnext[off] = val;
+    }
+    __syncwarp(kFaceLanes);  // the lanes' reads of level k's stages are done
+    if (r == 0) mbar_arrive(pr.empty + (q & (R::NB - 1)));
+  }
+}
+
 // Consumer loop of an interior block, specialised by whether the tile meets
 // the FEM block (FEMT) and whether it holds nodes one step inside an x or y
 // face (FACE).  Each consumer thread owns two tile rows (ty and ty + 8).
 template <typename T, bool ADJ, bool FEMT, bool FACE>
 __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot<T>& S, const Col (&C)[2],
-                                                const Producer<T>& pr, const bool (&active)[2], int z0, int z1) {
+                                                const Producer<T, !FEMT>& pr, const bool (&active)[2],
+                                                const XFace& X, int z0, int z1) {
   using P = kPipe<T>;
-  constexpr int D = P::D;
+  using R = Ring<T, !FEMT>;
+  constexpr int D = R::D;
   constexpr int kProd = kTileX * kTileY / 2;  // the producer thread
   const int t = (int)threadIdx.x;
   const long long budget = 1LL << 29;         // cycles a wait may take (~0.25 s)
@@ -659,11 +787,15 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     // Producer: the planes first read at level g overwrite stages last read
     // at level g - D - 1 (the edge-weight and stored-u rings are the
     // shortest), so they are issued once every consumer warp is done with it.
-    if (t != kProd) return;
+    if (t != kProd) {
+      if (FACE && X.on && t <= kProd + 16) xface_levels<T, ADJ, !FEMT>(A, S, pr, X, z0, z1, budget);
+      return;
+    }
+    for (int g = 0; g < D && z0 + g < z1; ++g) pr.issue(z0 + g, g == 0);
     int g = z0 + D;
     for (; g < z1; ++g) {
       const int q = g - D - 1 - z0;
-      if (q >= 0 && !mbar_wait(pr.empty + (q & (P::NB - 1)), (uint32_t)((q / P::NB) & 1), budget, A.err)) {
+      if (q >= 0 && !mbar_wait(pr.empty + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), budget, A.err)) {
         atomicExch(A.err, 1);
         break;
       }
@@ -674,8 +806,8 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     // given up): wait for the last issued levels, ignoring the abort flag
     const int no_abort = 0;
     const int issued = min(g, z1) - z0;
-    for (int q = max(0, issued - P::NB); q < issued; ++q)
-      mbar_wait(pr.full + (q & (P::NB - 1)), (uint32_t)((q / P::NB) & 1), budget, &no_abort);
+    for (int q = max(0, issued - R::NB); q < issued; ++q)
+      mbar_wait(pr.full + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), budget, &no_abort);
     return;
   }
   // Consumers: each warp waits for level k's planes, computes its nodes and
@@ -693,15 +825,15 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   int off1 = off0 + (kTileY / 2) * A.px;
   for (int k = z0; k < z1; ++k, off0 += pl, off1 += pl) {
     const int q = k - z0;
-    const bool ok = mbar_wait(pr.full + (q & (P::NB - 1)), (uint32_t)((q / P::NB) & 1), budget, A.err);
+    const bool ok = mbar_wait(pr.full + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), budget, A.err);
     if (!__all_sync(0xffffffffu, ok)) {
       if (tx == 0) atomicExch(A.err, 1);
       return;
     }
-    const T* Ck = pr.CR + (k & (P::SC - 1)) * P::CS;
-    const T* Cm = pr.CR + ((k - 1) & (P::SC - 1)) * P::CS;
-    const T* Cp = pr.CR + ((k + 1) & (P::SC - 1)) * P::CS;
-    const T* Pk = pr.PR + (k & (P::SP - 1)) * P::CS;
+    const T* Ck = pr.CR + (k & (R::SC - 1)) * P::CS;
+    const T* Cm = pr.CR + ((k - 1) & (R::SC - 1)) * P::CS;
+    const T* Cp = pr.CR + ((k + 1) & (R::SC - 1)) * P::CS;
+    const T* Pk = pr.PR + (k & (R::SP - 1)) * P::CS;
     const T* Wk = nullptr;
     const T* Wm = nullptr;
     const T* Hk = nullptr;
@@ -730,7 +862,7 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
                                                  Pk + o1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
     }
     __syncwarp();  // the warp's reads of level k's stages are done
-    if (tx == 0) mbar_arrive(pr.empty + (q & (P::NB - 1)));
+    if (tx == 0) mbar_arrive(pr.empty + (q & (R::NB - 1)));
   }
 }
 
@@ -744,7 +876,6 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   static_assert(kTileX == 32, "one warp per tile row");
   static_assert(kTileX * kTileY / 2 + 32 == kStepBlock, "eight consumer warps (two rows each) and a producer warp");
   using P = kPipe<T>;
-  constexpr int D = P::D;
   const int* item = A.items + 4 * b;  // (slot, tile, z0, z1)
   const int si = item[0];
   const int tyy = item[1] / A.ntx;
@@ -779,52 +910,51 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
       C[r].rz1 = A.rzr[2 * c + 1];
     }
   }
-  // block-uniform tile kinds
+  // x face column handled by the face lanes: one x face in the tile, and
+  // its column m off the FEM block
+  XFace X;
+  {
+    const bool xlo = i0 == 1, xhi = i0 + kTileX - 1 >= nx - 2;
+    X.mi = xlo ? 1 : nx - 2;
+    X.sd = xlo ? -1 : 1;
+    X.i0 = i0;
+    X.j0 = j0;
+    X.on = xlo != xhi && !(has_fem && X.mi >= A.fl[0] && X.mi <= A.fh[0]);
+    if (X.on) {
+      active[0] = active[0] && C[0].dxs == 0;
+      active[1] = active[1] && C[1].dxs == 0;
+    }
+  }
+  // block-uniform tile kinds: an item whose planes hold no FEM-owned node
+  // needs no edge weights or history and runs with the deep rings
   const bool fem_tile = has_fem && i0 <= A.fh[0] && i0 + kTileX - 1 >= A.fl[0] && j0 <= A.fh[1] &&
-                        j0 + kTileY - 1 >= A.fl[1];
+                        j0 + kTileY - 1 >= A.fl[1] && z0 <= A.fh[2] && z1 - 1 >= A.fl[2];
   const bool face_tile = i0 == 1 || i0 + kTileX - 1 >= nx - 2 || j0 == 1 || j0 + kTileY - 1 >= ny - 2;
-  Producer<T> pr;
-  pr.A = &A;
-  pr.S = &S;
-  pr.CR = sm;
-  pr.PR = pr.CR + P::SC * P::CS;
-  pr.WR = pr.PR + P::SP * P::CS;
-  pr.HR = pr.WR + P::SW * 3 * P::WS;
-  pr.full = reinterpret_cast<uint64_t*>(pr.HR + P::SH * P::WS);
-  pr.empty = pr.full + P::NB;
-  pr.z0 = z0;
-  pr.z1 = z1;
-  pr.xf = i0 - 1;  // multiples of 4: 16-byte aligned box origins
-  pr.yf = j0 - 1;
-  pr.xw = i0 - 1 - A.wx0;
-  pr.yw = j0 - 1 - A.wl[1];
-  pr.xh = i0 - 1 - A.hx0;
-  pr.yh = j0 - A.fl[1];
-  pr.fem_tile = fem_tile;
-  pr.hist_tile = pairing && fem_tile;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + P::elems);
   const int tp = kTileX * kTileY / 2;  // the producer thread
   if (t == tp) {
-    for (int q = 0; q < P::NB; ++q) {
-      mbar_init(pr.full + q, 1);
-      mbar_init(pr.empty + q, kTileX * kTileY / 2 / 32);
+    for (int q = 0; q < P::NBX; ++q) {
+      mbar_init(full + q, 1);
+      mbar_init(full + P::NBX + q, kTileX * kTileY / 2 / 32 + (X.on ? 1 : 0));  // consumer warps (+ face lanes)
     }
     mbar_init_fence();
   }
   pdl_wait();  // the previous level is complete: its output may be read, its input overwritten
   __syncthreads();
-  if (t == tp) {
-    for (int g = 0; g < D && z0 + g < z1; ++g) pr.issue(z0 + g, g == 0);
-  }
   if (fem_tile) {
+    Producer<T, false> pr;
+    pr.setup(A, S, sm, full, z0, z1, i0, j0, pairing);
     if (face_tile)
-      interior_levels<T, ADJ, true, true>(A, S, C, pr, active, z0, z1);
+      interior_levels<T, ADJ, true, true>(A, S, C, pr, active, X, z0, z1);
     else
-      interior_levels<T, ADJ, true, false>(A, S, C, pr, active, z0, z1);
+      interior_levels<T, ADJ, true, false>(A, S, C, pr, active, X, z0, z1);
   } else {
+    Producer<T, true> pr;
+    pr.setup(A, S, sm, full, z0, z1, i0, j0, false);
     if (face_tile)
-      interior_levels<T, ADJ, false, true>(A, S, C, pr, active, z0, z1);
+      interior_levels<T, ADJ, false, true>(A, S, C, pr, active, X, z0, z1);
     else
-      interior_levels<T, ADJ, false, false>(A, S, C, pr, active, z0, z1);
+      interior_levels<T, ADJ, false, false>(A, S, C, pr, active, X, z0, z1);
   }
 }
 

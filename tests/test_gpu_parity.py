@@ -99,6 +99,13 @@ CASES = {
                                               omega=15.0, courant=0.9, sigma_scale=2.0),
     "refined": lambda: synth.small_problem(n=11, fem=(2, 8), nsteps=60, omega=12.0, courant=0.8,
                                            refine_frac=0.4),
+    # tiles with a single x face (x extent > one tile): mirror face carrying the source, absorbing opposite
+    "wide_x_mirror_src_low": lambda: synth.small_problem(n=(41, 12, 11), fem=((3, 3, 3), (14, 8, 7)), nsteps=80,
+                                                         omega=14.0, courant=0.8, bc=(0, 1, 1, 0, 1, 1),
+                                                         src_face=synth.FACE_XM),
+    "wide_x_mirror_src_high": lambda: synth.small_problem(n=(43, 11, 12), fem=((28, 3, 4), (38, 7, 8)), nsteps=80,
+                                                          omega=14.0, courant=0.8, bc=(1, 0, 0, 1, 0, 1),
+                                                          src_face=synth.FACE_XP),
     "refined_neumann_ragged": lambda: synth.small_problem(n=(12, 11, 13), fem=((2, 2, 2), (9, 8, 10)), nsteps=60,
                                                           omega=12.0, courant=0.8, refine_frac=0.5,
                                                           bc=(0, 1, 0, 1, 1, 1)),
