@@ -7,9 +7,13 @@
 // blocks read levels k and k-1 and write disjoint nodes of level k+1.  An
 // interior block's producer warp stages the planes it needs (u^k with a
 // one-node halo, u^{k-1}, FEM edge weights, stored history) into shared
-// memory with bulk tensor copies two levels ahead; its eight consumer warps
-// (two tile rows per thread) march the z range reading only shared memory.
-// Consecutive launches overlap through programmatic dependent launch.
+// memory with bulk tensor copies, two levels ahead on items with FEM-owned
+// nodes and seven on the others (which stage only u^k and u^{k-1}); its
+// eight consumer warps (two tile rows per thread) march the z range reading
+// only shared memory, synchronised with the producer by per-level mbarriers
+// only.  In tiles with one x face, lanes of the producer warp compute the
+// column next to that face.  Consecutive launches overlap through
+// programmatic dependent launch.
 // Row kinds:
 //  * FDM rows, Eq. (fdmschemeforward): u^{k+1} = 2u^k - u^{k-1} + tau^2 Delta_h u^k,
 //  * FEM rows on the FEM-owned nodes, Eq. (fem) with lumped mass: on the
