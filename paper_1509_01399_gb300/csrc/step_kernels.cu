@@ -212,38 +212,71 @@ __device__ __noinline__ T adj_rhs(const StepArgs<T>& A, const Slot<T>& S, int i,
 // Inlined copy of adj_rhs (below).
 // Right-hand side of the transposed step at node m:
 // (B_j^T lambda^{j+1})_m - (C_{j+1}^T lambda^{j+2})_m + c^j_m.
+// Inlined form of adj_rhs for the edge tiles.  Every load is issued first,
+// predicated, and the row summed afterwards: the nodes of an edge tile's warp
+// take different branches (faces, absorbing rows, FEM weights), and loads
+// inside those branches would each wait for memory in turn.
 template <typename T>
 __device__ __forceinline__ T adj_rhs_inl(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k) {
   const T* __restrict__ l1 = S.cur;
   const long long id = lin(A, i, j, k);
   const int fbm = face_bits(i, j, k, A.nx, A.ny, A.nz);
-  T rhs;
-  if (fbm & S.mask_f) rhs = A.r * l1[id];
-  else rhs = (T(2) + A.c2 * row_diag(A, i, j, k)) * l1[id];
+  const long long wy = A.wpx, wz = (long long)A.wpx * A.wn[1];
+  const bool fo = fem_owned(A, i, j, k);
+  const long long w = fo ? widx(A, i, j, k) : 0;
+  const T* W = A.W;
+  T wd[6];  // this node's edge weights (FEM-owned nodes)
+  wd[0] = fo ? W[w] : T(0);
+  wd[1] = fo ? W[w - 1] : T(0);
+  wd[2] = fo ? W[A.wsz + w] : T(0);
+  wd[3] = fo ? W[A.wsz + w - wy] : T(0);
+  wd[4] = fo ? W[2 * A.wsz + w] : T(0);
+  wd[5] = fo ? W[2 * A.wsz + w - wz] : T(0);
+  const T lc = l1[id];
+  const T pv = S.prev[id];
+  const bool obs = S.obs_r != nullptr && ((fbm >> S.obs_face) & 1);
+  const T ov = obs ? S.obs_r[face_index(S.obs_face, i, j, k, A.nx, A.ny)] : T(0);
+  T nb[6], cw[6];
+  int nfb[6];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
+      const int q = 2 * ax + t;
       const int s = t ? 1 : -1;
       const int ni = i + (ax == 0 ? s : 0);
       const int nj = j + (ax == 1 ? s : 0);
       const int nk = k + (ax == 2 ? s : 0);
-      if (ni < 0 || ni >= A.nx || nj < 0 || nj >= A.ny || nk < 0 || nk >= A.nz) continue;
-      const long long nid = lin(A, ni, nj, nk);
-      const int fbn = face_bits(ni, nj, nk, A.nx, A.ny, A.nz) & S.mask_f;
-      if (fbn) {
-        // absorbing row of the neighbour couples to m only when m is its
-        // inward neighbour across the face on side s of axis ax
-        const int f = 2 * ax + (s > 0 ? 1 : 0);
-        if (fbn & (1 << f)) rhs += l1[nid] / T(__popc(fbn));
-      } else {
-        rhs += A.c2 * row_coef(A, ni, nj, nk, ax, -s) * l1[nid];
-      }
+      const bool inb = ni >= 0 && ni < A.nx && nj >= 0 && nj < A.ny && nk >= 0 && nk < A.nz;
+      nb[q] = l1[inb ? lin(A, ni, nj, nk) : id];
+      nfb[q] = inb ? (face_bits(ni, nj, nk, A.nx, A.ny, A.nz) & S.mask_f) : -1;
+      // coefficient of the neighbour's non-absorbing row on this node (row_coef)
+      const bool nfo = inb && fem_owned(A, ni, nj, nk);
+      const long long ws = ax == 0 ? 1 : (ax == 1 ? wy : wz);
+      const long long nw = nfo ? ax * A.wsz + (s < 0 ? widx(A, ni, nj, nk) : widx(A, ni, nj, nk) - ws) : 0;
+      const T wv = nfo ? W[nw] : T(0);
+      const int c = ax == 0 ? ni : (ax == 1 ? nj : nk);
+      const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
+      cw[q] = nfo ? wv : (((s < 0 && c == 0) || (s > 0 && c == n - 1)) ? T(2) : T(1));
     }
   }
-  if (!(fbm & S.mask_c)) rhs -= S.prev[id];
-  if (S.obs_r && ((fbm >> S.obs_face) & 1)) rhs += S.obs_r[face_index(S.obs_face, i, j, k, A.nx, A.ny)];
-  return rhs;
+  T rhs;
+  if (fbm & S.mask_f) rhs = A.r * lc;
+  else rhs = (T(2) + A.c2 * (fo ? -(wd[0] + wd[1] + wd[2] + wd[3] + wd[4] + wd[5]) : T(-6))) * lc;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (nfb[q] < 0) continue;
+    if (nfb[q]) {
+      // absorbing row of the neighbour couples to m only when m is its
+      // inward neighbour across the face on side s of axis ax
+      const int f = 2 * (q >> 1) + (q & 1);
+      if (nfb[q] & (1 << f)) rhs += nb[q] / T(__popc(nfb[q]));
+    } else {
+      rhs += A.c2 * cw[q] * nb[q];
+    }
+  }
+  if (!(fbm & S.mask_c)) rhs -= pv;
+  return rhs + ov;
 }
 
 // lambda^j at node m: solve E_{j-1}^T lambda^j = rhs, where E couples an
@@ -978,9 +1011,18 @@ __device__ __forceinline__ void fwd_edge_tile(const StepArgs<T>& A, int si, int 
   const long long id = valid ? lin(A, i, j, k) : 0;
   const int fall = valid ? face_bits(i, j, k, A.nx, A.ny, A.nz) : 0;
   const int fb = fall & S.mask_f;
+  // u^k at the node and at its inward neighbour across each absorbing face,
+  // loaded before the levels below (which then wait only on shared memory)
+  const T cself = valid ? S.cur[id] : T(0);
+  T cin[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int fa = (fb >> (2 * ax)) & 3;
+    cin[ax] = (valid && fa) ? S.cur[id + ((fa & 1) ? 1 : -1) * axis_stride(A, ax)] : T(0);
+  }
   T plain = T(0);  // the non-absorbing row, from level-k data only
   if (valid && !fb) {
-    plain = T(2) * S.cur[id] - S.prev[id] + A.c2 * row_lap_inl(A, S.cur, i, j, k);
+    plain = T(2) * cself - S.prev[id] + A.c2 * row_lap_inl(A, S.cur, i, j, k);
     if (S.src_face >= 0 && ((fall >> S.src_face) & 1)) plain += S.srcval;
   }
   nv[t] = plain;
@@ -994,12 +1036,10 @@ __device__ __forceinline__ void fwd_edge_tile(const StepArgs<T>& A, int si, int 
       for (int ax = 0; ax < 3; ++ax) {
         const int fa = (fb >> (2 * ax)) & 3;
         if (!fa) continue;
-        const int step = (fa & 1) ? 1 : -1;  // inward
-        const long long id1 = id + step * axis_stride(A, ax);
         const int t1 = edge_tile_peer(t, blk, q, ax, (fa & 1) ? 1 : 2);
-        acc += S.cur[id1] - A.r * nv[t1];
+        acc += cin[ax] - A.r * nv[t1];
       }
-      v = A.r * S.cur[id] + acc / T(__popc(fb));
+      v = A.r * cself + acc / T(__popc(fb));
     }
     __syncthreads();
     if (mine) nv[t] = v;
@@ -1185,10 +1225,28 @@ __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t) 
     const long long self = lat ? (long long)A.rrow[r] : 0;
     const T ui = lat ? S.cur[self] : S.ccur[r - A.nrl];
     T acc = T(0);
-    for (int e = A.rptr[r] + lane; e < A.rptr[r + 1]; e += 4) {
-      const int cidx = A.rcol[e];
-      const T uj = cidx < A.nlat ? S.cur[cidx] : S.ccur[cidx - A.nlat];
-      acc += A.rval[e] * (uj - ui);
+    const int e1 = A.rptr[r + 1];
+    // four of the lane's entries at a time: their column ids, weights and
+    // values are loaded before any is summed (same summation order)
+    for (int e = A.rptr[r] + lane; e < e1; e += 16) {
+      int cu[4];
+      T wu[4], uu[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool on = e + 4 * u < e1;
+        cu[u] = on ? A.rcol[e + 4 * u] : -1;
+        wu[u] = on ? A.rval[e + 4 * u] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool lat_col = cu[u] < A.nlat;
+        const T* base = lat_col ? S.cur : S.ccur;
+        const long long ci = lat_col ? (long long)cu[u] : (long long)cu[u] - A.nlat;
+        uu[u] = cu[u] >= 0 ? base[ci] : ui;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cu[u] >= 0) acc += wu[u] * (uu[u] - ui);
     }
     const unsigned grp = 0xFu << (threadIdx.x & 28);
     acc += __shfl_xor_sync(grp, acc, 1);
