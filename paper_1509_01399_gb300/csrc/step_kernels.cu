@@ -996,7 +996,7 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
 }
 
 template <typename T, bool ADJ>
-__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t);
+__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t, const T* k9);
 
 // Edge tile of the forward step.  Levels by the number of faces a node lies
 // on: nodes on no face take their interior row, then face, edge and corner
@@ -1114,7 +1114,12 @@ __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kerne
   b -= A.nhe;
   if (b < A.nhr) {
     pdl_wait();
-    refined_rows<T, ADJ>(A, (long long)b * kStepBlock + threadIdx.x);
+    if constexpr (ADJ) {  // the refined-voxel stiffness for the pairing threads, in shared memory
+      if (A.k9)
+        for (int q = (int)threadIdx.x; q < 81; q += kStepBlock) sh[q] = (T)A.k9[q];
+      __syncthreads();
+    }
+    refined_rows<T, ADJ>(A, (long long)b * kStepBlock + threadIdx.x, sh);
     return;
   }
   interior_block<T, ADJ>(A, b - A.nhr, sh);
@@ -1173,10 +1178,10 @@ __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __re
 // Pairing of a refined voxel: u^T K9 lambda over its 8 corners and centre,
 // K9 the stiffness of the refined unit voxel (a = 1); the host scales the
 // sum like the structured pairing.
-template <typename T>
+template <typename T, typename K>
 __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* __restrict__ hb,
                                           const T* __restrict__ chb, const T* __restrict__ lam,
-                                          const T* __restrict__ clam) {
+                                          const T* __restrict__ clam, const K* __restrict__ k9) {
   const int uid = A.refvox_id[v];
   const int x = uid % A.un[0], y = (uid / A.un[0]) % A.un[1], z = uid / (A.un[0] * A.un[1]);
   const int i = A.fl[0] + x, j = A.fl[1] + y, k = A.fl[2] + z;
@@ -1198,7 +1203,7 @@ __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* 
   for (int p = 0; p < 9; ++p) {
     T row = T(0);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) row += (T)A.k9[p * 9 + q] * l[q];
+    for (int q = 0; q < 9; ++q) row += (T)k9[p * 9 + q] * l[q];
     acc += u[p] * row;
   }
   return acc;
@@ -1211,7 +1216,7 @@ __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* 
 // adjoint runs the same rows on the mass-scaled lambda).  Adjoint threads
 // [nr, nr + nref): gradient pairing of the refined voxels.
 template <typename T, bool ADJ>
-__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t) {
+__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t, const T* k9) {
   // per slot: 4 lanes per sparse row, then (adjoint) one thread per refined
   // voxel, padded to a multiple of 4 so row lane groups stay warp aligned
   const int per = 4 * A.nr + (ADJ ? ((A.nref + 3) & ~3) : 0);
@@ -1270,7 +1275,7 @@ __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t) 
     const int v = r4 - 4 * A.nr;
     if (!S.hist_r || v >= A.nref) return;
     const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
-    A.G[(long long)si * nv + A.refvox_id[v]] += (double)refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur);
+    A.G[(long long)si * nv + A.refvox_id[v]] += (double)refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur, k9);
   }
 }
 
@@ -1282,7 +1287,7 @@ __global__ void refined_pair_kernel(const __grid_constant__ StepArgs<T> A) {
   const int v = (int)(t - (long long)si * A.nref);
   const Slot<T>& S = A.s[si];
   const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
-  A.G[(long long)si * nv + A.refvox_id[v]] += (double)refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur);
+  A.G[(long long)si * nv + A.refvox_id[v]] += (double)refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur, A.k9);
 }
 
 template <typename T>
