@@ -147,6 +147,23 @@ def test_fp32_parity_reference_33(H):
     assert rel_l2(gpu["g"], ora["g"]) <= TOL32_GRAD
 
 
+def test_fp32_parity_wide_x_faces(H):
+    """FP32 on a lattice wider than one tile in x (tiles with a single x face,
+    whose face column runs on the producer warp's lanes; items without FEM
+    nodes on the deep copy rings), mirror x face carrying the source."""
+    w = synth.small_problem(n=(70, 21, 19), fem=((6, 4, 4), (20, 16, 14)), nsteps=90, omega=14.0,
+                            courant=0.8, bc=(0, 1, 1, 0, 1, 1), src_face=synth.FACE_XM)
+    rng = np.random.default_rng(5)
+    P = oracle.problem_from_workload(w)
+    a_obs = 1.0 + 2.0 * rng.random(P.n_unknown)
+    a = w.a_true()
+    gpu = run_gpu(H, w, a, a_obs, precision="fp32")
+    ora = run_oracle(w, a, a_obs)
+    for s, t in enumerate(ora["trace"]):
+        assert rel_l2(gpu["trace"][s, :, : t.shape[1]], t) <= TOL32_TRACE
+    assert rel_l2(gpu["g"], ora["g"]) <= TOL32_GRAD
+
+
 def test_batched_sources_equal_single_runs(H):
     """Sources advanced together by one launch give, per source, exactly the
     trace of a run with that source alone, and the gradient is their sum."""
