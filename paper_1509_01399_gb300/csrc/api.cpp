@@ -281,7 +281,7 @@ constexpr double kZFaceLevelCost = 3.5;
 // kernel's resident blocks evenly.  Relative cost of one tile level, fitted
 // to per-block cycle counts on a 129^3 lattice (forward / transposed step),
 // the face weights then set by timing whole levels: 1 for a plain tile; 1.50
-// / 1.70 for a tile next to an x or y face; 1.22 / 1.26 for a tile meeting
+// / 1.70 for a tile next to an x or y face; 1.22 / 1.40 for a tile meeting
 // the FEM block, plus 0.88 / 2.10 on planes where it holds FEM-owned nodes;
 // plus kZFaceLevelCost on the two planes next to the z faces (they also
 // produce the face plane and, on the source face, the trace).
@@ -303,7 +303,7 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
         const bool face = i0 == 1 || i0 + kTileX - 1 >= nx - 2 || j0 == 1 || j0 + kTileY - 1 >= ny - 2;
         const bool femt = m->fem && i0 <= m->fh[0] && i0 + kTileX - 1 >= m->fl[0] && j0 <= m->fh[1] &&
                           j0 + kTileY - 1 >= m->fl[1];
-        const double base = face ? (adjoint ? 1.70 : 1.50) : (femt ? (adjoint ? 1.26 : 1.22) : 1.0);
+        const double base = face ? (adjoint ? 1.70 : 1.50) : (femt ? (adjoint ? 1.40 : 1.22) : 1.0);
         const Tile t{si, ty * ntx + tx, base, femt ? (adjoint ? 2.10 : 0.88) : 0.0};
         tiles.push_back(t);
         total += t.base * (nz - 2) + t.extra * fem_levels + 2 * kZFaceLevelCost;
