@@ -280,7 +280,7 @@ constexpr double kZFaceLevelCost = 3.5;
 // estimated cost, so that the items fill the chosen number of waves of the
 // kernel's resident blocks evenly.  Relative cost of one tile level, fitted
 // to per-block cycle counts on a 129^3 lattice (forward / transposed step),
-// the face weights then set by timing whole levels: 1 for a plain tile; 1.50
+// then adjusted by timing whole levels: 1 for a plain tile; 1.50
 // / 1.70 for a tile next to an x or y face; 1.22 / 1.40 for a tile meeting
 // the FEM block, plus 0.88 / 2.10 on planes where it holds FEM-owned nodes;
 // plus kZFaceLevelCost on the two planes next to the z faces (they also
