@@ -99,6 +99,9 @@ CASES = {
                                               omega=15.0, courant=0.9, sigma_scale=2.0),
     "refined": lambda: synth.small_problem(n=11, fem=(2, 8), nsteps=60, omega=12.0, courant=0.8,
                                            refine_frac=0.4),
+    # a tile row off both y faces
+    "tall_tiles": lambda: synth.small_problem(n=(37, 38, 12), fem=((5, 5, 3), (30, 30, 8)), nsteps=45, omega=15.0,
+                                              courant=0.9, bc=(1, 1, 0, 1, 1, 1), src_face=synth.FACE_ZP),
     # tiles with a single x face (x extent > one tile): mirror face carrying the source, absorbing opposite
     "wide_x_mirror_src_low": lambda: synth.small_problem(n=(41, 12, 11), fem=((3, 3, 3), (14, 8, 7)), nsteps=80,
                                                          omega=14.0, courant=0.8, bc=(0, 1, 1, 0, 1, 1),
@@ -148,10 +151,11 @@ def test_fp32_parity_reference_33(H):
 
 
 def test_fp32_parity_wide_x_faces(H):
-    """FP32 on a lattice wider than one tile in x (tiles with a single x face,
-    whose face column runs on the producer warp's lanes; items without FEM
-    nodes on the deep copy rings), mirror x face carrying the source."""
-    w = synth.small_problem(n=(70, 21, 19), fem=((6, 4, 4), (20, 16, 14)), nsteps=90, omega=14.0,
+    """FP32 on a lattice wider than one tile in x and y (tiles with a single x
+    face, whose face column runs on the producer warp's lanes; a tile row off
+    both y faces; items without FEM nodes on the deep copy rings), mirror x
+    face carrying the source."""
+    w = synth.small_problem(n=(70, 38, 19), fem=((6, 4, 4), (20, 30, 14)), nsteps=90, omega=14.0,
                             courant=0.8, bc=(0, 1, 1, 0, 1, 1), src_face=synth.FACE_XM)
     rng = np.random.default_rng(5)
     P = oracle.problem_from_workload(w)
