@@ -267,13 +267,13 @@ void step_geometry(const hyb_mesh* m, int* npb, int* ntx, int* small, int* nedge
   *npb = *ntx * nty;
 }
 
-// Waves of resident interior blocks the work items are cut for: two when
-// each resident block would get few tile levels (blocks that finish early
-// take the second wave's items; more waves would make the items so short
-// that the wait for their first planes dominates), three when there is much
-// work (blocks of uneven speed then even out within each SM).  Both set by
-// timing whole levels.
-constexpr int kStepWavesFew = 2, kStepWavesMany = 3;
+// Waves of resident interior blocks the work items are cut for: one when
+// each resident block would get few tile levels (a block's first level waits
+// for its planes, so long items pay off; two waves were 1-2 % faster for a
+// lone sweep but cost a sixth of the throughput with several sweeps sharing
+// the GPU), three when there is much work (blocks of uneven speed then even
+// out within each SM).
+constexpr int kStepWavesFew = 1, kStepWavesMany = 3;
 constexpr double kManyLevelsPerBlock = 40.0;
 constexpr double kZFaceLevelCost = 3.5;
 
