@@ -190,7 +190,7 @@ def run_sweeps_only(args):
 
 
 def algorithmic_bytes(w, es=4):
-    """SURVEY-style algorithmic bytes per launch: FDM-owned node reads u^k,
+    """Algorithmic bytes per launch: FDM-owned node reads u^k,
     u^{k-1} and writes u^{k+1} (3 es); a FEM-owned node adds its coefficient
     (forward) and, in the adjoint, the stored u^k (4 es / 5 es)."""
     n_nodes = w.n_nodes
