@@ -114,12 +114,20 @@ def refine_voxels(tet_nodes, tet_unknown, refine, n_lattice):
 
 @dataclass
 class Phase:
-    """Boundary state of one time step: the set of absorbing faces and the
-    source face (with its flux p(t_k)) in force at that step."""
+    """Boundary state of the step leaving t_k: the absorbing faces in force and
+    the faces that carry the plane-wave flux (Neumann faces with d_n u = g)."""
 
     abc_faces: tuple
-    src_face: int  # -1: none
-    p: float
+    src_faces: tuple
+    t: float
+
+
+def pulse(omega: float, s):
+    """p(s) = sin(omega s) on [0, t1], t1 = 2 pi / omega, and 0 elsewhere
+    (Eq. (f)); s may be an array."""
+    s = np.asarray(s, dtype=np.float64)
+    t1 = 2.0 * math.pi / omega
+    return np.where((s >= 0.0) & (s <= t1), np.sin(omega * s), 0.0)
 
 
 class Problem:
@@ -291,17 +299,68 @@ class Problem:
         return (sp.diags(self.fdm_owned.astype(float)) @ Lfd + sp.diags(self.owned.astype(float)) @ Lfe).tocsr()
 
     # ----------------------------------------------------------------- phase
+    def plane_wave(self, src):
+        """Geometry of the plane wave u = F(t - d.(x - x0)) that the source
+        launches: unit direction d (for a face source, d = -n of its face, the
+        wave of Model Problem 2), entry corner x0 (lattice index: the corner
+        where d.x is smallest) and the faces it enters through, each with the
+        factor -(d . n_f) > 0 of its Neumann flux
+        d_n u = -(d . n_f) p(t - d.(x - x0)) (Eq. (f) written for an oblique
+        incidence; for d = -n it is d_n u = p(t) of Eq. (model2))."""
+        d = getattr(src, "direction", None)
+        if d is None:
+            ax, side = divmod(src.face, 2)
+            d = np.zeros(3)
+            d[ax] = 1.0 if side == 0 else -1.0
+        d = np.asarray(d, dtype=np.float64)
+        d = d / math.sqrt(float(np.dot(d, d)))
+        i0 = [0 if d[ax] >= 0.0 else self.n[ax] - 1 for ax in range(3)]
+        entry = {}
+        for f in range(6):
+            ax, side = divmod(f, 2)
+            dn = d[ax] * (-1.0 if side == 0 else 1.0)
+            if dn < 0.0:
+                entry[f] = -dn
+        return d, i0, entry
+
+    def switch_time(self, src, f):
+        """Last instant at which entry face f carries the flux: t1 plus the
+        largest delay d.(x - x0) over the face (t1 for a face source)."""
+        d, i0, _ = self.plane_wave(src)
+        ax = f // 2
+        p, q = [b for b in range(3) if b != ax]
+        return 2.0 * math.pi / src.omega + self.h * (abs(d[p]) * (self.n[p] - 1) + abs(d[q]) * (self.n[q] - 1))
+
     def phase(self, src, k, dt):
-        """Boundary state for the step from t_k = k dt: the source face acts as
-        a Neumann face with flux p(t_k) while t_k <= t1 = 2 pi / omega, and
-        takes the mesh's own condition afterwards (Model Problem 2)."""
+        """Boundary state for the step from t_k = k dt: an entry face of the
+        source acts as a Neumann face with the plane-wave flux while
+        t_k <= its switch time, and takes the mesh's own condition afterwards
+        (Model Problem 2: S_{1,1} then S_{1,2})."""
         abc = [f for f in range(6) if self.bc[f] == BC_ABC]
+        t = k * dt
+        srcf = []
         if src is not None:
-            t = k * dt
-            if t <= 2.0 * math.pi / src.omega:
-                abc = [f for f in abc if f != src.face]
-                return Phase(tuple(abc), src.face, src.amp * math.sin(src.omega * t))
-        return Phase(tuple(abc), -1, 0.0)
+            _, _, entry = self.plane_wave(src)
+            srcf = [f for f in sorted(entry) if t <= self.switch_time(src, f)]
+            abc = [f for f in abc if f not in srcf]
+        return Phase(tuple(abc), tuple(srcf), t)
+
+    def source_term(self, src, ph: Phase, dt):
+        """s with s_i = tau^2 (2 / h) g_i on the non-absorbing nodes of the
+        flux faces: the mirror ghost u_g = u_in + 2 h g of d_n u = g, summed over
+        the flux faces a node lies on; g = amp (-(d . n_f)) p(t_k - d.(x_i - x0))."""
+        s = np.zeros(self.NT)
+        if not ph.src_faces:
+            return s
+        d, i0, entry = self.plane_wave(src)
+        level, _ = self.abc_structure(ph.abc_faces)
+        delay = self.h * (d[0] * (self.I[:, 0] - i0[0]) + d[1] * (self.I[:, 1] - i0[1]) +
+                          d[2] * (self.I[:, 2] - i0[2]))
+        p = pulse(src.omega, ph.t - delay)
+        for f in ph.src_faces:
+            m = self.on_face[f][: self.N] & (level[: self.N] == 0)
+            s[: self.N][m] += dt * dt * 2.0 / self.h * src.amp * entry[f] * p[m]
+        return s
 
     def abc_structure(self, abc_faces):
         """Level (number of absorbing faces a node lies on) and, per absorbing
@@ -322,8 +381,8 @@ class Problem:
         return level, pairs
 
     def step_matrices(self, Lop, phase: Phase, dt):
-        """E, B, C and the source vector s of one step written as
-        E u^{k+1} = B u^k - C u^{k-1} + s."""
+        """E, B, C of one step written as E u^{k+1} = B u^k - C u^{k-1} + s
+        (the source vector s is `source_term`)."""
         level, pairs = self.abc_structure(phase.abc_faces)
         r = (self.h - dt) / (self.h + dt)
         nonabc = (level == 0).astype(float)
@@ -347,11 +406,7 @@ class Problem:
         rr, cc = np.concatenate(rb), np.concatenate(cb)
         B = (B + sp.csr_matrix((np.concatenate(vb), (rr, cc)), shape=B.shape)).tocsr()
         E = (E + sp.csr_matrix((np.concatenate(ve), (rr, cc)), shape=E.shape)).tocsr()
-        s = np.zeros(self.NT)
-        if phase.src_face >= 0:
-            m = self.on_face[phase.src_face] & (level == 0)
-            s[m] = dt * dt * 2.0 * phase.p / self.h
-        return E, B, C.tocsr(), s
+        return E, B, C.tocsr()
 
     # --------------------------------------------------------------- forward
     def forward(self, a_unknown, src, nsteps, dt, init=None, keep_hist=False, keep_fields=False):
@@ -388,9 +443,8 @@ class Problem:
             lap = self.D @ u_fd
             new_fd = np.zeros(self.NT)
             new_fd[rows] = 2.0 * u_fd[rows] - u_fd_prev[rows] + tau2 * lap[rows]
-            if ph.src_face >= 0:
-                m = rows & self.on_face[ph.src_face]
-                new_fd[m] += tau2 * 2.0 * ph.p / h
+            if ph.src_faces:
+                new_fd[rows] += self.source_term(src, ph, dt)[rows]
             # 2. FEM rows at omega_* and omega_diamond, Eq. (fem)
             new_fe = np.zeros(self.NT)
             if self.has_fem:
@@ -437,15 +491,10 @@ class Problem:
         seq = []
         for k in range(nsteps + 2):
             ph = self.phase(src, k, dt)
-            key = (ph.abc_faces, ph.src_face)
+            key = (ph.abc_faces, ph.src_faces)
             if key not in cache:
                 cache[key] = self.step_matrices(Lop, ph, dt)
-            E, B, C, s = cache[key]
-            if ph.src_face >= 0:
-                s = s * 0.0
-                m = self.on_face[ph.src_face] & (self.abc_structure(ph.abc_faces)[0] == 0)
-                s[m] = dt * dt * 2.0 * ph.p / self.h
-            seq.append((key, s))
+            seq.append((key, ph))
         return cache, seq
 
     @staticmethod
@@ -474,11 +523,11 @@ class Problem:
         up = np.zeros(self.NT) if init is None else np.array(init[1], dtype=np.float64)
         trace = np.zeros((nsteps + 1, obs.size))
         trace[0] = u[obs]
-        strict = {key: self._strict_part(E) for key, (E, _, _, _) in cache.items()}
+        strict = {key: self._strict_part(E) for key, (E, _, _) in cache.items()}
         for k in range(nsteps):
-            key, s = seq[k]
-            E, B, C, _ = cache[key]
-            y = B @ u - C @ up + s
+            key, ph = seq[k]
+            E, B, C = cache[key]
+            y = B @ u - C @ up + self.source_term(src, ph, dt)
             if forcing is not None:
                 y = y + forcing[k]
             un = self._solve_unit(strict[key], y)
@@ -500,7 +549,7 @@ class Problem:
         Gacc = np.zeros(self.n_unknown)
         lams = [None] * (nsteps + 2) if keep_lambdas else None
         tr = {key: (self._strict_part(E, transpose=True), B.T.tocsr(), C.T.tocsr())
-              for key, (E, B, C, _) in cache.items()}
+              for key, (E, B, C) in cache.items()}
         for j in range(nsteps, 0, -1):
             _, BT, _ = tr[seq[j][0]]
             _, _, CT = tr[seq[j + 1][0]]
@@ -588,6 +637,22 @@ def quadratic_step(J0, dJ0, alpha_t, Jt):
     return min(max(alpha, 0.0), 4.0 * alpha_t)
 
 
+def projected_gradient(a, g, a_min, a_max):
+    """g with the components zeroed on voxels that sit at a bound of the
+    admissible set [a_min, a_max] (Eq. (admpar)) and whose gradient points out
+    of it (a = a_min with g > 0, a = a_max with g < 0): the projection clips
+    those components, so they can neither move nor lower F."""
+    blocked = ((a <= a_min) & (g > 0.0)) | ((a >= a_max) & (g < 0.0))
+    return np.where(blocked, 0.0, g)
+
+
+def drop_blocked(a, d, a_min, a_max):
+    """d with the components zeroed that would leave [a_min, a_max] at once
+    (a = a_min with d < 0, a = a_max with d > 0)."""
+    blocked = ((a <= a_min) & (d < 0.0)) | ((a >= a_max) & (d > 0.0))
+    return np.where(blocked, 0.0, d)
+
+
 def cg_direction(g, d_prev, gn2_prev, vol):
     """Fletcher-Reeves direction of Algorithm 3, Step 2: d^m = -g^m + beta^m d^{m-1},
     beta^m = ||g^m||^2 / ||g^{m-1}||^2 (L2 norms over the unknown voxels),
@@ -601,26 +666,42 @@ def cg_direction(g, d_prev, gn2_prev, vol):
 
 def cg_step(prob: Problem, a, sources, nsteps, dt, obs_traces, state: dict, gamma=0.01, a0=1.0,
             a_min=1.0, a_max=5.0, mode="quadrature"):
-    """One iteration of Algorithm 3: state and adjoint at a^m (Step 1), the
-    gradient g^m = int grad u . grad lambda dt + gamma (a^m - a0) as an L2
-    function on the voxels, the Fletcher-Reeves update with a quadratic-fit
-    step, and projection onto the admissible set [a_min, a_max] (Eq. (admpar))."""
+    """One iteration of Algorithm 3 on the admissible set [a_min, a_max]
+    (Eq. (admpar)): state and adjoint at a^m (Step 1); the gradient
+    g^m = int grad u . grad lambda dt + gamma (a^m - a0) as an L2 function on
+    the voxels; the Fletcher-Reeves update (Step 2) of the projected gradient
+    (`projected_gradient`), with the components of d^m that the projection
+    would clip at once dropped and a restart d^m = -g^m when d^m is not a
+    descent direction; the step length from the parabola through F(0), F'(0)
+    and F at a trial step; projection a^{m+1} = clip(a^m + alpha d^m).
+
+    The trial step is 0.5 / max|d^m| at the first iteration and whenever the
+    previous step failed to lower F (or was 0), else the previous step
+    length.  state: d, gn2 (||projected g^{m-1}||^2), alpha, J (F(a^{m-1})),
+    iter.  Returns (a^{m+1}, state, report); report['gnorm'] is ||g^m||_L2,
+    the stopping measure of Step 3."""
     vol = prob.voxel_volume
     J0, ge, _ = value_and_grad(prob, a, sources, nsteps, dt, obs_traces, gamma, a0, mode)
     g = ge / vol
-    d, beta, gn2 = cg_direction(g, state.get("d"), state.get("gn2"), vol)
+    gp = projected_gradient(a, g, a_min, a_max)
+    d, beta, gn2 = cg_direction(gp, state.get("d"), state.get("gn2"), vol)
+    d = drop_blocked(a, d, a_min, a_max)
     dJ0 = float(np.sum(ge * d))
     if dJ0 >= 0.0:
-        d, beta, dJ0 = -g, 0.0, -gn2
-    alpha_t = state.get("alpha")
-    if alpha_t is None or alpha_t <= 0.0:
+        d, beta = -gp, 0.0
+        dJ0 = float(np.sum(ge * d))
+    alpha_prev, J_prev = state.get("alpha"), state.get("J")
+    if alpha_prev is None or alpha_prev <= 0.0 or (J_prev is not None and J0 >= J_prev):
         alpha_t = 0.5 / max(float(np.max(np.abs(d))), 1e-300)
+    else:
+        alpha_t = alpha_prev
     a_t = np.clip(a + alpha_t * d, a_min, a_max)
     Jt, _, _ = value_and_grad(prob, a_t, sources, nsteps, dt, obs_traces, gamma, a0, mode, need_grad=False)
     alpha = quadratic_step(J0, dJ0, alpha_t, Jt)
     a_new = np.clip(a + alpha * d, a_min, a_max)
-    new_state = dict(d=d, gn2=gn2, alpha=alpha, iter=state.get("iter", 0) + 1)
-    report = dict(J=J0, gnorm=math.sqrt(gn2), alpha=alpha, beta=beta, dJ0=dJ0, J_trial=Jt, alpha_trial=alpha_t)
+    new_state = dict(d=d, gn2=gn2, alpha=alpha, J=J0, iter=state.get("iter", 0) + 1)
+    report = dict(J=J0, gnorm=math.sqrt(vol * float(np.sum(g * g))), gpnorm=math.sqrt(gn2), alpha=alpha,
+                  beta=beta, dJ0=dJ0, J_trial=Jt, alpha_trial=alpha_t)
     return a_new, new_state, report
 
 

@@ -31,13 +31,18 @@ BC_ABC = 1
 
 @dataclass
 class Source:
-    """Plane-wave Neumann source on one face: d_n u = amp * sin(omega t) for
-    0 < t <= 2 pi / omega, after which the face takes the mesh's own boundary
-    condition (Model Problem 2 with Eq. (f))."""
+    """Plane-wave source.  Without a direction: a Neumann flux on one face,
+    d_n u = amp * sin(omega t) for 0 < t <= 2 pi / omega, after which the face
+    takes the mesh's own boundary condition (Model Problem 2 with Eq. (f)).
+    With a direction d: the plane wave travelling along d, entering through
+    every face whose outward normal n has d . n < 0 with the flux
+    -(d . n) amp p(t - d . (x - x0)) (x0 the entry corner); `face` is then
+    the observation face whose trace is recorded."""
 
     face: int = FACE_ZP
     omega: float = 40.0
     amp: float = 1.0
+    direction: Optional[Tuple[float, float, float]] = None
 
     @property
     def t1(self) -> float:
@@ -172,6 +177,18 @@ def gaussian_bumps(fem_lo, fem_hi, h, origin, count, amp_range, width_range, rng
     return sigma.ravel()
 
 
+def add_noise_device(trace, level: float, seed: int = 1):
+    """The same noise model on a torch tensor (for traces too large for the
+    host): trace + level * max|trace| * xi, xi ~ N(0, 1) drawn by torch's
+    generator on the trace's device, seeded with `seed`; FP64 arithmetic."""
+    import torch
+    gen = torch.Generator(device=trace.device)
+    gen.manual_seed(int(seed))
+    t = trace.to(torch.float64)
+    xi = torch.randn(t.shape, generator=gen, device=t.device, dtype=torch.float64)
+    return t + level * t.abs().max() * xi
+
+
 def add_noise(trace: np.ndarray, level: float, seed: int = 1) -> np.ndarray:
     """u_obs = u + level * max|u| * xi with xi ~ N(0, 1) i.i.d. per entry
     (additive noise on the backscattered data, Sec. 9)."""
@@ -275,17 +292,33 @@ def serving_request(i: int, sizes=(33, 65, 97, 129), nsteps: Optional[int] = Non
                     nsteps, structured_dt(h, 3.0), 3.0, sigma, "fp32")
 
 
-def large_257(nsteps: int = 3000, n_src: int = 6) -> Workload:
-    """257^3 lattice (h = 1/128), FEM nodes 64..192, smooth Gaussian-bump
-    sigma, plane waves from the axis faces batched as independent sources,
-    FP32 fields with FP64 gradient accumulation."""
-    n, h, origin = cube_grid(257)
-    lo, hi = central_half(257)
+def large_257(nsteps: int = 3000, n_src: int = 8, refine: bool = True) -> Workload:
+    """The large batched workload on its 257^3 lattice (see `large_batched`)."""
+    return large_batched(257, nsteps, n_src, refine)
+
+
+def large_batched(N: int = 257, nsteps: int = 3000, n_src: int = 8, refine: bool = True) -> Workload:
+    """N^3 lattice on [-1,1]^3 (257: h = 1/128), FEM nodes = central half (64..192), smooth sigma
+    made of 4-8 Gaussian bumps (amplitude U[0, 1.5], width U[0.05, 0.15],
+    centres in the unknown block; seed 5), voxels with sigma > 0.1 max sigma
+    refined once, a_max = 2.5, 3000 steps at 0.9 of the refined mesh's
+    stability bound, checkpoints every 50 steps, FP32 fields with FP64
+    gradient accumulation.  Eight plane waves sin(40 t) batched as independent
+    sources: from the six faces (observed on their own face) and along the two
+    body diagonals +-(1, 1, 1) / sqrt(3) (entering through three faces,
+    observed on the z face they enter through).  Data: the FP64 forward at
+    the true coefficient plus 3 % noise; 10 CG iterations."""
+    n, h, origin = cube_grid(N)
+    lo, hi = central_half(N)
     rng = np.random.Generator(np.random.PCG64(5))
     sigma = gaussian_bumps(lo, hi, h, origin, int(rng.integers(4, 9)), (0.0, 1.5), (0.05, 0.15), rng)
-    faces = [FACE_XM, FACE_XP, FACE_YM, FACE_YP, FACE_ZM, FACE_ZP][:n_src]
-    return Workload("large_257", n, h, origin, lo, hi, ALL_ABC, [Source(f, 40.0) for f in faces],
-                    nsteps, structured_dt(h, 2.5), 2.5, sigma, "fp32", ckpt_every=50)
+    srcs = [Source(f, 40.0) for f in (FACE_XM, FACE_XP, FACE_YM, FACE_YP, FACE_ZM, FACE_ZP)]
+    srcs += [Source(FACE_ZM, 40.0, 1.0, (1.0, 1.0, 1.0)), Source(FACE_ZP, 40.0, 1.0, (-1.0, -1.0, -1.0))]
+    ref = (sigma > 0.1 * sigma.max()) if refine else None
+    dt = refined_dt(h, 2.5) if refine else structured_dt(h, 2.5)
+    return Workload("large_%d" % N, n, h, origin, lo, hi, ALL_ABC, srcs[:n_src], nsteps, dt, 2.5, sigma, "fp32",
+                    ckpt_every=50, refine=ref,
+                    extra=dict(cg_iters=10, gamma=0.01, a0=1.0, noise=0.03, noise_seed=1))
 
 
 def small_problem(n=9, fem=(2, 6), nsteps=60, bc=ALL_ABC, src_face=FACE_ZP, omega=12.0,

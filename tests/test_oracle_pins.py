@@ -384,3 +384,115 @@ def test_cg_step_decreases_functional_and_projects():
     J_end, _, _ = oracle.value_and_grad(P, a, [src], w.nsteps, w.dt, [obs], 0.0, 1.0, "quadrature",
                                         need_grad=False)
     assert J_end < Js[0]
+
+
+# ------------------------------------------------- quadrature of the functional
+@pytest.mark.parametrize("n", [(9, 7, 5), (4, 11, 6)])
+def test_face_weights_are_the_trapezoid_rule(n):
+    """The lumped face weights m_j of the misfit int_{S_T} (u - u~)^2 dS dt
+    (Eq. (functional)) are the tensor trapezoid rule on each face: they sum to
+    the face area (n_p - 1)(n_q - 1) h^2 and integrate every bilinear function
+    of the two in-face coordinates exactly.  (Not halving on the border, or
+    halving a corner only once, changes the sum.)"""
+    h = 0.3
+    P = Problem(n, h, None, None, (1,) * 6)
+    rng = np.random.default_rng(2)
+    for f in range(6):
+        ax = f // 2
+        p, q = [d for d in range(3) if d != ax]
+        w = P.face_weights(f)
+        nodes = P.face_nodes(f)
+        Lp, Lq = (n[p] - 1) * h, (n[q] - 1) * h
+        assert abs(w.sum() - Lp * Lq) < 1e-13 * Lp * Lq
+        x = h * P.I[nodes, p]
+        y = h * P.I[nodes, q]
+        c = rng.standard_normal(4)
+        f_val = c[0] + c[1] * x + c[2] * y + c[3] * x * y
+        exact = c[0] * Lp * Lq + c[1] * Lp ** 2 / 2 * Lq + c[2] * Lp * Lq ** 2 / 2 + c[3] * Lp ** 2 * Lq ** 2 / 4
+        assert abs(np.dot(w, f_val) - exact) < 1e-12 * (abs(exact) + Lp * Lq)
+        # corners carry a quarter, edge nodes a half, interior nodes the full h^2
+        on_p = (P.I[nodes, p] == 0) | (P.I[nodes, p] == n[p] - 1)
+        on_q = (P.I[nodes, q] == 0) | (P.I[nodes, q] == n[q] - 1)
+        np.testing.assert_allclose(w[on_p & on_q], h * h / 4)
+        np.testing.assert_allclose(w[on_p ^ on_q], h * h / 2)
+        np.testing.assert_allclose(w[~on_p & ~on_q], h * h)
+
+
+def test_time_weights_are_the_right_rectangle_rule():
+    """With quadrature weights the time integral of the misfit is the right
+    rectangle rule tau sum_{k=1}^{N} g(t_k): exact for constants (= T) and,
+    for g(t) = t, exactly T^2 / 2 + T tau / 2 (the rule's closed-form error)."""
+    P = Problem((5, 5, 5), 0.25, None, None, (1,) * 6)
+    N, dt = 37, 0.0123
+    T = N * dt
+    wk, mj = oracle.data_weights(P, synth.FACE_ZP, N, dt, "quadrature")
+    t = dt * np.arange(N + 1)
+    assert wk[0] == 0.0
+    assert abs(np.dot(wk, np.ones(N + 1)) - T) < 1e-14
+    assert abs(np.dot(wk, t) - (T * T / 2 + T * dt / 2)) < 1e-14
+    # plain weights: the unweighted sum over k >= 1 and every face node
+    wp, mp = oracle.data_weights(P, synth.FACE_ZP, N, dt, "plain")
+    assert wp.sum() == N and np.all(mp == 1.0)
+
+
+def test_misfit_of_a_constant_residual_is_half_c2_T_area():
+    """J = 1/2 int_{S_T} (u - u~)^2 dS dt for u - u~ = c on every face node and
+    every step: 1/2 c^2 T |face| with the quadrature weights."""
+    P = Problem((6, 7, 8), 0.2, None, None, (1,) * 6)
+    N, dt, c = 25, 0.03, 0.7
+    for f in range(6):
+        wk, mj = oracle.data_weights(P, f, N, dt, "quadrature")
+        obs = np.zeros((N + 1, mj.size))
+        J, cot = oracle.misfit(obs + c, obs, wk, mj)
+        ax = f // 2
+        area = np.prod([(P.n[d] - 1) * P.h for d in range(3) if d != ax])
+        assert abs(J - 0.5 * c * c * N * dt * area) < 1e-13 * J
+        np.testing.assert_allclose(cot[1:], c * dt * mj[None, :].repeat(N, 0))
+        assert np.all(cot[0] == 0.0)
+
+
+def test_projected_direction_by_hand():
+    """Three voxels, a_min = 1, a_max = 4: voxel 0 at the lower bound with
+    g > 0 (blocked: its gradient component is dropped), voxel 1 at the lower
+    bound with g < 0 (free: it moves up), voxel 2 at the upper bound with
+    g > 0 (free: it moves down).  A previous direction that pushes voxel 0
+    further down is dropped there too."""
+    a = np.array([1.0, 1.0, 4.0])
+    g = np.array([2.0, -1.0, 3.0])
+    gp = oracle.projected_gradient(a, g, 1.0, 4.0)
+    np.testing.assert_array_equal(gp, [0.0, -1.0, 3.0])
+    d, beta, gn2 = oracle.cg_direction(gp, np.array([-1.0, 1.0, 1.0]), 5.0, 2.0)
+    assert gn2 == 2.0 * (1.0 + 9.0) and beta == 4.0
+    np.testing.assert_array_equal(d, [-4.0, 5.0, 1.0])
+    np.testing.assert_array_equal(oracle.drop_blocked(a, d, 1.0, 4.0), [0.0, 5.0, 0.0])
+
+
+def test_projected_cg_descends_from_the_lower_bound():
+    """Started at a = a_min with data from a coefficient that is below the
+    background on part of the block (its gradient pushes those voxels out of
+    the admissible set), the projected iteration lowers F at every step; the
+    slope <g, d> it fits the parabola to is the slope of the projected path."""
+    w = synth.small_problem(n=9, fem=(2, 6), nsteps=80, omega=12.0, sigma_seed=5, courant=0.8)
+    P = oracle.problem_from_workload(w)
+    src = w.sources[0]
+    rng = np.random.default_rng(8)
+    a_true = 1.0 + 2.0 * rng.random(P.n_unknown) * (rng.random(P.n_unknown) < 0.5)
+    a_true[rng.random(P.n_unknown) < 0.3] = 0.6  # below a_min: unreachable
+    obs = P.forward(a_true, src, w.nsteps, w.dt)["trace"]
+    a = np.ones(P.n_unknown)
+    state = {}
+    Js = []
+    for _ in range(4):
+        a_prev = a
+        a, state, rep = oracle.cg_step(P, a, [src], w.nsteps, w.dt, [obs], state, gamma=0.0, a_min=1.0,
+                                       a_max=4.0)
+        Js.append(rep["J"])
+        # the directional derivative along the projected path equals <g, d>
+        eps = 1e-7 * rep["alpha_trial"]
+        Jp, _, _ = oracle.value_and_grad(P, np.clip(a_prev + eps * state["d"], 1.0, 4.0), [src], w.nsteps, w.dt,
+                                         [obs], 0.0, 1.0, "quadrature", need_grad=False)
+        assert abs((Jp - rep["J"]) / eps - rep["dJ0"]) < 1e-4 * abs(rep["dJ0"])
+    J_end, _, _ = oracle.value_and_grad(P, a, [src], w.nsteps, w.dt, [obs], 0.0, 1.0, "quadrature",
+                                        need_grad=False)
+    Js.append(J_end)
+    assert all(Js[i + 1] < Js[i] for i in range(len(Js) - 1)), Js
