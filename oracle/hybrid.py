@@ -571,6 +571,66 @@ class Problem:
             return out, lam1
         return out
 
+    def lumped_mass(self, a_unknown):
+        """Diagonal mass M in which the hybrid operator is symmetric: on
+        FDM-owned rows the lumped lattice mass h^3, halved for every axis on
+        which the node lies on the outer boundary; on FEM-owned rows the
+        lumped finite-element mass M^L (Sec. 7.2)."""
+        M = np.full(self.NT, self.h ** 3)
+        for d in range(3):
+            b = np.concatenate([(self.I[:, d] == 0) | (self.I[:, d] == self.n[d] - 1), np.zeros(self.NC, dtype=bool)])
+            M[b] *= 0.5
+        if self.has_fem:
+            _, ML = self.assemble(a_unknown)
+            M[self.owned] = ML[self.owned]
+        return M
+
+    def adjoint_paper(self, a_unknown, src, nsteps, dt, cot, hist, return_lambda=False):
+        """The paper's adjoint, solved backward in time by Algorithm 2 with
+        separate FDM and FEM arrays: Eq. (fdmschemeadjoint) on the FDM-owned
+        rows and the second line of Eq. (fem) on the FEM-owned rows,
+        lambda^{k-1} = 2 lambda^k - lambda^{k+1} + tau^2 Delta_h lambda^k + s^k,
+        from lambda^N = lambda^{N+1} = 0 (Eq. (adjoint1): lambda(T) =
+        lambda_t(T) = 0), with d_n lambda = 0 (mirror ghost) on every face.
+        The data residual enters on S_T as the mirror ghost of the flux
+        d_n lambda = -(u - u~) z_delta that Eq. (control1) puts there: with the
+        cotangent c^k = dJ/d(trace row k) = w_k m_j (u - u~), s^k_j = -tau c^k_j / M_j.
+        Returns g_c = tau sum_k int_c grad u^k . grad lambda^k (Eq. (gradient1),
+        same time index), the paper's approximation of dJ/da_c."""
+        h = self.h
+        tau2 = dt * dt
+        K, ML = self.assemble(a_unknown)
+        M = self.lumped_mass(a_unknown)
+        own = self.owned
+        obs = self.face_nodes(src.face)
+        ones = np.ones(self.NT)
+        lam_fd, lam_fd_next = np.zeros(self.NT), np.zeros(self.NT)   # lambda^k, lambda^{k+1}
+        lam_fe, lam_fe_next = np.zeros(self.NT), np.zeros(self.NT)
+        G = np.zeros(self.n_unknown)
+        for k in range(nsteps, 0, -1):
+            if k <= nsteps - 1 and self.n_unknown:
+                G += self.pair(hist[k], self._combine(lam_fd, lam_fe), ones)
+            # 1. FDM rows, Eq. (fdmschemeadjoint), Neumann ghosts on every face
+            rows = self.fdm_owned
+            new_fd = np.zeros(self.NT)
+            new_fd[rows] = 2.0 * lam_fd[rows] - lam_fd_next[rows] + tau2 * (self.D @ lam_fd)[rows]
+            new_fd[obs] += -dt * cot[k] / M[obs]
+            # 2. FEM rows, Eq. (fem) second line (the G term never reaches an owned row)
+            new_fe = np.zeros(self.NT)
+            if self.has_fem:
+                new_fe[own] = 2.0 * lam_fe[own] - lam_fe_next[own] - tau2 * (K @ lam_fe)[own] / ML[own]
+                # 3.-4. exchange of Algorithm 1 / Algorithm 2
+                new_fd[self.omega_diamond] = new_fe[self.omega_diamond]
+                new_fe[self.omega_o] = new_fd[self.omega_o]
+            # 5. swap
+            lam_fd_next, lam_fd = lam_fd, new_fd
+            lam_fe_next, lam_fe = lam_fe, new_fe
+        lam0 = self._combine(lam_fd, lam_fe)
+        if self.n_unknown:
+            G += self.pair(hist[0], lam0, ones)
+        out = dt * G
+        return (out, lam0) if return_lambda else out
+
     def pair(self, u_owned, lam, ML):
         """Per unknown voxel c: (lambda / M^L)^T K_c u = sum over the voxel's
         tetrahedra of |K| grad u . grad (lambda / M^L), with K_c the a = 1
@@ -608,20 +668,24 @@ def misfit(trace, obs, wk, mj):
 
 
 def value_and_grad(prob: Problem, a, sources, nsteps, dt, obs_traces, gamma=0.0, a0=1.0,
-                   mode="plain", need_grad=True):
+                   mode="plain", need_grad=True, adjoint="exact", init=None):
     """F(a) = sum over sources of the data misfit + gamma/2 sum_c |c| (a_c - a0)^2
-    and its Euclidean gradient dF/da_c (Eq. (functional), Eq. (grad1new))."""
+    and its Euclidean gradient dF/da_c (Eq. (functional), Eq. (grad1new)):
+    adjoint='exact' by the discrete adjoint, 'paper' by the paper's adjoint
+    scheme (`Problem.adjoint_paper`).  init: (u^0, u^{-1}) of Model Problem 1
+    (Eq. (model1)), the same for every source; None: Model Problem 2."""
     J = 0.5 * gamma * prob.voxel_volume * float(np.sum((a - a0) ** 2))
     g = gamma * prob.voxel_volume * (a - a0)
     traces = []
     for s, src in enumerate(sources):
-        res = prob.forward(a, src, nsteps, dt, keep_hist=need_grad)
+        res = prob.forward(a, src, nsteps, dt, keep_hist=need_grad, init=init)
         wk, mj = data_weights(prob, src.face, nsteps, dt, mode)
         Jd, cot = misfit(res["trace"], obs_traces[s], wk, mj)
         J += Jd
         traces.append(res["trace"])
         if need_grad:
-            g = g + prob.adjoint(a, src, nsteps, dt, cot, res["hist"])
+            adj = prob.adjoint if adjoint == "exact" else prob.adjoint_paper
+            g = g + adj(a, src, nsteps, dt, cot, res["hist"])
     return J, (g if need_grad else None), traces
 
 

@@ -353,6 +353,27 @@ def small_problem(n=9, fem=(2, 6), nsteps=60, bc=ALL_ABC, src_face=FACE_ZP, omeg
                     refine=refine)
 
 
+def model1_initial(w: Workload):
+    """Initial state of Model Problem 1 (Eq. (model1)) from Eq. (initcond):
+    u(x, 0) = exp(-(x1^2 + x2^2 + x3^2)) on the whole domain (the printed
+    exponent x3^3 read as x3^2), u_t(x, 0) = 0, started with
+    u^{-1} = u^0 - tau u_t(x, 0) = u^0.  Returns (u0, u_prev) on the lattice
+    nodes (x fastest) and (c0, c_prev) on the centre nodes of refined voxels
+    (in unknown-voxel order), each a float64 array."""
+    nx, ny, nz = w.n
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    X = [w.origin[0] + w.h * x, w.origin[1] + w.h * y, w.origin[2] + w.h * z]
+    u0 = np.exp(-(X[0] ** 2 + X[1] ** 2 + X[2] ** 2)).ravel()
+    c0 = np.zeros(0)
+    if w.refine is not None and np.any(w.refine):
+        ud = w.unknown_dims
+        ids = np.flatnonzero(w.refine)
+        cv = [ids % ud[0], (ids // ud[0]) % ud[1], ids // (ud[0] * ud[1])]
+        C = [w.origin[d] + w.h * (cv[d] + w.fem_lo[d] + 1 + 0.5) for d in range(3)]
+        c0 = np.exp(-(C[0] ** 2 + C[1] ** 2 + C[2] ** 2))
+    return (u0, u0.copy()), (c0, c0.copy())
+
+
 def random_cotangent(n_src, nsteps, n_obs, seed=7) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     c = rng.standard_normal((n_src, nsteps + 1, n_obs))

@@ -496,3 +496,122 @@ def test_projected_cg_descends_from_the_lower_bound():
                                         need_grad=False)
     Js.append(J_end)
     assert all(Js[i + 1] < Js[i] for i in range(len(Js) - 1)), Js
+
+
+# ------------------------------------------------------------ paper-mode adjoint
+@pytest.mark.parametrize("refine", [0.0, 0.4])
+@pytest.mark.parametrize("mode", ["plain", "quadrature"])
+def test_paper_adjoint_equals_exact_with_reflecting_faces(refine, mode):
+    """With reflecting faces everywhere (no absorbing rows, so the forward's
+    boundary never switches), the paper's adjoint (Eq. (fdmschemeadjoint) with
+    d_n lambda = 0, residual as the flux on S_T, same-index pairing of
+    Eq. (gradient1)) is the exact discrete adjoint written in the variable
+    lambda = -tau M^{-1} mu: the two gradients agree to rounding."""
+    w = synth.small_problem(n=10, fem=(2, 7), nsteps=70, omega=12.0, courant=0.8, bc=(0,) * 6,
+                            refine_frac=refine, sigma_seed=3)
+    P = oracle.problem_from_workload(w)
+    src = w.sources[0]
+    a = w.a_true()
+    obs = P.forward(np.ones(P.n_unknown), src, w.nsteps, w.dt)["trace"]
+    J, g_exact, _ = oracle.value_and_grad(P, a, [src], w.nsteps, w.dt, [obs], mode=mode)
+    J2, g_paper, _ = oracle.value_and_grad(P, a, [src], w.nsteps, w.dt, [obs], mode=mode, adjoint="paper")
+    assert J == J2
+    assert np.linalg.norm(g_paper - g_exact) < 1e-11 * np.linalg.norm(g_exact)
+
+
+def test_paper_adjoint_with_absorbing_faces_differs_but_agrees_in_direction():
+    """With absorbing faces the paper's adjoint keeps d_n lambda = 0 where the
+    forward absorbs (the absorbing terms of Eq. (lagrangian1) are dropped), so
+    its gradient is no longer the exact one: it differs by far more than
+    rounding, yet points the same way."""
+    w = synth.small_problem(n=10, fem=(2, 7), nsteps=90, omega=12.0, courant=0.8, sigma_seed=3)
+    P = oracle.problem_from_workload(w)
+    src = w.sources[0]
+    a = w.a_true()
+    obs = P.forward(np.ones(P.n_unknown), src, w.nsteps, w.dt)["trace"]
+    _, ge, _ = oracle.value_and_grad(P, a, [src], w.nsteps, w.dt, [obs], mode="quadrature")
+    _, gp, _ = oracle.value_and_grad(P, a, [src], w.nsteps, w.dt, [obs], mode="quadrature", adjoint="paper")
+    rel = np.linalg.norm(gp - ge) / np.linalg.norm(ge)
+    cos = float(np.dot(gp, ge) / (np.linalg.norm(gp) * np.linalg.norm(ge)))
+    assert rel > 1e-6 and cos > 0.5, (rel, cos)
+
+
+# ----------------------------------------------------- Model Problem 1 (IP1)
+def _ip1_init(w):
+    (u0, um), (c0, cm) = synth.model1_initial(w)
+    return np.concatenate([u0, c0]), np.concatenate([um, cm])
+
+
+def test_model1_initial_state_of_initcond():
+    """Eq. (initcond) on the lattice: u^0 = exp(-|x|^2) at every node (1 at the
+    origin), u^{-1} = u^0 (zero initial velocity); centre nodes of refined
+    voxels take the same function at the voxel centre."""
+    w = synth.small_problem(n=9, fem=(2, 6), nsteps=10, refine_frac=0.5)
+    w.origin = (-0.5, -0.5, -0.5)
+    (u0, um), (c0, cm) = synth.model1_initial(w)
+    assert u0.size == 9 ** 3 and np.array_equal(u0, um) and c0.size == int(w.refine.sum())
+    assert u0[4 + 9 * (4 + 9 * 4)] == 1.0  # node (4, 4, 4) sits at the origin
+    assert abs(u0[0] - math.exp(-0.75)) < 1e-15
+    ud = w.unknown_dims
+    first = int(np.flatnonzero(w.refine)[0])
+    cx, cy, cz = first % ud[0], (first // ud[0]) % ud[1], first // (ud[0] * ud[1])
+    xc = [-0.5 + w.h * (c + 2 + 1 + 0.5) for c in (cx, cy, cz)]
+    assert abs(c0[0] - math.exp(-sum(v * v for v in xc))) < 1e-15
+
+
+@pytest.mark.parametrize("refine", [0.0, 0.4])
+def test_model1_energy_conserved_from_nonzero_data(refine):
+    """Model Problem 1 with a Gaussian initial state, no source and reflecting
+    faces: the discrete energy is constant from the first step (the energy
+    identity of Sec. 4 with nonzero initial data), for a non-constant a."""
+    w = synth.small_problem(n=11, fem=(2, 8), nsteps=200, bc=(0,) * 6, sigma_scale=2.0, sigma_seed=9,
+                            refine_frac=refine, courant=0.8)
+    w.origin = (-0.5, -0.5, -0.5)
+    P = oracle.problem_from_workload(w)
+    a = w.a_true()
+    init = _ip1_init(w)
+    src = synth.Source(synth.FACE_ZP, 12.0, 0.0)  # amplitude 0: no flux
+    res = P.forward(a, src, w.nsteps, w.dt, init=init, keep_fields=True)
+    F = res["fields"]
+    M = P.lumped_mass(a)
+    import scipy.sparse as sps
+    Km = (sps.diags(M) @ P.space_operator(a)).tocsr()
+    assert abs(Km - Km.T).max() < 1e-12 * abs(Km).max()
+    E = []
+    for k in range(0, w.nsteps):
+        v = (F[k + 1] - F[k]) / w.dt
+        E.append(0.5 * np.dot(M * v, v) + 0.5 * F[k + 1] @ (Km @ F[k]))
+    E = np.array(E)
+    assert E[0] > 0 and np.abs(E - E[0]).max() < 1e-11 * E[0]
+
+
+def test_model1_gradient_matches_central_differences():
+    """Model Problem 1 (nonzero u^0): dJ/da from the adjoint, whose pairing
+    now has a k = 0 term, equals central differences of J on every voxel
+    (dropping that term fails this check)."""
+    w = synth.small_problem(n=9, fem=(2, 6), nsteps=60, omega=12.0, sigma_seed=1, courant=0.8)
+    w.origin = (-0.5, -0.5, -0.5)
+    P = oracle.problem_from_workload(w)
+    src = w.sources[0]
+    init = _ip1_init(w)
+    a = w.a_true()
+    obs = P.forward(1.0 + 1.5 * np.random.default_rng(2).random(P.n_unknown), src, w.nsteps, w.dt,
+                    init=init)["trace"]
+    J, g, _ = oracle.value_and_grad(P, a, [src], w.nsteps, w.dt, [obs], init=init)
+    eps = 1e-6
+    fd = np.zeros(P.n_unknown)
+    for c in range(P.n_unknown):
+        e = np.zeros(P.n_unknown)
+        e[c] = eps
+        Jp, _, _ = oracle.value_and_grad(P, a + e, [src], w.nsteps, w.dt, [obs], need_grad=False, init=init)
+        Jm, _, _ = oracle.value_and_grad(P, a - e, [src], w.nsteps, w.dt, [obs], need_grad=False, init=init)
+        fd[c] = (Jp - Jm) / (2 * eps)
+    assert np.linalg.norm(g - fd) < 1e-6 * np.linalg.norm(fd)
+    # the k = 0 pairing term is not negligible here
+    res = P.forward(a, src, w.nsteps, w.dt, keep_hist=True, init=init)
+    wk, mj = oracle.data_weights(P, src.face, w.nsteps, w.dt)
+    _, cot = oracle.misfit(res["trace"], obs, wk, mj)
+    _, lam1 = P.adjoint(a, src, w.nsteps, w.dt, cot, res["hist"], return_lambda=True)
+    _, ML = P.assemble(a)
+    k0 = -w.dt ** 2 * P.pair(res["hist"][0], lam1, ML)
+    assert np.linalg.norm(k0) > 1e-3 * np.linalg.norm(fd)
