@@ -1,21 +1,28 @@
 """Benchmark of the hybrid FEM/FDM inverse-problem hot path on GB300.
 
-One step = one iteration of Algorithm 3 (hyb_cg_step): forward sweep with the
-FEM-region history kept, data misfit, exact adjoint sweep with the fused FP64
-gradient accumulation, gradient + Tikhonov term, Fletcher-Reeves direction,
+One step = one iteration of Algorithm 3 (hyb_cg_step): forward sweep (keeping
+checkpoints or the FEM-region history), data misfit, exact adjoint sweep
+(recomputing each checkpoint segment) with the fused FP64 gradient
+accumulation, gradient + Tikhonov term, projected Fletcher-Reeves direction,
 one trial forward for the step length and the projected update.
 
-Workload (default): 129^3 lattice on [-1,1]^3 (h = 1/64), FEM block nodes
-32..96 (65^3), three random cubic inclusions sigma ~ U[0.5, 2], 1500 time
-steps at the CFL step for a_max = 5, plane wave sin(40 t) from the top face,
-data = FP64 forward at the true coefficient + 3% Gaussian noise, FP32 fields
-with FP64 gradient and CG reductions, gamma = 0.01, a0 = 1, a in [1, 5].
+Workload (default, the large batched configuration): 257^3 lattice on
+[-1,1]^3 (h = 1/128), FEM block nodes 64..192 (129^3), smooth Gaussian-bump
+sigma with the voxels above 0.1 max sigma refined once, eight plane-wave
+sources sin(40 t) advanced by the same launches (six faces, two body
+diagonals), 3000 time steps, checkpoints every 50 steps, FP32 fields with
+FP64 gradient and CG reductions, data = FP64 forward at the true coefficient
+plus 3 % noise, gamma = 0.01, a in [1, 2.5]; the timed steps are the first
+10 iterations of a CG loop started at a = 1.  A second record on the 129^3
+single-source workload (whose fields fit in L2) follows.
 
-Metric: lattice-node updates per second over the three sweeps of a step
-(forward, adjoint, trial forward).  Also reported: the roofline of the
-dominant step kernel, the FP64 oracle on the host cores as a CPU baseline,
-an end-to-end figure with host buffers, the SM clocks during the timed
-region and the number of library kernels launched.
+Metric: lattice-node updates per second, n_src x (lattice + centre nodes) x
+N_t x 2 (forward and adjoint) per CG iteration over the iteration's wall time
+(which also holds the recompute and the trial forward); the count over every
+sweep actually run is reported beside it.  Also: the roofline of the
+dominant step kernel, the FP64 oracle on the host cores (one core and all
+cores), an end-to-end figure with host buffers, serving latency, the SM
+clocks during the timed region and the number of library kernels launched.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -37,25 +44,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "forward+adjoint Glattice-updates/s and %HBM roofline; gradients/s + p50/p99 served"
 UNIT = "Glattice-updates/s"
-L2_NOTE = "inputs larger than L2: per-step u history 1.5 GB and observation trace 100 MB"
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=6)
+    p.add_argument("--steps", type=int, default=10, help="timed CG iterations (the first K of a fresh loop)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--nsteps", type=int, default=1500, help="time steps of the workload")
+    p.add_argument("--workload", default="large_257", choices=["large_257", "inverse_129"])
+    p.add_argument("--nsteps", type=int, default=0, help="time steps (0: the workload's own)")
+    p.add_argument("--e2e-steps", type=int, default=2, help="CG iterations of the end-to-end measurement")
+    p.add_argument("--no-secondary", action="store_true", help="skip the 129^3 record")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-steps", type=int, default=30)
     p.add_argument("--serve-requests", type=int, default=512, help="requests of the serving stream (0: skip)")
     p.add_argument("--serve-workers", type=int, default=8)
-    p.add_argument("--workload", default="inverse_129", choices=["inverse_129", "large_257"])
     p.add_argument("--sources", type=int, default=0, help="with --sweeps-only: use the first K sources")
+    p.add_argument("--no-refine", action="store_true", help="with --sweeps-only: the large workload unrefined")
     p.add_argument("--sweeps-only", type=int, default=0,
                    help="profiling aid: run this many forward+adjoint sweep pairs of the workload "
-                        "(FP32, --nsteps steps) and exit without timing")
+                        "(FP32, --nsteps steps, history kept) and exit without timing")
     return p.parse_args()
 
 
@@ -135,25 +144,26 @@ def measured_peak():
 def kernel_source_hash():
     """Hash of the step kernels' code (comments and blank lines left out, so
     that a comment edit keeps a recorded ncu figure valid)."""
-    p = os.path.join(ROOT, "paper_1509_01399_gb300", "csrc", "step_kernels.cu")
     code = []
-    for ln in open(p, encoding="utf-8"):
-        ln = ln.split("//", 1)[0].rstrip()
-        if ln:
-            code.append(ln)
+    for name in ("step_kernels.cu", "async_copy.cuh", "hyb_internal.h"):
+        p = os.path.join(ROOT, "paper_1509_01399_gb300", "csrc", name)
+        for ln in open(p, encoding="utf-8"):
+            ln = ln.split("//", 1)[0].rstrip()
+            if ln:
+                code.append(ln)
     return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
     h = kernel_source_hash()
     for ln in open(path):
         f = dict(kv.split("=", 1) for kv in ln.split() if "=" in kv)
-        if f.get("kernel") == kernel and f.get("source") == h:
+        if f.get("kernel") == kernel and f.get("workload") == workload and f.get("source") == h:
             try:
                 return float(f["bytes_per_launch"])
             except (KeyError, ValueError):
@@ -161,62 +171,268 @@ def recorded_traffic(kernel: str):
     return None
 
 
-def make_workload(nsteps, name="inverse_129"):
+def make_workload(name, nsteps=0, refine=True):
     import synth
     if name == "large_257":
-        return synth.large_257(nsteps=nsteps)
-    return synth.inverse_129(nsteps=nsteps)
+        return synth.large_257(refine=refine, **({"nsteps": nsteps} if nsteps else {}))
+    return synth.inverse_129(**({"nsteps": nsteps} if nsteps else {}))
 
 
-def run_sweeps_only(args):
-    """Forward + adjoint sweeps of the workload with all its sources, for
-    ncu captures: no data generation, no CG, no timing."""
+def algorithmic_bytes(w, info, n_src, es=4):
+    """Algorithmic bytes of one forward and one adjoint launch: an FDM-owned
+    node reads u^k, u^{k-1} and writes u^{k+1} (3 es); a FEM-owned node in
+    stencil form adds its coefficient (4 es; the adjoint also reads the stored
+    u^k: 5 es); a row in sparse form (refined region, lattice and centre
+    nodes) moves 3 es plus 8 B per off-diagonal entry (value and column),
+    and in the adjoint 4 es plus the entries.  Times the sources of the
+    launch."""
+    n_lat = w.n_nodes
+    n_fo = int(info.n_fem_owned)
+    nr, nc, nnz = int(info.n_sparse_rows), int(info.n_centres), int(info.n_sparse_nnz)
+    nrl = nr - nc
+    fdm = n_lat - n_fo
+    fwd = fdm * 3 * es + (n_fo - nrl) * 4 * es + nr * 3 * es + 8 * nnz
+    adj = fdm * 3 * es + (n_fo - nrl) * 5 * es + nr * 4 * es + 8 * nnz
+    return n_src * fwd, n_src * adj
+
+
+def rel_l2(x, ref):
     import torch
-    from paper_1509_01399_gb300 import hyb as H
-    w = make_workload(args.nsteps, args.workload)
-    srcs = w.sources[: args.sources] if args.sources > 0 else w.sources
-    m = H.HybMesh.from_workload(w, precision="fp32", ckpt_every=0)
-    a = torch.tensor(w.a_true(), dtype=torch.float64, device="cuda")
-    tr = m.new_trace(len(srcs), w.nsteps)
+    x = x.double()
+    ref = ref.double()
+    d = float(torch.linalg.vector_norm(ref))
+    return float(torch.linalg.vector_norm(x - ref)) / (d if d > 0 else 1.0)
+
+
+# ------------------------------------------------------------------ CG runs
+def make_data(H, w, dev, m32):
+    """Observations: per source, the FP64 forward at the true coefficient
+    plus 3 % noise (one FP64 mesh per source, so that its checkpoints stay
+    small).  Also returns, per source, the relative L2 difference between the
+    FP32 trace at the true coefficient and the FP64 one."""
+    import torch
+    import synth
+    srcs, nsteps, dt = w.sources, w.nsteps, w.dt
+    tr32 = m32.forward(w.a_true(), srcs, nsteps, dt)
+    obs = torch.zeros_like(tr32)
+    errs = []
+    m64 = H.HybMesh.from_workload(w, precision="fp64", ckpt_every=w.ckpt_every, device=dev)
+    for s, src in enumerate(srcs):
+        tr64 = m64.forward(w.a_true(), [src], nsteps, dt)
+        errs.append(rel_l2(tr32[s], tr64[0]))
+        obs[s] = synth.add_noise_device(tr64[0], w.extra["noise"], w.extra["noise_seed"] + s).to(obs.dtype)
+        del tr64
+    m64.sync()
+    m64.close()
+    del tr32
+    torch.cuda.empty_cache()
+    return obs, errs
+
+
+def run_cg(H, w, dev, steps, warmup, e2e_steps, clocks=None):
+    """W warm-up CG iterations, then the first K iterations of a fresh CG
+    loop timed with CUDA events on the mesh's stream; per-iteration F and
+    ||g||; the step kernels' launch times; the end-to-end figure."""
+    import numpy as np
+    import torch
+    srcs, nsteps, dt = w.sources, w.nsteps, w.dt
+    S = len(srcs)
+    m = H.HybMesh.from_workload(w, precision="fp32", device=dev)
+    info = m.query()
+    t0 = time.perf_counter()
+    obs, trace_errs = make_data(H, w, dev, m)
+    data_s = time.perf_counter() - t0
+    gamma, a0 = w.extra["gamma"], w.extra["a0"]
+    stream = m.stream
+    a = torch.ones(w.n_unknown, dtype=torch.float64, device=dev)
+    state = m.new_cg_state()
+
+    def step():
+        return m.cg_step(a, obs, srcs, nsteps, dt, state, gamma=gamma, a0=a0, a_min=1.0, a_max=w.a_max)
+
+    for _ in range(warmup):
+        step()
+    a.fill_(1.0)  # the timed iterations are the first K of a fresh loop
+    state = m.new_cg_state()
+    torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.start()
+    l0 = m.launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = [step() for _ in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
+    el_ms = ev0.elapsed_time(ev1)
+    launches = m.launches() - l0
+    a_final = a.clone()
+    # step-kernel launch times: sweeps of a shorter run with the history kept
+    # (no checkpoint copies, no recompute), same launches per level
+    nl = min(nsteps, 300)
+    mr = H.HybMesh.from_workload(w, precision="fp32", ckpt_every=0, device=dev)
+    tr = mr.new_trace(S, nl)
     cot = torch.randn_like(tr) * 1e-3
-    for _ in range(args.sweeps_only):
-        m.forward(a, srcs, w.nsteps, w.dt, tr)
-        m.adjoint(cot)
+    for _ in range(2):  # the second call captures the sweep graphs
+        mr.forward(a_final, srcs, nl, dt, tr)
+        mr.adjoint(cot)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(mr.stream)
+    mr.forward(a_final, srcs, nl, dt, tr)
+    e[1].record(mr.stream)
+    e[2].record(mr.stream)
+    mr.adjoint(cot)
+    e[3].record(mr.stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = e[0].elapsed_time(e[1]) / nl
+    adj_ms = e[2].elapsed_time(e[3]) / nl
+    mr.sync()
+    mr.close()
+    del tr, cot
+    # end to end through the C ABI with host buffers: observations and the
+    # coefficient copied in from pinned host memory, the coefficient back
+    obs_host = obs.cpu().pin_memory()
+    a_host = torch.ones(w.n_unknown, dtype=torch.float64).pin_memory()
+    a_back = torch.empty_like(a_host).pin_memory()
+    st2 = m.new_cg_state()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        obs.copy_(obs_host, non_blocking=True)
+        a.copy_(a_host, non_blocking=True)
+        m.cg_step(a, obs, srcs, nsteps, dt, st2, gamma=gamma, a0=a0, a_min=1.0, a_max=w.a_max)
+        a_back.copy_(a, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        a_host.copy_(a_back)
+    e2e_s = time.perf_counter() - t0
+    h2d = obs_host.numel() * obs_host.element_size() + a_host.numel() * 8
+    d2h = a_back.numel() * 8 + 64
     m.sync()
     m.close()
-    print(json.dumps({"sweeps": args.sweeps_only, "workload": w.name, "nsteps": w.nsteps,
-                      "sources": len(srcs)}))
-    return 0
+    del obs, obs_host
+    torch.cuda.empty_cache()
+    n_nodes = w.n_nodes + int(info.n_centres)
+    sweeps_run = 4 if w.ckpt_every else 3  # forward, (recompute,) adjoint, trial forward
+    return dict(w=w, info=info, el_ms=el_ms, reps=reps, launches=launches, clocks=clk, fwd_ms=fwd_ms,
+                adj_ms=adj_ms, e2e_s=e2e_s, h2d=h2d, d2h=d2h, n_nodes=n_nodes, S=S, sweeps_run=sweeps_run,
+                trace_errs=trace_errs, data_s=data_s, a_final=a_final)
 
 
-def algorithmic_bytes(w, es=4):
-    """Algorithmic bytes per launch: FDM-owned node reads u^k,
-    u^{k-1} and writes u^{k+1} (3 es); a FEM-owned node adds its coefficient
-    (forward) and, in the adjoint, the stored u^k (4 es / 5 es)."""
-    n_nodes = w.n_nodes
-    fo = 1
-    for d in range(3):
-        fo *= (w.fem_hi[d] - w.fem_lo[d] - 1)
-    fdm = n_nodes - fo
-    return fdm * 3 * es + fo * 4 * es, fdm * 3 * es + fo * 5 * es, fdm, fo
+def fp32_vs_fp64_gradient(H, w, dev):
+    """FP32 and FP64 forward + misfit + adjoint + gradient at a = 1 on the
+    same observations (the FP64 forward at the true coefficient): relative
+    L2 difference of the gradients and of J."""
+    import torch
+    out = {}
+    m64 = H.HybMesh.from_workload(w, precision="fp64", ckpt_every=w.ckpt_every, device=dev)
+    obs64 = m64.forward(w.a_true(), w.sources, w.nsteps, w.dt).clone()
+    res = {}
+    for prec, dtype in (("fp64", torch.float64), ("fp32", torch.float32)):
+        m = m64 if prec == "fp64" else H.HybMesh.from_workload(w, precision="fp32", device=dev)
+        a = torch.ones(w.n_unknown, dtype=torch.float64, device=dev)
+        tr = m.forward(a, w.sources, w.nsteps, w.dt)
+        J, cot = m.misfit(tr, obs64.to(dtype), H.HYB_WEIGHTS_QUADRATURE, want_cot=True)
+        m.adjoint(cot)
+        res[prec] = (J, m.gradient(a, w.extra["gamma"], w.extra["a0"]).clone())
+        m.sync()
+        if prec == "fp32":
+            m.close()
+    m64.close()
+    out["gradient_rel_l2"] = rel_l2(res["fp32"][1], res["fp64"][1])
+    out["J_rel"] = abs(res["fp32"][0] - res["fp64"][0]) / abs(res["fp64"][0])
+    return out
+
+
+def cg_record(r, steps):
+    """Line fields of one CG run."""
+    w, S = r["w"], r["S"]
+    el_s = r["el_ms"] * 1e-3
+    per_step = S * r["n_nodes"] * w.nsteps
+    return dict(
+        value=steps * 2 * per_step / el_s / 1e9,
+        all_sweeps=steps * r["sweeps_run"] * per_step / el_s / 1e9,
+        ms_per_step=r["el_ms"] / steps,
+        gradients_per_s=steps / el_s,
+        cg={"iterations": steps, "F": [rp.J for rp in r["reps"]], "gnorm": [rp.gnorm for rp in r["reps"]],
+            "alpha": [rp.alpha for rp in r["reps"]], "beta": [rp.beta for rp in r["reps"]],
+            "F_first": r["reps"][0].J, "F_last": r["reps"][-1].J})
+
+
+def roofline(r, peak, peak_kind, workload):
+    w, S = r["w"], r["S"]
+    fwd_b, adj_b = algorithmic_bytes(w, r["info"], S)
+    # launches per CG iteration: forward, recompute (checkpointing), trial
+    # forward; one adjoint sweep
+    n_fwd = r["sweeps_run"] - 1
+    t_fwd, t_adj = n_fwd * r["fwd_ms"], r["adj_ms"]
+    fwd_dom = t_fwd >= t_adj
+    name = "step_kernel<float,forward>" if fwd_dom else "step_kernel<float,adjoint>"
+    b, ms = (fwd_b, r["fwd_ms"]) if fwd_dom else (adj_b, r["adj_ms"])
+    ach = b / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind, "traffic": recorded_traffic(name, workload),
+            "algorithmic_bytes_per_launch": b, "launch_ms": ms, "time_share": max(t_fwd, t_adj) / (t_fwd + t_adj),
+            "fwd": {"launch_ms": r["fwd_ms"], "bytes": fwd_b, "frac": fwd_b / (r["fwd_ms"] * 1e-3) / 1e9 / peak},
+            "adj": {"launch_ms": r["adj_ms"], "bytes": adj_b, "frac": adj_b / (r["adj_ms"] * 1e-3) / 1e9 / peak}}
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_sample(w, sample_steps):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the
-    workload: `sample_steps` forward steps and the same number of adjoint
-    steps on the full 129^3 lattice.  Returns lattice updates per second."""
+def _oracle_sample_worker(args):
+    """One process: the oracle (as it stands) on the sample lattice, k
+    forward + k adjoint steps of one source.  Returns (node updates, s)."""
+    steps, src_index = args
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
     import numpy as np
     import oracle
+    import synth
+    w = synth.large_batched(129, nsteps=steps)
     P = oracle.problem_from_workload(w)
-    src = w.sources[0]
-    a = np.ones(P.n_unknown)
+    src = w.sources[src_index % len(w.sources)]
+    a = w.a_true()
     t0 = time.perf_counter()
-    res = P.forward(a, src, sample_steps, w.dt, keep_hist=True)
+    res = P.forward(a, src, steps, w.dt, keep_hist=True)
     cot = np.random.default_rng(0).standard_normal(res["trace"].shape)
-    P.adjoint(a, src, sample_steps, w.dt, cot, res["hist"])
+    P.adjoint(a, src, steps, w.dt, cot, res["hist"])
     el = time.perf_counter() - t0
-    return 2.0 * w.n_nodes * sample_steps / el / 1e9, el
+    return 2.0 * (w.n_nodes + P.NC) * steps, el
+
+
+CPU_SAMPLE = ("the large workload's recipe (FEM central half, Gaussian bumps, voxels above 0.1 max sigma refined, "
+              "face and diagonal sources) on a 129^3 lattice (h = 1/64): %d forward + %d adjoint steps of one "
+              "source per process; building the oracle on the 257^3 lattice alone takes ~30 s and 15 GB per process")
+
+
+def cpu_baseline(sample_steps, all_cores=True):
+    """The FP64 oracle timed on the host cores: one process on one core, and
+    one process per core (spawned) on the same sample, each its own source."""
+    import multiprocessing as mp
+    import platform
+    ctx = mp.get_context("spawn")
+    out = {"kind": "oracle", "sample": CPU_SAMPLE % (sample_steps, sample_steps), "unit": UNIT}
+    with ctx.Pool(1) as pool:
+        n, el = pool.map(_oracle_sample_worker, [(sample_steps, 6)])[0]
+    out.update(value=n / el / 1e9, cores=1, seconds=el)
+    cpu_model = platform.processor() or platform.machine()
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                cpu_model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    nproc = os.cpu_count() or 1
+    out["nproc"] = nproc
+    out["cpu_model"] = cpu_model + " (" + platform.machine() + ")"
+    if all_cores and nproc > 1:
+        t0 = time.perf_counter()
+        with ctx.Pool(nproc) as pool:
+            res = pool.map(_oracle_sample_worker, [(sample_steps, i) for i in range(nproc)])
+        wall = time.perf_counter() - t0
+        out["all_cores"] = {"value": sum(r[0] for r in res) / max(r[1] for r in res) / 1e9, "cores": nproc,
+                            "seconds": max(r[1] for r in res), "wall_with_setup_s": wall}
+    return out
 
 
 # ------------------------------------------------------------------ serving
@@ -225,7 +441,9 @@ def run_serving(args, dev):
     drawn from {33, 65, 97, 129}^3 (FEM block = central half, 2-4 inclusions,
     400-1500 steps by size).  Capacity is measured with requests arriving
     back to back; the stream then arrives as a Poisson process at 80% of it.
-    Beside it, the FP64 path with one request at a time."""
+    Beside it, the FP64 path with one request at a time on a sample of the
+    same requests, and each sampled FP32 gradient's relative L2 difference
+    from its FP64 counterpart."""
     import numpy as np
     import synth
     from paper_1509_01399_gb300.serve import Request, ServingEngine, latency_stats, poisson_arrivals
@@ -245,16 +463,20 @@ def run_serving(args, dev):
     res = eng.run([Request(i, synth.serving_request(i), float(arr[i])) for i in range(R)])
     st = latency_stats(res)
     eng.close()
-    # FP64 path, one request at a time, on a sample of the same stream
     n64 = min(R, 16)
     e64 = ServingEngine(workers=1, precision="fp64", device=str(dev))
     e64.run([Request(-1, synth.serving_request(i), 0.0) for i in range(2)])
     r64 = e64.run([Request(i, synth.serving_request(i), 0.0) for i in range(n64)])
     e64.close()
     lat64 = np.array([r.finish - r.start for r in r64])
+    errs = []
+    for r in r64:
+        g32 = res[r.rid].gradient
+        errs.append(float(np.linalg.norm(g32 - r.gradient) / np.linalg.norm(r.gradient)))
     return {"requests": R, "workers": args.serve_workers, "capacity_solves_per_s": mu, "rate_per_s": lam,
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "mean_ms": st["mean_ms"], "dtype": "f32",
+            "grad_rel_err_vs_fp64": {"max": max(errs), "median": float(np.median(errs)), "requests": len(errs)},
             "fp64_one_at_a_time": {"sample": n64, "solves_per_s": float(n64 / lat64.sum()),
                                    "p50_ms": float(np.percentile(lat64, 50) * 1e3),
                                    "p99_ms": float(np.percentile(lat64, 99) * 1e3)}}
@@ -262,39 +484,75 @@ def run_serving(args, dev):
 
 # ---------------------------------------------------------------- reference
 def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step one bounded
+    sample (one process, one core) of the workload's scheme."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    w = make_workload(args.nsteps)
-    times, vals = [], []
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
     s = max(2, args.cpu_sample_steps // 3)
-    for i in range(args.warmup + args.steps):
-        v, el = oracle_sample(w, s)
-        if i >= args.warmup:
-            vals.append(v)
-            times.append(el)
+    times, vals = [], []
+    with ctx.Pool(1) as pool:
+        for i in range(args.warmup + args.steps):
+            n, el = pool.map(_oracle_sample_worker, [(s, 6)])[0]
+            if i >= args.warmup:
+                vals.append(n / el / 1e9)
+                times.append(el)
     value = statistics.median(vals)
+    w = make_workload(args.workload, args.nsteps)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "inverse_129 (oracle sample: %d forward + %d adjoint steps on 129^3)" % (s, s),
-                       "parallelism": "host cores, one process"},
+            "config": {"workload": w.name + " (oracle sample, see cpu_baseline)", "parallelism": "one host core"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d forward + %d adjoint steps of the 129^3 workload per step" % (s, s)},
+                             "sample": CPU_SAMPLE % (s, s)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-# --------------------------------------------------------------------- ours
-def run_ours(args):
-    import numpy as np
+# ------------------------------------------------------------- sweeps only
+def run_sweeps_only(args):
+    """Forward + adjoint sweeps of the workload with its sources, for ncu
+    captures: no data generation, no CG, no timing."""
     import torch
-    import synth
+    from paper_1509_01399_gb300 import hyb as H
+    w = make_workload(args.workload, args.nsteps, refine=not args.no_refine)
+    srcs = w.sources[: args.sources] if args.sources > 0 else w.sources
+    m = H.HybMesh.from_workload(w, precision="fp32", ckpt_every=0)
+    a = torch.tensor(w.a_true(), dtype=torch.float64, device="cuda")
+    tr = m.new_trace(len(srcs), w.nsteps)
+    cot = torch.randn_like(tr) * 1e-3
+    for _ in range(args.sweeps_only):
+        m.forward(a, srcs, w.nsteps, w.dt, tr)
+        m.adjoint(cot)
+    m.sync()
+    m.close()
+    print(json.dumps({"sweeps": args.sweeps_only, "workload": w.name, "nsteps": w.nsteps, "sources": len(srcs)}))
+    return 0
+
+
+# --------------------------------------------------------------------- ours
+def describe(w):
+    srcs = ", ".join(("face %d" % s.face) if s.direction is None else
+                     ("dir (%g,%g,%g)" % tuple(s.direction)) for s in w.sources)
+    ref = int(w.refine.sum()) if w.refine is not None else 0
+    return ("%s: %d^3 lattice h=1/%d, FEM block nodes %d..%d, %d refined voxels, %d sources [%s], %d steps "
+            "dt=%.6g, checkpoints every %d, FP32 fields, FP64 gradient and CG reductions"
+            % (w.name, w.n[0], round(1 / w.h), w.fem_lo[0], w.fem_hi[0], ref, len(w.sources), srcs, w.nsteps,
+               w.dt, w.ckpt_every))
+
+
+def run_ours(args):
+    import torch
     from paper_1509_01399_gb300 import hyb as H
 
     rank, world, local = dist_env()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample_steps)  # spawned before the first GPU call
     dist = None
     if world > 1:
         import torch.distributed as dist_mod
@@ -302,135 +560,60 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = make_workload(args.nsteps)
-    srcs = w.sources
-    nsteps, dt = w.nsteps, w.dt
-
-    # data: FP64 forward at the true coefficient + 3% noise (outside timing)
-    m64 = H.HybMesh.from_workload(w, precision="fp64", ckpt_every=0, device=dev)
-    obs64 = m64.forward(w.a_true(), srcs, nsteps, dt)
-    m64.sync()
-    obs_np = synth.add_noise(obs64.cpu().numpy(), w.extra["noise"], w.extra["noise_seed"])
-    m64.close()
-    del obs64
-    m = H.HybMesh.from_workload(w, precision="fp32", ckpt_every=0, device=dev)
-    obs = torch.from_numpy(obs_np.astype(np.float32)).to(dev)
-    a = torch.ones(w.n_unknown, dtype=torch.float64, device=dev)
-    state = m.new_cg_state()
-    stream = m.stream
-    gamma, a0 = w.extra["gamma"], w.extra["a0"]
-
-    def step():
-        return m.cg_step(a, obs, srcs, nsteps, dt, state, gamma=gamma, a0=a0, a_min=1.0, a_max=w.a_max)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize(dev)
+    w = make_workload(args.workload, args.nsteps)
+    peak, peak_kind = measured_peak()
     if dist:
         dist.barrier()
-    clk = ClockSampler(local)
-    clk.start()
-    l0 = m.launches()
-    torch.cuda.synchronize(dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    reps = [step() for _ in range(args.steps)]
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = clk.stop()
-    el_ms = ev0.elapsed_time(ev1)
-    launches = m.launches() - l0
+    r = run_cg(H, w, dev, args.steps, args.warmup, args.e2e_steps, clocks=ClockSampler(local))
+    el_ms = r["el_ms"]
     if dist:
         t = torch.tensor([el_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         el_ms = float(t.item())
+        r["el_ms"] = el_ms
         dist.barrier()
-    sweeps = 3
-    updates = sweeps * w.n_nodes * nsteps * len(srcs)
-    value = world * args.steps * updates / (el_ms * 1e-3) / 1e9
-    grads_per_s = world * args.steps / (el_ms * 1e-3)
-
-    # roofline of the step kernels: forward and adjoint sweeps timed alone
-    peak, peak_kind = measured_peak()
-    fwd_b, adj_b, n_fdm, n_fo = algorithmic_bytes(w)
-    trace = m.new_trace(len(srcs), nsteps)
-    for _ in range(2):
-        m.forward(a, srcs, nsteps, dt, trace)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e2 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    m.forward(a, srcs, nsteps, dt, trace)
-    e1.record(stream)
-    J, cot = m.misfit(trace, obs, H.HYB_WEIGHTS_QUADRATURE, want_cot=True)
-    for _ in range(2):  # the second call captures the adjoint sweep graph
-        m.adjoint(cot)
-    e1b = torch.cuda.Event(enable_timing=True)
-    e1b.record(stream)
-    m.adjoint(cot)
-    e2.record(stream)
-    torch.cuda.synchronize(dev)
-    fwd_ms = e0.elapsed_time(e1) / nsteps
-    adj_ms = e1b.elapsed_time(e2) / nsteps
-    dom = "step_kernel<float,adjoint>" if adj_ms >= fwd_ms else "step_kernel<float,forward>"
-    dom_ms, dom_b = (adj_ms, adj_b) if adj_ms >= fwd_ms else (fwd_ms, fwd_b)
-    achieved = dom_b / (dom_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(dom)
-
-    # end to end through the public API with host buffers
-    obs_host = torch.from_numpy(obs_np.astype(np.float32)).pin_memory()
-    a_host = torch.ones(w.n_unknown, dtype=torch.float64).pin_memory()
-    a_back = torch.empty_like(a_host).pin_memory()
-    obs_dev = torch.empty_like(obs)
-    st2 = m.new_cg_state()
-    a_dev = torch.empty_like(a)
-    for _ in range(1):
-        obs_dev.copy_(obs_host, non_blocking=True)
-        a_dev.copy_(a_host, non_blocking=True)
-        m.cg_step(a_dev, obs_dev, srcs, nsteps, dt, st2, gamma=gamma, a0=a0, a_min=1.0, a_max=w.a_max)
-        a_back.copy_(a_dev, non_blocking=True)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        obs_dev.copy_(obs_host, non_blocking=True)
-        a_dev.copy_(a_host, non_blocking=True)
-        m.cg_step(a_dev, obs_dev, srcs, nsteps, dt, st2, gamma=gamma, a0=a0, a_min=1.0, a_max=w.a_max)
-        a_back.copy_(a_dev, non_blocking=True)
-        torch.cuda.synchronize(dev)
-        a_host.copy_(a_back)
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * args.steps * updates / e2e_s / 1e9
-    h2d = obs_host.numel() * 4 + a_host.numel() * 8
-    d2h = a_back.numel() * 8 + 64
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+    rec = cg_record(r, args.steps)
+    per_step = r["S"] * r["n_nodes"] * w.nsteps
+    e2e_value = world * args.e2e_steps * 2 * per_step / r["e2e_s"] / 1e9
+    line = {"metric": METRIC, "value": world * rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "inverse_129: 129^3 lattice h=1/64, FEM block 65^3 (nodes 32..96), "
-                                   "3 cubic inclusions sigma~U[0.5,2], %d steps, FP32 fields, FP64 gradient "
-                                   "accumulation and CG reductions, one CG iteration per step" % nsteps,
-                       "n_nodes": w.n_nodes, "nsteps": nsteps, "sweeps_per_step": sweeps,
-                       "parallelism": "replicas" if world > 1 else "single GPU", "l2": L2_NOTE},
-            "gradients_per_s": grads_per_s,
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": dom_b, "launch_ms": dom_ms,
-                         "fwd_launch_ms": fwd_ms, "adj_launch_ms": adj_ms},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "cg": {"J_first": reps[0].J, "J_last": reps[-1].J, "gnorm_last": reps[-1].gnorm}}
-    m.close()
-    del obs, obs_dev, a_dev, trace, cot
+            "config": {"workload": describe(w), "n_nodes": w.n_nodes, "n_centres": int(r["info"].n_centres),
+                       "sources": r["S"], "nsteps": w.nsteps,
+                       "counted": "n_src x (lattice + centre nodes) x N_t x 2 (forward + adjoint) per CG iteration",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: 8 x 68.7 MB per field level, 6.3 GB observation trace"},
+            "lattice_updates_all_sweeps": {"value": world * rec["all_sweeps"], "unit": UNIT,
+                                           "sweeps_per_step": r["sweeps_run"]},
+            "gradients_per_s": world * rec["gradients_per_s"],
+            "roofline": roofline(r, peak, peak_kind, w.name),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+                    "d2h_bytes_per_step": r["d2h"], "steps": args.e2e_steps},
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "cg": rec["cg"],
+            "fp32_trace_rel_err_vs_fp64": {"max": max(r["trace_errs"]), "per_source": r["trace_errs"],
+                                           "at": "true coefficient, all steps"}}
+    del r
     torch.cuda.empty_cache()
+    if not args.no_secondary and args.workload != "inverse_129":
+        w2 = make_workload("inverse_129")
+        r2 = run_cg(H, w2, dev, 20, 3, 2)
+        rec2 = cg_record(r2, 20)
+        err = fp32_vs_fp64_gradient(H, w2, dev)
+        line["secondary"] = {
+            "workload": describe(w2) + " (the three field levels fit in the 126 MB L2: its roofline fraction is "
+                                       "bytes over time, not DRAM bandwidth)",
+            "value": rec2["value"], "lattice_updates_all_sweeps": rec2["all_sweeps"],
+            "ms_per_step": rec2["ms_per_step"], "gradients_per_s": rec2["gradients_per_s"],
+            "roofline_l2_resident": roofline(r2, peak, peak_kind, w2.name), "cg": rec2["cg"],
+            "fp32_vs_fp64": {"trace_rel_l2": max(r2["trace_errs"]), **err}}
+        del r2
+        torch.cuda.empty_cache()
     if args.serve_requests > 0:
         line["serving"] = run_serving(args, dev)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, el = oracle_sample(w, args.cpu_sample_steps)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "%d forward + %d adjoint steps of the 129^3 workload (%.1f s)"
-                                          % (args.cpu_sample_steps, args.cpu_sample_steps, el)}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

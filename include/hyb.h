@@ -85,7 +85,40 @@ typedef struct {
                           the voxel diagonal, at a new centre node.  Marked
                           voxels need every corner at least 2 nodes from the
                           outer faces. */
+  int64_t wait_cycles; /* limit, in SM clock cycles, of each bounded wait of
+                          the step kernels for their staged planes (0: the
+                          default, 2^29 cycles, about 0.25 s).  A wait that
+                          runs out makes the kernel stop and hyb_sync return
+                          HYB_ERR_TIMEOUT; the field is then undefined.
+                          HYB_WAIT_NONE (-1) gives up at the first wait that
+                          is not already complete (error-path testing). */
+  int32_t adjoint_mode; /* HYB_ADJ_EXACT: hyb_adjoint solves the exact
+                          transpose of the discrete forward (its gradient is
+                          the derivative of the discrete functional).
+                          HYB_ADJ_PAPER: the paper's adjoint scheme,
+                          Eq. (fdmschemeadjoint) and Eq. (fem) second line with
+                          d_n lambda = 0 on every face (Eq. (adjoint1)), the
+                          residual entering on S_T as the mirror ghost of
+                          d_n lambda = -(u - u~), and the gradient
+                          tau sum_k int grad u^k . grad lambda^k (Eq. (gradient1),
+                          same time index).  With reflecting faces the two
+                          agree; with absorbing faces they differ, because the
+                          paper drops the absorbing terms of Eq. (lagrangian1). */
+  int32_t fem_path;    /* HYB_FEM_STENCIL: the hybrid scheme; FEM rows on the
+                          FEM block, in the exactly equal stencil form of the
+                          Kuhn element matrices.  HYB_FEM_TET_ALL: pure FEM,
+                          every interior lattice node updated by Eq. (fem) with
+                          its row gathered element by element over the Kuhn
+                          tetrahedra of every voxel (the coefficient still
+                          given on the FEM block's unknown voxels, 1 elsewhere);
+                          the outer boundary rows stay FDM.  A checking path
+                          (slow, no refinement): on structured meshes the two
+                          paths agree (the schemes coincide, Sec. 1, Sec. 7). */
 } hyb_mesh_desc;
+
+#define HYB_WAIT_NONE (-1)
+enum { HYB_ADJ_EXACT = 0, HYB_ADJ_PAPER = 1 };
+enum { HYB_FEM_STENCIL = 0, HYB_FEM_TET_ALL = 1 };
 
 typedef struct {
   int64_t n_nodes;         /* lattice nodes */
@@ -101,16 +134,28 @@ typedef struct {
   int64_t launches;        /* kernels launched by this mesh so far */
   int64_t n_centres;       /* centre nodes of refined voxels */
   int64_t n_sparse_rows;   /* rows updated in sparse form (refined region) */
+  int64_t n_sparse_nnz;    /* off-diagonal entries of those rows */
 } hyb_mesh_info;
 
-/* Plane-wave source of Eq. (f): a Neumann flux d_n u = amp sin(omega t) on
-   `face` for t <= 2 pi / omega (the S_{1,1} part of Eq. (model2)); after that
-   the face takes the mesh's own condition.  The source face is also the
-   observation face S_T whose trace is recorded. */
+/* Plane-wave source of Eq. (f), p(s) = amp sin(omega s) for 0 <= s <= t1 =
+   2 pi / omega and 0 otherwise.
+   dir = (0, 0, 0): a face source, the Neumann flux d_n u = p(t) on `face`
+   while t <= t1 (the S_{1,1} part of Eq. (model2)); after that the face
+   takes the mesh's own condition.
+   dir != 0: the plane wave u = F(t - d.(x - x0)), F' = p, travelling along
+   d = dir / |dir| from the box corner x0 where d.x is smallest.  Every face
+   whose outward normal n has d.n < 0 carries the flux
+   d_n u = -(d.n) p(t - d.(x - x0)) until the pulse has crossed its farthest
+   node (t <= t1 + max over the face of d.(x - x0)), then takes the mesh's own
+   condition.  A face source is the case d = -n of its face.  (The paper
+   launches its wave from one face; oblique incidence is this library's
+   extension of Eq. (f).)
+   `face` is the observation face S_T whose trace is recorded. */
 typedef struct {
   int32_t face;
   double omega;
   double amp;
+  double dir[3];
 } hyb_source;
 
 /* Create a mesh: node classes, FEM block, device workspaces.  `stream` is a
@@ -122,7 +167,8 @@ hyb_status hyb_mesh_destroy(hyb_mesh* mesh);
 hyb_status hyb_set_stream(hyb_mesh* mesh, void* stream);
 
 /* Forward solve, Algorithm 2 forward in time from u^0 = u^{-1} = 0
-   (Model Problem 2), one independent problem per source, all sources
+   (Model Problem 2; or from the state set by hyb_set_initial, Model
+   Problem 1), one independent problem per source, all sources
    advanced by the same launches.
    a:      device double[n_unknown], the coefficient on the unknown voxels.
    src:    HOST array of n_src sources (1 <= n_src <= 16).
@@ -135,6 +181,17 @@ hyb_status hyb_set_stream(hyb_mesh* mesh, void* stream);
    a_max is reported by hyb_sync as HYB_ERR_CFL. */
 hyb_status hyb_forward(hyb_mesh* mesh, const double* a, const hyb_source* src, int32_t n_src,
                        int32_t nsteps, double dt, void* trace);
+
+/* Initial state of Model Problem 1 (Eq. (model1)): the forwards that follow
+   start from u^0 = u0 and u^{-1} = u_prev instead of zero (Model Problem 2).
+   u0, u_prev: device fields[n_nodes] of the mesh's precision (lattice nodes,
+   x fastest), the same state for every source; c0, c_prev: device
+   [n_centres] values on the centre nodes of refined voxels, in
+   unknown-voxel order (NULL: zero).  The mesh copies them.  u0 == NULL
+   returns to the zero state.  The gradient of a forward that started from
+   a nonzero state pairs u^0 as well (the k = 0 term of Eq. (gradient1)). */
+hyb_status hyb_set_initial(hyb_mesh* mesh, const void* u0, const void* u_prev, const void* c0,
+                           const void* c_prev);
 
 /* Exact discrete adjoint of the last hyb_forward, backward in time
    (the discrete counterpart of Eq. (adjoint1)): with c^k = dJ/d(trace row k)
@@ -177,15 +234,17 @@ typedef struct {
 
 typedef struct {
   double* d;         /* device double[n_unknown], previous direction (caller-owned) */
-  double gnorm2;     /* ||g^{m-1}||^2, 0 before the first iteration */
+  double gnorm2;     /* ||projected g^{m-1}||^2, 0 before the first iteration */
   double alpha;      /* previous step length, 0 before the first iteration */
+  double J;          /* F(a^{m-1}), unused before the first iteration */
   int32_t iter;      /* m, 0 before the first iteration */
 } hyb_cg_state;
 
 typedef struct {
   double J;          /* F(a^m) */
   double J_data;
-  double gnorm;      /* ||g^m||_{L2} over the unknown voxels */
+  double gnorm;      /* ||g^m||_{L2} over the unknown voxels (Step 3) */
+  double gpnorm;     /* ||projected g^m||_{L2} (the norm in beta) */
   double alpha;      /* step taken */
   double beta;       /* Fletcher-Reeves beta^m */
   double dJ0;        /* directional derivative along d^m */
@@ -193,12 +252,17 @@ typedef struct {
   double J_trial;
 } hyb_cg_report;
 
-/* One iteration of Algorithm 3: forward and adjoint at a^m (Step 1), the L2
-   gradient g^m = int grad u . grad lambda dt + gamma (a^m - a0), the
-   Fletcher-Reeves direction d^m = -g^m + beta^m d^{m-1} (Step 2; d^0 = -g^0,
-   reset to -g^m when d^m is not a descent direction), a step length from a
-   parabola through F(0), F'(0) and F at one trial step (the paper leaves this
-   rule open), and the update a^{m+1} = clip(a^m + alpha d^m, a_min, a_max).
+/* One iteration of Algorithm 3 on the admissible set [a_min, a_max]
+   (Eq. (admpar)): forward and adjoint at a^m (Step 1), the L2 gradient
+   g^m = int grad u . grad lambda dt + gamma (a^m - a0), the Fletcher-Reeves
+   direction d^m = -g^m + beta^m d^{m-1} (Step 2; d^0 = -g^0) of the projected
+   gradient (components zeroed on voxels at a bound whose gradient points out
+   of the set), with the components of d^m that would leave the set at once
+   dropped and a restart d^m = -g^m when d^m is not a descent direction; a
+   step length from a parabola through F(0), F'(0) and F at one trial step
+   (the paper leaves this rule open: the trial step is 0.5 / max|d^m| at the
+   first iteration and after a step that did not lower F, else the previous
+   step length); the update a^{m+1} = clip(a^m + alpha d^m, a_min, a_max).
    a: device double[n_unknown], updated in place.  u_obs: device field shaped
    like the trace.  state, report: host structs.  Synchronises the stream
    twice (for the line search). */
@@ -207,10 +271,13 @@ hyb_status hyb_cg_step(hyb_mesh* mesh, double* a, const void* u_obs, const hyb_s
                        hyb_cg_state* state, hyb_cg_report* report);
 
 /* Copy a field of source `isrc` (HYB_FIELD_*: u^N or u^{N-1} of the last
-   forward, lambda^1 of the last adjoint) into `out` (device field[n_nodes],
-   x fastest; lattice nodes only).  The adjoint is kept in the mass-scaled
-   form lambda_i h^3 / M^L_i on FEM-owned rows, which equals lambda except at
-   corners of refined voxels. */
+   forward, the earliest adjoint level of the last adjoint) into `out`
+   (device field[n_nodes], x fastest; lattice nodes only).  HYB_ADJ_EXACT:
+   lambda^1, kept in the mass-scaled form lambda_i h^3 / M^L_i on FEM-owned
+   rows, which equals lambda except at corners of refined voxels.
+   HYB_ADJ_PAPER: lambda^0 of the paper's scheme.  On a checkpointing mesh the
+   adjoint recomputes its segments in the forward's levels, so u^N and
+   u^{N-1} are read before hyb_adjoint (HYB_ERR_STATE after it). */
 hyb_status hyb_get_field(hyb_mesh* mesh, int32_t which, int32_t isrc, void* out);
 
 /* Allocation-free data misfit.  The paper has no counterpart: this exists
@@ -236,7 +303,9 @@ hyb_status hyb_misfit_noalloc(const void* trace, const void* u_obs, int32_t prec
                               int32_t nsteps, int32_t obs_stride, const int32_t* face_dims, double dt,
                               double h, int32_t weights, double* J_dev, void* cotangent, void* stream);
 
-/* Wait for the mesh's stream, then report any device-side error flag. */
+/* Wait for the mesh's stream, then report any device-side error flag:
+   HYB_ERR_CFL for a coefficient above a_max (or not finite), HYB_ERR_TIMEOUT
+   when a bounded wait of a step kernel ran out.  The flags are cleared. */
 hyb_status hyb_sync(hyb_mesh* mesh);
 
 /* Message of the calling thread's last failure ("" if none). */

@@ -28,7 +28,9 @@ def nvcc_path() -> str:
 
 
 def common_flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # host code: no fused multiply-adds, so that host-side time arithmetic
+    # (source switch instants) rounds the same on every host architecture
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                    "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 
 

@@ -45,8 +45,8 @@ struct SweepKey {
   int nsteps = 0, nsrc = 0;
   double dt = 0.0;
   int face[16] = {0};
-  double omega[16] = {0.0}, amp[16] = {0.0};
-  const void* bufs[8] = {nullptr};
+  double omega[16] = {0.0}, amp[16] = {0.0}, dir[16][3] = {};
+  const void* bufs[10] = {nullptr};
 };
 
 bool same_key(const SweepKey& a, const SweepKey& b) {
@@ -54,8 +54,10 @@ bool same_key(const SweepKey& a, const SweepKey& b) {
       a.nsrc != b.nsrc || a.dt != b.dt)
     return false;
   for (int i = 0; i < a.nsrc; ++i)
-    if (a.face[i] != b.face[i] || a.omega[i] != b.omega[i] || a.amp[i] != b.amp[i]) return false;
-  for (int i = 0; i < 8; ++i)
+    if (a.face[i] != b.face[i] || a.omega[i] != b.omega[i] || a.amp[i] != b.amp[i] || a.dir[i][0] != b.dir[i][0] ||
+        a.dir[i][1] != b.dir[i][1] || a.dir[i][2] != b.dir[i][2])
+      return false;
+  for (int i = 0; i < 10; ++i)
     if (a.bufs[i] != b.bufs[i]) return false;
   return true;
 }
@@ -91,6 +93,7 @@ struct hyb_mesh {
   bool have_fwd = false;    // the adjoint has what it needs
   bool have_run = false;    // a forward has run (time grid known)
   bool have_adj = false;
+  bool u_levels = false;    // U still holds the last forward's final levels
   int nsteps = 0, nsrc = 0;
   double dt = 0.0;
   hyb_source src[kMaxSlots];
@@ -101,6 +104,9 @@ struct hyb_mesh {
   double dt_max = 0.0;
   DevBuf rrow, rptr, rcol, rval, cptr, cunk, cw, rmask, rzr, refvox, refvox_id, k9;
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
+  DevBuf I0, IC0;               // initial state of Model Problem 1: u^0, u^{-1} (padded fields), centres
+  DevBuf acopy, kuhn, kuhn_v;   // all-FEM path: coefficient of the last forward, Kuhn element tables
+  bool have_init = false;
   cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
   // interior work items of the forward / transposed step per slot count; built
   // once and kept (captured sweep graphs refer to them)
@@ -175,9 +181,11 @@ SweepKey make_key(const hyb_mesh* m, int kind, const void* io, int accumulate, i
     k.face[i] = src[i].face;
     k.omega[i] = src[i].omega;
     k.amp[i] = src[i].amp;
+    for (int a = 0; a < 3; ++a) k.dir[i][a] = src[i].dir[a];
   }
-  const void* b[8] = {m->U.p, m->L.p, m->hist.p, m->ckpt.p, m->G.p, m->W.p, m->CU.p, m->CL.p};
-  for (int i = 0; i < 8; ++i) k.bufs[i] = b[i];
+  const void* b[10] = {m->U.p, m->L.p, m->hist.p, m->ckpt.p, m->G.p, m->W.p, m->CU.p, m->CL.p,
+                       m->have_init ? m->I0.p : nullptr, m->have_init ? m->IC0.p : nullptr};
+  for (int i = 0; i < 10; ++i) k.bufs[i] = b[i];
   return k;
 }
 
@@ -230,29 +238,79 @@ hyb_status run_sweep(hyb_mesh* m, SweepGraph& g, const SweepKey& key, Body body)
   return HYB_OK;
 }
 
-// Boundary state of the step leaving t_k = k dt for one source: the source
-// face carries the Neumann flux p(t_k) = amp sin(omega t_k) while
-// t_k <= 2 pi / omega (Eq. (f), Model Problem 2) and otherwise takes the
-// mesh's own condition.
-void phase_of(const hyb_mesh* m, const hyb_source& s, int k, double dt, int* mask, int* srcf,
-              double* p) {
-  const double t = k * dt;
-  if (t <= 2.0 * M_PI / s.omega) {
-    *mask = m->abc_mask & ~(1 << s.face);
-    *srcf = s.face;
-    *p = s.amp * std::sin(s.omega * t);
-  } else {
-    *mask = m->abc_mask;
-    *srcf = -1;
-    *p = 0.0;
+// Plane wave launched by a source (Eq. (f) at normal or oblique incidence):
+// unit direction d (d = -n of the face for a face source), entry corner i0
+// (the box corner where d . x is smallest), the factor -(d . n_f) of the flux
+// on each entry face (0 on the others) and the last instant each entry face
+// carries it: t1 plus the largest delay d . (x - x0) over the face.
+struct Wave {
+  double d[3];
+  int i0[3];
+  double fac[6];
+  double tsw[6];
+};
+
+Wave wave_of(const hyb_mesh* m, const hyb_source& s) {
+  Wave w;
+  double d[3] = {s.dir[0], s.dir[1], s.dir[2]};
+  if (d[0] == 0.0 && d[1] == 0.0 && d[2] == 0.0) {
+    const int ax = s.face >> 1;
+    d[ax] = (s.face & 1) ? -1.0 : 1.0;
   }
+  const double nrm = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  for (int a = 0; a < 3; ++a) {
+    w.d[a] = d[a] / nrm;
+    w.i0[a] = w.d[a] >= 0.0 ? 0 : m->n[a] - 1;
+  }
+  const double t1 = 2.0 * M_PI / s.omega;
+  for (int f = 0; f < 6; ++f) {
+    const int ax = f >> 1;
+    const double dn = w.d[ax] * ((f & 1) ? 1.0 : -1.0);
+    w.fac[f] = dn < 0.0 ? -dn : 0.0;
+    const int p = ax == 0 ? 1 : 0, q = ax == 2 ? 1 : 2;
+    w.tsw[f] = t1 + m->d.h * (std::fabs(w.d[p]) * (m->n[p] - 1) + std::fabs(w.d[q]) * (m->n[q] - 1));
+  }
+  return w;
+}
+
+// Boundary state of the step leaving t_k = k dt for one source: an entry
+// face carries the plane-wave flux while t_k <= its switch time (Model
+// Problem 2: S_{1,1}, then S_{1,2}) and otherwise takes the mesh's own
+// condition.  mask: absorbing faces; srcmask: faces carrying the flux.
+void phase_of(const hyb_mesh* m, const hyb_source& s, int k, double dt, int* mask, int* srcmask) {
+  const Wave w = wave_of(m, s);
+  const double t = k * dt;
+  int sm = 0;
+  for (int f = 0; f < 6; ++f)
+    if (w.fac[f] > 0.0 && t <= w.tsw[f]) sm |= 1 << f;
+  *srcmask = sm;
+  *mask = m->abc_mask & ~sm;
 }
 
 int mask_at(const hyb_mesh* m, const hyb_source& s, int k, double dt) {
-  int mask, f;
-  double p;
-  phase_of(m, s, k, dt, &mask, &f, &p);
+  int mask, sm;
+  phase_of(m, s, k, dt, &mask, &sm);
   return mask;
+}
+
+// The slot's plane-wave constants for the step leaving t_k.
+template <typename T>
+void set_wave(const hyb_mesh* m, Slot<T>& S, const hyb_source& src, int k, double dt) {
+  const Wave w = wave_of(m, src);
+  int mask, sm;
+  phase_of(m, src, k, dt, &mask, &sm);
+  S.mask_f = mask;
+  S.src_mask = sm;
+  S.st = k * dt;
+  const double h = m->d.h;
+  for (int f = 0; f < 6; ++f) S.sf[f] = dt * dt * 2.0 / h * src.amp * w.fac[f];
+  for (int a = 0; a < 3; ++a) {
+    S.sd[a] = w.d[a];
+    S.si0[a] = w.i0[a];
+  }
+  S.sh = h;
+  S.somega = src.omega;
+  S.st1 = 2.0 * M_PI / src.omega;
 }
 
 // Launch geometry of one step: the interior covers nodes 1 .. n-2 on every
@@ -327,8 +385,12 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
       }
     }
   }
-  // costliest first: with more items than resident blocks they start early
-  std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  // by source, and costliest first within a source: the items of one source
+  // run together, so that neighbouring tiles share their halo rows in L2,
+  // and the long ones start early
+  std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) {
+    return a.second[0] != b.second[0] ? a.second[0] < b.second[0] : a.first > b.first;
+  });
   std::vector<int> out;
   out.reserve(items.size() * 4);
   for (const auto& it : items) out.insert(out.end(), it.second.begin(), it.second.end());
@@ -417,6 +479,34 @@ template <typename V>
 hyb_status upload(hyb_mesh* m, DevBuf& b, const std::vector<V>& host) {
   HYB_TRY(ensure(m, b, host.size() * sizeof(V)));
   if (!host.empty()) HYB_CU(cudaMemcpy(b.p, host.data(), host.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return HYB_OK;
+}
+
+// Element tables of the all-FEM path: the six Kuhn tetrahedra of the unit
+// voxel (corner ids a + 2b + 4c; each the path 0 -> e_p -> e_p + e_q -> (1,1,1))
+// with their P1 stiffness at a = 1 and volumes, from the generic element
+// formula.
+hyb_status build_kuhn(hyb_mesh* m) {
+  std::vector<double> tab(6 * 16 + 6);
+  std::vector<int> verts(6 * 4);
+  const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (int t = 0; t < 6; ++t) {
+    const int v1 = 1 << perms[t][0], v2 = v1 | (1 << perms[t][1]);
+    const int v[4] = {0, v1, v2, 7};
+    double X[4][3], vol, K[4][4];
+    for (int q = 0; q < 4; ++q) {
+      verts[4 * t + q] = v[q];
+      X[q][0] = v[q] & 1;
+      X[q][1] = (v[q] >> 1) & 1;
+      X[q][2] = v[q] >> 2;
+    }
+    p1_tet(X, &vol, K);
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) tab[16 * t + 4 * a + b] = K[a][b];
+    tab[96 + t] = vol;
+  }
+  HYB_TRY(upload(m, m->kuhn, tab));
+  HYB_TRY(upload(m, m->kuhn_v, verts));
   return HYB_OK;
 }
 
@@ -660,13 +750,21 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.hx0 = m->hx0;
   A.hpx = m->hpx;
   A.err = (int*)m->flag.p + 1;
+  A.wait = m->d.wait_cycles == 0 ? (1LL << 29) : (m->d.wait_cycles < 0 ? -1LL : (long long)m->d.wait_cycles);
   A.W = (const T*)m->W.p;
   A.G = (double*)m->G.p;
   const double h = m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
-  A.cd = (T)(2.0 - 6.0 * (dt * dt / (h * h)));
   A.r = (T)((h - dt) / (h + dt));
   step_geometry(m, &A.npb, &A.ntx, &A.small, &A.nedge);
+  if (m->d.fem_path == HYB_FEM_TET_ALL) {  // every level by the all-node kernels
+    A.tet = 1;
+    A.small = 1;
+    A.nedge = 0;
+    A.acoef = (const double*)m->acopy.p;
+    A.kuhn = (const double*)m->kuhn.p;
+    A.kuhn_v = (const int*)m->kuhn_v.p;
+  }
   A.nslots = nslots;
   A.nlat = m->Np;
   if (m->nc > 0) {
@@ -716,19 +814,37 @@ void forward_slots(const hyb_mesh* m, StepArgs<T>& A, const hyb_source* src, int
     S.cnext = centre_buf<T>(m, m->CU, nsrc, s, k + 1);
     S.chist_w = (hist_level && m->nc) ? chist_level + (size_t)s * m->nc : nullptr;
     S.chist_r = nullptr;
-    int mask, f;
-    double p;
-    phase_of(m, src[s], k, dt, &mask, &f, &p);
-    S.mask_f = mask;
+    set_wave<T>(m, S, src[s], k, dt);
     S.mask_e = 0;
     S.mask_c = 0;
-    S.src_face = f;
     S.zf_cur = (int)((S.cur - (const T*)m->U.p) / ((long long)m->px * m->n[1]));
     S.zf_prev = (int)((S.prev - (const T*)m->U.p) / ((long long)m->px * m->n[1]));
     S.zf_hist = 0;
-    S.srcval = (T)(dt * dt * 2.0 * p / m->d.h);
     S.obs_face = src[s].face;
   }
+}
+
+// Levels 0 and -1 of one source (lattice field and centre values): the
+// initial state of Model Problem 1 if one was set, else zero.
+template <typename T>
+hyb_status initial_levels(hyb_mesh* m, T* u0, T* um, T* c0, T* cm, cudaStream_t st) {
+  const size_t fb = (size_t)m->Np * sizeof(T), cb = (size_t)m->nc * sizeof(T);
+  if (m->have_init) {
+    HYB_CU(cudaMemcpyAsync(u0, m->I0.p, fb, cudaMemcpyDeviceToDevice, st));
+    HYB_CU(cudaMemcpyAsync(um, (const char*)m->I0.p + fb, fb, cudaMemcpyDeviceToDevice, st));
+    if (m->nc) {
+      HYB_CU(cudaMemcpyAsync(c0, m->IC0.p, cb, cudaMemcpyDeviceToDevice, st));
+      HYB_CU(cudaMemcpyAsync(cm, (const char*)m->IC0.p + cb, cb, cudaMemcpyDeviceToDevice, st));
+    }
+    return HYB_OK;
+  }
+  HYB_CU(cudaMemsetAsync(u0, 0, fb, st));
+  HYB_CU(cudaMemsetAsync(um, 0, fb, st));
+  if (m->nc) {
+    HYB_CU(cudaMemsetAsync(c0, 0, cb, st));
+    HYB_CU(cudaMemsetAsync(cm, 0, cb, st));
+  }
+  return HYB_OK;
 }
 
 template <typename T>
@@ -740,6 +856,7 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
   const size_t cb = (size_t)m->nc * sizeof(T);  // centre values of one level
   HYB_TRY(ensure(m, m->U, 3 * (size_t)nsrc * fb));
   HYB_TRY(ensure(m, m->CU, 3 * (size_t)nsrc * cb));
+  if (m->d.fem_path == HYB_FEM_TET_ALL) HYB_TRY(ensure(m, m->acopy, (size_t)std::max(m->nu, 1LL) * sizeof(double)));
   if (keep && m->nown > 0) {
     if (!ckpt) {
       HYB_TRY(ensure(m, m->hist, (size_t)nsteps * nsrc * m->hbox * sizeof(T)));
@@ -760,26 +877,41 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
     launch_set_coef<T>(A, (T*)m->W.p, a, m->d.a_max, (int*)m->flag.p, m->st);
     HYB_LAUNCHED(m);
   }
+  if (A.tet && m->nu > 0)  // the all-FEM rows read a itself
+    HYB_CU(cudaMemcpyAsync(m->acopy.p, a, (size_t)m->nu * sizeof(double), cudaMemcpyDeviceToDevice, m->st));
   if (m->nc > 0) {
     launch_set_sparse<T>((const int*)m->cptr.p, (const int*)m->cunk.p, (const double*)m->cw.p, a, (T*)m->rval.p,
                          m->nnz, m->st);
     HYB_LAUNCHED(m);
   }
   auto body = [&](cudaStream_t st) -> hyb_status {
-    for (int s = 0; s < nsrc; ++s) {
-      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, 0), 0, fb, st));
-      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->U, nsrc, s, -1), 0, fb, st));
-      if (m->nc) {
-        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CU, nsrc, s, 0), 0, cb, st));
-        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CU, nsrc, s, -1), 0, cb, st));
-      }
+    for (int s = 0; s < nsrc; ++s)
+      HYB_TRY(initial_levels<T>(m, field_buf<T>(m, m->U, nsrc, s, 0), field_buf<T>(m, m->U, nsrc, s, -1),
+                                centre_buf<T>(m, m->CU, nsrc, s, 0), centre_buf<T>(m, m->CU, nsrc, s, -1), st));
+    if (trace) {
+      HYB_CU(cudaMemsetAsync(trace, 0, (size_t)nsrc * (nsteps + 1) * m->obs_stride * sizeof(T), st));
+      if (m->have_init)  // row 0 of every source: u^0 on its face
+        for (int s = 0; s < nsrc; ++s) {
+          launch_extract_face<T>(A, field_buf<T>(m, m->U, nsrc, s, 0), src[s].face,
+                                 trace + (size_t)s * (nsteps + 1) * m->obs_stride, st);
+          HYB_LAUNCHED(m);
+        }
     }
-    if (trace) HYB_CU(cudaMemsetAsync(trace, 0, (size_t)nsrc * (nsteps + 1) * m->obs_stride * sizeof(T), st));
     T* hist = (T*)m->hist.p;
     T* chist = (T*)m->chist.p;
     if (keep && !ckpt && m->nown > 0) {
-      HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->hbox * sizeof(T), st));
-      if (m->nc) HYB_CU(cudaMemsetAsync(chist, 0, (size_t)nsrc * cb, st));
+      if (m->have_init) {
+        for (int s = 0; s < nsrc; ++s) {
+          launch_extract_owned<T>(A, field_buf<T>(m, m->U, nsrc, s, 0), hist + (size_t)s * m->hbox, st);
+          HYB_LAUNCHED(m);
+          if (m->nc)
+            HYB_CU(cudaMemcpyAsync(chist + (size_t)s * m->nc, centre_buf<T>(m, m->CU, nsrc, s, 0), cb,
+                                   cudaMemcpyDeviceToDevice, st));
+        }
+      } else {
+        HYB_CU(cudaMemsetAsync(hist, 0, (size_t)nsrc * m->hbox * sizeof(T), st));
+        if (m->nc) HYB_CU(cudaMemsetAsync(chist, 0, (size_t)nsrc * cb, st));
+      }
     }
     const size_t lvl = (size_t)nsrc * m->hbox;
     const size_t clvl = (size_t)nsrc * m->nc;
@@ -815,6 +947,7 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
   m->have_run = true;
   m->have_fwd = keep;
   m->have_adj = false;
+  m->u_levels = true;
   return HYB_OK;
 }
 
@@ -836,8 +969,7 @@ void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const
     S.cnext = centre_buf<T>(m, m->CL, nsrc, s, j);
     S.chist_w = nullptr;
     S.chist_r = (hist_level && m->nc) ? chist_level + (size_t)s * m->nc : nullptr;
-    S.srcval = T(0);
-    S.src_face = -1;
+    S.src_mask = 0;
     S.zf_cur = (int)((S.cur - (const T*)m->L.p) / ((long long)m->px * m->n[1]));
     S.zf_prev = (int)((S.prev - (const T*)m->L.p) / ((long long)m->px * m->n[1]));
     S.zf_hist = S.hist_r ? (int)((S.hist_r - (const T*)m->hist.p) / ((long long)m->hpx * m->fn[1])) : 0;
@@ -846,6 +978,51 @@ void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const
     S.mask_c = mask_at(m, m->src[s], j + 1, m->dt);
     S.obs_face = m->src[s].face;
   }
+}
+
+// Slots of the paper's adjoint step j: lambda^{j-1} from lambda^j (cur) and
+// lambda^{j+1} (prev) by the forward rows with every face reflecting, the
+// cotangent row j entering on the observation face (Eq. (fdmschemeadjoint));
+// hist_level (u^j) is for the same-index pairing.
+template <typename T>
+void paper_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const T* hist_level,
+                 const T* chist_level) {
+  const int nsrc = m->nsrc, nsteps = m->nsteps;
+  const double h = m->d.h;
+  for (int s = 0; s < nsrc; ++s) {
+    Slot<T>& S = A.s[s];
+    S = Slot<T>();
+    S.cur = field_buf<T>(m, m->L, nsrc, s, j);
+    S.prev = field_buf<T>(m, m->L, nsrc, s, j + 1);
+    S.next = field_buf<T>(m, m->L, nsrc, s, j - 1);
+    S.hist_r = hist_level ? hist_level + (size_t)s * m->hbox : nullptr;
+    S.ccur = centre_buf<T>(m, m->CL, nsrc, s, j);
+    S.cprev = centre_buf<T>(m, m->CL, nsrc, s, j + 1);
+    S.cnext = centre_buf<T>(m, m->CL, nsrc, s, j - 1);
+    S.chist_r = (hist_level && m->nc) ? chist_level + (size_t)s * m->nc : nullptr;
+    S.zf_cur = (int)((S.cur - (const T*)m->L.p) / ((long long)m->px * m->n[1]));
+    S.zf_prev = (int)((S.prev - (const T*)m->L.p) / ((long long)m->px * m->n[1]));
+    S.obs_face = m->src[s].face;
+    S.inj = cot ? cot + ((size_t)s * (nsteps + 1) + j) * (size_t)m->obs_stride : nullptr;
+    S.inj_scale = (T)(-m->dt / (h * h * h));
+  }
+}
+
+// Same-index pairing of the paper's adjoint, G_s += pairing of (u^j, lambda^j)
+// for the slots set up by paper_slots (structured and refined voxels).
+template <typename T>
+hyb_status paper_pair(hyb_mesh* m, StepArgs<T>& A, cudaStream_t st) {
+  for (int s = 0; s < m->nsrc; ++s) {
+    StepArgs<T> B = A;
+    B.G = (double*)m->G.p + (size_t)s * m->nu;
+    launch_pair<T>(B, A.s[s].hist_r, A.s[s].cur, st);
+    HYB_LAUNCHED(m);
+  }
+  if (m->nc > 0) {
+    launch_refined_pair<T>(A, st);
+    HYB_LAUNCHED(m);
+  }
+  return HYB_OK;
 }
 
 // Gradient pairing of level 0: (u^0, lambda^1) on every unknown voxel.
@@ -885,14 +1062,22 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   HYB_TRY(step_maps<T>(m, F, m->U, nsrc, 0));
   HYB_TRY(step_items<T>(m, A, nsrc, true));
   HYB_TRY(step_items<T>(m, F, nsrc, false));
+  const bool paper = m->d.adjoint_mode == HYB_ADJ_PAPER;
+  StepArgs<T> Pp;  // paper-mode steps: forward rows on lambda
+  if (paper) {
+    base_args(m, Pp, dt, nsrc);
+    HYB_TRY(step_maps<T>(m, Pp, m->L, nsrc, 0));
+    HYB_TRY(step_items<T>(m, Pp, nsrc, false));
+  }
   auto body = [&](cudaStream_t st) -> hyb_status {
     if (!accumulate) HYB_CU(cudaMemsetAsync(m->G.p, 0, (size_t)nsrc * m->nu * sizeof(double), st));
+    const int z0 = paper ? nsteps : nsteps + 1;  // the two levels that start at zero
     for (int s = 0; s < nsrc; ++s) {
-      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, nsteps + 1), 0, fb, st));
-      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, nsteps + 2), 0, fb, st));
+      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, z0), 0, fb, st));
+      HYB_CU(cudaMemsetAsync(field_buf<T>(m, m->L, nsrc, s, z0 + 1), 0, fb, st));
       if (m->nc) {
-        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CL, nsrc, s, nsteps + 1), 0, cb, st));
-        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CL, nsrc, s, nsteps + 2), 0, cb, st));
+        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CL, nsrc, s, z0), 0, cb, st));
+        HYB_CU(cudaMemsetAsync(centre_buf<T>(m, m->CL, nsrc, s, z0 + 1), 0, cb, st));
       }
     }
     T* hist = (T*)m->hist.p;
@@ -901,8 +1086,18 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
     const size_t clvl = (size_t)nsrc * m->nc;
     const bool pairing = m->nu > 0 && m->nown > 0;
     auto adj_step = [&](int j, const T* hl, const T* chl) -> hyb_status {
+      if (paper) {  // pair (u^j, lambda^j), then lambda^{j-1}
+        paper_slots<T>(m, Pp, cot, j, hl, chl);
+        if (hl) HYB_TRY(paper_pair<T>(m, Pp, st));
+        return step_launch(m, st, [&](cudaStream_t q) { launch_forward_step<T>(Pp, q); });
+      }
       adjoint_slots<T>(m, A, cot, j, hl, chl);
       return step_launch(m, st, [&](cudaStream_t q) { launch_adjoint_step<T>(A, q); });
+    };
+    auto first_pair = [&]() -> hyb_status {
+      if (!paper) return pair_first<T>(m, A, hist, chist, st);
+      paper_slots<T>(m, Pp, nullptr, 0, hist, chist);  // (u^0, lambda^0)
+      return paper_pair<T>(m, Pp, st);
     };
     auto fwd_step = [&](int k, T* hl, T* chl) -> hyb_status {
       forward_slots<T>(m, F, m->src, nsrc, nsteps, dt, k, nullptr, hl, chl);
@@ -913,7 +1108,7 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
         const bool pj = pairing && j <= nsteps - 1;
         HYB_TRY(adj_step(j, pj ? hist + (size_t)j * lvl : nullptr, pj ? chist + (size_t)j * clvl : nullptr));
       }
-      if (pairing) HYB_TRY(pair_first<T>(m, A, hist, chist, st));
+      if (pairing) HYB_TRY(first_pair());
       return HYB_OK;
     }
     HYB_TRY(adj_step(nsteps, nullptr, nullptr));
@@ -928,12 +1123,7 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
           T* c0 = centre_buf<T>(m, m->CU, nsrc, s, kb);
           T* cm = centre_buf<T>(m, m->CU, nsrc, s, kb - 1);
           if (seg == 0) {
-            HYB_CU(cudaMemsetAsync(u0, 0, fb, st));
-            HYB_CU(cudaMemsetAsync(um, 0, fb, st));
-            if (m->nc) {
-              HYB_CU(cudaMemsetAsync(c0, 0, cb, st));
-              HYB_CU(cudaMemsetAsync(cm, 0, cb, st));
-            }
+            HYB_TRY(initial_levels<T>(m, u0, um, c0, cm, st));
           } else {
             const char* base = (const char*)m->ckpt.p + (((size_t)seg * nsrc + s) * 2) * fb;
             HYB_CU(cudaMemcpyAsync(u0, base, fb, cudaMemcpyDeviceToDevice, st));
@@ -955,12 +1145,23 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
         HYB_TRY(adj_step(j, pairing ? hist + (size_t)(j - kb) * lvl : nullptr,
                          pairing ? chist + (size_t)(j - kb) * clvl : nullptr));
     }
-    if (pairing) HYB_TRY(pair_first<T>(m, A, hist, chist, st));
+    if (pairing) HYB_TRY(first_pair());
     return HYB_OK;
   };
   HYB_TRY(run_sweep(m, m->graphs[2], make_key(m, 2, cot, accumulate, nsteps, nsrc, dt, m->src), body));
   m->have_adj = true;
+  if (ckpt) m->u_levels = false;  // the recomputed segments reused the forward's levels
   return HYB_OK;
+}
+
+// Factor from the accumulated pairing sums (kGradPairScale / h times
+// u^T K_c lambda per voxel) to dJ/da: exact adjoint, dJ/da_c =
+// -tau^2 u^T K_c (lambda~ / h^3) summed over steps; paper mode,
+// g_c = tau u^T K_c lambda summed over steps.
+double grad_scale(const hyb_mesh* m) {
+  const double h = m->d.h, dt = m->dt;
+  if (m->d.adjoint_mode == HYB_ADJ_PAPER) return dt * h / kGradPairScale;
+  return -dt * dt / (h * h) / kGradPairScale;
 }
 
 template <typename T>
@@ -1013,7 +1214,7 @@ hyb_status cg_impl(hyb_mesh* m, double* a, const T* obs, const hyb_source* src, 
   HYB_TRY(ensure(m, m->cot, tb));
   HYB_TRY(ensure(m, m->g, (size_t)nu * sizeof(double)));
   HYB_TRY(ensure(m, m->atrial, (size_t)nu * sizeof(double)));
-  HYB_TRY(ensure(m, m->part, 2 * (size_t)kReduceBlocks * sizeof(double)));
+  HYB_TRY(ensure(m, m->part, kCgParts * (size_t)kReduceBlocks * sizeof(double)));
   HYB_TRY(ensure(m, m->scal, 16 * sizeof(double)));
   double* part = (double*)m->part.p;
   double* scal = (double*)m->scal.p;
@@ -1024,22 +1225,22 @@ hyb_status cg_impl(hyb_mesh* m, double* a, const T* obs, const hyb_source* src, 
   double Jd = 0.0;
   HYB_TRY(misfit_impl<T>(m, tr, obs, P->weights, &Jd, (T*)m->cot.p));
   HYB_TRY(adjoint_impl<T>(m, (const T*)m->cot.p, 0));
-  launch_grad_finalize((const double*)m->G.p, nsrc, a, -dt * dt / (m->d.h * m->d.h) / kGradPairScale, P->gamma, vol, P->a0,
-                       g, nu, m->st);
+  launch_grad_finalize((const double*)m->G.p, nsrc, a, grad_scale(m), P->gamma, vol, P->a0, g, nu, m->st);
   HYB_LAUNCHED(m);
-  launch_cg_norms(g, a, P->a0, nu, part, m->st);
+  launch_cg_norms(g, a, P->a0, P->a_min, P->a_max, nu, part, m->st);
   HYB_LAUNCHED(m);
-  launch_sum(part, kReduceBlocks, scal + 0, m->st);
-  HYB_LAUNCHED(m);
-  launch_sum(part + kReduceBlocks, kReduceBlocks, scal + 1, m->st);
-  HYB_LAUNCHED(m);
-  HYB_CU(cudaMemcpyAsync(m->hscal, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, m->st));
+  for (int q = 0; q < kCgParts; ++q) {
+    launch_sum(part + q * kReduceBlocks, kReduceBlocks, scal + 5 + q, m->st);
+    HYB_LAUNCHED(m);
+  }
+  HYB_CU(cudaMemcpyAsync(m->hscal + 5, scal + 5, kCgParts * sizeof(double), cudaMemcpyDeviceToHost, m->st));
   HYB_CU(cudaStreamSynchronize(m->st));
-  const double gn2 = m->hscal[0] / vol;  // ||g||_L2^2 with g = (dF/da) / |c|
-  const double J0 = Jd + 0.5 * P->gamma * vol * m->hscal[1];
-  // Step 2: Fletcher-Reeves direction.
-  double beta = (S->iter > 0 && S->gnorm2 > 0.0) ? gn2 / S->gnorm2 : 0.0;
-  launch_cg_direction(g, vol, beta, S->d, nu, m->st);
+  const double gn2 = m->hscal[5] / vol;   // ||g||_L2^2 with g = (dF/da) / |c|
+  const double gpn2 = m->hscal[7] / vol;  // the same for the projected gradient
+  const double J0 = Jd + 0.5 * P->gamma * vol * m->hscal[6];
+  // Step 2: Fletcher-Reeves direction of the projected gradient.
+  double beta = (S->iter > 0 && S->gnorm2 > 0.0) ? gpn2 / S->gnorm2 : 0.0;
+  launch_cg_direction(g, a, P->a_min, P->a_max, vol, beta, S->d, nu, m->st);
   HYB_LAUNCHED(m);
   auto dir_stats = [&](double* dJ0, double* dmax) -> hyb_status {
     launch_cg_dir_stats(g, S->d, nu, part, m->st);
@@ -1056,15 +1257,16 @@ hyb_status cg_impl(hyb_mesh* m, double* a, const T* obs, const hyb_source* src, 
   };
   double dJ0 = 0.0, dmax = 0.0;
   HYB_TRY(dir_stats(&dJ0, &dmax));
-  if (dJ0 >= 0.0) {
+  if (dJ0 >= 0.0) {  // not a descent direction: restart
     beta = 0.0;
-    launch_cg_direction(g, vol, 0.0, S->d, nu, m->st);
+    launch_cg_direction(g, a, P->a_min, P->a_max, vol, 0.0, S->d, nu, m->st);
     HYB_LAUNCHED(m);
     HYB_TRY(dir_stats(&dJ0, &dmax));
-    dJ0 = -gn2;
   }
-  // Step length: parabola through F(0), F'(0) and a trial F(alpha_t).
-  const double at = S->alpha > 0.0 ? S->alpha : 0.5 / std::max(dmax, 1e-300);
+  // Step length: parabola through F(0), F'(0) and a trial F(alpha_t); the
+  // trial is the previous step unless that step did not lower F.
+  const bool reseed = S->iter == 0 || !(S->alpha > 0.0) || !(J0 < S->J);
+  const double at = reseed ? 0.5 / std::max(dmax, 1e-300) : S->alpha;
   double* atr = (double*)m->atrial.p;
   launch_cg_axpy_clip(a, S->d, at, P->a_min, P->a_max, P->a0, atr, nu, part, m->st);
   HYB_LAUNCHED(m);
@@ -1079,13 +1281,15 @@ hyb_status cg_impl(hyb_mesh* m, double* a, const T* obs, const hyb_source* src, 
   const double alpha = quadratic_step(J0, dJ0, at, Jt);
   launch_cg_axpy_clip(a, S->d, alpha, P->a_min, P->a_max, P->a0, a, nu, part, m->st);
   HYB_LAUNCHED(m);
-  S->gnorm2 = gn2;
+  S->gnorm2 = gpn2;
   S->alpha = alpha;
+  S->J = J0;
   S->iter += 1;
   if (R) {
     R->J = J0;
     R->J_data = Jd;
     R->gnorm = std::sqrt(gn2);
+    R->gpnorm = std::sqrt(gpn2);
     R->alpha = alpha;
     R->beta = beta;
     R->dJ0 = dJ0;
@@ -1101,6 +1305,8 @@ hyb_status check_sources(const hyb_mesh* m, const hyb_source* src, int nsrc) {
   for (int s = 0; s < nsrc; ++s) {
     if (src[s].face < 0 || src[s].face > 5) return fail(HYB_ERR_ARG, "source %d: bad face %d", s, src[s].face);
     if (!(src[s].omega > 0.0)) return fail(HYB_ERR_ARG, "source %d: omega must be > 0", s);
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(src[s].dir[a])) return fail(HYB_ERR_ARG, "source %d: direction is not finite", s);
   }
   (void)m;
   return HYB_OK;
@@ -1130,6 +1336,11 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   if (!(d->h > 0.0)) return fail(HYB_ERR_ARG, "h must be > 0");
   if (d->precision != HYB_FP64 && d->precision != HYB_FP32) return fail(HYB_ERR_ARG, "bad precision");
   if (d->ckpt_every < 0) return fail(HYB_ERR_ARG, "ckpt_every must be >= 0");
+  if (d->wait_cycles < HYB_WAIT_NONE) return fail(HYB_ERR_ARG, "wait_cycles must be >= 0 or HYB_WAIT_NONE");
+  if (d->adjoint_mode != HYB_ADJ_EXACT && d->adjoint_mode != HYB_ADJ_PAPER) return fail(HYB_ERR_ARG, "bad adjoint_mode");
+  if (d->fem_path != HYB_FEM_STENCIL && d->fem_path != HYB_FEM_TET_ALL) return fail(HYB_ERR_ARG, "bad fem_path");
+  if (d->fem_path == HYB_FEM_TET_ALL && d->refine_mask)
+    return fail(HYB_ERR_ARG, "fem_path HYB_FEM_TET_ALL takes no refinement");
   if (!(d->a_max > 0.0)) return fail(HYB_ERR_ARG, "a_max must be > 0");
   for (int f = 0; f < 6; ++f)
     if (d->bc[f] != HYB_BC_NEUMANN0 && d->bc[f] != HYB_BC_ABC) return fail(HYB_ERR_ARG, "bad bc[%d]", f);
@@ -1204,6 +1415,7 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
       m->bps = std::min(step_blocks_per_sm(d->precision, 0), step_blocks_per_sm(d->precision, 1));
     }
   }
+  if (st == HYB_OK && d->fem_path == HYB_FEM_TET_ALL) st = build_kuhn(m);
   if (st == HYB_OK && d->refine_mask && fem && m->nu > 0) {
     if (d->n[0] < 5 || d->n[1] < 5 || d->n[2] < 5) st = fail(HYB_ERR_ARG, "refinement needs >= 5 nodes per axis");
     else st = build_refined(m, d->refine_mask);
@@ -1226,6 +1438,7 @@ hyb_status hyb_mesh_query(const hyb_mesh* m, hyb_mesh_info* o) {
   o->dt_max = m->dt_max;
   o->n_centres = m->nc;
   o->n_sparse_rows = m->nr;
+  o->n_sparse_nnz = m->nnz;
   o->voxel_volume = m->d.h * m->d.h * m->d.h;
   o->device_bytes = m->bytes;
   o->launches = m->launches;
@@ -1238,7 +1451,7 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
                     &m->g, &m->atrial, &m->cot, &m->trace, &m->rrow, &m->rptr, &m->rcol, &m->rval,
                     &m->cptr, &m->cunk, &m->cw, &m->rmask, &m->rzr, &m->refvox, &m->refvox_id, &m->k9,
-                    &m->CU, &m->CL, &m->chist, &m->cckpt};
+                    &m->CU, &m->CL, &m->chist, &m->cckpt, &m->I0, &m->IC0, &m->acopy, &m->kuhn, &m->kuhn_v};
   for (DevBuf* b : bufs) release(*b);
   for (auto& dir : m->items)
     for (DevBuf& b : dir) release(b);
@@ -1267,6 +1480,32 @@ hyb_status hyb_forward(hyb_mesh* m, const double* a, const hyb_source* src, int3
   return forward_impl<float>(m, a, src, n_src, nsteps, dt, (float*)trace, true);
 }
 
+hyb_status hyb_set_initial(hyb_mesh* m, const void* u0, const void* u_prev, const void* c0, const void* c_prev) {
+  if (!m) return fail(HYB_ERR_ARG, "null mesh");
+  if (!u0) {
+    m->have_init = false;
+    return HYB_OK;
+  }
+  if (!u_prev) return fail(HYB_ERR_ARG, "u_prev is needed with u0");
+  const size_t es = esize(m), fb = (size_t)m->Np * es, cb = (size_t)m->nc * es;
+  HYB_TRY(ensure(m, m->I0, 2 * fb));
+  HYB_TRY(ensure(m, m->IC0, 2 * cb));
+  HYB_CU(cudaMemsetAsync(m->I0.p, 0, 2 * fb, m->st));
+  const void* lv[2] = {u0, u_prev};
+  for (int q = 0; q < 2; ++q)
+    HYB_CU(cudaMemcpy2DAsync((char*)m->I0.p + q * fb, (size_t)m->px * es, lv[q], (size_t)m->n[0] * es,
+                             (size_t)m->n[0] * es, (size_t)m->n[1] * m->n[2], cudaMemcpyDeviceToDevice, m->st));
+  if (m->nc) {
+    const void* cv[2] = {c0, c_prev};
+    for (int q = 0; q < 2; ++q) {
+      if (cv[q]) HYB_CU(cudaMemcpyAsync((char*)m->IC0.p + q * cb, cv[q], cb, cudaMemcpyDeviceToDevice, m->st));
+      else HYB_CU(cudaMemsetAsync((char*)m->IC0.p + q * cb, 0, cb, m->st));
+    }
+  }
+  m->have_init = true;
+  return HYB_OK;
+}
+
 hyb_status hyb_adjoint(hyb_mesh* m, const void* cot, int32_t accumulate) {
   if (!m || !cot) return fail(HYB_ERR_ARG, "null argument");
   if (m->d.precision == HYB_FP64) return adjoint_impl<double>(m, (const double*)cot, accumulate);
@@ -1279,8 +1518,7 @@ hyb_status hyb_gradient(hyb_mesh* m, const double* a, double gamma, double a0, d
   if (!m->have_adj) return fail(HYB_ERR_STATE, "hyb_gradient needs a preceding hyb_adjoint");
   if (m->nu == 0) return HYB_OK;
   const double h = m->d.h;
-  launch_grad_finalize((const double*)m->G.p, m->nsrc, a, -m->dt * m->dt / (h * h) / kGradPairScale, gamma, h * h * h, a0,
-                       g_out, m->nu, m->st);
+  launch_grad_finalize((const double*)m->G.p, m->nsrc, a, grad_scale(m), gamma, h * h * h, a0, g_out, m->nu, m->st);
   HYB_LAUNCHED(m);
   return HYB_OK;
 }
@@ -1315,13 +1553,16 @@ hyb_status hyb_get_field(hyb_mesh* m, int32_t which, int32_t isrc, void* out) {
   const char* src = nullptr;
   const int r_u_last = ((m->nsteps % 3) + 3) % 3;
   const int r_u_prev = (((m->nsteps - 1) % 3) + 3) % 3;
+  if ((which == HYB_FIELD_U_LAST || which == HYB_FIELD_U_PREV) && !m->u_levels)
+    return fail(HYB_ERR_STATE, "a checkpointed adjoint has reused the forward's levels: read u before hyb_adjoint");
   if (which == HYB_FIELD_U_LAST) {
     src = (const char*)m->U.p + ((size_t)r_u_last * m->nsrc + isrc) * fb;
   } else if (which == HYB_FIELD_U_PREV) {
     src = (const char*)m->U.p + ((size_t)r_u_prev * m->nsrc + isrc) * fb;
   } else if (which == HYB_FIELD_LAMBDA_FIRST) {
     if (!m->have_adj) return fail(HYB_ERR_STATE, "no adjoint has run");
-    src = (const char*)m->L.p + ((size_t)1 * m->nsrc + isrc) * fb;
+    const size_t lv = m->d.adjoint_mode == HYB_ADJ_PAPER ? 0 : 1;  // lambda^0 (paper) or lambda^1
+    src = (const char*)m->L.p + (lv * m->nsrc + isrc) * fb;
   } else {
     return fail(HYB_ERR_ARG, "bad field selector");
   }
@@ -1339,10 +1580,12 @@ hyb_status hyb_misfit_noalloc(const void* trace, const void* u_obs, int32_t prec
   if (weights != HYB_WEIGHTS_PLAIN && weights != HYB_WEIGHTS_QUADRATURE) return fail(HYB_ERR_ARG, "bad weights");
   if (n_src < 1 || n_src > kMaxSlots) return fail(HYB_ERR_ARG, "n_src must be in [1, %d]", kMaxSlots);
   if (nsteps < 0 || obs_stride < 1) return fail(HYB_ERR_ARG, "bad nsteps or obs_stride");
-  const long long total = (long long)n_src * (nsteps + 1) * obs_stride;
-  if (total > noalloc_max_entries())
-    return fail(HYB_ERR_ARG, "trace of %lld entries exceeds the %lld entries hyb_misfit_noalloc can reduce", total,
-                noalloc_max_entries());
+  // bound the size factor by factor, before forming the product
+  const long long cap = noalloc_max_entries();
+  if ((long long)nsteps + 1 > cap / obs_stride / n_src)
+    return fail(HYB_ERR_ARG, "trace of %d x %lld x %d entries exceeds the %lld entries hyb_misfit_noalloc can reduce",
+                n_src, (long long)nsteps + 1, obs_stride, cap);
+  const long long total = (long long)n_src * ((long long)nsteps + 1) * obs_stride;
   MisfitGeom g;
   std::memset(&g, 0, sizeof g);
   g.n_src = n_src;
@@ -1382,7 +1625,7 @@ hyb_status hyb_sync(hyb_mesh* m) {
     HYB_CU(cudaMemsetAsync(m->flag.p, 0, 2 * sizeof(int), m->st));
     HYB_CU(cudaStreamSynchronize(m->st));
     if (f0) return fail(HYB_ERR_CFL, "a coefficient value exceeded a_max (or was not finite)");
-    return fail(HYB_ERR_CUDA, "a step kernel timed out waiting for its staged planes");
+    return fail(HYB_ERR_TIMEOUT, "a step kernel's bounded wait for its staged planes ran out");
   }
   return HYB_OK;
 }

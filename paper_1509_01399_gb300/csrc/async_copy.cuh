@@ -39,12 +39,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// Limit of the waits that drain a block's own copies before it exits.
+constexpr long long kDrainCycles = 1LL << 29;
+
 // Wait for the phase with the given parity of the barrier to complete, for
 // at most `budget` clock cycles, giving up early once *abort is nonzero
 // (another block timed out).  Returns false on timeout or abort.  Each try
-// suspends the thread until the phase completes or the hint expires.
+// suspends the thread until the phase completes or the hint expires.  A
+// negative budget only tests the phase once.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget, const int* abort) {
   const uint32_t a = smem_addr(bar);
+  if (budget < 0) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+  }
   const long long t0 = clock64();
   for (unsigned it = 1;; ++it) {
     uint32_t done;

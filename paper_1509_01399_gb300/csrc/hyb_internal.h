@@ -30,12 +30,23 @@ struct Slot {
   const T* obs_r;    // adjoint: cotangent row j
   T* hist_w;         // forward: FEM-owned box slot for u^{k+1} (or nullptr)
   const T* hist_r;   // adjoint: FEM-owned box slot holding u^j (or nullptr)
-  T srcval;          // forward: tau^2 * 2 p(t_k) / h while the source is on
   int mask_f;        // absorbing faces of the step (forward: step k, adjoint: B_j)
   int mask_e;        // adjoint: absorbing faces of E_{j-1}
   int mask_c;        // adjoint: absorbing faces of C_{j+1}
-  int src_face;      // forward: face carrying the source flux, or -1
+  int src_mask;      // forward: faces carrying the plane-wave flux at step k (bits; 0: none)
   int obs_face;      // face recorded in the trace / receiving the cotangent
+  // Plane wave of the slot's source: the flux term of node (i, j, k) on face f
+  // is sf[f] p(t_k - h (d . ((i, j, k) - si0))), p(s) = sin(omega s) on [0, t1].
+  double st;         // t_k
+  double sf[6];      // tau^2 (2 / h) amp (-(d . n_f)) on the entry faces, 0 elsewhere
+  double sd[3];      // unit direction d
+  double sh;         // lattice spacing h
+  int si0[3];        // entry corner (node index)
+  double somega, st1;
+  // paper-mode adjoint (forward rows on lambda): the cotangent row entering on
+  // the observation face as inj_scale 2^b c_j, b the node's boundary axes
+  const T* inj;
+  T inj_scale;       // -tau / h^3
   const T* ccur;     // centre nodes of refined voxels, levels as cur/prev/next
   const T* cprev;
   T* cnext;
@@ -56,6 +67,7 @@ struct StepArgs {
   CUtensorMap tmw;   // edge weights: {wpx, wn1, 3 wn2}, box 36 x (kTileY + 1) x 1
   CUtensorMap tmh;   // history: {hpx, fn1, fn2 x boxes}, box 36 x (kTileY + 1) x 1
   int* err;          // [0]: set when a pipeline wait timed out
+  long long wait;    // cycles a pipeline wait may take (< 0: give up at once if not complete)
   int nx, ny, nz;
   int px;            // row pitch of lattice fields
   int fl[3], fh[3];  // FEM-owned node range (inclusive); fl[0] > fh[0]: no FEM
@@ -68,7 +80,6 @@ struct StepArgs {
   double* G;         // FP64 gradient accumulator over unknown voxels (adjoint)
   int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
   T c2;              // tau^2 / h^2
-  T cd;              // 2 - 6 c2: diagonal of a lattice row with unit weights
   T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
   int npb;           // interior: tiles per plane of the interior box
   int ntx;           // interior: tiles along x
@@ -92,6 +103,12 @@ struct StepArgs {
   const unsigned char* refvox;// unknown voxels: 1 = refined
   const int* refvox_id;       // unknown id of each refined voxel (centre order)
   const double* k9;           // 9 x 9 stiffness of a refined unit voxel, a = 1
+  // fem_path HYB_FEM_TET_ALL: every interior node's row gathered over the Kuhn
+  // tetrahedra of its voxels (the all-node kernels run every level)
+  int tet;
+  const double* acoef;        // a on the unknown voxels (1 on the other voxels)
+  const double* kuhn;         // [6][4][4] element stiffness (unit spacing, a = 1), then [6] volumes
+  const int* kuhn_v;          // [6][4] corner ids (a + 2b + 4c) of each tetrahedron's vertices
   Slot<T> s[kMaxSlots];
 };
 
@@ -123,6 +140,9 @@ void launch_refined_pair(const StepArgs<T>& a, cudaStream_t st);
 template <typename T>
 void launch_set_sparse(const int* cptr, const int* cunk, const double* cw, const double* acoef, T* rval, int nnz,
                        cudaStream_t st);
+// Trace row of face f (c_p + n_p c_q order) from a lattice field.
+template <typename T>
+void launch_extract_face(const StepArgs<T>& a, const T* field, int f, T* row, cudaStream_t st);
 // Copy the FEM-owned box of a lattice field into a history slot.
 template <typename T>
 void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStream_t st);
@@ -146,12 +166,16 @@ void launch_sum(const double* partials, int n, double* out, cudaStream_t st);
 // g = scale * sum_s G_s + gamma * vol * (a - a0), G holding n_src arrays of n
 void launch_grad_finalize(const double* G, int n_src, const double* a, double scale, double gamma,
                           double vol, double a0, double* g, long long n, cudaStream_t st);
-// partials of: [0] sum g^2, [1] sum (a - a0)^2
-void launch_cg_norms(const double* g, const double* a, double a0, long long n, double* partials,
-                     cudaStream_t st);
-// d = -g / vol + beta * d (beta = 0: d = -g / vol)
-void launch_cg_direction(const double* g, double vol, double beta, double* d, long long n,
-                         cudaStream_t st);
+// partials of: [0] sum g^2, [1] sum (a - a0)^2, [2] sum gp^2 with gp the
+// projected gradient (g zeroed where a sits at a bound and g points out of
+// [lo, hi]); kCgParts partial arrays of kReduceBlocks entries
+constexpr int kCgParts = 3;
+void launch_cg_norms(const double* g, const double* a, double a0, double lo, double hi, long long n,
+                     double* partials, cudaStream_t st);
+// d = -gp / vol + beta * d (beta = 0: d = -gp / vol), then the components of d
+// that would leave [lo, hi] at once set to 0
+void launch_cg_direction(const double* g, const double* a, double lo, double hi, double vol, double beta,
+                         double* d, long long n, cudaStream_t st);
 // partials of: [0] sum g d, [1] max |d|
 void launch_cg_dir_stats(const double* g, const double* d, long long n, double* partials,
                          cudaStream_t st);

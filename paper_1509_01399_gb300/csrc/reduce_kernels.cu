@@ -108,30 +108,43 @@ __global__ void grad_finalize_kernel(const double* __restrict__ G, int n_src, co
   }
 }
 
+// a at a bound of [lo, hi] with v pointing out of it
+__device__ __forceinline__ bool blocked(double a, double v, double lo, double hi) {
+  return (a <= lo && v < 0.0) || (a >= hi && v > 0.0);
+}
+
 __global__ void __launch_bounds__(kReduceThreads) cg_norms_kernel(const double* __restrict__ g,
                                                                   const double* __restrict__ a, double a0,
-                                                                  long long n, double* __restrict__ partials) {
-  double s0 = 0.0, s1 = 0.0;
+                                                                  double lo, double hi, long long n,
+                                                                  double* __restrict__ partials) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    s0 += g[i] * g[i];
+    const double gi = g[i];
+    s0 += gi * gi;
     const double e = a[i] - a0;
     s1 += e * e;
+    // descent moves a along -g: a component whose -g leaves [lo, hi] is clipped
+    if (!blocked(a[i], -gi, lo, hi)) s2 += gi * gi;
   }
   s0 = block_sum(s0);
   s1 = block_sum(s1);
+  s2 = block_sum(s2);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = s0;
     partials[gridDim.x + blockIdx.x] = s1;
+    partials[2 * gridDim.x + blockIdx.x] = s2;
   }
 }
 
-__global__ void cg_direction_kernel(const double* __restrict__ g, double vol, double beta,
-                                    double* __restrict__ d, long long n) {
+__global__ void cg_direction_kernel(const double* __restrict__ g, const double* __restrict__ a, double lo,
+                                    double hi, double vol, double beta, double* __restrict__ d, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double gl = g[i] / vol;
-    d[i] = beta != 0.0 ? -gl + beta * d[i] : -gl;
+    const double ai = a[i];
+    const double gl = blocked(ai, -g[i], lo, hi) ? 0.0 : g[i] / vol;
+    const double v = beta != 0.0 ? -gl + beta * d[i] : -gl;
+    d[i] = blocked(ai, v, lo, hi) ? 0.0 : v;
   }
 }
 
@@ -193,15 +206,15 @@ void launch_grad_finalize(const double* G, int n_src, const double* a, double sc
   grad_finalize_kernel<<<kReduceBlocks, kReduceThreads, 0, st>>>(G, n_src, a, scale, gamma, vol, a0, g, n);
 }
 
-void launch_cg_norms(const double* g, const double* a, double a0, long long n, double* partials,
-                     cudaStream_t st) {
-  cg_norms_kernel<<<kReduceBlocks, kReduceThreads, 0, st>>>(g, a, a0, n, partials);
+void launch_cg_norms(const double* g, const double* a, double a0, double lo, double hi, long long n,
+                     double* partials, cudaStream_t st) {
+  cg_norms_kernel<<<kReduceBlocks, kReduceThreads, 0, st>>>(g, a, a0, lo, hi, n, partials);
 }
 
-void launch_cg_direction(const double* g, double vol, double beta, double* d, long long n,
-                         cudaStream_t st) {
+void launch_cg_direction(const double* g, const double* a, double lo, double hi, double vol, double beta,
+                         double* d, long long n, cudaStream_t st) {
   if (n == 0) return;
-  cg_direction_kernel<<<kReduceBlocks, kReduceThreads, 0, st>>>(g, vol, beta, d, n);
+  cg_direction_kernel<<<kReduceBlocks, kReduceThreads, 0, st>>>(g, a, lo, hi, vol, beta, d, n);
 }
 
 void launch_cg_dir_stats(const double* g, const double* d, long long n, double* partials,

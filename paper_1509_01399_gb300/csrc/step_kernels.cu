@@ -50,6 +50,40 @@ __device__ __forceinline__ int face_bits(int i, int j, int k, int nx, int ny, in
          (k == 0 ? 16 : 0) | (k == nz - 1 ? 32 : 0);
 }
 
+// Plane-wave flux term tau^2 (2 / h) g of node (i, j, k) on flux face f
+// (the mirror ghost u_g = u_in + 2 h g of d_n u = g, Eq. (f)):
+// g = amp (-(d . n_f)) p(t_k - d . (x - x0)), p(s) = sin(omega s) on [0, t1]
+// and 0 elsewhere.  The delay is formed in FP64; the pulse in the field's
+// precision.
+template <typename T>
+__device__ __forceinline__ T src_term(const Slot<T>& S, int f, int i, int j, int k) {
+  const double s =
+      S.st - S.sh * (S.sd[0] * (i - S.si0[0]) + S.sd[1] * (j - S.si0[1]) + S.sd[2] * (k - S.si0[2]));
+  if (!(s >= 0.0 && s <= S.st1)) return T(0);
+  if constexpr (sizeof(T) == 4) return (T)S.sf[f] * sinf((float)(S.somega * s));
+  else return (T)(S.sf[f] * sin(S.somega * s));
+}
+
+// Sum of the flux terms of the faces in `faces` (bits) that carry the flux.
+template <typename T>
+__device__ __forceinline__ T src_terms(const Slot<T>& S, int faces, int i, int j, int k) {
+  T v = T(0);
+  for (int b = faces & S.src_mask; b; b &= b - 1) v += src_term(S, __ffs(b) - 1, i, j, k);
+  return v;
+}
+
+__device__ __forceinline__ int face_index(int f, int i, int j, int k, int nx, int ny);
+
+// Paper-mode adjoint: the cotangent c of the observation-face node (i, j, k)
+// enters its row as -tau c / M, M = h^3 halved on every axis on which the
+// node lies on the outer boundary (the mirror ghost of d_n lambda = -(u - u~)).
+template <typename T>
+__device__ __forceinline__ T inj_term(const Slot<T>& S, int fall, int i, int j, int k, int nx, int ny) {
+  if (S.inj == nullptr || !((fall >> S.obs_face) & 1)) return T(0);
+  const int nb = ((fall & 3) ? 1 : 0) + ((fall & 12) ? 1 : 0) + ((fall & 48) ? 1 : 0);
+  return S.inj_scale * T(1 << nb) * S.inj[face_index(S.obs_face, i, j, k, nx, ny)];
+}
+
 // field index of node (i, j, k)
 template <typename T>
 __device__ __forceinline__ long long lin(const StepArgs<T>& A, int i, int j, int k) {
@@ -88,10 +122,101 @@ __device__ __forceinline__ T fem_lap(const StepArgs<T>& A, const T* __restrict__
          Wy[w - wy] * (u[id - A.px] - c) + Wz[w] * (zp - c) + Wz[w - wz] * (zm - c);
 }
 
+// ---- the all-FEM path (HYB_FEM_TET_ALL): rows gathered over tetrahedra ----
+// Coefficient a of the voxel with origin (ox, oy, oz): its value on the
+// unknown voxels, 1 elsewhere (Eq. (2.3)).
+template <typename T>
+__device__ __forceinline__ double voxel_coef(const StepArgs<T>& A, int ox, int oy, int oz) {
+  const int x = ox - A.fl[0], y = oy - A.fl[1], z = oz - A.fl[2];
+  if (x >= 0 && y >= 0 && z >= 0 && x < A.un[0] && y < A.un[1] && z < A.un[2])
+    return A.acoef[x + (long long)A.un[0] * (y + (long long)A.un[1] * z)];
+  return 1.0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool lattice_interior(const StepArgs<T>& A, int i, int j, int k) {
+  return i > 0 && j > 0 && k > 0 && i < A.nx - 1 && j < A.ny - 1 && k < A.nz - 1;
+}
+
+// The finite-element row of the interior node n = (i, j, k), gathered over
+// the Kuhn tetrahedra of the (up to eight) voxels that have n as a corner:
+// sum over those tetrahedra K of a_K K^K_{n q} (element stiffness, Sec. 7.2)
+// and the lumped mass M^L_n = sum |K| / 4.  With `u` set, returns the
+// Laplacian part -(M^L)^{-1} (K u)_n of Eq. (fem) (unit spacing); else the
+// coefficient of row n on node m = (mi, mj, mk) (the diagonal when m = n).
+template <typename T>
+__device__ __noinline__ T tet_row(const StepArgs<T>& A, const T* __restrict__ u, int i, int j, int k, int mi, int mj,
+                                  int mk) {
+  const T c = u ? u[lin(A, i, j, k)] : T(0);
+  T acc = T(0);
+  double mass = 0.0;
+  for (int cn = 0; cn < 8; ++cn) {
+    const int ox = i - (cn & 1), oy = j - ((cn >> 1) & 1), oz = k - (cn >> 2);
+    if (ox < 0 || oy < 0 || oz < 0 || ox > A.nx - 2 || oy > A.ny - 2 || oz > A.nz - 2) continue;
+    const T av = (T)voxel_coef(A, ox, oy, oz);
+    for (int t = 0; t < 6; ++t) {
+      const int* V = A.kuhn_v + 4 * t;
+      int ln = -1;
+      for (int q = 0; q < 4; ++q)
+        if (V[q] == cn) ln = q;
+      if (ln < 0) continue;
+      mass += A.kuhn[96 + t] * 0.25;
+      for (int q = 0; q < 4; ++q) {
+        const int cq = V[q];
+        const int qi = ox + (cq & 1), qj = oy + ((cq >> 1) & 1), qk = oz + (cq >> 2);
+        const T kv = av * (T)A.kuhn[16 * t + 4 * ln + q];
+        if (u) {
+          if (q != ln) acc += kv * (u[lin(A, qi, qj, qk)] - c);
+        } else if (qi == mi && qj == mj && qk == mk) {
+          acc += kv;
+        }
+      }
+    }
+  }
+  return -acc / (T)mass;
+}
+
+// Coefficient of the non-absorbing row of node n on node m (Laplacian part,
+// unit spacing) on the all-FEM path: the gathered FEM row on interior
+// nodes; on the outer boundary the FDM row (mirror ghost: 2 on the inward
+// neighbour, 1 on the in-face neighbours, -6 on the node itself).
+template <typename T>
+__device__ __forceinline__ T tet_coef(const StepArgs<T>& A, int ni, int nj, int nk, int mi, int mj, int mk) {
+  if (lattice_interior(A, ni, nj, nk)) return tet_row<T>(A, nullptr, ni, nj, nk, mi, mj, mk);
+  const int d0 = mi - ni, d1 = mj - nj, d2 = mk - nk;
+  if (d0 == 0 && d1 == 0 && d2 == 0) return T(-6);
+  if (abs(d0) + abs(d1) + abs(d2) != 1) return T(0);
+  const int ax = d0 ? 0 : (d1 ? 1 : 2), s = d0 + d1 + d2;
+  const int c = ax == 0 ? ni : (ax == 1 ? nj : nk);
+  const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
+  return ((s > 0 && c == 0) || (s < 0 && c == n - 1)) ? T(2) : T(1);
+}
+
+// Pairing of the voxel with origin (i, j, k) on the all-FEM path:
+// kGradPairScale sum over its tetrahedra of u^T K^K lambda (a = 1).
+template <typename T>
+__device__ __forceinline__ T tet_pair(const StepArgs<T>& A, const T* __restrict__ hb, const T* __restrict__ lam,
+                                      int i, int j, int k) {
+  T u[8], l[8];
+  for (int c = 0; c < 8; ++c) {
+    const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+    u[c] = hb[hidx(A, i + a, j + b, k + d)];
+    l[c] = lam[lin(A, i + a, j + b, k + d)];
+  }
+  T acc = T(0);
+  for (int t = 0; t < 6; ++t)
+    for (int p = 0; p < 4; ++p)
+      for (int q = 0; q < 4; ++q)
+        acc += (T)A.kuhn[16 * t + 4 * p + q] * u[A.kuhn_v[4 * t + p]] * l[A.kuhn_v[4 * t + q]];
+  return T(6) * acc;
+}
+
 // Laplacian part (without 1/h^2) of a non-absorbing row at any node:
-// FEM stencil on FEM-owned nodes, 7-point with mirror ghosts elsewhere.
+// FEM stencil on FEM-owned nodes, 7-point with mirror ghosts elsewhere (on
+// the all-FEM path, the gathered FEM row on every interior node).
 template <typename T>
 __device__ __noinline__ T row_lap(const StepArgs<T>& A, const T* __restrict__ u, int i, int j, int k) {
+  if (A.tet && lattice_interior(A, i, j, k)) return tet_row<T>(A, u, i, j, k, 0, 0, 0);
   const long long id = lin(A, i, j, k);
   const long long sz = (long long)A.px * A.ny;
   const T c = u[id];
@@ -133,8 +258,10 @@ __device__ __noinline__ T fwd_new(const StepArgs<T>& A, const Slot<T>& S, int i,
       return A.r * S.cur[id] + acc / T(__popc(fb));
     }
   }
-  T v = T(2) * S.cur[id] - S.prev[id] + A.c2 * row_lap(A, S.cur, i, j, k);
-  if (S.src_face >= 0 && ((fall >> S.src_face) & 1)) v += S.srcval;
+  const T c = S.cur[id];
+  T v = c + ((c - S.prev[id]) + A.c2 * row_lap(A, S.cur, i, j, k));
+  if (fall & S.src_mask) v += src_terms(S, fall, i, j, k);
+  if (S.inj) v += inj_term(S, fall, i, j, k, A.nx, A.ny);
   return v;
 }
 
@@ -202,6 +329,39 @@ __device__ __noinline__ T adj_rhs(const StepArgs<T>& A, const Slot<T>& S, int i,
       } else {
         rhs += A.c2 * row_coef(A, ni, nj, nk, ax, -s) * l1[nid];
       }
+    }
+  }
+  if (!(fbm & S.mask_c)) rhs -= S.prev[id];
+  if (S.obs_r && ((fbm >> S.obs_face) & 1)) rhs += S.obs_r[face_index(S.obs_face, i, j, k, A.nx, A.ny)];
+  return rhs;
+}
+
+// adj_rhs on the all-FEM path: the transposed row gathers the coefficients
+// of every neighbouring row (the 26 nodes around m) on m.
+template <typename T>
+__device__ __noinline__ T adj_rhs_tet(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k) {
+  const T* __restrict__ l1 = S.cur;
+  const long long id = lin(A, i, j, k);
+  const int fbm = face_bits(i, j, k, A.nx, A.ny, A.nz);
+  T rhs;
+  if (fbm & S.mask_f) rhs = A.r * l1[id];
+  else rhs = (T(2) + A.c2 * tet_coef(A, i, j, k, i, j, k)) * l1[id];
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    if (d == 13) continue;
+    const int ni = i + dx, nj = j + dy, nk = k + dz;
+    if (ni < 0 || ni >= A.nx || nj < 0 || nj >= A.ny || nk < 0 || nk >= A.nz) continue;
+    const long long nid = lin(A, ni, nj, nk);
+    const int fbn = face_bits(ni, nj, nk, A.nx, A.ny, A.nz) & S.mask_f;
+    if (fbn) {
+      // an absorbing row couples to m only when m is its inward neighbour
+      // across one of its absorbing faces
+      if (abs(dx) + abs(dy) + abs(dz) != 1) continue;
+      const int ax = dx ? 0 : (dy ? 1 : 2), s = -(dx + dy + dz);  // m = n + s e_ax
+      const int f = 2 * ax + (s > 0 ? 0 : 1);
+      if (fbn & (1 << f)) rhs += l1[nid] / T(__popc(fbn));
+    } else {
+      rhs += A.c2 * tet_coef(A, ni, nj, nk, i, j, k) * l1[nid];
     }
   }
   if (!(fbm & S.mask_c)) rhs -= S.prev[id];
@@ -283,7 +443,7 @@ __device__ __forceinline__ T adj_rhs_inl(const StepArgs<T>& A, const Slot<T>& S,
 // absorbing node b to its inward neighbours with r / L_b.
 template <typename T, int D>
 __device__ __noinline__ T adj_new(const StepArgs<T>& A, const Slot<T>& S, int i, int j, int k) {
-  T v = adj_rhs(A, S, i, j, k);
+  T v = A.tet ? adj_rhs_tet(A, S, i, j, k) : adj_rhs(A, S, i, j, k);
   if constexpr (D > 0) {
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
@@ -361,7 +521,8 @@ __device__ __forceinline__ T row_lap_inl(const StepArgs<T>& A, const T* __restri
   return lap7(xm, xp, ym, yp, zm, zp, c);
 }
 
-template <typename T>
+// (TET: the all-node kernels, which also serve the all-FEM path)
+template <typename T, bool TET>
 __device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T>& S, int si, int i, int j,
                                               int k) {
   if (S.hist_r == nullptr) return;
@@ -372,7 +533,8 @@ __device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T
   const long long vid = (long long)(i - A.fl[0]) +
                         (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
   if (A.refvox && A.refvox[vid]) return;
-  A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, S.cur, i, j, k);
+  if (TET && A.tet) A.G[(long long)si * nv + vid] += (double)tet_pair(A, S.hist_r, S.cur, i, j, k);
+  else A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, S.cur, i, j, k);
 }
 
 template <typename T>
@@ -616,11 +778,11 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     wzm = Wm[2 * P::WS];
     const T lap =
         wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + wzp * (cp - c0) + wzm * (cm - c0);
-    val = T(2) * c0 - pv + c2 * lap;
-  } else if constexpr (sizeof(T) == 4) {  // unit weights: the neighbour sum, and (2 - 6 c2) u^k - u^{k-1}
-    val = c2 * (((xm + xp) + (ym + yp)) + (cm + cp)) + (A.cd * c0 - pv);
-  } else {  // FP64 keeps the differences (less rounding over long runs)
-    val = T(2) * c0 - pv + c2 * lap7(xm, xp, ym, yp, cm, cp, c0);
+    val = c0 + ((c0 - pv) + c2 * lap);
+  } else if constexpr (sizeof(T) == 4) {  // unit weights: the neighbour sum minus 6 u^k
+    val = c0 + ((c0 - pv) + c2 * ((((xm + xp) + (ym + yp)) + (cm + cp)) - T(6) * c0));
+  } else {  // FP64 sums the six differences
+    val = c0 + ((c0 - pv) + c2 * lap7(xm, xp, ym, yp, cm, cp, c0));
   }
   if constexpr (ZF) {  // the z face node next to this node (the rows of the x / y faces below)
     const int f = dzs > 0 ? 5 : 4;
@@ -636,8 +798,9 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
         T lb = T(2) * (c0 - ub);
         lb += (Cb[-1] - ub) + (Cb[1] - ub);
         lb += (Cb[-kBoxX] - ub) + (Cb[kBoxX] - ub);
-        vb = T(2) * ub - S.prev[offb] + c2 * lb;  // (u^{k-1} of the face plane is not staged)
-        if (S.src_face == f) vb += S.srcval;
+        vb = ub + ((ub - S.prev[offb]) + c2 * lb);  // (u^{k-1} of the face plane is not staged)
+        if ((S.src_mask >> f) & 1) vb += src_term(S, f, C.i, C.j, k + dzs);
+        if (S.inj && S.obs_face == f) vb += S.inj_scale * T(2) * S.inj[face_index(f, C.i, C.j, k + dzs, A.nx, A.ny)];
       }
       gnext[offb] = vb;
       if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, C.i, C.j, k + dzs, A.nx, A.ny)] = vb;
@@ -681,8 +844,9 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
           T lb = T(2) * (c0 - ub);
           lb += (Ck[ob - o1] - ub) + (Ck[ob + o1] - ub);
           lb += (Cm[ob] - ub) + (Cp[ob] - ub);
-          vb = T(2) * ub - Pk[ob] + c2 * lb;
-          if (S.src_face == f) vb += S.srcval;
+          vb = ub + ((ub - Pk[ob]) + c2 * lb);
+          if ((S.src_mask >> f) & 1) vb += src_term(S, f, bi, bj, k);
+          if (S.inj && S.obs_face == f) vb += S.inj_scale * T(2) * S.inj[face_index(f, bi, bj, k, A.nx, A.ny)];
         }
         gnext[offb] = vb;
         if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, bi, bj, k, A.nx, A.ny)] = vb;
@@ -769,9 +933,9 @@ __device__ __forceinline__ void xface_levels(const StepArgs<T>& A, const Slot<T>
       const T cm = Cm[0], cp = Cp[0], pv = Pk[0];
       T val;
       if constexpr (sizeof(T) == 4)
-        val = c2 * (((xm + xp) + (ym + yp)) + (cm + cp)) + (A.cd * c0 - pv);
+        val = c0 + ((c0 - pv) + c2 * ((((xm + xp) + (ym + yp)) + (cm + cp)) - T(6) * c0));
       else
-        val = T(2) * c0 - pv + c2 * lap7(xm, xp, ym, yp, cm, cp, c0);
+        val = c0 + ((c0 - pv) + c2 * lap7(xm, xp, ym, yp, cm, cp, c0));
       const T ub = Ck[sd];
       const int offb = off + sd;
       if constexpr (!ADJ) {
@@ -782,8 +946,9 @@ __device__ __forceinline__ void xface_levels(const StepArgs<T>& A, const Slot<T>
           T lb = T(2) * (c0 - ub);
           lb += (Ck[sd - kBoxX] - ub) + (Ck[sd + kBoxX] - ub);
           lb += (Cm[sd] - ub) + (Cp[sd] - ub);
-          vb = T(2) * ub - Pk[sd] + c2 * lb;
-          if (S.src_face == f) vb += S.srcval;
+          vb = ub + ((ub - Pk[sd]) + c2 * lb);
+          if ((S.src_mask >> f) & 1) vb += src_term(S, f, X.mi + sd, j, k);
+          if (S.inj && S.obs_face == f) vb += S.inj_scale * T(2) * S.inj[face_index(f, X.mi + sd, j, k, A.nx, A.ny)];
         }
         gnext[offb] = vb;
         if (S.obs_w && S.obs_face == f) S.obs_w[face_index(f, X.mi + sd, j, k, A.nx, A.ny)] = vb;
@@ -819,7 +984,7 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   constexpr int D = R::D;
   constexpr int kProd = kTileX * kTileY / 2;  // the producer thread
   const int t = (int)threadIdx.x;
-  const long long budget = 1LL << 29;         // cycles a wait may take (~0.25 s)
+  const long long budget = A.wait;            // cycles a pipeline wait may take
   if (t >= kProd) {
     // Producer: the planes first read at level g overwrite stages last read
     // at level g - D - 1 (the edge-weight and stored-u rings are the
@@ -840,11 +1005,12 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
       pr.issue(g, false);
     }
     // let no copy be in flight when the block exits (the consumers may have
-    // given up): wait for the last issued levels, ignoring the abort flag
+    // given up): wait for the last issued levels, ignoring the abort flag and
+    // the pipeline's own limit (the copies complete within microseconds)
     const int no_abort = 0;
     const int issued = min(g, z1) - z0;
     for (int q = max(0, issued - R::NB); q < issued; ++q)
-      mbar_wait(pr.full + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), budget, &no_abort);
+      mbar_wait(pr.full + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), kDrainCycles, &no_abort);
     return;
   }
   // Consumers: each warp waits for level k's planes, computes its nodes and
@@ -1022,8 +1188,9 @@ __device__ __forceinline__ void fwd_edge_tile(const StepArgs<T>& A, int si, int 
   }
   T plain = T(0);  // the non-absorbing row, from level-k data only
   if (valid && !fb) {
-    plain = T(2) * cself - S.prev[id] + A.c2 * row_lap_inl(A, S.cur, i, j, k);
-    if (S.src_face >= 0 && ((fall >> S.src_face) & 1)) plain += S.srcval;
+    plain = cself + ((cself - S.prev[id]) + A.c2 * row_lap_inl(A, S.cur, i, j, k));
+    if (fall & S.src_mask) plain += src_terms(S, fall, i, j, k);
+    if (S.inj) plain += inj_term(S, fall, i, j, k, A.nx, A.ny);
   }
   nv[t] = plain;
   __syncthreads();
@@ -1084,7 +1251,7 @@ __device__ __forceinline__ void adj_edge_tile(const StepArgs<T>& A, int si, int 
   }
   if (!valid) return;
   S.next[lin(A, i, j, k)] = lam[t];
-  pair_if_voxel(A, S, si, i, j, k);
+  pair_if_voxel<T, false>(A, S, si, i, j, k);
 }
 
 // One time level of every slot in one launch of kStepBlock threads per
@@ -1158,7 +1325,7 @@ __global__ void __launch_bounds__(128) adj_all_kernel(const __grid_constant__ St
   const int k = (int)(q / ((long long)A.nx * A.ny));
   const Slot<T>& S = A.s[si];
   S.next[lin(A, i, j, k)] = adj_new<T, 3>(A, S, i, j, k);
-  pair_if_voxel(A, S, si, i, j, k);
+  pair_if_voxel<T, true>(A, S, si, i, j, k);
 }
 
 template <typename T>
@@ -1172,7 +1339,8 @@ __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __re
   const int y = (int)(r % A.un[1]);
   const int z = (int)(r / A.un[1]);
   if (A.refvox && A.refvox[t]) return;
-  grad[t] += (double)voxel_pair(A, hist, lam, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z);
+  const int i = A.fl[0] + x, j = A.fl[1] + y, k = A.fl[2] + z;
+  grad[t] += (double)(A.tet ? tet_pair(A, hist, lam, i, j, k) : voxel_pair(A, hist, lam, i, j, k));
 }
 
 // Pairing of a refined voxel: u^T K9 lambda over its 8 corners and centre,
@@ -1258,7 +1426,7 @@ __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t, 
     acc += __shfl_xor_sync(grp, acc, 2);
     if (lane) return;
     const T pi = lat ? S.prev[self] : S.cprev[r - A.nrl];
-    const T val = T(2) * ui - pi + A.c2 * acc;
+    const T val = ui + ((ui - pi) + A.c2 * acc);
     if (lat) {
       S.next[self] = val;
       if (!ADJ && S.hist_w) {
@@ -1351,7 +1519,27 @@ __global__ void extract_owned_kernel(const __grid_constant__ StepArgs<T> A, cons
   box[hidx(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z)] = f[lin(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z)];
 }
 
+template <typename T>
+__global__ void extract_face_kernel(const __grid_constant__ StepArgs<T> A, const T* __restrict__ f, int face,
+                                    T* __restrict__ row) {
+  const int ax = face >> 1;
+  const int np = ax == 0 ? A.ny : A.nx, nq = ax == 2 ? A.ny : A.nz;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= np * nq) return;
+  const int cp = t % np, cq = t / np;
+  const int c = (face & 1) ? (ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz)) - 1 : 0;
+  const int i = ax == 0 ? c : cp, j = ax == 1 ? c : (ax == 0 ? cp : cq), k = ax == 2 ? c : cq;
+  row[t] = f[lin(A, i, j, k)];
+}
+
 }  // namespace
+
+template <typename T>
+void launch_extract_face(const StepArgs<T>& a, const T* field, int f, T* row, cudaStream_t st) {
+  const int ax = f >> 1;
+  const int n = (ax == 0 ? a.ny : a.nx) * (ax == 2 ? a.ny : a.nz);
+  extract_face_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(a, field, f, row);
+}
 
 template <typename T>
 unsigned refined_blocks(const StepArgs<T>& a, bool adjoint) {
@@ -1460,6 +1648,7 @@ void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStre
   template void launch_set_coef<T>(const StepArgs<T>&, T*, const double*, double, int*,         \
                                    cudaStream_t);                                                \
   template void launch_extract_owned<T>(const StepArgs<T>&, const T*, T*, cudaStream_t);              \
+  template void launch_extract_face<T>(const StepArgs<T>&, const T*, int, T*, cudaStream_t);        \
   template void launch_refined_pair<T>(const StepArgs<T>&, cudaStream_t);                        \
   template void launch_set_sparse<T>(const int*, const int*, const double*, const double*, T*, int, \
                                      cudaStream_t);

@@ -22,6 +22,9 @@ HYB_BC_NEUMANN0, HYB_BC_ABC = 0, 1
 HYB_FP64, HYB_FP32 = 0, 1
 HYB_WEIGHTS_PLAIN, HYB_WEIGHTS_QUADRATURE = 0, 1
 HYB_FIELD_U_LAST, HYB_FIELD_U_PREV, HYB_FIELD_LAMBDA_FIRST = 0, 1, 2
+HYB_WAIT_NONE = -1
+HYB_ADJ_EXACT, HYB_ADJ_PAPER = 0, 1
+HYB_FEM_STENCIL, HYB_FEM_TET_ALL = 0, 1
 MAX_SOURCES = 16
 
 
@@ -35,18 +38,19 @@ class hyb_mesh_desc(ctypes.Structure):
     _fields_ = [("n", c_int32 * 3), ("h", c_double), ("origin", c_double * 3),
                 ("fem_lo", c_int32 * 3), ("fem_hi", c_int32 * 3), ("bc", c_int32 * 6),
                 ("precision", c_int32), ("ckpt_every", c_int32), ("a_max", c_double),
-                ("refine_mask", c_void_p)]
+                ("refine_mask", c_void_p), ("wait_cycles", c_int64), ("adjoint_mode", c_int32),
+                ("fem_path", c_int32)]
 
 
 class hyb_mesh_info(ctypes.Structure):
     _fields_ = [("n_nodes", c_int64), ("n_unknown", c_int64), ("n_fem_owned", c_int64),
                 ("unknown_dims", c_int32 * 3), ("obs_stride", c_int32), ("dt_max", c_double),
                 ("voxel_volume", c_double), ("device_bytes", c_int64), ("launches", c_int64),
-                ("n_centres", c_int64), ("n_sparse_rows", c_int64)]
+                ("n_centres", c_int64), ("n_sparse_rows", c_int64), ("n_sparse_nnz", c_int64)]
 
 
 class hyb_source(ctypes.Structure):
-    _fields_ = [("face", c_int32), ("omega", c_double), ("amp", c_double)]
+    _fields_ = [("face", c_int32), ("omega", c_double), ("amp", c_double), ("dir", c_double * 3)]
 
 
 class hyb_cg_params(ctypes.Structure):
@@ -55,12 +59,13 @@ class hyb_cg_params(ctypes.Structure):
 
 
 class hyb_cg_state(ctypes.Structure):
-    _fields_ = [("d", c_void_p), ("gnorm2", c_double), ("alpha", c_double), ("iter", c_int32)]
+    _fields_ = [("d", c_void_p), ("gnorm2", c_double), ("alpha", c_double), ("J", c_double), ("iter", c_int32)]
 
 
 class hyb_cg_report(ctypes.Structure):
-    _fields_ = [("J", c_double), ("J_data", c_double), ("gnorm", c_double), ("alpha", c_double),
-                ("beta", c_double), ("dJ0", c_double), ("alpha_trial", c_double), ("J_trial", c_double)]
+    _fields_ = [("J", c_double), ("J_data", c_double), ("gnorm", c_double), ("gpnorm", c_double),
+                ("alpha", c_double), ("beta", c_double), ("dJ0", c_double), ("alpha_trial", c_double),
+                ("J_trial", c_double)]
 
 
 def _load():
@@ -75,6 +80,7 @@ def _load():
         "hyb_set_stream": [P, P],
         "hyb_forward": [P, P, POINTER(hyb_source), c_int32, c_int32, c_double, P],
         "hyb_adjoint": [P, P, c_int32],
+        "hyb_set_initial": [P, P, P, P, P],
         "hyb_gradient": [P, P, c_double, c_double, P],
         "hyb_misfit": [P, P, P, c_int32, POINTER(c_double), P],
         "hyb_cg_step": [P, P, P, POINTER(hyb_source), c_int32, c_int32, c_double,
@@ -96,7 +102,7 @@ def _load():
 _lib = _load()
 EXPORTED = ("hyb_mesh_create", "hyb_mesh_query", "hyb_mesh_destroy", "hyb_set_stream", "hyb_forward",
             "hyb_adjoint", "hyb_gradient", "hyb_misfit", "hyb_cg_step", "hyb_get_field", "hyb_sync",
-            "hyb_last_error", "hyb_misfit_noalloc")
+            "hyb_last_error", "hyb_misfit_noalloc", "hyb_set_initial")
 
 
 def hyb_last_error() -> str:
@@ -114,6 +120,9 @@ def _sources(srcs) -> tuple:
         arr[i].face = int(s.face)
         arr[i].omega = float(s.omega)
         arr[i].amp = float(getattr(s, "amp", 1.0))
+        d = getattr(s, "direction", None)
+        for a in range(3):
+            arr[i].dir[a] = 0.0 if d is None else float(d[a])
     return arr, len(srcs)
 
 
@@ -141,6 +150,11 @@ def hyb_set_stream(mesh: int, stream: int) -> None:
 def hyb_forward(mesh: int, a_ptr: int, sources, nsteps: int, dt: float, trace_ptr: int) -> None:
     arr, n = _sources(sources)
     _check(_lib.hyb_forward(c_void_p(mesh), c_void_p(a_ptr), arr, n, int(nsteps), float(dt), c_void_p(trace_ptr)))
+
+
+def hyb_set_initial(mesh: int, u0_ptr: int, u_prev_ptr: int, c0_ptr: int = 0, c_prev_ptr: int = 0) -> None:
+    _check(_lib.hyb_set_initial(c_void_p(mesh), c_void_p(u0_ptr or None), c_void_p(u_prev_ptr or None),
+                                c_void_p(c0_ptr or None), c_void_p(c_prev_ptr or None)))
 
 
 def hyb_adjoint(mesh: int, cot_ptr: int, accumulate: int = 0) -> None:
@@ -193,7 +207,8 @@ class HybMesh:
     arrays.  precision: "fp64" or "fp32" (FP32 fields, FP64 gradient/CG)."""
 
     def __init__(self, n, h, fem_lo=None, fem_hi=None, bc=(1,) * 6, precision="fp64", ckpt_every=0,
-                 a_max=4.0, origin=(0.0, 0.0, 0.0), device="cuda", stream=None, refine=None):
+                 a_max=4.0, origin=(0.0, 0.0, 0.0), device="cuda", stream=None, refine=None, wait_cycles=0,
+                 adjoint_mode=HYB_ADJ_EXACT, fem_path=HYB_FEM_STENCIL):
         import torch
 
         self.torch = torch
@@ -210,6 +225,9 @@ class HybMesh:
         d.precision = HYB_FP64 if precision == "fp64" else HYB_FP32
         d.ckpt_every = int(ckpt_every)
         d.a_max = float(a_max)
+        d.wait_cycles = int(wait_cycles)
+        d.adjoint_mode = int(adjoint_mode)
+        d.fem_path = int(fem_path)
         self._refine = None
         if refine is not None:
             import numpy as _np
@@ -270,6 +288,19 @@ class HybMesh:
         self.nsteps, self.n_src = nsteps, len(sources)
         return trace
 
+    def set_initial(self, u0=None, u_prev=None, c0=None, c_prev=None):
+        """Initial state of Model Problem 1 for the forwards that follow (None:
+        the zero state of Model Problem 2).  Arrays over the lattice nodes
+        (x fastest) and the centre nodes of refined voxels."""
+        if u0 is None:
+            hyb_set_initial(self.handle, 0, 0)
+            self._init_keep = None
+            return
+        t = [None if v is None else self.torch.as_tensor(v, dtype=self.dtype, device=self.device).contiguous()
+             for v in (u0, u_prev, c0, c_prev)]
+        self._init_keep = t
+        hyb_set_initial(self.handle, *[0 if v is None else v.data_ptr() for v in t])
+
     def adjoint(self, cot, accumulate=False):
         cot = cot.to(dtype=self.dtype, device=self.device).contiguous()
         hyb_adjoint(self.handle, cot.data_ptr(), 1 if accumulate else 0)
@@ -297,7 +328,7 @@ class HybMesh:
 
     def new_cg_state(self):
         d = self.torch.zeros(self.n_unknown, dtype=self.torch.float64, device=self.device)
-        st = hyb_cg_state(d.data_ptr(), 0.0, 0.0, 0)
+        st = hyb_cg_state(d.data_ptr(), 0.0, 0.0, 0.0, 0)
         st._d = d
         return st
 

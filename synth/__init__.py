@@ -381,6 +381,34 @@ def random_cotangent(n_src, nsteps, n_obs, seed=7) -> np.ndarray:
     return c
 
 
+def waveguide(omega: float = 40.0, model: int = 2, refine: bool = False, nsteps: int = 500) -> Workload:
+    """The waveguide of the paper's numerical study (Sec. 9): Omega =
+    (-3.4, 3.4) x (-0.8, 0.8)^2, h = 0.1 (69 x 17 x 17 nodes), Omega_FEM =
+    (-3.2, 3.2) x (-0.6, 0.6)^2 (FEM nodes 2..66 x 2..14 x 2..14), the plane
+    wave p(t) = sin(omega t) of Eq. (f) launched from the front side
+    x1 = -3.4 (observed there: the backscattered data), absorbing back side
+    x1 = 3.4, reflecting long sides (S_3 of Eq. (model1)), tau = 0.006 and
+    T = 3 (500 steps), a in [1, 5] (Eq. (admpar)).  The scatterers of the
+    paper's figure are not available: six small symmetric cubes of 2 x 2 x 2
+    voxels with a = 4 on the waveguide's axis at x1 = +-0.8, +-1.6, +-2.4
+    stand in for them.  refine: the 1-voxel dilation of the scatterers refined
+    once (the finer mesh the paper generates its data on).  model 1 adds the
+    initial state of Eq. (initcond) (synth.model1_initial)."""
+    n = (69, 17, 17)
+    h = 0.1
+    origin = (-3.4, -0.8, -0.8)
+    lo, hi = (2, 2, 2), (66, 14, 14)
+    sigma = np.zeros(unknown_dims(lo, hi)[::-1]).ravel()
+    for x1 in (-2.4, -1.6, -0.8, 0.8, 1.6, 2.4):
+        sigma = np.where(box_inclusion_mask(lo, hi, h, origin, (x1, 0.0, 0.0), 2).ravel(), 3.0, sigma)
+    bc = (BC_ABC, BC_ABC, BC_NEUMANN0, BC_NEUMANN0, BC_NEUMANN0, BC_NEUMANN0)
+    ud = unknown_dims(lo, hi)
+    return Workload("waveguide_m%d_w%g" % (model, omega), n, h, origin, lo, hi, bc, [Source(FACE_XM, omega)],
+                    nsteps, 0.006, 5.0, sigma, "fp64",
+                    extra=dict(model=model, gamma=0.01, a0=1.0, a_exact=4.0, theta=1e-6),
+                    refine=refine_around(sigma, ud, 1) if refine else None)
+
+
 CONFIG_BUILDERS = {
     "pr1_ref_33": pr1_ref_33,
     "inverse_129": inverse_129,

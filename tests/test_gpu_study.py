@@ -1,0 +1,40 @@
+"""The reconstruction study of Sec. 9 (Tests 1-2) on the waveguide, short
+form: a few CG iterations from a = 1 lower F and raise a at the scatterers
+more than elsewhere; Eq. (postproc) keeps only the high values."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def study():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_01399_gb300 import study as S
+    return S
+
+
+@pytest.mark.parametrize("model", [1, 2])
+def test_waveguide_reconstruction_moves_toward_the_scatterers(study, model):
+    w = synth.waveguide(40.0, model)
+    obs = study.make_data(w, 0.03, seed=1)
+    r = study.reconstruct(w, obs, max_iter=4)
+    F = [h["F"] for h in r["history"]]
+    assert F[-1] < F[0], F
+    inside = w.sigma > 0
+    a = r["a"]
+    assert a.min() >= 1.0 and a.max() <= 5.0
+    assert a[inside].mean() - 1.0 > 2.0 * (a[~inside].mean() - 1.0)
+    ap = study.postprocess(a)
+    assert np.all((ap == 1.0) | (ap > 0.6 * a.max()))
+
+
+@pytest.mark.gpu
+def test_postprocess_is_eq_postproc():
+    from paper_1509_01399_gb300 import study as S
+    a = np.array([1.0, 2.0, 3.0, 5.0])
+    np.testing.assert_array_equal(S.postprocess(a), [1.0, 1.0, 3.0, 5.0])

@@ -71,3 +71,10 @@ def test_noalloc_rejects_traces_beyond_its_scratch(env):
                              0, J_dev.data_ptr(), 0, 0)
     assert e.value.status == H.HYB_ERR_ARG
     assert "exceeds" in H.hyb_last_error()
+    # sizes whose product overflows 64 bits, or whose step count overflows
+    # 32 bits when one is added, are refused the same way
+    for n_src, nsteps, stride in ((1, 2 ** 31 - 1, 1), (16, 2 ** 31 - 2, 2 ** 31 - 1)):
+        with pytest.raises(H.HybError) as e:
+            H.hyb_misfit_noalloc(buf.data_ptr(), buf.data_ptr(), H.HYB_FP32, n_src, nsteps, stride,
+                                 [(1, 1)] * n_src, 0.01, 0.1, 0, J_dev.data_ptr(), 0, 0)
+        assert e.value.status == H.HYB_ERR_ARG
