@@ -59,7 +59,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-steps", type=int, default=30)
     p.add_argument("--serve-requests", type=int, default=512, help="requests of the serving stream (0: skip)")
-    p.add_argument("--serve-workers", type=int, default=8)
+    p.add_argument("--serve-workers", type=int, default=4)
+    p.add_argument("--serve-batch", type=int, default=8, help="requests of one class per batched solve")
     p.add_argument("--sources", type=int, default=0, help="with --sweeps-only: use the first K sources")
     p.add_argument("--no-refine", action="store_true", help="with --sweeps-only: the large workload unrefined")
     p.add_argument("--sweeps-only", type=int, default=0,
@@ -180,19 +181,16 @@ def make_workload(name, nsteps=0, refine=True):
 
 def algorithmic_bytes(w, info, n_src, es=4):
     """Algorithmic bytes of one forward and one adjoint launch: an FDM-owned
-    node reads u^k, u^{k-1} and writes u^{k+1} (3 es); a FEM-owned node in
-    stencil form adds its coefficient (4 es; the adjoint also reads the stored
-    u^k: 5 es); a row in sparse form (refined region, lattice and centre
-    nodes) moves 3 es plus 8 B per off-diagonal entry (value and column),
-    and in the adjoint 4 es plus the entries.  Times the sources of the
-    launch."""
+    node reads u^k, u^{k-1} and writes u^{k+1} (3 es); a FEM-owned node adds
+    its coefficient (4 es; the adjoint also reads the stored u^k: 5 es); a
+    centre node of a refined voxel likewise (4 es / 5 es).  Times the
+    sources of the launch."""
     n_lat = w.n_nodes
     n_fo = int(info.n_fem_owned)
-    nr, nc, nnz = int(info.n_sparse_rows), int(info.n_centres), int(info.n_sparse_nnz)
-    nrl = nr - nc
+    nc = int(info.n_centres)
     fdm = n_lat - n_fo
-    fwd = fdm * 3 * es + (n_fo - nrl) * 4 * es + nr * 3 * es + 8 * nnz
-    adj = fdm * 3 * es + (n_fo - nrl) * 5 * es + nr * 4 * es + 8 * nnz
+    fwd = fdm * 3 * es + n_fo * 4 * es + nc * 4 * es
+    adj = fdm * 3 * es + n_fo * 5 * es + nc * 5 * es
     return n_src * fwd, n_src * adj
 
 
@@ -448,7 +446,7 @@ def run_serving(args, dev):
     import synth
     from paper_1509_01399_gb300.serve import Request, ServingEngine, latency_stats, poisson_arrivals
     R = args.serve_requests
-    eng = ServingEngine(workers=args.serve_workers, device=str(dev))
+    eng = ServingEngine(workers=args.serve_workers, device=str(dev), max_batch=args.serve_batch)
     sizes = (33, 65, 97, 129)
     warm = []
     for N in sizes:  # pools and sweep graphs of every class, outside timing
@@ -462,9 +460,10 @@ def run_serving(args, dev):
     arr = poisson_arrivals(R, lam, seed=3)
     res = eng.run([Request(i, synth.serving_request(i), float(arr[i])) for i in range(R)])
     st = latency_stats(res)
+    batches = {"batches": eng.batches, "max_batch": eng.max_batch_seen}
     eng.close()
     n64 = min(R, 16)
-    e64 = ServingEngine(workers=1, precision="fp64", device=str(dev))
+    e64 = ServingEngine(workers=1, precision="fp64", device=str(dev), max_batch=1)
     e64.run([Request(-1, synth.serving_request(i), 0.0) for i in range(2)])
     r64 = e64.run([Request(i, synth.serving_request(i), 0.0) for i in range(n64)])
     e64.close()
@@ -473,7 +472,8 @@ def run_serving(args, dev):
     for r in r64:
         g32 = res[r.rid].gradient
         errs.append(float(np.linalg.norm(g32 - r.gradient) / np.linalg.norm(r.gradient)))
-    return {"requests": R, "workers": args.serve_workers, "capacity_solves_per_s": mu, "rate_per_s": lam,
+    return {"requests": R, "workers": args.serve_workers, "max_batch": args.serve_batch, **batches,
+            "capacity_solves_per_s": mu, "rate_per_s": lam,
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "mean_ms": st["mean_ms"], "dtype": "f32",
             "grad_rel_err_vs_fp64": {"max": max(errs), "median": float(np.median(errs)), "requests": len(errs)},

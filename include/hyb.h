@@ -182,6 +182,27 @@ hyb_status hyb_set_stream(hyb_mesh* mesh, void* stream);
 hyb_status hyb_forward(hyb_mesh* mesh, const double* a, const hyb_source* src, int32_t n_src,
                        int32_t nsteps, double dt, void* trace);
 
+/* Batched forward: n_src independent problems on the same lattice class
+   advanced by the same launches, slot s with its own coefficient
+   a + s * n_unknown (device double[n_src][n_unknown]) and source src[s];
+   otherwise as hyb_forward.  hyb_adjoint then runs the batch's adjoints
+   (cotangent [n_src][nsteps + 1][obs_stride], each slot accumulating its
+   own gradient) and hyb_gradient_batch returns them one per slot.  This is
+   the serving form's iteration-level batching (not a construct of the
+   paper): a slot's arithmetic is the same alone and in a batch.  Not on the
+   HYB_FEM_TET_ALL path. */
+hyb_status hyb_forward_batch(hyb_mesh* mesh, const double* a, const hyb_source* src, int32_t n_src,
+                             int32_t nsteps, double dt, void* trace);
+/* Data misfit of every slot of the last forward on its own: J_host[s]
+   (HOST double[n_src]; the call synchronises) = 1/2 sum_{k>=1, j} w_k m_j
+   (u - u_obs)^2 over slot s's rows, as hyb_misfit computes it for a
+   one-slot mesh; cotangent (device, may be NULL) as hyb_misfit. */
+hyb_status hyb_misfit_batch(hyb_mesh* mesh, const void* trace, const void* u_obs, int32_t weights, double* J_host,
+                            void* cotangent);
+/* g_out[s] (device double[n_src][n_unknown]) = dJ_s/da_s + gamma |c| (a_s - a0)
+   for every slot of the last batch (Eq. (gradient1) per problem). */
+hyb_status hyb_gradient_batch(hyb_mesh* mesh, const double* a, double gamma, double a0, double* g_out);
+
 /* Initial state of Model Problem 1 (Eq. (model1)): the forwards that follow
    start from u^0 = u0 and u^{-1} = u_prev instead of zero (Model Problem 2).
    u0, u_prev: device fields[n_nodes] of the mesh's precision (lattice nodes,

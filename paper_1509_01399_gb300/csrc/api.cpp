@@ -40,6 +40,7 @@ struct DevBuf {
 // parameters of a captured CUDA graph.
 struct SweepKey {
   int kind = -1;  // 0 forward keeping history, 1 forward without, 2 adjoint
+  int batch = 0;  // per-slot coefficients
   const void* io = nullptr;
   int accumulate = 0;
   int nsteps = 0, nsrc = 0;
@@ -50,7 +51,7 @@ struct SweepKey {
 };
 
 bool same_key(const SweepKey& a, const SweepKey& b) {
-  if (a.kind != b.kind || a.io != b.io || a.accumulate != b.accumulate || a.nsteps != b.nsteps ||
+  if (a.kind != b.kind || a.batch != b.batch || a.io != b.io || a.accumulate != b.accumulate || a.nsteps != b.nsteps ||
       a.nsrc != b.nsrc || a.dt != b.dt)
     return false;
   for (int i = 0; i < a.nsrc; ++i)
@@ -94,6 +95,7 @@ struct hyb_mesh {
   bool have_run = false;    // a forward has run (time grid known)
   bool have_adj = false;
   bool u_levels = false;    // U still holds the last forward's final levels
+  bool batch = false;       // the last forward gave every slot its own coefficient
   int nsteps = 0, nsrc = 0;
   double dt = 0.0;
   hyb_source src[kMaxSlots];
@@ -102,7 +104,9 @@ struct hyb_mesh {
   // refined region
   int nc = 0, nr = 0, nrl = 0, nnz = 0;
   double dt_max = 0.0;
-  DevBuf rrow, rptr, rcol, rval, cptr, cunk, cw, rmask, rzr, refvox, refvox_id, k9;
+  DevBuf rmask, rzr, refvox, refvox_id, k9, rcid, avox;
+  double uK9[81], uK8[64], um9[9], um8[8];  // unit-voxel stiffness and lumped masses (refined, Kuhn)
+  std::vector<int> ref_rows;  // per interior tile and plane: tile rows holding refined-voxel corners
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
   DevBuf I0, IC0;               // initial state of Model Problem 1: u^0, u^{-1} (padded fields), centres
   DevBuf acopy, kuhn, kuhn_v;   // all-FEM path: coefficient of the last forward, Kuhn element tables
@@ -172,6 +176,7 @@ SweepKey make_key(const hyb_mesh* m, int kind, const void* io, int accumulate, i
                   const hyb_source* src) {
   SweepKey k;
   k.kind = kind;
+  k.batch = m->batch ? 1 : 0;
   k.io = io;
   k.accumulate = accumulate;
   k.nsteps = nsteps;
@@ -334,6 +339,7 @@ void step_geometry(const hyb_mesh* m, int* npb, int* ntx, int* small, int* nedge
 constexpr int kStepWavesFew = 1, kStepWavesMany = 3;
 constexpr double kManyLevelsPerBlock = 40.0;
 constexpr double kZFaceLevelCost = 3.5;
+constexpr double kRefRowCost = 0.3;  // a tile row holding refined-voxel corners (a plain level: 1)
 
 // Interior work items of one step launch, one per block: (slot, tile, z0,
 // z1).  Each tile's z range 1 .. n-2 is cut into pieces of about equal
@@ -373,11 +379,17 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
   const double cap = resident * (levels_per_block > kManyLevelsPerBlock ? kStepWavesMany : kStepWavesFew);
   const double target = total / cap;
   std::vector<std::pair<double, std::array<int, 4>>> items;
+  auto ref_cost = [&](const Tile& t, int k) {
+    return m->ref_rows.empty() ? 0.0 : kRefRowCost * m->ref_rows[(size_t)t.tile * nz + k];
+  };
+  for (const Tile& t : tiles)
+    for (int k = 1; k <= nz - 2; ++k) total += ref_cost(t, k);
   for (const Tile& t : tiles) {
     double acc = 0.0;
     int z0 = 1;
     for (int k = 1; k <= nz - 2; ++k) {
-      acc += t.base + ((k >= zf0 && k <= zf1) ? t.extra : 0.0) + ((k == 1 || k == nz - 2) ? kZFaceLevelCost : 0.0);
+      acc += t.base + ((k >= zf0 && k <= zf1) ? t.extra : 0.0) + ((k == 1 || k == nz - 2) ? kZFaceLevelCost : 0.0) +
+             ref_cost(t, k);
       if (acc >= target || k == nz - 2) {
         items.push_back({acc, {t.si, t.tile, z0, k + 1}});
         z0 = k + 1;
@@ -510,10 +522,11 @@ hyb_status build_kuhn(hyb_mesh* m) {
   return HYB_OK;
 }
 
-// Sparse rows of the refined region: the lattice nodes touching a refined
-// voxel (their rows see the twelve children of each refined voxel around
-// them) and the centre nodes.  Each entry keeps its per-voxel contributions
-// W = -K_loc / M_i (unit voxel), so the values follow the coefficient.
+// Refined region: the refined voxels' centre ids, the mask of their corners
+// (the rows the interior blocks correct), the unit-voxel tables, and the
+// stability bound: the rows of the corners and centres are assembled here
+// once, entry by entry from the unit-voxel matrices (a = 1), for their
+// row-sum (Gershgorin) bound and their counts only.
 hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   const long long nu = m->nu;
   std::vector<int> cid(nu, -1);
@@ -558,8 +571,7 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   std::sort(rows.begin(), rows.end());
   m->nrl = (int)rows.size();
   m->nr = m->nrl + m->nc;
-  std::vector<int> rptr(1, 0), rcol, cptr(1, 0), cunk;
-  std::vector<double> cw;
+  long long nnz = 0;
   double bound = 0.0;  // largest row-sum (Gershgorin) bound of M^{-1} K at a = 1, unit spacing
   auto emit_row = [&](std::vector<std::pair<long long, std::pair<int, double>>>& ent, double M) {
     std::sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
@@ -569,17 +581,13 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
       const long long col = ent[q].first;
       double wsum = 0.0;
       while (q < ent.size() && ent[q].first == col) {
-        cunk.push_back(ent[q].second.first);
-        cw.push_back(-ent[q].second.second / M);
         wsum += -ent[q].second.second / M;
         ++q;
       }
-      rcol.push_back((int)col);
-      cptr.push_back((int)cunk.size());
+      ++nnz;
       absum += std::fabs(wsum);
       sum += wsum;
     }
-    rptr.push_back((int)rcol.size());
     bound = std::max(bound, std::fabs(sum) + absum);
   };
   for (long long p : rows) {
@@ -618,21 +626,19 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
     }
     emit_row(ent, m9[8]);
   }
-  m->nnz = (int)rcol.size();
+  m->nnz = (int)nnz;
   // stability: the refined rows' bound at a = a_max, against h / sqrt(3 a_max)
   const double h = m->d.h;
   const double lam = std::max(12.0, bound) * m->d.a_max / (h * h);
   m->dt_max = std::min(m->dt_max, 2.0 / std::sqrt(lam));
-  std::vector<int> rrow(rows.begin(), rows.end());
   std::vector<double> k9(81);  // the kernels accumulate six times the pairing (see kGradPairScale)
   for (int q = 0; q < 81; ++q) k9[q] = 6.0 * K9[q];
-  HYB_TRY(upload(m, m->rrow, rrow));
-  HYB_TRY(upload(m, m->rptr, rptr));
-  HYB_TRY(upload(m, m->rcol, rcol));
-  HYB_TRY(upload(m, m->cptr, cptr));
-  HYB_TRY(upload(m, m->cunk, cunk));
-  HYB_TRY(upload(m, m->cw, cw));
+  for (int q = 0; q < 81; ++q) m->uK9[q] = K9[q];
+  for (int q = 0; q < 64; ++q) m->uK8[q] = K8[q];
+  for (int q = 0; q < 9; ++q) m->um9[q] = m9[q];
+  for (int q = 0; q < 8; ++q) m->um8[q] = m8[q];
   HYB_TRY(upload(m, m->rmask, rmask));
+  HYB_TRY(upload(m, m->rcid, cid));
   // z range of the sparse-row nodes of each FEM-owned column
   std::vector<int> rzr((size_t)2 * m->fn[0] * m->fn[1]);
   for (size_t c = 0; c < rzr.size() / 2; ++c) {
@@ -649,10 +655,28 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
         rzr[2 * c + 1] = std::max(rzr[2 * c + 1], m->fl[2] + k);
       }
   HYB_TRY(upload(m, m->rzr, rzr));
+  // tile rows (32 nodes in x at one y and z) holding refined corners, per
+  // interior tile and plane, for the work-item cost model
+  {
+    const int ntx = (m->n[0] - 2 + kTileX - 1) / kTileX, nty = (m->n[1] - 2 + kTileY - 1) / kTileY;
+    m->ref_rows.assign((size_t)ntx * nty * m->n[2], 0);
+    std::vector<unsigned char> seen((size_t)ntx * m->n[1] * m->n[2], 0);
+    for (int k = 0; k < m->fn[2]; ++k)
+      for (int j = 0; j < m->fn[1]; ++j)
+        for (int i = 0; i < m->fn[0]; ++i) {
+          const int x = m->fl[0] + i, y = m->fl[1] + j, z = m->fl[2] + k;
+          if (!rmask[(size_t)(x - m->hx0) + (size_t)m->hpx * (j + (size_t)m->fn[1] * k)]) continue;
+          const int tx = (x - 1) / kTileX, ty = (y - 1) / kTileY;
+          unsigned char& sr = seen[(size_t)tx + (size_t)ntx * (y + (size_t)m->n[1] * z)];
+          if (sr) continue;
+          sr = 1;
+          ++m->ref_rows[((size_t)ty * ntx + tx) * m->n[2] + z];
+        }
+  }
   HYB_TRY(upload(m, m->refvox, refv));
   HYB_TRY(upload(m, m->refvox_id, refid));
   HYB_TRY(upload(m, m->k9, k9));
-  HYB_TRY(ensure(m, m->rval, (size_t)m->nnz * esize(m)));
+  HYB_TRY(ensure(m, m->avox, (size_t)nu * esize(m)));
   return HYB_OK;
 }
 
@@ -704,8 +728,8 @@ hyb_status step_maps(const hyb_mesh* m, StepArgs<T>& A, const DevBuf& field, int
   HYB_TRY(encode_map<T>(&A.tmf, field.p, m->n[0], m->n[1], (uint64_t)m->n[2] * 3 * nsrc, m->px,
                         (uint64_t)m->px * m->n[1], 36, kTileY + 2));
   if (m->fem && m->wsz > 0)
-    HYB_TRY(encode_map<T>(&A.tmw, m->W.p, m->wpx, m->wn[1], 3ull * m->wn[2], m->wpx, (uint64_t)m->wpx * m->wn[1],
-                          36, kTileY + 1));
+    HYB_TRY(encode_map<T>(&A.tmw, m->W.p, m->wpx, m->wn[1], 3ull * m->wn[2] * (m->batch ? nsrc : 1), m->wpx,
+                          (uint64_t)m->wpx * m->wn[1], 36, kTileY + 1));
   if (hist_levels > 0 && m->hbox > 0)
     HYB_TRY(encode_map<T>(&A.tmh, m->hist.p, m->hpx, m->fn[1], (uint64_t)m->fn[2] * nsrc * hist_levels, m->hpx,
                           (uint64_t)m->hpx * m->fn[1], 36, kTileY + 1));
@@ -753,6 +777,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.wait = m->d.wait_cycles == 0 ? (1LL << 29) : (m->d.wait_cycles < 0 ? -1LL : (long long)m->d.wait_cycles);
   A.W = (const T*)m->W.p;
   A.G = (double*)m->G.p;
+  A.avox = (const T*)m->avox.p;
   const double h = m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
   A.r = (T)((h - dt) / (h + dt));
@@ -766,21 +791,32 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
     A.kuhn_v = (const int*)m->kuhn_v.p;
   }
   A.nslots = nslots;
-  A.nlat = m->Np;
   if (m->nc > 0) {
-    A.nr = m->nr;
-    A.nrl = m->nrl;
     A.nref = m->nc;
-    A.rrow = (const int*)m->rrow.p;
-    A.rptr = (const int*)m->rptr.p;
-    A.rcol = (const int*)m->rcol.p;
-    A.rval = (const T*)m->rval.p;
+    A.rcid = (const int*)m->rcid.p;
+    for (int q = 0; q < 81; ++q) A.rK9[q] = (T)m->uK9[q];
+    for (int c = 0; c < 8; ++c) {
+      for (int q = 0; q < 8; ++q) A.rdK[9 * c + q] = (T)(m->uK9[9 * c + q] - m->uK8[8 * c + q]);
+      A.rdK[9 * c + 8] = (T)m->uK9[9 * c + 8];
+      A.rm8[c] = (T)m->um8[c];
+    }
+    for (int q = 0; q < 9; ++q) A.rm9[q] = (T)m->um9[q];
     A.rmask = (const unsigned char*)m->rmask.p;
     A.rzr = (const int*)m->rzr.p;
     A.refvox = (const unsigned char*)m->refvox.p;
     A.refvox_id = (const int*)m->refvox_id.p;
     A.k9 = (const double*)m->k9.p;
   }
+}
+
+// The coefficient of slot s: its edge weights (and their plane in the
+// weight tensor map) and its refined voxels' a; per slot for a batch.
+template <typename T>
+void slot_coef(const hyb_mesh* m, Slot<T>& S, int s) {
+  const int q = m->batch ? s : 0;
+  S.W = (const T*)m->W.p + (size_t)q * 3 * m->wsz;
+  S.zf_w = q * 3 * m->wn[2];
+  S.avox = m->avox.p ? (const T*)m->avox.p + (size_t)q * m->nu : nullptr;
 }
 
 template <typename T>
@@ -814,6 +850,7 @@ void forward_slots(const hyb_mesh* m, StepArgs<T>& A, const hyb_source* src, int
     S.cnext = centre_buf<T>(m, m->CU, nsrc, s, k + 1);
     S.chist_w = (hist_level && m->nc) ? chist_level + (size_t)s * m->nc : nullptr;
     S.chist_r = nullptr;
+    slot_coef<T>(m, S, s);
     set_wave<T>(m, S, src[s], k, dt);
     S.mask_e = 0;
     S.mask_c = 0;
@@ -849,7 +886,7 @@ hyb_status initial_levels(hyb_mesh* m, T* u0, T* um, T* c0, T* cm, cudaStream_t 
 
 template <typename T>
 hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int nsrc, int nsteps,
-                        double dt, T* trace, bool keep) {
+                        double dt, T* trace, bool keep, bool batch = false) {
   const size_t fb = (size_t)m->Np * sizeof(T);
   const int C = m->d.ckpt_every;
   const bool ckpt = C > 0;
@@ -869,21 +906,23 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
       HYB_TRY(ensure(m, m->chist, (size_t)C * nsrc * cb));
     }
   }
+  const int ncoef = batch ? nsrc : 1;  // coefficient sets: one per slot for a batch
+  if (m->fem) HYB_TRY(ensure(m, m->W, (size_t)ncoef * 3 * m->wsz * sizeof(T)));
+  if (m->nc > 0) HYB_TRY(ensure(m, m->avox, (size_t)ncoef * m->nu * sizeof(T)));
+  m->batch = batch;
   StepArgs<T> A;
   base_args(m, A, dt, nsrc);
   HYB_TRY(step_maps<T>(m, A, m->U, nsrc, 0));
   HYB_TRY(step_items<T>(m, A, nsrc, false));
-  if (m->fem) {
-    launch_set_coef<T>(A, (T*)m->W.p, a, m->d.a_max, (int*)m->flag.p, m->st);
-    HYB_LAUNCHED(m);
-  }
+  if (m->fem)
+    for (int q = 0; q < ncoef; ++q) {
+      launch_set_coef<T>(A, (T*)m->W.p + (size_t)q * 3 * m->wsz,
+                         m->nc > 0 ? (T*)m->avox.p + (size_t)q * m->nu : nullptr, a + (size_t)q * m->nu,
+                         m->d.a_max, (int*)m->flag.p, m->st);
+      HYB_LAUNCHED(m);
+    }
   if (A.tet && m->nu > 0)  // the all-FEM rows read a itself
     HYB_CU(cudaMemcpyAsync(m->acopy.p, a, (size_t)m->nu * sizeof(double), cudaMemcpyDeviceToDevice, m->st));
-  if (m->nc > 0) {
-    launch_set_sparse<T>((const int*)m->cptr.p, (const int*)m->cunk.p, (const double*)m->cw.p, a, (T*)m->rval.p,
-                         m->nnz, m->st);
-    HYB_LAUNCHED(m);
-  }
   auto body = [&](cudaStream_t st) -> hyb_status {
     for (int s = 0; s < nsrc; ++s)
       HYB_TRY(initial_levels<T>(m, field_buf<T>(m, m->U, nsrc, s, 0), field_buf<T>(m, m->U, nsrc, s, -1),
@@ -969,6 +1008,7 @@ void adjoint_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const
     S.cnext = centre_buf<T>(m, m->CL, nsrc, s, j);
     S.chist_w = nullptr;
     S.chist_r = (hist_level && m->nc) ? chist_level + (size_t)s * m->nc : nullptr;
+    slot_coef<T>(m, S, s);
     S.src_mask = 0;
     S.zf_cur = (int)((S.cur - (const T*)m->L.p) / ((long long)m->px * m->n[1]));
     S.zf_prev = (int)((S.prev - (const T*)m->L.p) / ((long long)m->px * m->n[1]));
@@ -1005,6 +1045,7 @@ void paper_slots(const hyb_mesh* m, StepArgs<T>& A, const T* cot, int j, const T
     S.obs_face = m->src[s].face;
     S.inj = cot ? cot + ((size_t)s * (nsteps + 1) + j) * (size_t)m->obs_stride : nullptr;
     S.inj_scale = (T)(-m->dt / (h * h * h));
+    slot_coef<T>(m, S, s);
   }
 }
 
@@ -1194,6 +1235,44 @@ hyb_status misfit_impl(hyb_mesh* m, const T* trace, const T* obs, int weights, d
     HYB_CU(cudaMemcpyAsync(m->hscal + 8, (double*)m->scal.p + 8, sizeof(double), cudaMemcpyDeviceToHost, m->st));
     HYB_CU(cudaStreamSynchronize(m->st));
     *J = m->hscal[8];
+  }
+  return HYB_OK;
+}
+
+// Per-slot misfit of a batch: slot s's trace rows reduced on their own (the
+// same launches and summation order as a one-slot mesh), J of slot s to
+// J_host[s] (host, synchronises), cotangent rows as hyb_misfit.
+template <typename T>
+hyb_status misfit_batch_impl(hyb_mesh* m, const T* trace, const T* obs, int weights, double* J_host, T* cot) {
+  if (!m->have_run) return fail(HYB_ERR_STATE, "hyb_misfit_batch needs a preceding forward");
+  const int nsrc = m->nsrc;
+  const size_t rows = (size_t)(m->nsteps + 1) * m->obs_stride;
+  HYB_TRY(ensure(m, m->part, 2 * (size_t)kReduceBlocks * sizeof(double)));
+  HYB_TRY(ensure(m, m->scal, (16 + kMaxSlots) * sizeof(double)));
+  double* out = (double*)m->scal.p + 16;
+  const bool quad = weights == HYB_WEIGHTS_QUADRATURE;
+  for (int s = 0; s < nsrc; ++s) {
+    MisfitGeom g;
+    std::memset(&g, 0, sizeof g);
+    g.n_src = 1;
+    g.nsteps = m->nsteps;
+    g.stride = m->obs_stride;
+    const int ax = m->src[s].face >> 1;
+    g.face[0] = m->src[s].face;
+    g.np[0] = m->n[ax == 0 ? 1 : 0];
+    g.nq[0] = m->n[ax == 2 ? 1 : 2];
+    g.wt = quad ? m->dt : 1.0;
+    g.hh = quad ? m->d.h * m->d.h : 1.0;
+    g.halve = quad ? 1 : 0;
+    launch_misfit<T>(g, trace + s * rows, obs + s * rows, cot ? cot + s * rows : nullptr, (double*)m->part.p, m->st);
+    HYB_LAUNCHED(m);
+    launch_sum((double*)m->part.p, kReduceBlocks, out + s, m->st);
+    HYB_LAUNCHED(m);
+  }
+  if (J_host) {
+    HYB_CU(cudaMemcpyAsync(m->hscal, out, nsrc * sizeof(double), cudaMemcpyDeviceToHost, m->st));
+    HYB_CU(cudaStreamSynchronize(m->st));
+    for (int s = 0; s < nsrc; ++s) J_host[s] = m->hscal[s];
   }
   return HYB_OK;
 }
@@ -1394,7 +1473,7 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   hyb_status st = HYB_OK;
   if (fem) st = ensure(m, m->W, 3 * (size_t)m->wsz * esize(m));
   if (st == HYB_OK) st = ensure(m, m->flag, 2 * sizeof(int));
-  if (st == HYB_OK && cudaMallocHost(&m->hscal, 16 * sizeof(double)) != cudaSuccess) {
+  if (st == HYB_OK && cudaMallocHost(&m->hscal, (16 + kMaxSlots) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     m->hscal = nullptr;
     st = fail(HYB_ERR_OOM, "cudaMallocHost failed");
@@ -1449,8 +1528,8 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   if (!m) return HYB_OK;
   cudaStreamSynchronize(m->st);
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
-                    &m->g, &m->atrial, &m->cot, &m->trace, &m->rrow, &m->rptr, &m->rcol, &m->rval,
-                    &m->cptr, &m->cunk, &m->cw, &m->rmask, &m->rzr, &m->refvox, &m->refvox_id, &m->k9,
+                    &m->g, &m->atrial, &m->cot, &m->trace, &m->rmask, &m->rzr, &m->refvox, &m->refvox_id,
+                    &m->k9, &m->rcid, &m->avox,
                     &m->CU, &m->CL, &m->chist, &m->cckpt, &m->I0, &m->IC0, &m->acopy, &m->kuhn, &m->kuhn_v};
   for (DevBuf* b : bufs) release(*b);
   for (auto& dir : m->items)
@@ -1506,6 +1585,42 @@ hyb_status hyb_set_initial(hyb_mesh* m, const void* u0, const void* u_prev, cons
   return HYB_OK;
 }
 
+hyb_status hyb_forward_batch(hyb_mesh* m, const double* a, const hyb_source* src, int32_t n_src, int32_t nsteps,
+                             double dt, void* trace) {
+  if (!m || !trace) return fail(HYB_ERR_ARG, "null argument");
+  if (m->nu > 0 && !a) return fail(HYB_ERR_ARG, "null coefficient");
+  if (m->d.fem_path == HYB_FEM_TET_ALL) return fail(HYB_ERR_ARG, "no batches on the HYB_FEM_TET_ALL path");
+  HYB_TRY(check_sources(m, src, n_src));
+  HYB_TRY(check_time(m, nsteps, dt));
+  if (m->d.precision == HYB_FP64)
+    return forward_impl<double>(m, a, src, n_src, nsteps, dt, (double*)trace, true, true);
+  return forward_impl<float>(m, a, src, n_src, nsteps, dt, (float*)trace, true, true);
+}
+
+hyb_status hyb_misfit_batch(hyb_mesh* m, const void* trace, const void* u_obs, int32_t weights, double* J_host,
+                            void* cot) {
+  if (!m || !trace || !u_obs) return fail(HYB_ERR_ARG, "null argument");
+  if (weights != HYB_WEIGHTS_PLAIN && weights != HYB_WEIGHTS_QUADRATURE) return fail(HYB_ERR_ARG, "bad weights");
+  if (m->d.precision == HYB_FP64)
+    return misfit_batch_impl<double>(m, (const double*)trace, (const double*)u_obs, weights, J_host, (double*)cot);
+  return misfit_batch_impl<float>(m, (const float*)trace, (const float*)u_obs, weights, J_host, (float*)cot);
+}
+
+hyb_status hyb_gradient_batch(hyb_mesh* m, const double* a, double gamma, double a0, double* g_out) {
+  if (!m) return fail(HYB_ERR_ARG, "null mesh");
+  if (m->nu > 0 && (!a || !g_out)) return fail(HYB_ERR_ARG, "null coefficient or output");
+  if (!m->have_adj) return fail(HYB_ERR_STATE, "hyb_gradient_batch needs a preceding hyb_adjoint");
+  if (!m->batch) return fail(HYB_ERR_STATE, "hyb_gradient_batch needs a preceding hyb_forward_batch");
+  if (m->nu == 0) return HYB_OK;
+  const double h = m->d.h;
+  for (int s = 0; s < m->nsrc; ++s) {
+    launch_grad_finalize((const double*)m->G.p + (size_t)s * m->nu, 1, a + (size_t)s * m->nu, grad_scale(m), gamma,
+                         h * h * h, a0, g_out + (size_t)s * m->nu, m->nu, m->st);
+    HYB_LAUNCHED(m);
+  }
+  return HYB_OK;
+}
+
 hyb_status hyb_adjoint(hyb_mesh* m, const void* cot, int32_t accumulate) {
   if (!m || !cot) return fail(HYB_ERR_ARG, "null argument");
   if (m->d.precision == HYB_FP64) return adjoint_impl<double>(m, (const double*)cot, accumulate);
@@ -1516,6 +1631,7 @@ hyb_status hyb_gradient(hyb_mesh* m, const double* a, double gamma, double a0, d
   if (!m) return fail(HYB_ERR_ARG, "null mesh");
   if (m->nu > 0 && (!a || !g_out)) return fail(HYB_ERR_ARG, "null coefficient or output");
   if (!m->have_adj) return fail(HYB_ERR_STATE, "hyb_gradient needs a preceding hyb_adjoint");
+  if (m->batch) return fail(HYB_ERR_STATE, "the last forward was a batch: use hyb_gradient_batch");
   if (m->nu == 0) return HYB_OK;
   const double h = m->d.h;
   launch_grad_finalize((const double*)m->G.p, m->nsrc, a, grad_scale(m), gamma, h * h * h, a0, g_out, m->nu, m->st);

@@ -54,6 +54,12 @@ struct Slot {
   const T* chist_r;  // adjoint: centre values of u^j (or nullptr)
   int zf_cur, zf_prev;  // plane 0 of cur / prev in the field tensor map (tmf)
   int zf_hist;          // plane 0 of hist_r's box in the history tensor map (tmh)
+  // the slot's coefficient: edge weights [3][wsz] (plane 0 of its x array in
+  // the weight tensor map tmw) and the refined voxels' a; one set shared by
+  // every slot, or one per slot for batches of independent problems
+  const T* W;
+  int zf_w;
+  const T* avox;
 };
 
 // Lattice fields are stored with a row pitch px >= nx (a multiple of 4, so
@@ -76,7 +82,7 @@ struct StepArgs {
   int wx0, wpx;      // x origin and row pitch of the edge-weight arrays
   long long wsz;     // entries per axis array of the edge-weight box (wpx wn1 wn2)
   int hx0, hpx;      // x origin and row pitch of the FEM-owned (history) box
-  const T* W;        // [3][wsz]: weight of the edge (p, p + e_axis)
+  const T* W;        // [3][wsz]: weight of the edge (p, p + e_axis) (of slot 0)
   double* G;         // FP64 gradient accumulator over unknown voxels (adjoint)
   int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
   T c2;              // tau^2 / h^2
@@ -89,20 +95,25 @@ struct StepArgs {
   int nedge;         // edge tiles (128 nodes) per slot
   int nhe, nhr;      // step kernel: leading blocks of edge tiles, then of refined rows
   int nslots;
-  // refined region (nr == 0: nothing refined).  Sparse rows: the nrl
-  // lattice nodes touching a refined voxel, then the nref centre nodes.
-  int nr, nrl, nref;
-  long long nlat;             // lattice field entries (column ids >= nlat are centres)
-  const int* rrow;            // lattice id of each lattice sparse row
-  const int* rptr;            // CSR row pointers [nr + 1]
-  const int* rcol;            // column: lattice id, or nlat + centre index
-  const T* rval;              // weight W_ij of the off-diagonal entries
-  const unsigned char* rmask; // FEM-owned box: 1 = node updated by a sparse row
+  // refined region (nref == 0: nothing refined): unknown voxels bisected
+  // once (12 tetrahedra around a centre node).  The interior blocks evaluate
+  // the rows of their corners (the stencil row corrected by the refined
+  // voxels around the node) and of their centres from the staged planes.
+  int nref;                   // refined voxels (= centre nodes)
+  const unsigned char* rmask; // FEM-owned box: 1 = the node is a corner of a refined voxel
   const int* rzr;             // per FEM-owned column (i - fl0) + fn0 (j - fl1): [kmin, kmax] of its
-                              // sparse-row nodes (kmin > kmax: none); refined voxels lie inside
+                              // refined corners (kmin > kmax: none)
+  const int* rcid;            // per unknown voxel: its centre id if refined, else -1
+  const T* avox;              // per unknown voxel: the coefficient a (of slot 0; slots carry their own)
   const unsigned char* refvox;// unknown voxels: 1 = refined
   const int* refvox_id;       // unknown id of each refined voxel (centre order)
-  const double* k9;           // 9 x 9 stiffness of a refined unit voxel, a = 1
+  const double* k9;           // 9 x 9 stiffness of a refined unit voxel, a = 1 (level-0 pairing)
+  // unit-voxel tables (a = 1, corners a + 2b + 4c, centre 8): K9 of the
+  // refined voxel, dK[c][q] = K9[c][q] - K8[c][q] (q = 8: K9[c][8]) against
+  // the Kuhn voxel, and the lumped masses of both
+  T rK9[81];
+  T rdK[72];
+  T rm9[9], rm8[8];
   // fem_path HYB_FEM_TET_ALL: every interior node's row gathered over the Kuhn
   // tetrahedra of its voxels (the all-node kernels run every level)
   int tet;
@@ -124,22 +135,19 @@ int step_blocks_per_sm(int precision, int adjoint);
 // G[c] += voxel pairing of (u^0 in hist box, lambda^1) for one slot.
 template <typename T>
 void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t st);
-// Edge weights W from the per-voxel coefficient; raises *flag when a value
+// Edge weights W from the per-voxel coefficient (and, if avox is set, the
+// coefficient itself in the field precision); raises *flag when a value
 // exceeds a_max or is not finite.
 template <typename T>
-void launch_set_coef(const StepArgs<T>& a, T* W, const double* acoef, double a_max, int* flag,
+void launch_set_coef(const StepArgs<T>& a, T* W, T* avox, const double* acoef, double a_max, int* flag,
                      cudaStream_t st);
-// (The sparse rows of the refined region, identical for the forward and the
+// (The rows of the refined region, identical for the forward and the
 // mass-scaled adjoint, and the adjoint's gradient pairing of refined voxels
-// run in blocks of the step kernel.)
+// run in the interior blocks of the step kernel.)
 // Gradient pairing of refined voxels for level 0 (u^0 from the history
 // slots `hist`/`chist`, lambda^1 as the slots' cur/ccur).
 template <typename T>
 void launch_refined_pair(const StepArgs<T>& a, cudaStream_t st);
-// rval[e] = sum over the contributions of entry e of a(unk) * w (a = 1 for unk < 0).
-template <typename T>
-void launch_set_sparse(const int* cptr, const int* cunk, const double* cw, const double* acoef, T* rval, int nnz,
-                       cudaStream_t st);
 // Trace row of face f (c_p + n_p c_q order) from a lattice field.
 template <typename T>
 void launch_extract_face(const StepArgs<T>& a, const T* field, int f, T* row, cudaStream_t st);

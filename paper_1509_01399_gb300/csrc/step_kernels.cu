@@ -110,12 +110,12 @@ __device__ __forceinline__ long long widx(const StepArgs<T>& A, int i, int j, in
 
 // sum over the six axis edges of W_e (u_nb - u_c) at a FEM-owned node
 template <typename T>
-__device__ __forceinline__ T fem_lap(const StepArgs<T>& A, const T* __restrict__ u, long long id,
+__device__ __forceinline__ T fem_lap(const StepArgs<T>& A, const T* __restrict__ Wb, const T* __restrict__ u, long long id,
                                      int i, int j, int k, T c, T zm, T zp) {
   const long long w = widx(A, i, j, k);
-  const T* Wx = A.W;
-  const T* Wy = A.W + A.wsz;
-  const T* Wz = A.W + 2 * A.wsz;
+  const T* Wx = Wb;
+  const T* Wy = Wb + A.wsz;
+  const T* Wz = Wb + 2 * A.wsz;
   const long long wy = A.wpx;
   const long long wz = (long long)A.wpx * A.wn[1];
   return Wx[w] * (u[id + 1] - c) + Wx[w - 1] * (u[id - 1] - c) + Wy[w] * (u[id + A.px] - c) +
@@ -215,12 +215,13 @@ __device__ __forceinline__ T tet_pair(const StepArgs<T>& A, const T* __restrict_
 // FEM stencil on FEM-owned nodes, 7-point with mirror ghosts elsewhere (on
 // the all-FEM path, the gathered FEM row on every interior node).
 template <typename T>
-__device__ __noinline__ T row_lap(const StepArgs<T>& A, const T* __restrict__ u, int i, int j, int k) {
+__device__ __noinline__ T row_lap(const StepArgs<T>& A, const T* __restrict__ W, const T* __restrict__ u, int i, int j,
+                                  int k) {
   if (A.tet && lattice_interior(A, i, j, k)) return tet_row<T>(A, u, i, j, k, 0, 0, 0);
   const long long id = lin(A, i, j, k);
   const long long sz = (long long)A.px * A.ny;
   const T c = u[id];
-  if (fem_owned(A, i, j, k)) return fem_lap(A, u, id, i, j, k, c, u[id - sz], u[id + sz]);
+  if (fem_owned(A, i, j, k)) return fem_lap(A, W, u, id, i, j, k, c, u[id - sz], u[id + sz]);
   T lap = T(0);
   if (i == 0) lap += T(2) * (u[id + 1] - c);
   else if (i == A.nx - 1) lap += T(2) * (u[id - 1] - c);
@@ -259,7 +260,7 @@ __device__ __noinline__ T fwd_new(const StepArgs<T>& A, const Slot<T>& S, int i,
     }
   }
   const T c = S.cur[id];
-  T v = c + ((c - S.prev[id]) + A.c2 * row_lap(A, S.cur, i, j, k));
+  T v = c + ((c - S.prev[id]) + A.c2 * row_lap(A, S.W, S.cur, i, j, k));
   if (fall & S.src_mask) v += src_terms(S, fall, i, j, k);
   if (S.inj) v += inj_term(S, fall, i, j, k, A.nx, A.ny);
   return v;
@@ -268,11 +269,12 @@ __device__ __noinline__ T fwd_new(const StepArgs<T>& A, const Slot<T>& S, int i,
 // Coefficient of the non-absorbing row of node (i,j,k) on its neighbour
 // (i,j,k) + s e_ax (Laplacian part, without 1/h^2).
 template <typename T>
-__device__ __forceinline__ T row_coef(const StepArgs<T>& A, int i, int j, int k, int ax, int s) {
+__device__ __forceinline__ T row_coef(const StepArgs<T>& A, const T* __restrict__ W, int i, int j, int k, int ax,
+                                      int s) {
   if (fem_owned(A, i, j, k)) {
     const long long w = widx(A, i, j, k);
     const long long ws = ax == 0 ? 1 : (ax == 1 ? (long long)A.wpx : (long long)A.wpx * A.wn[1]);
-    return A.W[ax * A.wsz + (s > 0 ? w : w - ws)];
+    return W[ax * A.wsz + (s > 0 ? w : w - ws)];
   }
   const int c = ax == 0 ? i : (ax == 1 ? j : k);
   const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
@@ -281,12 +283,11 @@ __device__ __forceinline__ T row_coef(const StepArgs<T>& A, int i, int j, int k,
 }
 
 template <typename T>
-__device__ __forceinline__ T row_diag(const StepArgs<T>& A, int i, int j, int k) {
+__device__ __forceinline__ T row_diag(const StepArgs<T>& A, const T* __restrict__ W, int i, int j, int k) {
   if (fem_owned(A, i, j, k)) {
     const long long w = widx(A, i, j, k);
     const long long wy = A.wpx;
     const long long wz = (long long)A.wpx * A.wn[1];
-    const T* W = A.W;
     return -(W[w] + W[w - 1] + W[A.wsz + w] + W[A.wsz + w - wy] + W[2 * A.wsz + w] +
              W[2 * A.wsz + w - wz]);
   }
@@ -309,7 +310,7 @@ __device__ __noinline__ T adj_rhs(const StepArgs<T>& A, const Slot<T>& S, int i,
   const int fbm = face_bits(i, j, k, A.nx, A.ny, A.nz);
   T rhs;
   if (fbm & S.mask_f) rhs = A.r * l1[id];
-  else rhs = (T(2) + A.c2 * row_diag(A, i, j, k)) * l1[id];
+  else rhs = (T(2) + A.c2 * row_diag(A, S.W, i, j, k)) * l1[id];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
 #pragma unroll
@@ -327,7 +328,7 @@ __device__ __noinline__ T adj_rhs(const StepArgs<T>& A, const Slot<T>& S, int i,
         const int f = 2 * ax + (s > 0 ? 1 : 0);
         if (fbn & (1 << f)) rhs += l1[nid] / T(__popc(fbn));
       } else {
-        rhs += A.c2 * row_coef(A, ni, nj, nk, ax, -s) * l1[nid];
+        rhs += A.c2 * row_coef(A, S.W, ni, nj, nk, ax, -s) * l1[nid];
       }
     }
   }
@@ -384,7 +385,7 @@ __device__ __forceinline__ T adj_rhs_inl(const StepArgs<T>& A, const Slot<T>& S,
   const long long wy = A.wpx, wz = (long long)A.wpx * A.wn[1];
   const bool fo = fem_owned(A, i, j, k);
   const long long w = fo ? widx(A, i, j, k) : 0;
-  const T* W = A.W;
+  const T* W = S.W;
   T wd[6];  // this node's edge weights (FEM-owned nodes)
   wd[0] = fo ? W[w] : T(0);
   wd[1] = fo ? W[w - 1] : T(0);
@@ -507,11 +508,12 @@ __device__ __forceinline__ T lap7(T xm, T xp, T ym, T yp, T zm, T zp, T c) {
 
 // Laplacian part of a non-absorbing row (inlined form of row_lap).
 template <typename T>
-__device__ __forceinline__ T row_lap_inl(const StepArgs<T>& A, const T* __restrict__ u, int i, int j, int k) {
+__device__ __forceinline__ T row_lap_inl(const StepArgs<T>& A, const T* __restrict__ W, const T* __restrict__ u, int i,
+                                         int j, int k) {
   const long long id = lin(A, i, j, k);
   const long long sz = (long long)A.px * A.ny;
   const T c = u[id];
-  if (fem_owned(A, i, j, k)) return fem_lap(A, u, id, i, j, k, c, u[id - sz], u[id + sz]);
+  if (fem_owned(A, i, j, k)) return fem_lap(A, W, u, id, i, j, k, c, u[id - sz], u[id + sz]);
   const T xm = i > 0 ? u[id - 1] : u[id + 1];
   const T xp = i < A.nx - 1 ? u[id + 1] : u[id - 1];
   const T ym = j > 0 ? u[id - A.px] : u[id + A.px];
@@ -622,7 +624,8 @@ struct Col {
   int si, i, j;
   int dxs, dys;   // -1 / +1: one node inside the low / high face of x, y; 0: not
   bool xy_fem;    // (i, j) inside the FEM-owned range
-  bool xy_vox;    // (i, j) is the x-y origin of an unknown voxel and the step pairs
+  bool xy_uv;     // (i, j) is the x-y origin of an unknown voxel
+  bool xy_vox;    // ... and the step pairs
   int rz0, rz1;   // z range of the column's sparse-row nodes (rz0 > rz1: none)
 };
 
@@ -743,9 +746,94 @@ struct Producer {
     T* w = WR + (q & (P::SW - 1)) * 3 * P::WS;
     const int zq = q - A->wl[2];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) tma_load_3d(w + a * P::WS, &A->tmw, xw, yw, a * A->wn[2] + zq, bar);
+    for (int a = 0; a < 3; ++a) tma_load_3d(w + a * P::WS, &A->tmw, xw, yw, S->zf_w + a * A->wn[2] + zq, bar);
   }
 };
+
+// The row of a corner n = (i, j, k) of refined voxels (Eq. (fem) on the
+// locally refined mesh): the stencil row lapW of the Kuhn voxels (edge
+// weights over all voxels around n), corrected on every refined voxel v
+// around n by a_v (K9 - K8) of n's corner in v (its centre included) and
+// divided by the lumped mass of n in units of h^3 (the Kuhn corner masses,
+// or the bisected voxel's where refined).  Neighbours from the staged planes
+// Cm, Ck, Cp (n at offset 0), centres from the centre level `cen`.
+template <typename T>
+__device__ __noinline__ T refined_lap(const StepArgs<T>& A, const T* __restrict__ avox, const T* __restrict__ cen, int i,
+                                      int j, int k, const T* Cm, const T* Ck, const T* Cp, T lapW, T c0) {
+  // the eight voxels' centre ids, then their coefficients and centre values:
+  // independent loads issued together (voxel ids from the one of corner 0)
+  const int ox = i - A.fl[0], oy = j - A.fl[1], oz = k - A.fl[2];
+  const int v0 = ox + A.un[0] * (oy + A.un[1] * oz), sy = A.un[0], sz = A.un[0] * A.un[1];
+  int rc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    const bool in = ox - dx >= 0 && oy - dy >= 0 && oz - dz >= 0 && ox - dx < A.un[0] && oy - dy < A.un[1] &&
+                    oz - dz < A.un[2];
+    rc[c] = in ? A.rcid[v0 - dx - dy * sy - dz * sz] : -1;
+  }
+  T av[8], uc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int v = v0 - (c & 1) - ((c >> 1) & 1) * sy - (c >> 2) * sz;
+    av[c] = rc[c] >= 0 ? avox[v] : T(0);
+    uc[c] = rc[c] >= 0 ? cen[rc[c]] : T(0);
+  }
+  T corr = T(0), mass = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    if (rc[c] < 0) {
+      mass += A.rm8[c];
+      continue;
+    }
+    mass += A.rm9[c];
+    T sv = A.rdK[9 * c + 8] * (uc[c] - c0);
+    // K9 - K8 couples the diagonal corners 0 and 7 to the six others and
+    // the six others to 0 and 7 only (the other entries vanish)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool diag_c = c == 0 || c == 7, diag_q = q == 0 || q == 7;
+      if (q == c || diag_c == diag_q) continue;
+      const int qx = (q & 1) - dx, qy = ((q >> 1) & 1) - dy, qz = (q >> 2) - dz;
+      const T* pl = qz < 0 ? Cm : (qz > 0 ? Cp : Ck);
+      sv += A.rdK[9 * c + q] * (pl[qx + qy * kBoxX] - c0);
+    }
+    corr += av[c] * sv;
+  }
+  return (lapW - corr) / mass;
+}
+
+// Refined voxel rc (unknown voxel vid) whose origin is the interior node at
+// offset 0 of the staged planes Ck (its plane) and Cp (the next): its centre
+// row (Eq. (fem) on the twelve tetrahedra around the centre), and in the
+// transposed step with pairing its gradient pairing u^T K9 lambda over the
+// corners (u from the staged history Hk, Hp) and the centre.
+template <typename T, bool ADJ>
+__device__ __noinline__ void refined_voxel(const StepArgs<T>& A, const Slot<T>& S, int si, int rc, int vid, bool pair,
+                                           const T* Ck, const T* Cp, const T* Hk, const T* Hp) {
+  const T q[8] = {Ck[0], Ck[1], Ck[kBoxX], Ck[kBoxX + 1], Cp[0], Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
+  const T uc = S.ccur[rc];
+  T sv = T(0);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) sv += A.rK9[72 + p] * (q[p] - uc);
+  const T vc = uc + ((uc - S.cprev[rc]) - A.c2 * S.avox[vid] * sv / A.rm9[8]);
+  S.cnext[rc] = vc;
+  if (!ADJ && S.chist_w) S.chist_w[rc] = vc;
+  if (ADJ && pair) {
+    const T u[9] = {Hk[0], Hk[1], Hk[kBoxX], Hk[kBoxX + 1], Hp[0], Hp[1], Hp[kBoxX], Hp[kBoxX + 1], S.chist_r[rc]};
+    T pr = T(0);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      T row = A.rK9[9 * p + 8] * uc;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) row += A.rK9[9 * p + j] * q[j];
+      pr += u[p] * row;
+    }
+    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+    atomicAdd(A.G + (long long)si * nv + vid, (double)(T(kGradPairScale) * pr));
+  }
+}
 
 // One node (i, j, k) of an interior block from the staged planes: Ck, Cm, Cp
 // are this node in the u^k boxes of planes k, k-1, k+1, Pk in the u^{k-1}
@@ -754,7 +842,7 @@ struct Producer {
 // one step inside a z face (dzs = -1 / +1: the low / high one) and the node
 // also produces the face node next to it.  Tiles without FACE hold no node
 // one step inside an x or y face.
-template <typename T, bool ADJ, bool FEMT, bool FACE, bool ZF>
+template <typename T, bool ADJ, bool FEMT, bool FACE, bool ZF, bool REF>
 __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T>& S, T* __restrict__ gnext,
                                               const Col& C, int k, int off, int dzs, const T* Ck, const T* Cm,
                                               const T* Cp, const T* Pk, const T* Wk, const T* Wm, const T* Hk,
@@ -776,8 +864,12 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     wyp = Wk[P::WS];
     wzp = Wk[2 * P::WS];
     wzm = Wm[2 * P::WS];
-    const T lap =
+    T lap =
         wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + wzp * (cp - c0) + wzm * (cm - c0);
+    if constexpr (REF) {
+      if (k >= C.rz0 && k <= C.rz1 && A.rmask[(C.i - A.hx0) + A.hpx * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]))])
+        lap = refined_lap(A, S.avox, S.ccur, C.i, C.j, k, Cm, Ck, Cp, lap, c0);
+    }
     val = c0 + ((c0 - pv) + c2 * lap);
   } else if constexpr (sizeof(T) == 4) {  // unit weights: the neighbour sum minus 6 u^k
     val = c0 + ((c0 - pv) + c2 * ((((xm + xp) + (ym + yp)) + (cm + cp)) - T(6) * c0));
@@ -871,19 +963,23 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     return;
   }
   const int bo = (C.i - A.hx0) + A.hpx * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]));
-  const bool rz = k >= C.rz0 && k <= C.rz1;  // the column has sparse-row nodes here
-  if (!(rz && A.rmask[bo])) {  // sparse rows are written by the refined rows
-    gnext[off] = val;
-    if (!ADJ && S.hist_w) S.hist_w[bo] = val;
+  gnext[off] = val;
+  if (!ADJ && S.hist_w) S.hist_w[bo] = val;
+  // the voxel with origin (i, j, k): the centre row if it is refined, and
+  // (transposed step with pairing) its gradient pairing
+  const int vz = A.un[0] * A.un[1];
+  const bool vox = C.xy_uv && k < A.fl[2] + A.un[2];
+  const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
+  int rc = -1;
+  if constexpr (REF) {
+    rc = (vox && k >= C.rz0 && k <= C.rz1) ? A.rcid[vid] : -1;
+    if (rc >= 0) refined_voxel<T, ADJ>(A, S, C.si, rc, vid, C.xy_vox, Ck, Cp, Hk, Hp);
   }
   if constexpr (ADJ) {
-    if (C.xy_vox && k < A.fl[2] + A.un[2]) {
+    if (C.xy_vox && vox && rc < 0) {
       const T u[8] = {Hk[0], Hk[1], Hk[kBoxX], Hk[kBoxX + 1], Hp[0], Hp[1], Hp[kBoxX], Hp[kBoxX + 1]};
       const T l[8] = {c0, xp, yp, Ck[kBoxX + 1], cp, Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
-      const int vz = A.un[0] * A.un[1];
-      const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
-      if (!(rz && A.refvox[vid]))
-        atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
+      atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
     }
   }
 }
@@ -975,7 +1071,7 @@ __device__ __forceinline__ void xface_levels(const StepArgs<T>& A, const Slot<T>
 // Consumer loop of an interior block, specialised by whether the tile meets
 // the FEM block (FEMT) and whether it holds nodes one step inside an x or y
 // face (FACE).  Each consumer thread owns two tile rows (ty and ty + 8).
-template <typename T, bool ADJ, bool FEMT, bool FACE>
+template <typename T, bool ADJ, bool FEMT, bool FACE, bool REF>
 __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot<T>& S, const Col (&C)[2],
                                                 const Producer<T, !FEMT>& pr, const bool (&active)[2],
                                                 const XFace& X, int z0, int z1) {
@@ -1051,17 +1147,17 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     const int dzs = k == 1 ? -1 : (k == nz - 2 ? 1 : 0);
     if (dzs != 0) {
       if (act0)
-        interior_node<T, ADJ, FEMT, FACE, true>(A, S, gnext, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0,
+        interior_node<T, ADJ, FEMT, FACE, true, REF>(A, S, gnext, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0,
                                                 Pk + o0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
       if (act1)
-        interior_node<T, ADJ, FEMT, FACE, true>(A, S, gnext, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1,
+        interior_node<T, ADJ, FEMT, FACE, true, REF>(A, S, gnext, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1,
                                                 Pk + o1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
     } else {
       if (act0)
-        interior_node<T, ADJ, FEMT, FACE, false>(A, S, gnext, C[0], k, off0, 0, Ck + o0, Cm + o0, Cp + o0,
+        interior_node<T, ADJ, FEMT, FACE, false, REF>(A, S, gnext, C[0], k, off0, 0, Ck + o0, Cm + o0, Cp + o0,
                                                  Pk + o0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
       if (act1)
-        interior_node<T, ADJ, FEMT, FACE, false>(A, S, gnext, C[1], k, off1, 0, Ck + o1, Cm + o1, Cp + o1,
+        interior_node<T, ADJ, FEMT, FACE, false, REF>(A, S, gnext, C[1], k, off1, 0, Ck + o1, Cm + o1, Cp + o1,
                                                  Pk + o1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
     }
     __syncwarp();  // the warp's reads of level k's stages are done
@@ -1103,8 +1199,9 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
     C[r].dys = (C[r].j == 1) ? -1 : (C[r].j == ny - 2 ? 1 : 0);
     active[r] = t < kTileX * kTileY / 2 && C[r].i <= nx - 2 && C[r].j <= ny - 2 && !(C[r].dxs != 0 && C[r].dys != 0);
     C[r].xy_fem = has_fem && C[r].i >= A.fl[0] && C[r].i <= A.fh[0] && C[r].j >= A.fl[1] && C[r].j <= A.fh[1];
-    C[r].xy_vox = pairing && C[r].i >= A.fl[0] && C[r].i < A.fl[0] + A.un[0] && C[r].j >= A.fl[1] &&
-                  C[r].j < A.fl[1] + A.un[1];
+    C[r].xy_uv = has_fem && C[r].i >= A.fl[0] && C[r].i < A.fl[0] + A.un[0] && C[r].j >= A.fl[1] &&
+                 C[r].j < A.fl[1] + A.un[1];
+    C[r].xy_vox = pairing && C[r].xy_uv;
     C[r].rz0 = 1;
     C[r].rz1 = 0;
     if (A.rzr && C[r].xy_fem) {
@@ -1144,25 +1241,35 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   }
   pdl_wait();  // the previous level is complete: its output may be read, its input overwritten
   __syncthreads();
+  // items whose columns hold refined-voxel corners in their z range take the
+  // variant with the refined rows (block-uniform)
+  const bool ref_tile =
+      __syncthreads_or(fem_tile && t < kTileX * kTileY / 2 &&
+                       ((C[0].rz0 <= C[0].rz1 && C[0].rz0 < z1 && C[0].rz1 >= z0) ||
+                        (C[1].rz0 <= C[1].rz1 && C[1].rz0 < z1 && C[1].rz1 >= z0)));
   if (fem_tile) {
     Producer<T, false> pr;
     pr.setup(A, S, sm, full, z0, z1, i0, j0, pairing);
-    if (face_tile)
-      interior_levels<T, ADJ, true, true>(A, S, C, pr, active, X, z0, z1);
-    else
-      interior_levels<T, ADJ, true, false>(A, S, C, pr, active, X, z0, z1);
+    if (ref_tile) {
+      if (face_tile)
+        interior_levels<T, ADJ, true, true, true>(A, S, C, pr, active, X, z0, z1);
+      else
+        interior_levels<T, ADJ, true, false, true>(A, S, C, pr, active, X, z0, z1);
+    } else {
+      if (face_tile)
+        interior_levels<T, ADJ, true, true, false>(A, S, C, pr, active, X, z0, z1);
+      else
+        interior_levels<T, ADJ, true, false, false>(A, S, C, pr, active, X, z0, z1);
+    }
   } else {
     Producer<T, true> pr;
     pr.setup(A, S, sm, full, z0, z1, i0, j0, false);
     if (face_tile)
-      interior_levels<T, ADJ, false, true>(A, S, C, pr, active, X, z0, z1);
+      interior_levels<T, ADJ, false, true, false>(A, S, C, pr, active, X, z0, z1);
     else
-      interior_levels<T, ADJ, false, false>(A, S, C, pr, active, X, z0, z1);
+      interior_levels<T, ADJ, false, false, false>(A, S, C, pr, active, X, z0, z1);
   }
 }
-
-template <typename T, bool ADJ>
-__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t, const T* k9);
 
 // Edge tile of the forward step.  Levels by the number of faces a node lies
 // on: nodes on no face take their interior row, then face, edge and corner
@@ -1188,7 +1295,7 @@ __device__ __forceinline__ void fwd_edge_tile(const StepArgs<T>& A, int si, int 
   }
   T plain = T(0);  // the non-absorbing row, from level-k data only
   if (valid && !fb) {
-    plain = cself + ((cself - S.prev[id]) + A.c2 * row_lap_inl(A, S.cur, i, j, k));
+    plain = cself + ((cself - S.prev[id]) + A.c2 * row_lap_inl(A, S.W, S.cur, i, j, k));
     if (fall & S.src_mask) plain += src_terms(S, fall, i, j, k);
     if (S.inj) plain += inj_term(S, fall, i, j, k, A.nx, A.ny);
   }
@@ -1278,18 +1385,7 @@ __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kerne
       fwd_edge_tile<T>(A, si, blk, t, sh + 128 * half);
     return;
   }
-  b -= A.nhe;
-  if (b < A.nhr) {
-    pdl_wait();
-    if constexpr (ADJ) {  // the refined-voxel stiffness for the pairing threads, in shared memory
-      if (A.k9)
-        for (int q = (int)threadIdx.x; q < 81; q += kStepBlock) sh[q] = (T)A.k9[q];
-      __syncthreads();
-    }
-    refined_rows<T, ADJ>(A, (long long)b * kStepBlock + threadIdx.x, sh);
-    return;
-  }
-  interior_block<T, ADJ>(A, b - A.nhr, sh);
+  interior_block<T, ADJ>(A, b - A.nhe, sh);
 }
 
 // Lattices with fewer than 5 nodes on some axis: every node by the generic
@@ -1377,76 +1473,6 @@ __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* 
   return acc;
 }
 
-// Refined region of one time level (run by the trailing blocks of the edge
-// launch).  Threads [0, nr): the sparse rows,
-// u^{k+1}_i = 2 u^k_i - u^{k-1}_i + tau^2/h^2 sum_j W_ij (u^k_j - u^k_i),
-// lattice rows into the field, centre rows into the centre array (the
-// adjoint runs the same rows on the mass-scaled lambda).  Adjoint threads
-// [nr, nr + nref): gradient pairing of the refined voxels.
-template <typename T, bool ADJ>
-__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t, const T* k9) {
-  // per slot: 4 lanes per sparse row, then (adjoint) one thread per refined
-  // voxel, padded to a multiple of 4 so row lane groups stay warp aligned
-  const int per = 4 * A.nr + (ADJ ? ((A.nref + 3) & ~3) : 0);
-  if (t >= (long long)per * A.nslots) return;
-  const int si = (int)(t / per);
-  const int r4 = (int)(t - (long long)si * per);
-  const Slot<T>& S = A.s[si];
-  if (r4 < 4 * A.nr) {
-    const int r = r4 >> 2, lane = r4 & 3;
-    const bool lat = r < A.nrl;
-    const long long self = lat ? (long long)A.rrow[r] : 0;
-    const T ui = lat ? S.cur[self] : S.ccur[r - A.nrl];
-    T acc = T(0);
-    const int e1 = A.rptr[r + 1];
-    // four of the lane's entries at a time: their column ids, weights and
-    // values are loaded before any is summed (same summation order)
-    for (int e = A.rptr[r] + lane; e < e1; e += 16) {
-      int cu[4];
-      T wu[4], uu[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool on = e + 4 * u < e1;
-        cu[u] = on ? A.rcol[e + 4 * u] : -1;
-        wu[u] = on ? A.rval[e + 4 * u] : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool lat_col = cu[u] < A.nlat;
-        const T* base = lat_col ? S.cur : S.ccur;
-        const long long ci = lat_col ? (long long)cu[u] : (long long)cu[u] - A.nlat;
-        uu[u] = cu[u] >= 0 ? base[ci] : ui;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (cu[u] >= 0) acc += wu[u] * (uu[u] - ui);
-    }
-    const unsigned grp = 0xFu << (threadIdx.x & 28);
-    acc += __shfl_xor_sync(grp, acc, 1);
-    acc += __shfl_xor_sync(grp, acc, 2);
-    if (lane) return;
-    const T pi = lat ? S.prev[self] : S.cprev[r - A.nrl];
-    const T val = ui + ((ui - pi) + A.c2 * acc);
-    if (lat) {
-      S.next[self] = val;
-      if (!ADJ && S.hist_w) {
-        const int i = (int)(self % A.px), j = (int)((self / A.px) % A.ny), k = (int)(self / ((long long)A.px * A.ny));
-        S.hist_w[hidx(A, i, j, k)] = val;
-      }
-    } else {
-      S.cnext[r - A.nrl] = val;
-      if (!ADJ && S.chist_w) S.chist_w[r - A.nrl] = val;
-    }
-    return;
-  }
-  if constexpr (ADJ) {
-    const int v = r4 - 4 * A.nr;
-    if (!S.hist_r || v >= A.nref) return;
-    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
-    A.G[(long long)si * nv + A.refvox_id[v]] += (double)refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur, k9);
-  }
-}
-
 template <typename T>
 __global__ void refined_pair_kernel(const __grid_constant__ StepArgs<T> A) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1459,24 +1485,14 @@ __global__ void refined_pair_kernel(const __grid_constant__ StepArgs<T> A) {
 }
 
 template <typename T>
-__global__ void set_sparse_kernel(const int* __restrict__ cptr, const int* __restrict__ cunk,
-                                  const double* __restrict__ cw, const double* __restrict__ a, T* __restrict__ rval,
-                                  int nnz) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nnz) return;
-  double v = 0.0;
-  for (int q = cptr[e]; q < cptr[e + 1]; ++q) v += (cunk[q] >= 0 ? a[cunk[q]] : 1.0) * cw[q];
-  rval[e] = (T)v;
-}
-
-template <typename T>
-__global__ void set_coef_kernel(const __grid_constant__ StepArgs<T> A, T* __restrict__ W,
+__global__ void set_coef_kernel(const __grid_constant__ StepArgs<T> A, T* __restrict__ W, T* __restrict__ avox,
                                 const double* __restrict__ a, double a_max, int* flag) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
   if (t < nv) {
     const double v = a[t];
     if (!(v <= a_max * (1.0 + 1e-12)) || !(v == v)) atomicExch(flag, 1);
+    if (avox) avox[t] = (T)v;
   }
   if (t >= A.wsz) return;
   const int p[3] = {A.wx0 + (int)(t % A.wpx), A.wl[1] + (int)((t / A.wpx) % A.wn[1]),
@@ -1541,12 +1557,6 @@ void launch_extract_face(const StepArgs<T>& a, const T* field, int f, T* row, cu
   extract_face_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(a, field, f, row);
 }
 
-template <typename T>
-unsigned refined_blocks(const StepArgs<T>& a, bool adjoint) {
-  const long long n = (long long)(4 * a.nr + (adjoint ? ((a.nref + 3) & ~3) : 0)) * a.nslots;
-  return (unsigned)((n + kStepBlock - 1) / kStepBlock);
-}
-
 template <typename T, bool ADJ>
 void launch_step(const StepArgs<T>& a, cudaStream_t st) {
   if (a.small) {
@@ -1559,8 +1569,7 @@ void launch_step(const StepArgs<T>& a, cudaStream_t st) {
   }
   StepArgs<T> b = a;
   b.nhe = ((a.nedge + 1) / 2) * a.nslots;
-  b.nhr = (int)refined_blocks(a, ADJ);
-  const long long grid = (long long)b.nhe + b.nhr + a.nitems;
+  const long long grid = (long long)b.nhe + a.nitems;
   // programmatic dependent launch: this level's blocks may start while the
   // previous step launch drains (they wait for it before touching its data)
   cudaLaunchConfig_t cfg = {};
@@ -1612,13 +1621,6 @@ void launch_refined_pair(const StepArgs<T>& a, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_set_sparse(const int* cptr, const int* cunk, const double* cw, const double* acoef, T* rval, int nnz,
-                       cudaStream_t st) {
-  if (nnz == 0) return;
-  set_sparse_kernel<T><<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(cptr, cunk, cw, acoef, rval, nnz);
-}
-
-template <typename T>
 void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t st) {
   const long long nv = (long long)a.un[0] * a.un[1] * a.un[2];
   if (nv == 0) return;
@@ -1626,12 +1628,12 @@ void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t
 }
 
 template <typename T>
-void launch_set_coef(const StepArgs<T>& a, T* W, const double* acoef, double a_max, int* flag,
+void launch_set_coef(const StepArgs<T>& a, T* W, T* avox, const double* acoef, double a_max, int* flag,
                      cudaStream_t st) {
   const long long nv = (long long)a.un[0] * a.un[1] * a.un[2];
   const long long n = a.wsz > nv ? a.wsz : nv;
   if (n == 0) return;
-  set_coef_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, W, acoef, a_max, flag);
+  set_coef_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, W, avox, acoef, a_max, flag);
 }
 
 template <typename T>
@@ -1645,13 +1647,11 @@ void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStre
   template void launch_forward_step<T>(const StepArgs<T>&, cudaStream_t);                        \
   template void launch_adjoint_step<T>(const StepArgs<T>&, cudaStream_t);                        \
   template void launch_pair<T>(const StepArgs<T>&, const T*, const T*, cudaStream_t);            \
-  template void launch_set_coef<T>(const StepArgs<T>&, T*, const double*, double, int*,         \
+  template void launch_set_coef<T>(const StepArgs<T>&, T*, T*, const double*, double, int*,     \
                                    cudaStream_t);                                                \
   template void launch_extract_owned<T>(const StepArgs<T>&, const T*, T*, cudaStream_t);              \
   template void launch_extract_face<T>(const StepArgs<T>&, const T*, int, T*, cudaStream_t);        \
-  template void launch_refined_pair<T>(const StepArgs<T>&, cudaStream_t);                        \
-  template void launch_set_sparse<T>(const int*, const int*, const double*, const double*, T*, int, \
-                                     cudaStream_t);
+  template void launch_refined_pair<T>(const StepArgs<T>&, cudaStream_t);
 
 HYB_INSTANTIATE(float)
 HYB_INSTANTIATE(double)

@@ -81,6 +81,9 @@ def _load():
         "hyb_forward": [P, P, POINTER(hyb_source), c_int32, c_int32, c_double, P],
         "hyb_adjoint": [P, P, c_int32],
         "hyb_set_initial": [P, P, P, P, P],
+        "hyb_forward_batch": [P, P, POINTER(hyb_source), c_int32, c_int32, c_double, P],
+        "hyb_gradient_batch": [P, P, c_double, c_double, P],
+        "hyb_misfit_batch": [P, P, P, c_int32, POINTER(c_double), P],
         "hyb_gradient": [P, P, c_double, c_double, P],
         "hyb_misfit": [P, P, P, c_int32, POINTER(c_double), P],
         "hyb_cg_step": [P, P, P, POINTER(hyb_source), c_int32, c_int32, c_double,
@@ -102,7 +105,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("hyb_mesh_create", "hyb_mesh_query", "hyb_mesh_destroy", "hyb_set_stream", "hyb_forward",
             "hyb_adjoint", "hyb_gradient", "hyb_misfit", "hyb_cg_step", "hyb_get_field", "hyb_sync",
-            "hyb_last_error", "hyb_misfit_noalloc", "hyb_set_initial")
+            "hyb_last_error", "hyb_misfit_noalloc", "hyb_set_initial", "hyb_forward_batch",
+            "hyb_gradient_batch", "hyb_misfit_batch")
 
 
 def hyb_last_error() -> str:
@@ -155,6 +159,23 @@ def hyb_forward(mesh: int, a_ptr: int, sources, nsteps: int, dt: float, trace_pt
 def hyb_set_initial(mesh: int, u0_ptr: int, u_prev_ptr: int, c0_ptr: int = 0, c_prev_ptr: int = 0) -> None:
     _check(_lib.hyb_set_initial(c_void_p(mesh), c_void_p(u0_ptr or None), c_void_p(u_prev_ptr or None),
                                 c_void_p(c0_ptr or None), c_void_p(c_prev_ptr or None)))
+
+
+def hyb_forward_batch(mesh: int, a_ptr: int, sources, nsteps: int, dt: float, trace_ptr: int) -> None:
+    arr, n = _sources(sources)
+    _check(_lib.hyb_forward_batch(c_void_p(mesh), c_void_p(a_ptr), arr, n, int(nsteps), float(dt),
+                                  c_void_p(trace_ptr)))
+
+
+def hyb_misfit_batch(mesh: int, trace_ptr: int, obs_ptr: int, weights: int, n_src: int, cot_ptr: int = 0):
+    J = (c_double * n_src)()
+    _check(_lib.hyb_misfit_batch(c_void_p(mesh), c_void_p(trace_ptr), c_void_p(obs_ptr), int(weights), J,
+                                 c_void_p(cot_ptr) if cot_ptr else None))
+    return [float(v) for v in J]
+
+
+def hyb_gradient_batch(mesh: int, a_ptr: int, gamma: float, a0: float, g_ptr: int) -> None:
+    _check(_lib.hyb_gradient_batch(c_void_p(mesh), c_void_p(a_ptr), float(gamma), float(a0), c_void_p(g_ptr)))
 
 
 def hyb_adjoint(mesh: int, cot_ptr: int, accumulate: int = 0) -> None:

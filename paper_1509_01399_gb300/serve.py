@@ -1,4 +1,5 @@
-"""Serving form: continuous batching of forward + adjoint + gradient solves.
+"""Serving form: continuous, iteration-level batching of forward + adjoint +
+gradient solves.
 
 A request is one FP32 solve on its own lattice (Model Problem 2 with its own
 coefficient a = 1 + sigma): the forward sweep records the trace on the
@@ -8,19 +9,23 @@ copied to the host.
 
 The engine keeps a pool of meshes per lattice class (size, FEM block, step
 count, source) resident on the device, with their fields and checkpoints.
-A request is admitted as soon as a worker is free and a mesh of its class is
-free, or a new one fits in the HBM budget; otherwise it waits.  Each worker
-owns a CUDA stream, so the solves of all admitted requests run concurrently
-on the GPU, and requests that arrive while others are in flight join as
-soon as a slot and memory free up.  A request's arithmetic depends only on
-its own mesh and inputs, so its result is the same alone and in a mix.
+Arriving requests queue by class; a worker takes up to max_batch waiting
+requests of one class and advances them together: one launch per time level
+carries every request of the batch as its own slot with its own coefficient
+(hyb_forward_batch), and the per-request misfits, adjoints and gradients
+follow in the same way.  A batch is admitted as soon as a worker is free and
+a mesh of its class is free, or a new one fits in the HBM budget; otherwise
+it waits.  Each worker owns a CUDA stream, so batches of different classes
+run concurrently on the GPU, and requests that arrive while others are in
+flight join the next batch of their class.  A slot's arithmetic depends only
+on its own coefficient and source, so a request's result is the same alone
+and in a batch.
 """
 from __future__ import annotations
 
 import math
 import threading
 import time
-from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional
 
@@ -79,25 +84,26 @@ class _Pooled:
         self.mesh = mesh
         self.key = key
         self.nbytes = nbytes
-        self.trace = None
-        self.grad = None
+        self.bufs = None
 
 
 class ServingEngine:
     """Continuous-batching solve engine on one GPU.
 
     hbm_budget: bytes of device memory the pooled meshes may hold (default:
-    half of the free memory at start).  workers: concurrent solves (one CUDA
-    stream each)."""
+    half of the free memory at start).  workers: concurrent batches (one CUDA
+    stream each).  max_batch: requests of one lattice class advanced by the
+    same launches (iteration-level batching, hyb_forward_batch)."""
 
     def __init__(self, hbm_budget: Optional[int] = None, workers: int = 8, precision: str = "fp32",
-                 device: str = "cuda:0"):
+                 device: str = "cuda:0", max_batch: int = 8):
         self.device = torch.device(device)
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             hbm_budget = int(0.5 * free)
         self.budget = int(hbm_budget)
         self.workers = int(workers)
+        self.max_batch = max(1, min(int(max_batch), H.MAX_SOURCES))
         self.precision = precision
         self._cv = threading.Condition()
         self._free: Dict[tuple, List[_Pooled]] = {}
@@ -110,13 +116,15 @@ class ServingEngine:
         self.in_flight = 0
         self.max_in_flight = 0
         self.max_meshes = 0
+        self.max_batch_seen = 0
+        self.batches = 0
 
     # ---------------------------------------------------------- admission
     def _acquire(self, w) -> _Pooled:
         key = class_key(w, self.precision)
-        need = estimate_bytes(w, self.precision)
+        need = estimate_bytes(w, self.precision) * self.max_batch
         if need > self.budget:
-            raise H.HybError(H.HYB_ERR_OOM, f"request needs ~{need} bytes, above the HBM budget {self.budget}")
+            raise H.HybError(H.HYB_ERR_OOM, f"a batch needs ~{need} bytes, above the HBM budget {self.budget}")
         with self._cv:
             while True:
                 lst = self._free.get(key)
@@ -177,59 +185,120 @@ class ServingEngine:
                 m.close()
             return self._obs[key]
 
-    def solve(self, req: Request, t0: float = 0.0) -> Result:
-        w = req.workload
+    def _buffers(self, p: _Pooled, w, obs):
+        """Per-mesh device arrays for a batch of up to max_batch requests:
+        coefficients, observations (the class's, once per slot), trace,
+        cotangent, gradients, and the pinned host copy of the gradients."""
+        if p.bufs is None:
+            B, m = self.max_batch, p.mesh
+            tr = torch.zeros((B, w.nsteps + 1, m.obs_stride), dtype=m.dtype, device=self.device)
+            p.bufs = dict(a=torch.empty((B, m.n_unknown), dtype=torch.float64, device=self.device),
+                          obs=obs.expand(B, -1, -1).contiguous(), trace=tr, cot=torch.empty_like(tr),
+                          g=torch.empty((B, m.n_unknown), dtype=torch.float64, device=self.device),
+                          host=torch.empty((B, m.n_unknown), dtype=torch.float64).pin_memory())
+        return p.bufs
+
+    def solve_batch(self, reqs: List[Request], t0: float = 0.0) -> List[Result]:
+        """One batched solve of requests of one class: forward, per-request
+        misfit, adjoint and per-request gradient, all requests advanced by the
+        same launches on the worker's stream."""
+        w = reqs[0].workload
         obs = self.observations(w)
         s = self._stream()
         stream = self._streams[s]
         start = time.perf_counter() - t0
+        b = len(reqs)
         try:
             with torch.cuda.stream(stream):
                 p = self._acquire(w)
                 try:
                     m = p.mesh
                     m.set_stream(stream)
-                    if p.trace is None:
-                        p.trace = m.new_trace(len(w.sources), w.nsteps)
-                        p.cot = torch.empty_like(p.trace)
-                        p.a = torch.empty(m.n_unknown, dtype=torch.float64, device=self.device)
-                        p.grad = torch.empty(m.n_unknown, dtype=torch.float64, device=self.device)
-                        p.host = torch.empty(m.n_unknown, dtype=torch.float64).pin_memory()
-                    p.a.copy_(torch.from_numpy(1.0 + np.asarray(w.sigma, dtype=np.float64)), non_blocking=False)
-                    H.hyb_forward(m.handle, p.a.data_ptr(), w.sources, w.nsteps, w.dt, p.trace.data_ptr())
-                    J = H.hyb_misfit(m.handle, p.trace.data_ptr(), obs.data_ptr(), H.HYB_WEIGHTS_PLAIN, True,
-                                     p.cot.data_ptr())
-                    H.hyb_adjoint(m.handle, p.cot.data_ptr(), 0)
-                    H.hyb_gradient(m.handle, p.a.data_ptr(), 0.0, 1.0, p.grad.data_ptr())
-                    p.host.copy_(p.grad, non_blocking=True)
+                    bf = self._buffers(p, w, obs)
+                    host_a = np.stack([1.0 + np.asarray(r.workload.sigma, dtype=np.float64) for r in reqs])
+                    bf["a"][:b].copy_(torch.from_numpy(host_a), non_blocking=False)
+                    srcs = [r.workload.sources[0] for r in reqs]
+                    H.hyb_forward_batch(m.handle, bf["a"].data_ptr(), srcs, w.nsteps, w.dt, bf["trace"].data_ptr())
+                    J = H.hyb_misfit_batch(m.handle, bf["trace"].data_ptr(), bf["obs"].data_ptr(),
+                                           H.HYB_WEIGHTS_PLAIN, b, bf["cot"].data_ptr())
+                    H.hyb_adjoint(m.handle, bf["cot"].data_ptr(), 0)
+                    H.hyb_gradient_batch(m.handle, bf["a"].data_ptr(), 0.0, 1.0, bf["g"].data_ptr())
+                    bf["host"][:b].copy_(bf["g"][:b], non_blocking=True)
                     H.hyb_sync(m.handle)
-                    g = p.host.numpy().copy()
+                    g = bf["host"][:b].numpy().copy()
                 finally:
                     self._release(p)
         finally:
             self._stream_done(s)
         finish = time.perf_counter() - t0
-        return Result(req.rid, g, J, req.arrival, start, finish, class_key(w, self.precision))
+        with self._cv:
+            self.batches += 1
+            self.max_batch_seen = max(self.max_batch_seen, b)
+        key = class_key(w, self.precision)
+        return [Result(r.rid, g[i], J[i], r.arrival, start, finish, key) for i, r in enumerate(reqs)]
+
+    def solve(self, req: Request, t0: float = 0.0) -> Result:
+        return self.solve_batch([req], t0)[0]
 
     # -------------------------------------------------------------- stream
     def run(self, requests: List[Request]) -> List[Result]:
-        """Serve requests arriving at their `arrival` times (seconds from now):
-        a dispatcher hands each one, at its arrival, to a pool of `workers`
-        threads; it starts as soon as a worker and memory allow.  Returns the
-        results in request order."""
+        """Serve requests arriving at their `arrival` times (seconds from now).
+        Arrivals join a queue per lattice class; each of `workers` threads
+        takes the class whose oldest request has waited longest and solves up
+        to max_batch of its waiting requests in one batch, so requests that
+        arrive while others are on the GPU join the next batch of their class
+        as soon as a worker and memory free up.  Returns the results in
+        request order."""
         for r in requests:  # observation traces are inputs, prepared up front
             self.observations(r.workload)
         torch.cuda.synchronize(self.device)
         order = sorted(requests, key=lambda r: r.arrival)
+        queues: Dict[tuple, List[Request]] = {}
+        qcv = threading.Condition()
+        done: Dict[int, Result] = {}
+        state = {"pending": len(order), "error": None}
         t0 = time.perf_counter()
-        with ThreadPoolExecutor(max_workers=self.workers) as ex:
-            futs = []
-            for r in order:
-                delay = r.arrival - (time.perf_counter() - t0)
-                if delay > 0:
-                    time.sleep(delay)
-                futs.append(ex.submit(self.solve, r, t0))
-            done = {f.result().rid: f.result() for f in futs}
+
+        def worker():
+            while True:
+                with qcv:
+                    while True:
+                        if state["pending"] == 0 or state["error"] is not None:
+                            return
+                        ready = [(q[0].arrival, k) for k, q in queues.items() if q]
+                        if ready:
+                            _, k = min(ready)
+                            batch = queues[k][: self.max_batch]
+                            del queues[k][: len(batch)]
+                            break
+                        qcv.wait()
+                try:
+                    res = self.solve_batch(batch, t0)
+                except Exception as e:  # surfaces in the dispatcher
+                    with qcv:
+                        state["error"] = e
+                        qcv.notify_all()
+                    return
+                with qcv:
+                    for r in res:
+                        done[r.rid] = r
+                    state["pending"] -= len(res)
+                    qcv.notify_all()
+
+        threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.workers)]
+        for th in threads:
+            th.start()
+        for r in order:
+            delay = r.arrival - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            with qcv:
+                queues.setdefault(class_key(r.workload, self.precision), []).append(r)
+                qcv.notify_all()
+        for th in threads:
+            th.join()
+        if state["error"] is not None:
+            raise state["error"]
         return [done[r.rid] for r in requests]
 
     def close(self):
