@@ -104,7 +104,7 @@ struct hyb_mesh {
   // refined region
   int nc = 0, nr = 0, nrl = 0, nnz = 0;
   double dt_max = 0.0;
-  DevBuf rmask, rzr, refvox, refvox_id, k9, rcid, avox;
+  DevBuf rmask, rzr, refvox, refvox_id, k9, rcid, avox, rrow;
   double uK9[81], uK8[64], um9[9], um8[8];  // unit-voxel stiffness and lumped masses (refined, Kuhn)
   std::vector<int> ref_rows;  // per interior tile and plane: tile rows holding refined-voxel corners
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
@@ -339,7 +339,7 @@ void step_geometry(const hyb_mesh* m, int* npb, int* ntx, int* small, int* nedge
 constexpr int kStepWavesFew = 1, kStepWavesMany = 3;
 constexpr double kManyLevelsPerBlock = 40.0;
 constexpr double kZFaceLevelCost = 3.5;
-constexpr double kRefRowCost = 0.3;  // a tile row holding refined-voxel corners (a plain level: 1)
+constexpr double kRefRowCost = 0.05;  // a tile row holding refined-voxel corners (a plain level: 1)
 
 // Interior work items of one step launch, one per block: (slot, tile, z0,
 // z1).  Each tile's z range 1 .. n-2 is cut into pieces of about equal
@@ -639,6 +639,7 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   for (int q = 0; q < 8; ++q) m->um8[q] = m8[q];
   HYB_TRY(upload(m, m->rmask, rmask));
   HYB_TRY(upload(m, m->rcid, cid));
+  HYB_TRY(upload(m, m->rrow, rows));
   // z range of the sparse-row nodes of each FEM-owned column
   std::vector<int> rzr((size_t)2 * m->fn[0] * m->fn[1]);
   for (size_t c = 0; c < rzr.size() / 2; ++c) {
@@ -793,6 +794,8 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.nslots = nslots;
   if (m->nc > 0) {
     A.nref = m->nc;
+    A.nrl = m->nrl;
+    A.rrow = (const long long*)m->rrow.p;
     A.rcid = (const int*)m->rcid.p;
     for (int q = 0; q < 81; ++q) A.rK9[q] = (T)m->uK9[q];
     for (int c = 0; c < 8; ++c) {
@@ -1529,7 +1532,7 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   cudaStreamSynchronize(m->st);
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
                     &m->g, &m->atrial, &m->cot, &m->trace, &m->rmask, &m->rzr, &m->refvox, &m->refvox_id,
-                    &m->k9, &m->rcid, &m->avox,
+                    &m->k9, &m->rcid, &m->avox, &m->rrow,
                     &m->CU, &m->CL, &m->chist, &m->cckpt, &m->I0, &m->IC0, &m->acopy, &m->kuhn, &m->kuhn_v};
   for (DevBuf* b : bufs) release(*b);
   for (auto& dir : m->items)

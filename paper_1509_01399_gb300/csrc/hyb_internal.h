@@ -96,10 +96,13 @@ struct StepArgs {
   int nhe, nhr;      // step kernel: leading blocks of edge tiles, then of refined rows
   int nslots;
   // refined region (nref == 0: nothing refined): unknown voxels bisected
-  // once (12 tetrahedra around a centre node).  The interior blocks evaluate
-  // the rows of their corners (the stencil row corrected by the refined
-  // voxels around the node) and of their centres from the staged planes.
+  // once (12 tetrahedra around a centre node).  Leading blocks of the step
+  // launch evaluate the rows of their corners (the stencil row corrected by
+  // the refined voxels around the node) and of their centres; the interior
+  // blocks skip those nodes.
   int nref;                   // refined voxels (= centre nodes)
+  int nrl;                    // corners of refined voxels (lattice rows of the refined region)
+  const long long* rrow;      // lattice id of each such corner
   const unsigned char* rmask; // FEM-owned box: 1 = the node is a corner of a refined voxel
   const int* rzr;             // per FEM-owned column (i - fl0) + fn0 (j - fl1): [kmin, kmax] of its
                               // refined corners (kmin > kmax: none)

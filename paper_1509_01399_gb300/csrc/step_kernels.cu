@@ -750,91 +750,6 @@ struct Producer {
   }
 };
 
-// The row of a corner n = (i, j, k) of refined voxels (Eq. (fem) on the
-// locally refined mesh): the stencil row lapW of the Kuhn voxels (edge
-// weights over all voxels around n), corrected on every refined voxel v
-// around n by a_v (K9 - K8) of n's corner in v (its centre included) and
-// divided by the lumped mass of n in units of h^3 (the Kuhn corner masses,
-// or the bisected voxel's where refined).  Neighbours from the staged planes
-// Cm, Ck, Cp (n at offset 0), centres from the centre level `cen`.
-template <typename T>
-__device__ __noinline__ T refined_lap(const StepArgs<T>& A, const T* __restrict__ avox, const T* __restrict__ cen, int i,
-                                      int j, int k, const T* Cm, const T* Ck, const T* Cp, T lapW, T c0) {
-  // the eight voxels' centre ids, then their coefficients and centre values:
-  // independent loads issued together (voxel ids from the one of corner 0)
-  const int ox = i - A.fl[0], oy = j - A.fl[1], oz = k - A.fl[2];
-  const int v0 = ox + A.un[0] * (oy + A.un[1] * oz), sy = A.un[0], sz = A.un[0] * A.un[1];
-  int rc[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-    const bool in = ox - dx >= 0 && oy - dy >= 0 && oz - dz >= 0 && ox - dx < A.un[0] && oy - dy < A.un[1] &&
-                    oz - dz < A.un[2];
-    rc[c] = in ? A.rcid[v0 - dx - dy * sy - dz * sz] : -1;
-  }
-  T av[8], uc[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int v = v0 - (c & 1) - ((c >> 1) & 1) * sy - (c >> 2) * sz;
-    av[c] = rc[c] >= 0 ? avox[v] : T(0);
-    uc[c] = rc[c] >= 0 ? cen[rc[c]] : T(0);
-  }
-  T corr = T(0), mass = T(0);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-    if (rc[c] < 0) {
-      mass += A.rm8[c];
-      continue;
-    }
-    mass += A.rm9[c];
-    T sv = A.rdK[9 * c + 8] * (uc[c] - c0);
-    // K9 - K8 couples the diagonal corners 0 and 7 to the six others and
-    // the six others to 0 and 7 only (the other entries vanish)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const bool diag_c = c == 0 || c == 7, diag_q = q == 0 || q == 7;
-      if (q == c || diag_c == diag_q) continue;
-      const int qx = (q & 1) - dx, qy = ((q >> 1) & 1) - dy, qz = (q >> 2) - dz;
-      const T* pl = qz < 0 ? Cm : (qz > 0 ? Cp : Ck);
-      sv += A.rdK[9 * c + q] * (pl[qx + qy * kBoxX] - c0);
-    }
-    corr += av[c] * sv;
-  }
-  return (lapW - corr) / mass;
-}
-
-// Refined voxel rc (unknown voxel vid) whose origin is the interior node at
-// offset 0 of the staged planes Ck (its plane) and Cp (the next): its centre
-// row (Eq. (fem) on the twelve tetrahedra around the centre), and in the
-// transposed step with pairing its gradient pairing u^T K9 lambda over the
-// corners (u from the staged history Hk, Hp) and the centre.
-template <typename T, bool ADJ>
-__device__ __noinline__ void refined_voxel(const StepArgs<T>& A, const Slot<T>& S, int si, int rc, int vid, bool pair,
-                                           const T* Ck, const T* Cp, const T* Hk, const T* Hp) {
-  const T q[8] = {Ck[0], Ck[1], Ck[kBoxX], Ck[kBoxX + 1], Cp[0], Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
-  const T uc = S.ccur[rc];
-  T sv = T(0);
-#pragma unroll
-  for (int p = 0; p < 8; ++p) sv += A.rK9[72 + p] * (q[p] - uc);
-  const T vc = uc + ((uc - S.cprev[rc]) - A.c2 * S.avox[vid] * sv / A.rm9[8]);
-  S.cnext[rc] = vc;
-  if (!ADJ && S.chist_w) S.chist_w[rc] = vc;
-  if (ADJ && pair) {
-    const T u[9] = {Hk[0], Hk[1], Hk[kBoxX], Hk[kBoxX + 1], Hp[0], Hp[1], Hp[kBoxX], Hp[kBoxX + 1], S.chist_r[rc]};
-    T pr = T(0);
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-      T row = A.rK9[9 * p + 8] * uc;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) row += A.rK9[9 * p + j] * q[j];
-      pr += u[p] * row;
-    }
-    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
-    atomicAdd(A.G + (long long)si * nv + vid, (double)(T(kGradPairScale) * pr));
-  }
-}
-
 // One node (i, j, k) of an interior block from the staged planes: Ck, Cm, Cp
 // are this node in the u^k boxes of planes k, k-1, k+1, Pk in the u^{k-1}
 // box, Wk / Wm in the edge-weight arrays of planes k / k-1, Hk / Hp in the
@@ -864,12 +779,8 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     wyp = Wk[P::WS];
     wzp = Wk[2 * P::WS];
     wzm = Wm[2 * P::WS];
-    T lap =
+    const T lap =
         wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + wzp * (cp - c0) + wzm * (cm - c0);
-    if constexpr (REF) {
-      if (k >= C.rz0 && k <= C.rz1 && A.rmask[(C.i - A.hx0) + A.hpx * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]))])
-        lap = refined_lap(A, S.avox, S.ccur, C.i, C.j, k, Cm, Ck, Cp, lap, c0);
-    }
     val = c0 + ((c0 - pv) + c2 * lap);
   } else if constexpr (sizeof(T) == 4) {  // unit weights: the neighbour sum minus 6 u^k
     val = c0 + ((c0 - pv) + c2 * ((((xm + xp) + (ym + yp)) + (cm + cp)) - T(6) * c0));
@@ -963,20 +874,15 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     return;
   }
   const int bo = (C.i - A.hx0) + A.hpx * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]));
-  gnext[off] = val;
-  if (!ADJ && S.hist_w) S.hist_w[bo] = val;
-  // the voxel with origin (i, j, k): the centre row if it is refined, and
-  // (transposed step with pairing) its gradient pairing
-  const int vz = A.un[0] * A.un[1];
-  const bool vox = C.xy_uv && k < A.fl[2] + A.un[2];
-  const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
-  int rc = -1;
-  if constexpr (REF) {
-    rc = (vox && k >= C.rz0 && k <= C.rz1) ? A.rcid[vid] : -1;
-    if (rc >= 0) refined_voxel<T, ADJ>(A, S, C.si, rc, vid, C.xy_vox, Ck, Cp, Hk, Hp);
+  const bool rz = REF && k >= C.rz0 && k <= C.rz1;  // the column has refined corners here
+  if (!(rz && A.rmask[bo])) {  // (the refined rows write those)
+    gnext[off] = val;
+    if (!ADJ && S.hist_w) S.hist_w[bo] = val;
   }
   if constexpr (ADJ) {
-    if (C.xy_vox && vox && rc < 0) {
+    const int vz = A.un[0] * A.un[1];
+    const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
+    if (C.xy_vox && k < A.fl[2] + A.un[2] && !(rz && A.refvox[vid])) {
       const T u[8] = {Hk[0], Hk[1], Hk[kBoxX], Hk[kBoxX + 1], Hp[0], Hp[1], Hp[kBoxX], Hp[kBoxX + 1]};
       const T l[8] = {c0, xp, yp, Ck[kBoxX + 1], cp, Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
       atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
@@ -1361,6 +1267,9 @@ __device__ __forceinline__ void adj_edge_tile(const StepArgs<T>& A, int si, int 
   pair_if_voxel<T, false>(A, S, si, i, j, k);
 }
 
+template <typename T, bool ADJ>
+__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t);
+
 // One time level of every slot in one launch of kStepBlock threads per
 // block: first the edge tiles (two 128-node tiles per block, so their short
 // dependent chains start early), then the refined sparse rows, then the
@@ -1385,7 +1294,13 @@ __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kerne
       fwd_edge_tile<T>(A, si, blk, t, sh + 128 * half);
     return;
   }
-  interior_block<T, ADJ>(A, b - A.nhe, sh);
+  b -= A.nhe;
+  if (b < A.nhr) {
+    pdl_wait();
+    refined_rows<T, ADJ>(A, (long long)b * kStepBlock + threadIdx.x);
+    return;
+  }
+  interior_block<T, ADJ>(A, b - A.nhr, sh);
 }
 
 // Lattices with fewer than 5 nodes on some axis: every node by the generic
@@ -1442,6 +1357,105 @@ __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __re
 // Pairing of a refined voxel: u^T K9 lambda over its 8 corners and centre,
 // K9 the stiffness of the refined unit voxel (a = 1); the host scales the
 // sum like the structured pairing.
+// Refined region of one time level, in the leading blocks of the step
+// launch (one thread per row), the same rows for the forward and the
+// mass-scaled adjoint.  A corner n of refined voxels: the Kuhn stencil row
+// lapW (the edge weights over the voxels around n) corrected on every refined
+// voxel v around n by a_v (K9 - K8) of n's corner in v, which couples the
+// voxel's diagonal corners 0 and 7 to its six others, the six others to 0
+// and 7, and every corner to the centre; divided by n's lumped mass in units
+// of h^3.  A centre c of voxel v: a_v K9 of the centre on the eight corners
+// over its mass.  Then u^{k+1} = u^k + ((u^k - u^{k-1}) + tau^2/h^2 lap).
+// Every load of a row is issued before the row is summed.
+template <typename T, bool ADJ>
+__device__ __forceinline__ void refined_corner(const StepArgs<T>& A, const Slot<T>& S, int r) {
+  const long long id = A.rrow[r];
+  const int i = (int)(id % A.px), j = (int)((id / A.px) % A.ny), k = (int)(id / ((long long)A.px * A.ny));
+  const long long sy = A.px, sz = (long long)A.px * A.ny;
+  const T* __restrict__ u = S.cur;
+  const T c0 = u[id], pv = S.prev[id];
+  const T zm = u[id - sz], zp = u[id + sz];
+  const T lapW = fem_lap(A, S.W, u, id, i, j, k, c0, zm, zp);
+  // the eight voxels around n (n is corner c of the voxel with origin n - c)
+  const int ox = i - A.fl[0], oy = j - A.fl[1], oz = k - A.fl[2];
+  const int v0 = ox + A.un[0] * (oy + A.un[1] * oz), vy = A.un[0], vz = A.un[0] * A.un[1];
+  int rc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    const bool in = ox - dx >= 0 && oy - dy >= 0 && oz - dz >= 0 && ox - dx < A.un[0] && oy - dy < A.un[1] &&
+                    oz - dz < A.un[2];
+    rc[c] = in ? A.rcid[v0 - dx - dy * vy - dz * vz] : -1;
+  }
+  T corr = T(0), mass = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    const bool ref = rc[c] >= 0;
+    mass += ref ? A.rm9[c] : A.rm8[c];
+    const T av = ref ? S.avox[v0 - dx - dy * vy - dz * vz] : T(0);
+    const T uc = ref ? S.ccur[rc[c]] : c0;
+    T sv = A.rdK[9 * c + 8] * (uc - c0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool diag_c = c == 0 || c == 7, diag_q = q == 0 || q == 7;
+      if (q == c || diag_c == diag_q) continue;
+      const long long o = ((q & 1) - dx) + ((long long)((q >> 1) & 1) - dy) * sy + ((long long)(q >> 2) - dz) * sz;
+      sv += A.rdK[9 * c + q] * ((ref ? u[id + o] : c0) - c0);
+    }
+    corr += av * sv;
+  }
+  const T val = c0 + ((c0 - pv) + A.c2 * ((lapW - corr) / mass));
+  S.next[id] = val;
+  if (!ADJ && S.hist_w) S.hist_w[hidx(A, i, j, k)] = val;
+}
+
+template <typename T, bool ADJ>
+__device__ __forceinline__ void refined_centre(const StepArgs<T>& A, const Slot<T>& S, int v) {
+  const int vid = A.refvox_id[v];
+  const int x = vid % A.un[0], y = (vid / A.un[0]) % A.un[1], z = vid / (A.un[0] * A.un[1]);
+  const long long l0 = lin(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z);
+  const long long sy = A.px, sz = (long long)A.px * A.ny;
+  T q[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) q[c] = S.cur[l0 + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz];
+  const T uc = S.ccur[v], up = S.cprev[v], av = S.avox[vid];
+  T sv = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) sv += A.rK9[72 + c] * (q[c] - uc);
+  const T vc = uc + ((uc - up) - A.c2 * av * sv / A.rm9[8]);
+  S.cnext[v] = vc;
+  if (!ADJ && S.chist_w) S.chist_w[v] = vc;
+}
+
+template <typename T, typename K>
+__device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* __restrict__ hb,
+                                          const T* __restrict__ chb, const T* __restrict__ lam,
+                                          const T* __restrict__ clam, const K* __restrict__ k9);
+
+// Threads of the refined leading blocks, per slot: the corner rows, the
+// centre rows, then (transposed step with pairing) one per refined voxel.
+template <typename T, bool ADJ>
+__device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t) {
+  const int per = A.nrl + A.nref + (ADJ ? A.nref : 0);
+  if (t >= (long long)per * A.nslots) return;
+  const int si = (int)(t / per);
+  const int r = (int)(t - (long long)si * per);
+  const Slot<T>& S = A.s[si];
+  if (r < A.nrl) {
+    refined_corner<T, ADJ>(A, S, r);
+  } else if (r < A.nrl + A.nref) {
+    refined_centre<T, ADJ>(A, S, r - A.nrl);
+  } else if constexpr (ADJ) {
+    if (!S.hist_r) return;
+    const int v = r - A.nrl - A.nref;
+    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+    // the unit-voxel K9 from the launch parameters (kGradPairScale times the pairing, as the other kernels)
+    A.G[(long long)si * nv + A.refvox_id[v]] +=
+        (double)(T(kGradPairScale) * refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur, A.rK9));
+  }
+}
+
 template <typename T, typename K>
 __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* __restrict__ hb,
                                           const T* __restrict__ chb, const T* __restrict__ lam,
@@ -1569,7 +1583,9 @@ void launch_step(const StepArgs<T>& a, cudaStream_t st) {
   }
   StepArgs<T> b = a;
   b.nhe = ((a.nedge + 1) / 2) * a.nslots;
-  const long long grid = (long long)b.nhe + a.nitems;
+  const long long nref_threads = (long long)(a.nrl + a.nref + (ADJ ? a.nref : 0)) * a.nslots;
+  b.nhr = (int)((nref_threads + kStepBlock - 1) / kStepBlock);
+  const long long grid = (long long)b.nhe + b.nhr + a.nitems;
   // programmatic dependent launch: this level's blocks may start while the
   // previous step launch drains (they wait for it before touching its data)
   cudaLaunchConfig_t cfg = {};
