@@ -397,11 +397,14 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
       }
     }
   }
-  // by source, and costliest first within a source: the items of one source
-  // run together, so that neighbouring tiles share their halo rows in L2,
-  // and the long ones start early
+  // by source, then by z slab, then by tile: the items of one source run
+  // together, and the blocks resident at one time cover one slab of
+  // neighbouring tiles, whose halo columns and slab-boundary planes they then
+  // share in L2
   std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) {
-    return a.second[0] != b.second[0] ? a.second[0] < b.second[0] : a.first > b.first;
+    if (a.second[0] != b.second[0]) return a.second[0] < b.second[0];
+    if (a.second[2] != b.second[2]) return a.second[2] < b.second[2];
+    return a.second[1] < b.second[1];
   });
   std::vector<int> out;
   out.reserve(items.size() * 4);
@@ -490,7 +493,14 @@ void unit_voxel_matrices(double K8[64], double m8[8], double K9[81], double m9[9
 template <typename V>
 hyb_status upload(hyb_mesh* m, DevBuf& b, const std::vector<V>& host) {
   HYB_TRY(ensure(m, b, host.size() * sizeof(V)));
-  if (!host.empty()) HYB_CU(cudaMemcpy(b.p, host.data(), host.size() * sizeof(V), cudaMemcpyHostToDevice));
+  // on the mesh's stream, so that its kernels are ordered after the copy
+  // whatever kind of stream it is (a synchronous copy from pageable memory
+  // may return before its DMA lands and orders only the legacy stream), then
+  // wait for it: host is a temporary
+  if (!host.empty()) {
+    HYB_CU(cudaMemcpyAsync(b.p, host.data(), host.size() * sizeof(V), cudaMemcpyHostToDevice, m->st));
+    HYB_CU(cudaStreamSynchronize(m->st));
+  }
   return HYB_OK;
 }
 

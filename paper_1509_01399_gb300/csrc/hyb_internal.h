@@ -93,10 +93,10 @@ struct StepArgs {
   int nitems;
   int small;         // some axis has < 5 nodes: one generic kernel per level
   int nedge;         // edge tiles (128 nodes) per slot
-  int nhe, nhr;      // step kernel: leading blocks of edge tiles, then of refined rows
+  int nhe, nhr;      // step kernel: leading blocks of edge tiles, trailing blocks of refined rows
   int nslots;
   // refined region (nref == 0: nothing refined): unknown voxels bisected
-  // once (12 tetrahedra around a centre node).  Leading blocks of the step
+  // once (12 tetrahedra around a centre node).  Trailing blocks of the step
   // launch evaluate the rows of their corners (the stencil row corrected by
   // the refined voxels around the node) and of their centres; the interior
   // blocks skip those nodes.

@@ -2,8 +2,9 @@
 //
 // One time level of every slot (source / problem) is one launch of
 // step_kernel: its leading blocks run the edge tiles (nodes within one node
-// of two faces) and the refined sparse rows, the other blocks the interior
-// (all other nodes), one work item (slot, 32 x 16 tile, z range) each.  All
+// of two faces), the next ones the interior (all other nodes), one work item
+// (slot, 32 x 16 tile, z range) each, and its trailing blocks the rows of
+// the refined region.  All
 // blocks read levels k and k-1 and write disjoint nodes of level k+1.  An
 // interior block's producer warp stages the planes it needs (u^k with a
 // one-node halo, u^{k-1}, FEM edge weights, stored history) into shared
@@ -1272,9 +1273,10 @@ __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t);
 
 // One time level of every slot in one launch of kStepBlock threads per
 // block: first the edge tiles (two 128-node tiles per block, so their short
-// dependent chains start early), then the refined sparse rows, then the
-// interior blocks.  All blocks read levels k, k-1 and write disjoint nodes
-// of level k+1.
+// dependent chains start early), then the interior blocks, then the rows of
+// the refined region (gathers of short latency-bound rows, which fill the
+// slots the interior blocks free towards the end of the level).  All blocks
+// read levels k, k-1 and write disjoint nodes of level k+1.
 template <typename T, bool ADJ>
 __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kernel(const __grid_constant__ StepArgs<T> A) {
   extern __shared__ __align__(128) unsigned char hyb_smem[];  // kPipe<T>::bytes
@@ -1295,12 +1297,12 @@ __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kerne
     return;
   }
   b -= A.nhe;
-  if (b < A.nhr) {
+  if (b >= A.nitems) {
     pdl_wait();
-    refined_rows<T, ADJ>(A, (long long)b * kStepBlock + threadIdx.x);
+    refined_rows<T, ADJ>(A, (long long)(b - A.nitems) * kStepBlock + threadIdx.x);
     return;
   }
-  interior_block<T, ADJ>(A, b - A.nhr, sh);
+  interior_block<T, ADJ>(A, b, sh);
 }
 
 // Lattices with fewer than 5 nodes on some axis: every node by the generic
@@ -1357,7 +1359,7 @@ __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __re
 // Pairing of a refined voxel: u^T K9 lambda over its 8 corners and centre,
 // K9 the stiffness of the refined unit voxel (a = 1); the host scales the
 // sum like the structured pairing.
-// Refined region of one time level, in the leading blocks of the step
+// Refined region of one time level, in the trailing blocks of the step
 // launch (one thread per row), the same rows for the forward and the
 // mass-scaled adjoint.  A corner n of refined voxels: the Kuhn stencil row
 // lapW (the edge weights over the voxels around n) corrected on every refined
@@ -1433,7 +1435,7 @@ __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* 
                                           const T* __restrict__ chb, const T* __restrict__ lam,
                                           const T* __restrict__ clam, const K* __restrict__ k9);
 
-// Threads of the refined leading blocks, per slot: the corner rows, the
+// Threads of the refined trailing blocks, per slot: the corner rows, the
 // centre rows, then (transposed step with pairing) one per refined voxel.
 template <typename T, bool ADJ>
 __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t) {
