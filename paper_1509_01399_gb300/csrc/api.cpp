@@ -79,12 +79,12 @@ struct hyb_mesh {
   cudaStream_t st = nullptr;
   int n[3] = {0, 0, 0};
   long long N = 0;    // lattice nodes
-  int px = 0;         // row pitch of the lattice fields (multiple of 4)
+  int px = 0;         // row pitch of the lattice fields (multiple of 8)
   long long Np = 0;   // entries of one lattice field (px ny nz)
   bool fem = false;
   int fl[3], fh[3], fn[3], wl[3], wn[3], un[3];
   int wx0 = 0, wpx = 0;  // edge-weight arrays: x origin and row pitch (multiples of 4)
-  int hx0 = 0, hpx = 0;  // FEM-owned (history) box: x origin and row pitch (multiples of 4)
+  int hx0 = 0, hpx = 0;  // FEM-owned (history) box: x origin and row pitch (multiples of 8)
   long long wsz = 0, nu = 0, nown = 0;
   long long hbox = 0;    // entries of one history box (hpx fn1 fn2)
   int obs_stride = 0;
@@ -319,13 +319,13 @@ void set_wave(const hyb_mesh* m, Slot<T>& S, const hyb_source& src, int k, doubl
 }
 
 // Launch geometry of one step: the interior covers nodes 1 .. n-2 on every
-// axis in 32 x 16 tiles; the edge tiles cover the nodes within one node of
+// axis in 32 x 16 tiles (in x from tile_x0: FP32 tiles start at x = 0); the edge tiles cover the nodes within one node of
 // two faces.  Lattices with fewer than 5 nodes on an axis use a single
 // generic kernel instead.
 void step_geometry(const hyb_mesh* m, int* npb, int* ntx, int* small, int* nedge) {
   *small = (m->n[0] < 5 || m->n[1] < 5 || m->n[2] < 5) ? 1 : 0;
   *nedge = *small ? 0 : 1 + (m->n[0] - 4 + 7) / 8 + (m->n[1] - 4 + 7) / 8 + (m->n[2] - 4 + 7) / 8;
-  *ntx = (m->n[0] - 2 + kTileX - 1) / kTileX;
+  *ntx = (m->n[0] - 1 - tile_x0(m->d.precision) + kTileX - 1) / kTileX;
   const int nty = (m->n[1] - 2 + kTileY - 1) / kTileY;
   *npb = *ntx * nty;
 }
@@ -353,7 +353,8 @@ constexpr double kRefRowCost = 0.05;  // a tile row holding refined-voxel corner
 // produce the face plane and, on the source face, the trace).
 std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
   const int nx = m->n[0], ny = m->n[1], nz = m->n[2];
-  const int ntx = (nx - 2 + kTileX - 1) / kTileX, nty = (ny - 2 + kTileY - 1) / kTileY;
+  const int x0 = tile_x0(m->d.precision);
+  const int ntx = (nx - 1 - x0 + kTileX - 1) / kTileX, nty = (ny - 2 + kTileY - 1) / kTileY;
   struct Tile {
     int si, tile;
     double base, extra;
@@ -365,8 +366,8 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
   for (int si = 0; si < nslots; ++si)
     for (int ty = 0; ty < nty; ++ty)
       for (int tx = 0; tx < ntx; ++tx) {
-        const int i0 = 1 + tx * kTileX, j0 = 1 + ty * kTileY;
-        const bool face = i0 == 1 || i0 + kTileX - 1 >= nx - 2 || j0 == 1 || j0 + kTileY - 1 >= ny - 2;
+        const int i0 = x0 + tx * kTileX, j0 = 1 + ty * kTileY;
+        const bool face = i0 <= 1 || i0 + kTileX - 1 >= nx - 2 || j0 == 1 || j0 + kTileY - 1 >= ny - 2;
         const bool femt = m->fem && i0 <= m->fh[0] && i0 + kTileX - 1 >= m->fl[0] && j0 <= m->fh[1] &&
                           j0 + kTileY - 1 >= m->fl[1];
         const double base = face ? (adjoint ? 1.70 : 1.50) : (femt ? (adjoint ? 1.40 : 1.22) : 1.0);
@@ -669,7 +670,8 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   // tile rows (32 nodes in x at one y and z) holding refined corners, per
   // interior tile and plane, for the work-item cost model
   {
-    const int ntx = (m->n[0] - 2 + kTileX - 1) / kTileX, nty = (m->n[1] - 2 + kTileY - 1) / kTileY;
+    const int x0 = tile_x0(m->d.precision);
+    const int ntx = (m->n[0] - 1 - x0 + kTileX - 1) / kTileX, nty = (m->n[1] - 2 + kTileY - 1) / kTileY;
     m->ref_rows.assign((size_t)ntx * nty * m->n[2], 0);
     std::vector<unsigned char> seen((size_t)ntx * m->n[1] * m->n[2], 0);
     for (int k = 0; k < m->fn[2]; ++k)
@@ -677,7 +679,7 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
         for (int i = 0; i < m->fn[0]; ++i) {
           const int x = m->fl[0] + i, y = m->fl[1] + j, z = m->fl[2] + k;
           if (!rmask[(size_t)(x - m->hx0) + (size_t)m->hpx * (j + (size_t)m->fn[1] * k)]) continue;
-          const int tx = (x - 1) / kTileX, ty = (y - 1) / kTileY;
+          const int tx = (x - x0) / kTileX, ty = (y - 1) / kTileY;
           unsigned char& sr = seen[(size_t)tx + (size_t)ntx * (y + (size_t)m->n[1] * z)];
           if (sr) continue;
           sr = 1;
@@ -737,13 +739,13 @@ hyb_status encode_map(CUtensorMap* map, const void* base, uint64_t d0, uint64_t 
 template <typename T>
 hyb_status step_maps(const hyb_mesh* m, StepArgs<T>& A, const DevBuf& field, int nsrc, int hist_levels) {
   HYB_TRY(encode_map<T>(&A.tmf, field.p, m->n[0], m->n[1], (uint64_t)m->n[2] * 3 * nsrc, m->px,
-                        (uint64_t)m->px * m->n[1], 36, kTileY + 2));
+                        (uint64_t)m->px * m->n[1], Box<T>::BX, kBoxY));
   if (m->fem && m->wsz > 0)
     HYB_TRY(encode_map<T>(&A.tmw, m->W.p, m->wpx, m->wn[1], 3ull * m->wn[2] * (m->batch ? nsrc : 1), m->wpx,
-                          (uint64_t)m->wpx * m->wn[1], 36, kTileY + 1));
+                          (uint64_t)m->wpx * m->wn[1], Box<T>::BX, kHBoxY));
   if (hist_levels > 0 && m->hbox > 0)
     HYB_TRY(encode_map<T>(&A.tmh, m->hist.p, m->hpx, m->fn[1], (uint64_t)m->fn[2] * nsrc * hist_levels, m->hpx,
-                          (uint64_t)m->hpx * m->fn[1], 36, kTileY + 1));
+                          (uint64_t)m->hpx * m->fn[1], Box<T>::BX, kHBoxY));
   return HYB_OK;
 }
 
@@ -1449,7 +1451,7 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   m->st = (cudaStream_t)stream;
   for (int a = 0; a < 3; ++a) m->n[a] = d->n[a];
   m->N = (long long)d->n[0] * d->n[1] * d->n[2];
-  m->px = (d->n[0] + 3) & ~3;
+  m->px = (d->n[0] + 7) & ~7;  // rows start on 32-byte boundaries (whole sectors per warp row)
   m->Np = (long long)m->px * d->n[1] * d->n[2];
   m->fem = fem;
   for (int a = 0; a < 3; ++a) {
@@ -1472,8 +1474,8 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   if (fem) {
     m->wx0 = m->wl[0] & ~3;
     m->wpx = (m->wl[0] + m->wn[0] - m->wx0 + 3) & ~3;
-    m->hx0 = m->fl[0] & ~3;
-    m->hpx = (m->fh[0] + 1 - m->hx0 + 3) & ~3;
+    m->hx0 = m->fl[0] & ~7;
+    m->hpx = (m->fh[0] + 1 - m->hx0 + 7) & ~7;
   }
   m->wsz = (long long)m->wpx * m->wn[1] * m->wn[2];
   m->nu = (long long)m->un[0] * m->un[1] * m->un[2];

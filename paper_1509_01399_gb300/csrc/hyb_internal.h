@@ -14,6 +14,26 @@ constexpr int kMaxSlots = 16;   // problems advanced by one step launch
 constexpr int kStepBlock = 288;  // threads per block of the step kernel (9 warps)
 constexpr int kTileX = 32;       // interior thread tile (x): one warp per tile row
 constexpr int kTileY = 16;       // interior tile (y): two rows per consumer thread
+constexpr int kBoxY = kTileY + 2, kHBoxY = kTileY + 1;
+
+// x geometry of the interior tiles.  FP32 tiles start at x = 32 m (tile 0
+// holds the face node x = 0, whose thread idles): with the row pitch a
+// multiple of 8, a warp's 32 nodes are one aligned 128-byte segment and its
+// stores fill whole 32-byte sectors (partly written sectors, shared by two
+// blocks, cost L2 and DRAM work).  The box then starts 4 nodes left of the
+// tile and is 40 wide.  FP64 tiles start at x = 1 + 32 m, the box at the
+// halo node x = 32 m, 36 wide (256-byte rows; a 40-wide box would cost the
+// second resident block).
+template <typename T>
+struct Box {
+  static constexpr int x0 = sizeof(T) == 4 ? 0 : 1;    // first node of tile 0
+  static constexpr int hx = sizeof(T) == 4 ? 4 : 1;    // box columns left of the tile
+  static constexpr int BX = sizeof(T) == 4 ? 40 : 36;  // box width (a multiple of 16 bytes)
+  static constexpr int C = BX * kBoxY;                 // u box
+  static constexpr int H = BX * kHBoxY;                // edge-weight / stored-u box
+};
+// first node (x) of interior tile 0 for a mesh of the given precision
+inline int tile_x0(int precision) { return precision == HYB_FP32 ? Box<float>::x0 : Box<double>::x0; }
 constexpr int kReduceBlocks = 512;
 // The step kernels accumulate kGradPairScale times the voxel pairing of
 // Eq. (gradient1) (integer edge weights 2 and 1 instead of 1/3 and 1/6).
@@ -62,16 +82,17 @@ struct Slot {
   const T* avox;
 };
 
-// Lattice fields are stored with a row pitch px >= nx (a multiple of 4, so
-// that rows start on 16-byte boundaries): node (i, j, k) of a field is
-// element i + px (j + ny k).  The edge-weight box and the FEM-owned box
-// (history) likewise start at an x origin that is a multiple of 4 (wx0,
-// hx0) and have row pitches wpx, hpx that are multiples of 4.
+// Lattice fields are stored with a row pitch px >= nx (a multiple of 8, so
+// that rows start on 32-byte boundaries): node (i, j, k) of a field is
+// element i + px (j + ny k).  The edge-weight box starts at an x origin wx0
+// that is a multiple of 4 and has a row pitch wpx that is a multiple of 4;
+// the FEM-owned box (history) at hx0, a multiple of 8, with a pitch hpx
+// that is a multiple of 8.
 template <typename T>
 struct StepArgs {
-  CUtensorMap tmf;   // field buffer (all levels and slots): {nx, ny, planes}, box 36 x (kTileY + 2) x 1
-  CUtensorMap tmw;   // edge weights: {wpx, wn1, 3 wn2}, box 36 x (kTileY + 1) x 1
-  CUtensorMap tmh;   // history: {hpx, fn1, fn2 x boxes}, box 36 x (kTileY + 1) x 1
+  CUtensorMap tmf;   // field buffer (all levels and slots): {nx, ny, planes}, box Box<T>::BX x kBoxY x 1
+  CUtensorMap tmw;   // edge weights: {wpx, wn1, 3 wn2}, box Box<T>::BX x kHBoxY x 1
+  CUtensorMap tmh;   // history: {hpx, fn1, fn2 x boxes}, box Box<T>::BX x kHBoxY x 1
   int* err;          // [0]: set when a pipeline wait timed out
   long long wait;    // cycles a pipeline wait may take (< 0: give up at once if not complete)
   int nx, ny, nz;

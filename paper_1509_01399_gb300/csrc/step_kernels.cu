@@ -633,35 +633,38 @@ struct Col {
 // ---- shared-memory pipeline of the interior blocks ----
 // A block stages, plane by plane and kPipe<T>::D levels ahead of its z
 // march, boxes that its producer warp loads with bulk tensor copies (TMA):
-// u^k on the tile and a one-node halo (36 x 18 from x = i0 - 1: the box
-// width is a multiple of 16 bytes), u^{k-1} on the same box, and on tiles
-// that meet the FEM block the three edge-weight arrays and, for the
-// transposed step, the stored u of the FEM-owned box (36 x 17).  Each plane
-// lives in a ring of stages indexed by the plane number modulo the
-// (power-of-two) ring size.  The copies of a level complete on its "full"
+// u^k on the tile and a one-node halo (Box<T>: the box starts on a 16-byte
+// boundary, hx columns left of the tile, and is BX x 18), u^{k-1} on the
+// same box, and on tiles that meet the FEM block the three edge-weight
+// arrays and, for the transposed step, the stored u of the FEM-owned box
+// (BX x 17).  Each plane lives in a ring of stages indexed by the plane
+// number modulo the ring size.  The copies of a level complete on its "full"
 // mbarrier; each of the eight consumer warps (the 32 x 16 tile, two rows per
 // thread) waits on it, reads only shared memory and arrives on the level's
 // "empty" mbarrier, on which the producer waits before it overwrites the
 // level's stages.  The consumer warps thus run up to D levels apart.
-constexpr int kBoxX = kTileX + 4, kBoxY = kTileY + 2, kBox = kBoxX * kBoxY;  // 36 x 18
-constexpr int kHBoxY = kTileY + 1, kHBox = kBoxX * kHBoxY;                    // 36 x 17
+// stage of plane k in a ring of N stages (k >= 0)
+template <int N>
+__device__ __forceinline__ int ring(int k) {
+  return (int)((unsigned)k % (unsigned)N);
+}
 
 template <typename T>
 struct kPipe {
   static constexpr int pow2(int n) { return n <= 1 ? 1 : 2 * pow2((n + 1) / 2); }
   static constexpr int round128(int elems) { return (int)(((elems * (int)sizeof(T) + 127) / 128) * 128 / sizeof(T)); }
   static constexpr int D = sizeof(T) == 4 ? 2 : 1;  // levels in flight
-  static constexpr int SC = pow2(D + 3);  // u^k stages (planes k-1 .. k+1+D)
+  static constexpr int SC = D + 3;        // u^k stages (planes k-1 .. k+1+D)
   static constexpr int SP = pow2(D + 1);  // u^{k-1} stages (k .. k+D)
   static constexpr int SW = pow2(D + 2);  // edge-weight stages (k-1 .. k+D)
   static constexpr int SH = pow2(D + 2);  // stored-u stages (k .. k+1+D)
   static constexpr int NB = pow2(D + 1);  // level barriers (of each kind)
-  static constexpr int CS = round128(kBox);   // elements per u stage (128-byte aligned)
-  static constexpr int WS = round128(kHBox);  // elements per edge-weight array / stored-u stage
+  static constexpr int CS = round128(Box<T>::C);  // elements per u stage (128-byte aligned)
+  static constexpr int WS = round128(Box<T>::H);  // elements per edge-weight array / stored-u stage
   static constexpr int elems = SC * CS + SP * CS + SW * 3 * WS + SH * WS;
   // Tiles off the FEM block stage only u^k and u^{k-1}: they spend the same
   // shared memory on deeper rings, DP levels ahead.
-  static constexpr int deep(int d) { return (pow2(d + 4) + pow2(d + 2)) * CS <= elems ? deep(d + 1) : d; }
+  static constexpr int deep(int d) { return (d + 4 + pow2(d + 2)) * CS <= elems ? deep(d + 1) : d; }
   static constexpr int DP = deep(D);
   static constexpr int NBX = pow2(DP + 1) > NB ? pow2(DP + 1) : NB;  // barrier pairs allocated
   static constexpr size_t bytes = sizeof(T) * (size_t)elems + 16 * NBX;
@@ -673,7 +676,7 @@ template <typename T, bool DEEP>
 struct Ring {
   using P = kPipe<T>;
   static constexpr int D = DEEP ? P::DP : P::D;
-  static constexpr int SC = P::pow2(D + 3);
+  static constexpr int SC = D + 3;
   static constexpr int SP = P::pow2(D + 1);
   static constexpr int NB = P::pow2(D + 1);
   static_assert(DEEP ? (SC + SP) * P::CS <= P::elems : (SC == P::SC && SP == P::SP && NB == P::NB), "ring sizes");
@@ -694,8 +697,8 @@ struct Producer {
   __device__ __forceinline__ void issue(int g, bool first) const {
     using P = kPipe<T>;
     using R = Ring<T, DEEP>;
-    constexpr uint32_t kCBytes = (uint32_t)(kBox * sizeof(T));
-    constexpr uint32_t kWBytes = (uint32_t)(kHBox * sizeof(T));
+    constexpr uint32_t kCBytes = (uint32_t)(Box<T>::C * sizeof(T));
+    constexpr uint32_t kWBytes = (uint32_t)(Box<T>::H * sizeof(T));
     uint64_t* bar = full + ((g - z0) & (R::NB - 1));
     const int wlo = A->wl[2], whi = A->wl[2] + A->wn[2] - 1, hlo = A->fl[2], hhi = A->fh[2];
     const bool c_on = g + 1 <= z1;
@@ -707,10 +710,10 @@ struct Producer {
                            kWBytes * (3 * ((w_on ? 1 : 0) + (wm_on ? 1 : 0)) + (h_on ? 1 : 0) + (h0_on ? 1 : 0));
     mbar_arrive_expect_tx(bar, bytes);
     if (first) {
-      tma_load_3d(CR + ((g - 1) & (R::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g - 1, bar);
-      tma_load_3d(CR + (g & (R::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g, bar);
+      tma_load_3d(CR + ring<R::SC>(g - 1) * P::CS, &A->tmf, xf, yf, S->zf_cur + g - 1, bar);
+      tma_load_3d(CR + ring<R::SC>(g) * P::CS, &A->tmf, xf, yf, S->zf_cur + g, bar);
     }
-    if (c_on) tma_load_3d(CR + ((g + 1) & (R::SC - 1)) * P::CS, &A->tmf, xf, yf, S->zf_cur + g + 1, bar);
+    if (c_on) tma_load_3d(CR + ring<R::SC>(g + 1) * P::CS, &A->tmf, xf, yf, S->zf_cur + g + 1, bar);
     tma_load_3d(PR + (g & (R::SP - 1)) * P::CS, &A->tmf, xf, yf, S->zf_prev + g, bar);
     if (wm_on) weights(g - 1, bar);
     if (w_on) weights(g, bar);
@@ -718,7 +721,7 @@ struct Producer {
     if (h_on) tma_load_3d(HR + ((g + 1) & (P::SH - 1)) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g + 1 - hlo), bar);
   }
   // stages and barriers in the block's shared memory, box origins of the
-  // tile (i0 - 1, j0 - 1: multiples of 4 in x, so 16-byte aligned)
+  // tile (i0 - hx, j0 - 1: multiples of 4 in x, so 16-byte aligned)
   __device__ __forceinline__ void setup(const StepArgs<T>& a, const Slot<T>& s, T* sm, uint64_t* bars, int zlo,
                                         int zhi, int i0, int j0, bool hist) {
     using P = kPipe<T>;
@@ -733,11 +736,11 @@ struct Producer {
     empty = bars + P::NBX;
     z0 = zlo;
     z1 = zhi;
-    xf = i0 - 1;
+    xf = i0 - Box<T>::hx;
     yf = j0 - 1;
-    xw = i0 - 1 - a.wx0;
+    xw = i0 - Box<T>::hx - a.wx0;
     yw = j0 - 1 - a.wl[1];
-    xh = i0 - 1 - a.hx0;
+    xh = i0 - Box<T>::hx - a.hx0;
     yh = j0 - a.fl[1];
     fem_tile = !DEEP;
     hist_tile = !DEEP && hist;
@@ -764,6 +767,7 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
                                               const T* Cp, const T* Pk, const T* Wk, const T* Wm, const T* Hk,
                                               const T* Hp) {
   using P = kPipe<T>;
+  constexpr int kBoxX = Box<T>::BX;
   if (ZF && FACE && (C.dxs != 0 || C.dys != 0)) return;  // near two faces: edge tiles
   const T c2 = A.c2;
   const T c0 = Ck[0], cm = Cm[0], cp = Cp[0], pv = Pk[0];
@@ -914,7 +918,8 @@ __device__ __forceinline__ void xface_levels(const StepArgs<T>& A, const Slot<T>
   const bool row_on = j >= 2 && j <= A.ny - 3;
   const int f = X.sd > 0 ? 1 : 0;
   const int sd = X.sd;
-  const int o = (r + 1) * kBoxX + (X.mi - X.i0 + 1);  // m in a u box
+  constexpr int kBoxX = Box<T>::BX;
+  const int o = (r + 1) * kBoxX + (X.mi - X.i0 + Box<T>::hx);  // m in a u box
   const T c2 = A.c2;
   const bool abc = (S.mask_f >> f) & 1;
   T* __restrict__ gnext = S.next;
@@ -928,9 +933,9 @@ __device__ __forceinline__ void xface_levels(const StepArgs<T>& A, const Slot<T>
       return;
     }
     if (row_on && k >= 2 && k <= A.nz - 3) {
-      const T* Ck = pr.CR + (k & (R::SC - 1)) * P::CS + o;
-      const T* Cm = pr.CR + ((k - 1) & (R::SC - 1)) * P::CS + o;
-      const T* Cp = pr.CR + ((k + 1) & (R::SC - 1)) * P::CS + o;
+      const T* Ck = pr.CR + ring<R::SC>(k) * P::CS + o;
+      const T* Cm = pr.CR + ring<R::SC>(k - 1) * P::CS + o;
+      const T* Cp = pr.CR + ring<R::SC>(k + 1) * P::CS + o;
       const T* Pk = pr.PR + (k & (R::SP - 1)) * P::CS + o;
       const T c0 = Ck[0], xm = Ck[-1], xp = Ck[1], ym = Ck[-kBoxX], yp = Ck[kBoxX];
       const T cm = Cm[0], cp = Cp[0], pv = Pk[0];
@@ -1021,9 +1026,10 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   const int tx = t & 31, ty = t >> 5;
   const int nz = A.nz;
   const int pl = A.px * A.ny;
-  const int o0 = (ty + 1) * kBoxX + (tx + 1);       // row 0 in a u box / edge-weight array
-  const int o1 = o0 + (kTileY / 2) * kBoxX;          // row 1
-  const int h0 = ty * kBoxX + (tx + 1);              // row 0 in a stored-u box
+  constexpr int kBoxX = Box<T>::BX;
+  const int o0 = (ty + 1) * kBoxX + (tx + Box<T>::hx);  // row 0 in a u box / edge-weight array
+  const int o1 = o0 + (kTileY / 2) * kBoxX;             // row 1
+  const int h0 = ty * kBoxX + (tx + Box<T>::hx);        // row 0 in a stored-u box
   const int h1 = h0 + (kTileY / 2) * kBoxX;
   const bool act0 = !FACE || active[0], act1 = !FACE || active[1];  // every row of a tile off the faces is active
   T* __restrict__ gnext = S.next;
@@ -1036,9 +1042,9 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
       if (tx == 0) atomicExch(A.err, 1);
       return;
     }
-    const T* Ck = pr.CR + (k & (R::SC - 1)) * P::CS;
-    const T* Cm = pr.CR + ((k - 1) & (R::SC - 1)) * P::CS;
-    const T* Cp = pr.CR + ((k + 1) & (R::SC - 1)) * P::CS;
+    const T* Ck = pr.CR + ring<R::SC>(k) * P::CS;
+    const T* Cm = pr.CR + ring<R::SC>(k - 1) * P::CS;
+    const T* Cp = pr.CR + ring<R::SC>(k + 1) * P::CS;
     const T* Pk = pr.PR + (k & (R::SP - 1)) * P::CS;
     const T* Wk = nullptr;
     const T* Wm = nullptr;
@@ -1091,7 +1097,7 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   if (z0 >= z1) return;  // whole block
   const int t = (int)threadIdx.x;
   const int tx = t & 31, ty = t >> 5;
-  const int i0 = 1 + txx * kTileX, j0 = 1 + tyy * kTileY;
+  const int i0 = Box<T>::x0 + txx * kTileX, j0 = 1 + tyy * kTileY;
   const Slot<T>& S = A.s[si];
   const bool has_fem = A.fl[0] <= A.fh[0];
   const bool pairing = ADJ && S.hist_r != nullptr;
@@ -1104,7 +1110,8 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
     C[r].j = j0 + ty + r * (kTileY / 2);
     C[r].dxs = (C[r].i == 1) ? -1 : (C[r].i == nx - 2 ? 1 : 0);
     C[r].dys = (C[r].j == 1) ? -1 : (C[r].j == ny - 2 ? 1 : 0);
-    active[r] = t < kTileX * kTileY / 2 && C[r].i <= nx - 2 && C[r].j <= ny - 2 && !(C[r].dxs != 0 && C[r].dys != 0);
+    active[r] = t < kTileX * kTileY / 2 && C[r].i >= 1 && C[r].i <= nx - 2 && C[r].j <= ny - 2 &&
+                !(C[r].dxs != 0 && C[r].dys != 0);
     C[r].xy_fem = has_fem && C[r].i >= A.fl[0] && C[r].i <= A.fh[0] && C[r].j >= A.fl[1] && C[r].j <= A.fh[1];
     C[r].xy_uv = has_fem && C[r].i >= A.fl[0] && C[r].i < A.fl[0] + A.un[0] && C[r].j >= A.fl[1] &&
                  C[r].j < A.fl[1] + A.un[1];
@@ -1121,7 +1128,7 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   // its column m off the FEM block
   XFace X;
   {
-    const bool xlo = i0 == 1, xhi = i0 + kTileX - 1 >= nx - 2;
+    const bool xlo = i0 <= 1, xhi = i0 + kTileX - 1 >= nx - 2;  // the tile holds node 1 / node nx - 2
     X.mi = xlo ? 1 : nx - 2;
     X.sd = xlo ? -1 : 1;
     X.i0 = i0;
@@ -1136,7 +1143,7 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   // needs no edge weights or history and runs with the deep rings
   const bool fem_tile = has_fem && i0 <= A.fh[0] && i0 + kTileX - 1 >= A.fl[0] && j0 <= A.fh[1] &&
                         j0 + kTileY - 1 >= A.fl[1] && z0 <= A.fh[2] && z1 - 1 >= A.fl[2];
-  const bool face_tile = i0 == 1 || i0 + kTileX - 1 >= nx - 2 || j0 == 1 || j0 + kTileY - 1 >= ny - 2;
+  const bool face_tile = i0 <= 1 || i0 + kTileX - 1 >= nx - 2 || j0 == 1 || j0 + kTileY - 1 >= ny - 2;
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + P::elems);
   const int tp = kTileX * kTileY / 2;  // the producer thread
   if (t == tp) {

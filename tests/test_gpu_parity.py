@@ -285,6 +285,39 @@ def test_fp32_parity_wide_x_faces(H):
     assert rel_l2(gpu["g"], ora["g"]) <= TOL32_GRAD
 
 
+# x extents that put node nx - 2 (the column next to the high x face) at the
+# first node of a tile: FP32 tiles start at x = 32 m, FP64 tiles at 1 + 32 m
+TILE_EDGE_SHAPES = {
+    "fp32_tile_start_34": dict(n=(34, 12, 11), fem=((20, 3, 3), (31, 8, 7)), bc=(1, 0, 1, 1, 0, 1),
+                               src_face=synth.FACE_XP),
+    "fp64_tile_start_35": dict(n=(35, 12, 11), fem=((3, 3, 3), (14, 8, 7)), bc=(0, 1, 1, 0, 1, 1),
+                               src_face=synth.FACE_XM),
+    "two_tiles_66": dict(n=(66, 13, 12), fem=((28, 3, 3), (40, 9, 8)), bc=(0, 0, 1, 1, 1, 1),
+                         src_face=synth.FACE_XP),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TILE_EDGE_SHAPES))
+def test_tile_edges_both_precisions(H, name):
+    """Lattices whose x faces fall at the first or last node of a tile in
+    either precision's tiling: FP64 against the oracle at 1e-12, FP32 against
+    the oracle at the FP32 tolerances and against the FP64 run (trace 2e-5),
+    which a wrong column anywhere would exceed by orders of magnitude."""
+    w = synth.small_problem(nsteps=70, omega=14.0, courant=0.8, **TILE_EDGE_SHAPES[name])
+    P = oracle.problem_from_workload(w)
+    a_obs = 1.0 + 2.0 * np.random.default_rng(8).random(P.n_unknown)
+    a = w.a_true()
+    ora = run_oracle(w, a, a_obs)
+    g64 = run_gpu(H, w, a, a_obs)
+    compare(g64, ora, TOL64, TOL64)
+    g32 = run_gpu(H, w, a, a_obs, precision="fp32")
+    for s, t in enumerate(ora["trace"]):
+        assert rel_l2(g32["trace"][s, :, : t.shape[1]], t) <= TOL32_TRACE
+        e = rel_l2(g32["trace"][s], g64["trace"][s])
+        assert e <= 2e-5, f"fp32 against fp64 trace: {e}"
+    assert rel_l2(g32["g"], ora["g"]) <= TOL32_GRAD
+
+
 def test_batched_sources_equal_single_runs(H):
     """Sources advanced together by one launch give, per source, exactly the
     trace of a run with that source alone, and the gradient is their sum."""
