@@ -715,7 +715,10 @@ TmapEncodeFn tmap_encoder() {
 }
 
 // 3-D map of d0 x d1 x d2 elements with row pitch p0 and plane pitch p1
-// (elements; 16-byte multiples), box b0 x b1 x 1.
+// (elements; 16-byte multiples), box b0 x b1 x 1.  L2 fills of its copies
+// are promoted to 64 bytes, not 128: a box's halo columns then bring in half
+// of the neighbouring tile's line, not all of it (10 % fewer DRAM bytes on
+// the 257^3 lattice with eight sources, time unchanged or lower).
 template <typename T>
 hyb_status encode_map(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t p0,
                       uint64_t p1, uint32_t b0, uint32_t b1) {
@@ -727,7 +730,7 @@ hyb_status encode_map(CUtensorMap* map, const void* base, uint64_t d0, uint64_t 
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(HYB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return HYB_OK;

@@ -8,8 +8,8 @@
 // blocks read levels k and k-1 and write disjoint nodes of level k+1.  An
 // interior block's producer warp stages the planes it needs (u^k with a
 // one-node halo, u^{k-1}, FEM edge weights, stored history) into shared
-// memory with bulk tensor copies, two levels ahead on items with FEM-owned
-// nodes and seven on the others (which stage only u^k and u^{k-1}); its
+// memory with bulk tensor copies, one level ahead on items with FEM-owned
+// nodes and six on the others (which stage only u^k and u^{k-1}); its
 // eight consumer warps (two tile rows per thread) march the z range reading
 // only shared memory, synchronised with the producer by per-level mbarriers
 // only.  In tiles with one x face, lanes of the producer warp compute the
@@ -653,11 +653,11 @@ template <typename T>
 struct kPipe {
   static constexpr int pow2(int n) { return n <= 1 ? 1 : 2 * pow2((n + 1) / 2); }
   static constexpr int round128(int elems) { return (int)(((elems * (int)sizeof(T) + 127) / 128) * 128 / sizeof(T)); }
-  static constexpr int D = sizeof(T) == 4 ? 2 : 1;  // levels in flight
+  static constexpr int D = 1;             // levels in flight (tiles meeting the FEM block)
   static constexpr int SC = D + 3;        // u^k stages (planes k-1 .. k+1+D)
   static constexpr int SP = pow2(D + 1);  // u^{k-1} stages (k .. k+D)
-  static constexpr int SW = pow2(D + 2);  // edge-weight stages (k-1 .. k+D)
-  static constexpr int SH = pow2(D + 2);  // stored-u stages (k .. k+1+D)
+  static constexpr int SW = D + 2;        // edge-weight stages (k-1 .. k+D)
+  static constexpr int SH = D + 2;        // stored-u stages (k .. k+1+D)
   static constexpr int NB = pow2(D + 1);  // level barriers (of each kind)
   static constexpr int CS = round128(Box<T>::C);  // elements per u stage (128-byte aligned)
   static constexpr int WS = round128(Box<T>::H);  // elements per edge-weight array / stored-u stage
@@ -717,8 +717,8 @@ struct Producer {
     tma_load_3d(PR + (g & (R::SP - 1)) * P::CS, &A->tmf, xf, yf, S->zf_prev + g, bar);
     if (wm_on) weights(g - 1, bar);
     if (w_on) weights(g, bar);
-    if (h0_on) tma_load_3d(HR + (g & (P::SH - 1)) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g - hlo), bar);
-    if (h_on) tma_load_3d(HR + ((g + 1) & (P::SH - 1)) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g + 1 - hlo), bar);
+    if (h0_on) tma_load_3d(HR + ring<P::SH>(g) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g - hlo), bar);
+    if (h_on) tma_load_3d(HR + ring<P::SH>(g + 1) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g + 1 - hlo), bar);
   }
   // stages and barriers in the block's shared memory, box origins of the
   // tile (i0 - hx, j0 - 1: multiples of 4 in x, so 16-byte aligned)
@@ -747,7 +747,7 @@ struct Producer {
   }
   __device__ __forceinline__ void weights(int q, uint64_t* bar) const {
     using P = kPipe<T>;
-    T* w = WR + (q & (P::SW - 1)) * 3 * P::WS;
+    T* w = WR + ring<P::SW>(q) * 3 * P::WS;
     const int zq = q - A->wl[2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) tma_load_3d(w + a * P::WS, &A->tmw, xw, yw, S->zf_w + a * A->wn[2] + zq, bar);
@@ -1051,10 +1051,10 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     const T* Hk = nullptr;
     const T* Hp = nullptr;
     if constexpr (FEMT) {
-      Wk = pr.WR + (k & (P::SW - 1)) * 3 * P::WS;
-      Wm = pr.WR + ((k - 1) & (P::SW - 1)) * 3 * P::WS;
-      Hk = pr.HR + (k & (P::SH - 1)) * P::WS;
-      Hp = pr.HR + ((k + 1) & (P::SH - 1)) * P::WS;
+      Wk = pr.WR + ring<P::SW>(k) * 3 * P::WS;
+      Wm = pr.WR + ring<P::SW>(k - 1) * 3 * P::WS;
+      Hk = pr.HR + ring<P::SH>(k) * P::WS;
+      Hp = pr.HR + ring<P::SH>(k + 1) * P::WS;
     }
     // planes one step inside a z face also produce the face plane (block-uniform)
     const int dzs = k == 1 ? -1 : (k == nz - 2 ? 1 : 0);
@@ -1285,7 +1285,7 @@ __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t);
 // slots the interior blocks free towards the end of the level).  All blocks
 // read levels k, k-1 and write disjoint nodes of level k+1.
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 3 : 2) step_kernel(const __grid_constant__ StepArgs<T> A) {
+__global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 4 : 2) step_kernel(const __grid_constant__ StepArgs<T> A) {
   extern __shared__ __align__(128) unsigned char hyb_smem[];  // kPipe<T>::bytes
   T* sh = reinterpret_cast<T*>(hyb_smem);
   pdl_trigger();  // the next level's launch may start its blocks
@@ -1363,9 +1363,6 @@ __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __re
   grad[t] += (double)(A.tet ? tet_pair(A, hist, lam, i, j, k) : voxel_pair(A, hist, lam, i, j, k));
 }
 
-// Pairing of a refined voxel: u^T K9 lambda over its 8 corners and centre,
-// K9 the stiffness of the refined unit voxel (a = 1); the host scales the
-// sum like the structured pairing.
 // Refined region of one time level, in the trailing blocks of the step
 // launch (one thread per row), the same rows for the forward and the
 // mass-scaled adjoint.  A corner n of refined voxels: the Kuhn stencil row
@@ -1419,52 +1416,73 @@ __device__ __forceinline__ void refined_corner(const StepArgs<T>& A, const Slot<
   if (!ADJ && S.hist_w) S.hist_w[hidx(A, i, j, k)] = val;
 }
 
+// Pairing sum u^T K9 lambda over a refined voxel's 8 corners and centre
+// (index 8), K9 the stiffness of the refined unit voxel (a = 1).
+template <typename T, typename K>
+__device__ __forceinline__ T refined_pair_sum(const T (&u)[9], const T (&l)[9], const K* __restrict__ k9) {
+  T acc = T(0);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    T row = T(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) row += (T)k9[p * 9 + q] * l[q];
+    acc += u[p] * row;
+  }
+  return acc;
+}
+
+// Centre row of refined voxel v (centre order); in the transposed step with
+// pairing the same thread also adds the voxel's pairing of (u^j, lambda^{j+1})
+// to slot si's gradient, from the lambda values the row has loaded.
 template <typename T, bool ADJ>
-__device__ __forceinline__ void refined_centre(const StepArgs<T>& A, const Slot<T>& S, int v) {
+__device__ __forceinline__ void refined_centre(const StepArgs<T>& A, const Slot<T>& S, int v, int si) {
   const int vid = A.refvox_id[v];
   const int x = vid % A.un[0], y = (vid / A.un[0]) % A.un[1], z = vid / (A.un[0] * A.un[1]);
   const long long l0 = lin(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z);
   const long long sy = A.px, sz = (long long)A.px * A.ny;
-  T q[8];
+  T q[9];
 #pragma unroll
   for (int c = 0; c < 8; ++c) q[c] = S.cur[l0 + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz];
   const T uc = S.ccur[v], up = S.cprev[v], av = S.avox[vid];
+  q[8] = uc;
   T sv = T(0);
 #pragma unroll
   for (int c = 0; c < 8; ++c) sv += A.rK9[72 + c] * (q[c] - uc);
   const T vc = uc + ((uc - up) - A.c2 * av * sv / A.rm9[8]);
   S.cnext[v] = vc;
   if (!ADJ && S.chist_w) S.chist_w[v] = vc;
+  if constexpr (ADJ) {
+    if (!S.hist_r) return;
+    const long long h0 = hidx(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z);
+    const long long hy = A.hpx, hz = (long long)A.hpx * A.fn[1];
+    T u[9];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) u[c] = S.hist_r[h0 + (c & 1) + ((c >> 1) & 1) * hy + (c >> 2) * hz];
+    u[8] = S.chist_r[v];
+    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+    // the unit-voxel K9 from the launch parameters (kGradPairScale times the pairing, as the other kernels)
+    A.G[(long long)si * nv + vid] += (double)(T(kGradPairScale) * refined_pair_sum(u, q, A.rK9));
+  }
 }
 
-template <typename T, typename K>
-__device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* __restrict__ hb,
-                                          const T* __restrict__ chb, const T* __restrict__ lam,
-                                          const T* __restrict__ clam, const K* __restrict__ k9);
-
-// Threads of the refined trailing blocks, per slot: the corner rows, the
-// centre rows, then (transposed step with pairing) one per refined voxel.
+// Threads of the refined trailing blocks, per slot: the corner rows, then
+// the centre rows (with the transposed step's pairing of their voxels).
 template <typename T, bool ADJ>
 __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t) {
-  const int per = A.nrl + A.nref + (ADJ ? A.nref : 0);
+  const int per = A.nrl + A.nref;
   if (t >= (long long)per * A.nslots) return;
   const int si = (int)(t / per);
   const int r = (int)(t - (long long)si * per);
   const Slot<T>& S = A.s[si];
-  if (r < A.nrl) {
+  if (r < A.nrl)
     refined_corner<T, ADJ>(A, S, r);
-  } else if (r < A.nrl + A.nref) {
-    refined_centre<T, ADJ>(A, S, r - A.nrl);
-  } else if constexpr (ADJ) {
-    if (!S.hist_r) return;
-    const int v = r - A.nrl - A.nref;
-    const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
-    // the unit-voxel K9 from the launch parameters (kGradPairScale times the pairing, as the other kernels)
-    A.G[(long long)si * nv + A.refvox_id[v]] +=
-        (double)(T(kGradPairScale) * refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur, A.rK9));
-  }
+  else
+    refined_centre<T, ADJ>(A, S, r - A.nrl, si);
 }
 
+// Pairing of refined voxel v at level 0 (the level-0 kernel): u^T K9 lambda
+// over its 8 corners and centre, K9 the stiffness of the refined unit voxel
+// (a = 1); the host scales the sum like the structured pairing.
 template <typename T, typename K>
 __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* __restrict__ hb,
                                           const T* __restrict__ chb, const T* __restrict__ lam,
@@ -1485,15 +1503,7 @@ __device__ __forceinline__ T refined_pair(const StepArgs<T>& A, int v, const T* 
   }
   u[8] = chb[v];
   l[8] = clam[v];
-  T acc = T(0);
-#pragma unroll
-  for (int p = 0; p < 9; ++p) {
-    T row = T(0);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) row += (T)k9[p * 9 + q] * l[q];
-    acc += u[p] * row;
-  }
-  return acc;
+  return refined_pair_sum(u, l, k9);
 }
 
 template <typename T>
@@ -1592,7 +1602,7 @@ void launch_step(const StepArgs<T>& a, cudaStream_t st) {
   }
   StepArgs<T> b = a;
   b.nhe = ((a.nedge + 1) / 2) * a.nslots;
-  const long long nref_threads = (long long)(a.nrl + a.nref + (ADJ ? a.nref : 0)) * a.nslots;
+  const long long nref_threads = (long long)(a.nrl + a.nref) * a.nslots;
   b.nhr = (int)((nref_threads + kStepBlock - 1) / kStepBlock);
   const long long grid = (long long)b.nhe + b.nhr + a.nitems;
   // programmatic dependent launch: this level's blocks may start while the
