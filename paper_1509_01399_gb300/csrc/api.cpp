@@ -743,6 +743,8 @@ template <typename T>
 hyb_status step_maps(const hyb_mesh* m, StepArgs<T>& A, const DevBuf& field, int nsrc, int hist_levels) {
   HYB_TRY(encode_map<T>(&A.tmf, field.p, m->n[0], m->n[1], (uint64_t)m->n[2] * 3 * nsrc, m->px,
                         (uint64_t)m->px * m->n[1], Box<T>::BX, kBoxY));
+  HYB_TRY(encode_map<T>(&A.tmp, field.p, m->n[0], m->n[1], (uint64_t)m->n[2] * 3 * nsrc, m->px,
+                        (uint64_t)m->px * m->n[1], Box<T>::PX, kTileY));
   if (m->fem && m->wsz > 0)
     HYB_TRY(encode_map<T>(&A.tmw, m->W.p, m->wpx, m->wn[1], 3ull * m->wn[2] * (m->batch ? nsrc : 1), m->wpx,
                           (uint64_t)m->wpx * m->wn[1], Box<T>::BX, kHBoxY));

@@ -31,6 +31,11 @@ struct Box {
   static constexpr int BX = sizeof(T) == 4 ? 40 : 36;  // box width (a multiple of 16 bytes)
   static constexpr int C = BX * kBoxY;                 // u box
   static constexpr int H = BX * kHBoxY;                // edge-weight / stored-u box
+  // u^{k-1} on tiles off the faces: only the tile's own nodes are read, so
+  // the box has no y halo and (FP32) no x halo: PX x kTileY from x = i0 - phx
+  static constexpr int phx = sizeof(T) == 4 ? 0 : 1;
+  static constexpr int PX = sizeof(T) == 4 ? 32 : 34;
+  static constexpr int P = PX * kTileY;
 };
 // first node (x) of interior tile 0 for a mesh of the given precision
 inline int tile_x0(int precision) { return precision == HYB_FP32 ? Box<float>::x0 : Box<double>::x0; }
@@ -93,6 +98,7 @@ struct StepArgs {
   CUtensorMap tmf;   // field buffer (all levels and slots): {nx, ny, planes}, box Box<T>::BX x kBoxY x 1
   CUtensorMap tmw;   // edge weights: {wpx, wn1, 3 wn2}, box Box<T>::BX x kHBoxY x 1
   CUtensorMap tmh;   // history: {hpx, fn1, fn2 x boxes}, box Box<T>::BX x kHBoxY x 1
+  CUtensorMap tmp;   // field buffer as tmf, box Box<T>::PX x kTileY x 1 (u^{k-1} off the faces)
   int* err;          // [0]: set when a pipeline wait timed out
   long long wait;    // cycles a pipeline wait may take (< 0: give up at once if not complete)
   int nx, ny, nz;

@@ -690,14 +690,15 @@ struct Producer {
   T *CR, *PR, *WR, *HR;
   uint64_t* full;   // [NB]: the planes of a level have landed (one arrival: the producer, plus bytes)
   uint64_t* empty;  // [NB]: the consumer warps are done with a level (eight arrivals)
-  int z0, z1, xf, yf, xw, yw, xh, yh;
-  bool fem_tile, hist_tile;
+  int z0, z1, xf, yf, xw, yw, xh, yh, xp, yp;
+  bool fem_tile, hist_tile, pface;  // pface: u^{k-1} with its halo (tiles holding face-adjacent nodes)
   // the planes first read at level g (the first level also reads planes
   // g - 1 and g of u^k, g - 1 of the weights and g of the stored u)
   __device__ __forceinline__ void issue(int g, bool first) const {
     using P = kPipe<T>;
     using R = Ring<T, DEEP>;
     constexpr uint32_t kCBytes = (uint32_t)(Box<T>::C * sizeof(T));
+    constexpr uint32_t kPBytes = (uint32_t)(Box<T>::P * sizeof(T));
     constexpr uint32_t kWBytes = (uint32_t)(Box<T>::H * sizeof(T));
     uint64_t* bar = full + ((g - z0) & (R::NB - 1));
     const int wlo = A->wl[2], whi = A->wl[2] + A->wn[2] - 1, hlo = A->fl[2], hhi = A->fh[2];
@@ -706,7 +707,7 @@ struct Producer {
     const bool wm_on = !DEEP && first && fem_tile && g - 1 >= wlo && g - 1 <= whi;
     const bool h_on = !DEEP && hist_tile && g + 1 >= hlo && g + 1 <= hhi;
     const bool h0_on = !DEEP && first && hist_tile && g >= hlo && g <= hhi;
-    const uint32_t bytes = kCBytes * ((c_on ? 1 : 0) + 1 + (first ? 2 : 0)) +
+    const uint32_t bytes = kCBytes * ((c_on ? 1 : 0) + (pface ? 1 : 0) + (first ? 2 : 0)) + (pface ? 0u : kPBytes) +
                            kWBytes * (3 * ((w_on ? 1 : 0) + (wm_on ? 1 : 0)) + (h_on ? 1 : 0) + (h0_on ? 1 : 0));
     mbar_arrive_expect_tx(bar, bytes);
     if (first) {
@@ -714,7 +715,10 @@ struct Producer {
       tma_load_3d(CR + ring<R::SC>(g) * P::CS, &A->tmf, xf, yf, S->zf_cur + g, bar);
     }
     if (c_on) tma_load_3d(CR + ring<R::SC>(g + 1) * P::CS, &A->tmf, xf, yf, S->zf_cur + g + 1, bar);
-    tma_load_3d(PR + (g & (R::SP - 1)) * P::CS, &A->tmf, xf, yf, S->zf_prev + g, bar);
+    if (pface)
+      tma_load_3d(PR + (g & (R::SP - 1)) * P::CS, &A->tmf, xf, yf, S->zf_prev + g, bar);
+    else
+      tma_load_3d(PR + (g & (R::SP - 1)) * P::CS, &A->tmp, xp, yp, S->zf_prev + g, bar);
     if (wm_on) weights(g - 1, bar);
     if (w_on) weights(g, bar);
     if (h0_on) tma_load_3d(HR + ring<P::SH>(g) * P::WS, &A->tmh, xh, yh, S->zf_hist + (g - hlo), bar);
@@ -723,7 +727,7 @@ struct Producer {
   // stages and barriers in the block's shared memory, box origins of the
   // tile (i0 - hx, j0 - 1: multiples of 4 in x, so 16-byte aligned)
   __device__ __forceinline__ void setup(const StepArgs<T>& a, const Slot<T>& s, T* sm, uint64_t* bars, int zlo,
-                                        int zhi, int i0, int j0, bool hist) {
+                                        int zhi, int i0, int j0, bool hist, bool face) {
     using P = kPipe<T>;
     using R = Ring<T, DEEP>;
     A = &a;
@@ -742,6 +746,9 @@ struct Producer {
     yw = j0 - 1 - a.wl[1];
     xh = i0 - Box<T>::hx - a.hx0;
     yh = j0 - a.fl[1];
+    xp = i0 - Box<T>::phx;
+    yp = j0;
+    pface = face;
     fem_tile = !DEEP;
     hist_tile = !DEEP && hist;
   }
@@ -1031,6 +1038,9 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   const int o1 = o0 + (kTileY / 2) * kBoxX;             // row 1
   const int h0 = ty * kBoxX + (tx + Box<T>::hx);        // row 0 in a stored-u box
   const int h1 = h0 + (kTileY / 2) * kBoxX;
+  // u^{k-1}: the u box layout on face tiles, else the halo-free box
+  const int p0 = FACE ? o0 : ty * Box<T>::PX + (tx + Box<T>::phx);
+  const int p1 = FACE ? o1 : p0 + (kTileY / 2) * Box<T>::PX;
   const bool act0 = !FACE || active[0], act1 = !FACE || active[1];  // every row of a tile off the faces is active
   T* __restrict__ gnext = S.next;
   int off0 = C[0].i + A.px * C[0].j + pl * z0;       // field offsets of the two nodes
@@ -1061,17 +1071,17 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     if (dzs != 0) {
       if (act0)
         interior_node<T, ADJ, FEMT, FACE, true, REF>(A, S, gnext, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0,
-                                                Pk + o0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
+                                                Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
       if (act1)
         interior_node<T, ADJ, FEMT, FACE, true, REF>(A, S, gnext, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1,
-                                                Pk + o1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
+                                                Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
     } else {
       if (act0)
         interior_node<T, ADJ, FEMT, FACE, false, REF>(A, S, gnext, C[0], k, off0, 0, Ck + o0, Cm + o0, Cp + o0,
-                                                 Pk + o0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
+                                                 Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
       if (act1)
         interior_node<T, ADJ, FEMT, FACE, false, REF>(A, S, gnext, C[1], k, off1, 0, Ck + o1, Cm + o1, Cp + o1,
-                                                 Pk + o1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
+                                                 Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
     }
     __syncwarp();  // the warp's reads of level k's stages are done
     if (tx == 0) mbar_arrive(pr.empty + (q & (R::NB - 1)));
@@ -1163,7 +1173,7 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
                         (C[1].rz0 <= C[1].rz1 && C[1].rz0 < z1 && C[1].rz1 >= z0)));
   if (fem_tile) {
     Producer<T, false> pr;
-    pr.setup(A, S, sm, full, z0, z1, i0, j0, pairing);
+    pr.setup(A, S, sm, full, z0, z1, i0, j0, pairing, face_tile);
     if (ref_tile) {
       if (face_tile)
         interior_levels<T, ADJ, true, true, true>(A, S, C, pr, active, X, z0, z1);
@@ -1177,7 +1187,7 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
     }
   } else {
     Producer<T, true> pr;
-    pr.setup(A, S, sm, full, z0, z1, i0, j0, false);
+    pr.setup(A, S, sm, full, z0, z1, i0, j0, false, face_tile);
     if (face_tile)
       interior_levels<T, ADJ, false, true, false>(A, S, C, pr, active, X, z0, z1);
     else
