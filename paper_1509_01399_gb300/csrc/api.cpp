@@ -104,7 +104,7 @@ struct hyb_mesh {
   // refined region
   int nc = 0, nr = 0, nrl = 0, nnz = 0;
   double dt_max = 0.0;
-  DevBuf rmask, rzr, refvox, refvox_id, k9, rcid, avox, rrow;
+  DevBuf rmask, rzr, refvox, refvox_id, k9, rcid, avox, rpos, rvxyz;
   double uK9[81], uK8[64], um9[9], um8[8];  // unit-voxel stiffness and lumped masses (refined, Kuhn)
   std::vector<int> ref_rows;  // per interior tile and plane: tile rows holding refined-voxel corners
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
@@ -650,7 +650,16 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   for (int q = 0; q < 8; ++q) m->um8[q] = m8[q];
   HYB_TRY(upload(m, m->rmask, rmask));
   HYB_TRY(upload(m, m->rcid, cid));
-  HYB_TRY(upload(m, m->rrow, rows));
+  // corner positions packed for the kernel: (i | j << 16, k)
+  if (m->n[0] > 65535 || m->n[1] > 65535) return fail(HYB_ERR_ARG, "refinement needs n < 65536 along x and y");
+  std::vector<unsigned> pos(2 * rows.size());
+  for (size_t r = 0; r < rows.size(); ++r) {
+    const long long id = rows[r], plane = (long long)m->px * m->n[1];
+    const long long i = id % m->px, j = (id / m->px) % m->n[1], k = id / plane;
+    pos[2 * r] = (unsigned)i | ((unsigned)j << 16);
+    pos[2 * r + 1] = (unsigned)k;
+  }
+  HYB_TRY(upload(m, m->rpos, pos));
   // z range of the sparse-row nodes of each FEM-owned column
   std::vector<int> rzr((size_t)2 * m->fn[0] * m->fn[1]);
   for (size_t c = 0; c < rzr.size() / 2; ++c) {
@@ -688,6 +697,14 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   }
   HYB_TRY(upload(m, m->refvox, refv));
   HYB_TRY(upload(m, m->refvox_id, refid));
+  // the refined voxels' origins packed for the kernel: (x | y << 16, z) in unknown-voxel coordinates
+  std::vector<unsigned> vxyz(2 * refid.size());
+  for (size_t v = 0; v < refid.size(); ++v) {
+    const long long id = refid[v];
+    vxyz[2 * v] = (unsigned)(id % m->un[0]) | ((unsigned)((id / m->un[0]) % m->un[1]) << 16);
+    vxyz[2 * v + 1] = (unsigned)(id / ((long long)m->un[0] * m->un[1]));
+  }
+  HYB_TRY(upload(m, m->rvxyz, vxyz));
   HYB_TRY(upload(m, m->k9, k9));
   HYB_TRY(ensure(m, m->avox, (size_t)nu * esize(m)));
   return HYB_OK;
@@ -812,7 +829,8 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   if (m->nc > 0) {
     A.nref = m->nc;
     A.nrl = m->nrl;
-    A.rrow = (const long long*)m->rrow.p;
+    A.rpos = (const uint2*)m->rpos.p;
+    A.rvxyz = (const uint2*)m->rvxyz.p;
     A.rcid = (const int*)m->rcid.p;
     for (int q = 0; q < 81; ++q) A.rK9[q] = (T)m->uK9[q];
     for (int c = 0; c < 8; ++c) {
@@ -1549,7 +1567,7 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   cudaStreamSynchronize(m->st);
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
                     &m->g, &m->atrial, &m->cot, &m->trace, &m->rmask, &m->rzr, &m->refvox, &m->refvox_id,
-                    &m->k9, &m->rcid, &m->avox, &m->rrow,
+                    &m->k9, &m->rcid, &m->avox, &m->rpos, &m->rvxyz,
                     &m->CU, &m->CL, &m->chist, &m->cckpt, &m->I0, &m->IC0, &m->acopy, &m->kuhn, &m->kuhn_v};
   for (DevBuf* b : bufs) release(*b);
   for (auto& dir : m->items)

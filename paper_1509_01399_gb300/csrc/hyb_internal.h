@@ -129,7 +129,7 @@ struct StepArgs {
   // blocks skip those nodes.
   int nref;                   // refined voxels (= centre nodes)
   int nrl;                    // corners of refined voxels (lattice rows of the refined region)
-  const long long* rrow;      // lattice id of each such corner
+  const uint2* rpos;          // each such corner (i | j << 16, k)
   const unsigned char* rmask; // FEM-owned box: 1 = the node is a corner of a refined voxel
   const int* rzr;             // per FEM-owned column (i - fl0) + fn0 (j - fl1): [kmin, kmax] of its
                               // refined corners (kmin > kmax: none)
@@ -137,6 +137,7 @@ struct StepArgs {
   const T* avox;              // per unknown voxel: the coefficient a (of slot 0; slots carry their own)
   const unsigned char* refvox;// unknown voxels: 1 = refined
   const int* refvox_id;       // unknown id of each refined voxel (centre order)
+  const uint2* rvxyz;         // its origin in unknown-voxel coordinates (x | y << 16, z)
   const double* k9;           // 9 x 9 stiffness of a refined unit voxel, a = 1 (level-0 pairing)
   // unit-voxel tables (a = 1, corners a + 2b + 4c, centre 8): K9 of the
   // refined voxel, dK[c][q] = K9[c][q] - K8[c][q] (q = 8: K9[c][8]) against

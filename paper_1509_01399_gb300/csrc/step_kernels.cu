@@ -1385,13 +1385,40 @@ __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __re
 // Every load of a row is issued before the row is summed.
 template <typename T, bool ADJ>
 __device__ __forceinline__ void refined_corner(const StepArgs<T>& A, const Slot<T>& S, int r) {
-  const long long id = A.rrow[r];
-  const int i = (int)(id % A.px), j = (int)((id / A.px) % A.ny), k = (int)(id / ((long long)A.px * A.ny));
+  const uint2 pos = A.rpos[r];
+  const int i = (int)(pos.x & 0xffffu), j = (int)(pos.x >> 16), k = (int)pos.y;
   const long long sy = A.px, sz = (long long)A.px * A.ny;
+  const long long id = i + sy * j + sz * k;
   const T* __restrict__ u = S.cur;
-  const T c0 = u[id], pv = S.prev[id];
-  const T zm = u[id - sz], zp = u[id + sz];
-  const T lapW = fem_lap(A, S.W, u, id, i, j, k, c0, zm, zp);
+  // the node's 3 x 3 x 3 neighbourhood (index (dx+1) + 3 (dy+1) + 9 (dz+1)):
+  // a refined voxel's K9 - K8 couples n only to the six face neighbours
+  // (which the stencil reads too) and to the six neighbours across the
+  // diagonals of the coordinate planes with equal signs; a corner of a
+  // refined voxel lies inside the FEM block, so all of them are lattice nodes
+  T nb[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) nb[q] = T(0);
+  nb[13] = u[id];
+  nb[12] = u[id - 1];
+  nb[14] = u[id + 1];
+  nb[10] = u[id - sy];
+  nb[16] = u[id + sy];
+  nb[4] = u[id - sz];
+  nb[22] = u[id + sz];
+  nb[9] = u[id - 1 - sy];
+  nb[17] = u[id + 1 + sy];
+  nb[3] = u[id - 1 - sz];
+  nb[23] = u[id + 1 + sz];
+  nb[1] = u[id - sy - sz];
+  nb[25] = u[id + sy + sz];
+  const T c0 = nb[13], pv = S.prev[id];
+  const long long w = widx(A, i, j, k);
+  const T* Wx = S.W;
+  const T* Wy = S.W + A.wsz;
+  const T* Wz = S.W + 2 * A.wsz;
+  const long long wy = A.wpx, wz = (long long)A.wpx * A.wn[1];
+  const T lapW = Wx[w] * (nb[14] - c0) + Wx[w - 1] * (nb[12] - c0) + Wy[w] * (nb[16] - c0) +
+                 Wy[w - wy] * (nb[10] - c0) + Wz[w] * (nb[22] - c0) + Wz[w - wz] * (nb[4] - c0);
   // the eight voxels around n (n is corner c of the voxel with origin n - c)
   const int ox = i - A.fl[0], oy = j - A.fl[1], oz = k - A.fl[2];
   const int v0 = ox + A.un[0] * (oy + A.un[1] * oz), vy = A.un[0], vz = A.un[0] * A.un[1];
@@ -1416,8 +1443,8 @@ __device__ __forceinline__ void refined_corner(const StepArgs<T>& A, const Slot<
     for (int q = 0; q < 8; ++q) {
       const bool diag_c = c == 0 || c == 7, diag_q = q == 0 || q == 7;
       if (q == c || diag_c == diag_q) continue;
-      const long long o = ((q & 1) - dx) + ((long long)((q >> 1) & 1) - dy) * sy + ((long long)(q >> 2) - dz) * sz;
-      sv += A.rdK[9 * c + q] * ((ref ? u[id + o] : c0) - c0);
+      const int o = ((q & 1) - dx + 1) + 3 * (((q >> 1) & 1) - dy + 1) + 9 * ((q >> 2) - dz + 1);
+      sv += A.rdK[9 * c + q] * (nb[o] - c0);
     }
     corr += av * sv;
   }
@@ -1447,7 +1474,8 @@ __device__ __forceinline__ T refined_pair_sum(const T (&u)[9], const T (&l)[9], 
 template <typename T, bool ADJ>
 __device__ __forceinline__ void refined_centre(const StepArgs<T>& A, const Slot<T>& S, int v, int si) {
   const int vid = A.refvox_id[v];
-  const int x = vid % A.un[0], y = (vid / A.un[0]) % A.un[1], z = vid / (A.un[0] * A.un[1]);
+  const uint2 xyz = A.rvxyz[v];
+  const int x = (int)(xyz.x & 0xffffu), y = (int)(xyz.x >> 16), z = (int)xyz.y;
   const long long l0 = lin(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z);
   const long long sy = A.px, sz = (long long)A.px * A.ny;
   T q[9];
