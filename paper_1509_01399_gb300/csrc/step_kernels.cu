@@ -1045,6 +1045,16 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   T* __restrict__ gnext = S.next;
   int off0 = C[0].i + A.px * C[0].j + pl * z0;       // field offsets of the two nodes
   int off1 = off0 + (kTileY / 2) * A.px;
+  // ring stages of planes k - 1, k, k + 1 (rotated from level to level
+  // instead of reduced modulo the ring size at every level)
+  int scm = ring<R::SC>(z0 - 1), sck = ring<R::SC>(z0), scp = ring<R::SC>(z0 + 1);
+  int swm = 0, swk = 0, shk = 0, shp = 0;
+  if constexpr (FEMT) {
+    swm = ring<P::SW>(z0 - 1);
+    swk = ring<P::SW>(z0);
+    shk = ring<P::SH>(z0);
+    shp = ring<P::SH>(z0 + 1);
+  }
   for (int k = z0; k < z1; ++k, off0 += pl, off1 += pl) {
     const int q = k - z0;
     const bool ok = mbar_wait(pr.full + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), budget, A.err);
@@ -1052,19 +1062,19 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
       if (tx == 0) atomicExch(A.err, 1);
       return;
     }
-    const T* Ck = pr.CR + ring<R::SC>(k) * P::CS;
-    const T* Cm = pr.CR + ring<R::SC>(k - 1) * P::CS;
-    const T* Cp = pr.CR + ring<R::SC>(k + 1) * P::CS;
+    const T* Ck = pr.CR + sck * P::CS;
+    const T* Cm = pr.CR + scm * P::CS;
+    const T* Cp = pr.CR + scp * P::CS;
     const T* Pk = pr.PR + (k & (R::SP - 1)) * P::CS;
     const T* Wk = nullptr;
     const T* Wm = nullptr;
     const T* Hk = nullptr;
     const T* Hp = nullptr;
     if constexpr (FEMT) {
-      Wk = pr.WR + ring<P::SW>(k) * 3 * P::WS;
-      Wm = pr.WR + ring<P::SW>(k - 1) * 3 * P::WS;
-      Hk = pr.HR + ring<P::SH>(k) * P::WS;
-      Hp = pr.HR + ring<P::SH>(k + 1) * P::WS;
+      Wk = pr.WR + swk * 3 * P::WS;
+      Wm = pr.WR + swm * 3 * P::WS;
+      Hk = pr.HR + shk * P::WS;
+      Hp = pr.HR + shp * P::WS;
     }
     // planes one step inside a z face also produce the face plane (block-uniform)
     const int dzs = k == 1 ? -1 : (k == nz - 2 ? 1 : 0);
@@ -1085,6 +1095,15 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     }
     __syncwarp();  // the warp's reads of level k's stages are done
     if (tx == 0) mbar_arrive(pr.empty + (q & (R::NB - 1)));
+    scm = sck;
+    sck = scp;
+    scp = scp + 1 == R::SC ? 0 : scp + 1;
+    if constexpr (FEMT) {
+      swm = swk;
+      swk = swk + 1 == P::SW ? 0 : swk + 1;
+      shk = shp;
+      shp = shp + 1 == P::SH ? 0 : shp + 1;
+    }
   }
 }
 
