@@ -70,15 +70,17 @@ def make_data(w, noise: float, seed: int, device="cuda") -> torch.Tensor:
     return out
 
 
-def reconstruct(w, obs: torch.Tensor, max_iter: int = 15, device="cuda") -> Dict:
+def reconstruct(w, obs: torch.Tensor, max_iter: int = 15, device="cuda", gamma=None) -> Dict:
     """Algorithm 3 from a = a0 on the unrefined mesh; stops at ||g|| <= theta,
-    at stabilised ||g|| (relative change < 1 %) or after max_iter."""
+    at stabilised ||g|| (relative change < 1 %) or after max_iter.  gamma:
+    the regularisation parameter (default: the workload's, 0.01)."""
+    gamma = w.extra["gamma"] if gamma is None else gamma
     m = _mesh(w, device)
     a = torch.full((w.n_unknown,), w.extra["a0"], dtype=torch.float64, device=device)
     st = m.new_cg_state()
     hist = []
     for it in range(max_iter):
-        rep = m.cg_step(a, obs, w.sources, w.nsteps, w.dt, st, gamma=w.extra["gamma"], a0=w.extra["a0"],
+        rep = m.cg_step(a, obs, w.sources, w.nsteps, w.dt, st, gamma=gamma, a0=w.extra["a0"],
                         a_min=1.0, a_max=w.a_max)
         hist.append(dict(m=it, F=rep.J, J_data=rep.J_data, gnorm=rep.gnorm, alpha=rep.alpha, beta=rep.beta))
         if rep.gnorm <= w.extra["theta"]:
@@ -95,18 +97,19 @@ def reconstruct(w, obs: torch.Tensor, max_iter: int = 15, device="cuda") -> Dict
 
 
 def run(omegas=(20.0, 30.0, 40.0, 50.0, 60.0), noises=(0.03, 0.10), models=(1, 2), max_iter=15,
-        device="cuda") -> List[Dict]:
+        device="cuda", gamma=None) -> List[Dict]:
     rows = []
     for model in models:
         for noise in noises:
             for omega in omegas:
                 w = synth.waveguide(omega, model)
                 obs = make_data(w, noise, seed=1)
-                r = reconstruct(w, obs, max_iter, device)
+                r = reconstruct(w, obs, max_iter, device, gamma)
                 ap = postprocess(r["a"])
                 amax = float(ap.max())
                 inside = w.sigma > 0
                 rows.append(dict(model=model, test=1 if model == 1 else 2, noise=noise, omega=omega,
+                                 gamma=w.extra["gamma"] if gamma is None else gamma,
                                  max_a=amax, error_pct=100.0 * abs(amax - w.extra["a_exact"]) / w.extra["a_exact"],
                                  N=r["iterations"],
                                  mean_a_in_scatterers=float(r["a"][inside].mean()),
@@ -121,8 +124,9 @@ def main(argv=None):
     p.add_argument("--noise", type=float, nargs="+", default=[0.03, 0.10])
     p.add_argument("--models", type=int, nargs="+", default=[1, 2])
     p.add_argument("--max-iter", type=int, default=15)
+    p.add_argument("--gamma", type=float, default=None, help="regularisation parameter (default 0.01)")
     args = p.parse_args(argv)
-    rows = run(args.omegas, args.noise, args.models, args.max_iter)
+    rows = run(args.omegas, args.noise, args.models, args.max_iter, gamma=args.gamma)
     for r in rows:
         print(json.dumps({k: v for k, v in r.items() if k != "history"}))
     print(json.dumps({"histories": [{"model": r["model"], "noise": r["noise"], "omega": r["omega"],
