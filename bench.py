@@ -438,7 +438,8 @@ def run_serving(args, dev):
     """Serving stream: FP32 forward + adjoint + gradient solves on lattices
     drawn from {33, 65, 97, 129}^3 (FEM block = central half, 2-4 inclusions,
     400-1500 steps by size).  Capacity is measured with requests arriving
-    back to back; the stream then arrives as a Poisson process at 80% of it.
+    back to back; the stream then arrives as a Poisson process at 80% of it,
+    served in batches and, for comparison, one request per solve.
     Beside it, the FP64 path with one request at a time on a sample of the
     same requests, and each sampled FP32 gradient's relative L2 difference
     from its FP64 counterpart."""
@@ -462,6 +463,11 @@ def run_serving(args, dev):
     st = latency_stats(res)
     batches = {"batches": eng.batches, "max_batch": eng.max_batch_seen}
     eng.close()
+    # the same arrivals served one request per solve (no batching), for comparison
+    e1 = ServingEngine(workers=args.serve_workers, device=str(dev), max_batch=1)
+    e1.run(warm)
+    st1 = latency_stats(e1.run([Request(i, synth.serving_request(i), float(arr[i])) for i in range(R)]))
+    e1.close()
     n64 = min(R, 16)
     e64 = ServingEngine(workers=1, precision="fp64", device=str(dev), max_batch=1)
     e64.run([Request(-1, synth.serving_request(i), 0.0) for i in range(2)])
@@ -476,6 +482,8 @@ def run_serving(args, dev):
             "capacity_solves_per_s": mu, "rate_per_s": lam,
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "mean_ms": st["mean_ms"], "dtype": "f32",
+            "unbatched_same_arrivals": {"solves_per_s": st1["solves_per_s"], "p50_ms": st1["p50_ms"],
+                                        "p99_ms": st1["p99_ms"]},
             "grad_rel_err_vs_fp64": {"max": max(errs), "median": float(np.median(errs)), "requests": len(errs)},
             "fp64_one_at_a_time": {"sample": n64, "solves_per_s": float(n64 / lat64.sum()),
                                    "p50_ms": float(np.percentile(lat64, 50) * 1e3),

@@ -648,7 +648,14 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
   for (int q = 0; q < 64; ++q) m->uK8[q] = K8[q];
   for (int q = 0; q < 9; ++q) m->um9[q] = m9[q];
   for (int q = 0; q < 8; ++q) m->um8[q] = m8[q];
-  HYB_TRY(upload(m, m->rmask, rmask));
+  {  // device flags over the FEM-owned box: bit 0 corner of a refined voxel, bit 1 origin of one
+    std::vector<unsigned char> flags(rmask);
+    for (int u : refid) {
+      const int x = u % m->un[0], y = (u / m->un[0]) % m->un[1], z = u / (m->un[0] * m->un[1]);
+      flags[(size_t)(m->fl[0] + x - m->hx0) + (size_t)m->hpx * (y + (size_t)m->fn[1] * z)] |= 2;
+    }
+    HYB_TRY(upload(m, m->rmask, flags));
+  }
   HYB_TRY(upload(m, m->rcid, cid));
   // corner positions packed for the kernel: (i | j << 16, k)
   if (m->n[0] > 65535 || m->n[1] > 65535) return fail(HYB_ERR_ARG, "refinement needs n < 65536 along x and y");

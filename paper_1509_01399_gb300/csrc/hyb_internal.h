@@ -130,7 +130,8 @@ struct StepArgs {
   int nref;                   // refined voxels (= centre nodes)
   int nrl;                    // corners of refined voxels (lattice rows of the refined region)
   const uint2* rpos;          // each such corner (i | j << 16, k)
-  const unsigned char* rmask; // FEM-owned box: 1 = the node is a corner of a refined voxel
+  const unsigned char* rmask; // FEM-owned box: bit 0 = the node is a corner of a refined voxel,
+                              // bit 1 = the voxel with its origin at the node is refined
   const int* rzr;             // per FEM-owned column (i - fl0) + fn0 (j - fl1): [kmin, kmax] of its
                               // refined corners (kmin > kmax: none)
   const int* rcid;            // per unknown voxel: its centre id if refined, else -1

@@ -772,7 +772,7 @@ template <typename T, bool ADJ, bool FEMT, bool FACE, bool ZF, bool REF>
 __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T>& S, T* __restrict__ gnext,
                                               const Col& C, int k, int off, int dzs, const T* Ck, const T* Cm,
                                               const T* Cp, const T* Pk, const T* Wk, const T* Wm, const T* Hk,
-                                              const T* Hp) {
+                                              const T* Hp, int rf) {
   using P = kPipe<T>;
   constexpr int kBoxX = Box<T>::BX;
   if (ZF && FACE && (C.dxs != 0 || C.dys != 0)) return;  // near two faces: edge tiles
@@ -886,15 +886,15 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     return;
   }
   const int bo = (C.i - A.hx0) + A.hpx * ((C.j - A.fl[1]) + A.fn[1] * (k - A.fl[2]));
-  const bool rz = REF && k >= C.rz0 && k <= C.rz1;  // the column has refined corners here
-  if (!(rz && A.rmask[bo])) {  // (the refined rows write those)
+  // rf: the node's refinement flags (0 off the columns' refined z ranges)
+  if (!(REF && (rf & 1))) {  // (the refined rows write those)
     gnext[off] = val;
     if (!ADJ && S.hist_w) S.hist_w[bo] = val;
   }
   if constexpr (ADJ) {
     const int vz = A.un[0] * A.un[1];
     const int vid = (C.i - A.fl[0]) + A.un[0] * (C.j - A.fl[1]) + vz * (k - A.fl[2]);
-    if (C.xy_vox && k < A.fl[2] + A.un[2] && !(rz && A.refvox[vid])) {
+    if (C.xy_vox && k < A.fl[2] + A.un[2] && !(REF && (rf & 2))) {
       const T u[8] = {Hk[0], Hk[1], Hk[kBoxX], Hk[kBoxX + 1], Hp[0], Hp[1], Hp[kBoxX], Hp[kBoxX + 1]};
       const T l[8] = {c0, xp, yp, Ck[kBoxX + 1], cp, Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
       atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
@@ -1045,6 +1045,17 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   T* __restrict__ gnext = S.next;
   int off0 = C[0].i + A.px * C[0].j + pl * z0;       // field offsets of the two nodes
   int off1 = off0 + (kTileY / 2) * A.px;
+  // refinement flags of the two nodes, loaded one level ahead (their
+  // latency then overlaps the wait for the level's planes)
+  auto rflag = [&](const Col& c, int kk) -> int {
+    if (!REF || kk < c.rz0 || kk > c.rz1) return 0;
+    return A.rmask[(c.i - A.hx0) + A.hpx * ((c.j - A.fl[1]) + A.fn[1] * (kk - A.fl[2]))];
+  };
+  int rfn0 = 0, rfn1 = 0;
+  if constexpr (REF) {
+    rfn0 = rflag(C[0], z0);
+    rfn1 = rflag(C[1], z0);
+  }
   // ring stages of planes k - 1, k, k + 1 (rotated from level to level
   // instead of reduced modulo the ring size at every level)
   int scm = ring<R::SC>(z0 - 1), sck = ring<R::SC>(z0), scp = ring<R::SC>(z0 + 1);
@@ -1057,6 +1068,13 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
   }
   for (int k = z0; k < z1; ++k, off0 += pl, off1 += pl) {
     const int q = k - z0;
+    const int rf0 = rfn0, rf1 = rfn1;
+    if constexpr (REF) {
+      if (k + 1 < z1) {
+        rfn0 = rflag(C[0], k + 1);
+        rfn1 = rflag(C[1], k + 1);
+      }
+    }
     const bool ok = mbar_wait(pr.full + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), budget, A.err);
     if (!__all_sync(0xffffffffu, ok)) {
       if (tx == 0) atomicExch(A.err, 1);
@@ -1081,17 +1099,17 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     if (dzs != 0) {
       if (act0)
         interior_node<T, ADJ, FEMT, FACE, true, REF>(A, S, gnext, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0,
-                                                Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
+                                                Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0, rf0);
       if (act1)
         interior_node<T, ADJ, FEMT, FACE, true, REF>(A, S, gnext, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1,
-                                                Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
+                                                Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1, rf1);
     } else {
       if (act0)
         interior_node<T, ADJ, FEMT, FACE, false, REF>(A, S, gnext, C[0], k, off0, 0, Ck + o0, Cm + o0, Cp + o0,
-                                                 Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0);
+                                                 Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0, rf0);
       if (act1)
         interior_node<T, ADJ, FEMT, FACE, false, REF>(A, S, gnext, C[1], k, off1, 0, Ck + o1, Cm + o1, Cp + o1,
-                                                 Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1);
+                                                 Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1, rf1);
     }
     __syncwarp();  // the warp's reads of level k's stages are done
     if (tx == 0) mbar_arrive(pr.empty + (q & (R::NB - 1)));
@@ -1518,7 +1536,8 @@ __device__ __forceinline__ void refined_centre(const StepArgs<T>& A, const Slot<
     u[8] = S.chist_r[v];
     const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
     // the unit-voxel K9 from the launch parameters (kGradPairScale times the pairing, as the other kernels)
-    A.G[(long long)si * nv + vid] += (double)(T(kGradPairScale) * refined_pair_sum(u, q, A.rK9));
+    // the only update of this entry in the launch: a reduction without return needs no load
+    atomicAdd(A.G + (long long)si * nv + vid, (double)(T(kGradPairScale) * refined_pair_sum(u, q, A.rK9)));
   }
 }
 
