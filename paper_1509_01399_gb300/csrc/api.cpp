@@ -106,7 +106,6 @@ struct hyb_mesh {
   double dt_max = 0.0;
   DevBuf rmask, rzr, refvox, refvox_id, k9, rcid, avox, rpos, rvxyz;
   double uK9[81], uK8[64], um9[9], um8[8];  // unit-voxel stiffness and lumped masses (refined, Kuhn)
-  std::vector<int> ref_rows;  // per interior tile and plane: tile rows holding refined-voxel corners
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
   DevBuf I0, IC0;               // initial state of Model Problem 1: u^0, u^{-1} (padded fields), centres
   DevBuf acopy, kuhn, kuhn_v;   // all-FEM path: coefficient of the last forward, Kuhn element tables
@@ -339,7 +338,6 @@ void step_geometry(const hyb_mesh* m, int* npb, int* ntx, int* small, int* nedge
 constexpr int kStepWavesFew = 1, kStepWavesMany = 3;
 constexpr double kManyLevelsPerBlock = 40.0;
 constexpr double kZFaceLevelCost = 3.5;
-constexpr double kRefRowCost = 0.05;  // a tile row holding refined-voxel corners (a plain level: 1)
 
 // Interior work items of one step launch, one per block: (slot, tile, z0,
 // z1).  Each tile's z range 1 .. n-2 is cut into pieces of about equal
@@ -380,17 +378,11 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
   const double cap = resident * (levels_per_block > kManyLevelsPerBlock ? kStepWavesMany : kStepWavesFew);
   const double target = total / cap;
   std::vector<std::pair<double, std::array<int, 4>>> items;
-  auto ref_cost = [&](const Tile& t, int k) {
-    return m->ref_rows.empty() ? 0.0 : kRefRowCost * m->ref_rows[(size_t)t.tile * nz + k];
-  };
-  for (const Tile& t : tiles)
-    for (int k = 1; k <= nz - 2; ++k) total += ref_cost(t, k);
   for (const Tile& t : tiles) {
     double acc = 0.0;
     int z0 = 1;
     for (int k = 1; k <= nz - 2; ++k) {
-      acc += t.base + ((k >= zf0 && k <= zf1) ? t.extra : 0.0) + ((k == 1 || k == nz - 2) ? kZFaceLevelCost : 0.0) +
-             ref_cost(t, k);
+      acc += t.base + ((k >= zf0 && k <= zf1) ? t.extra : 0.0) + ((k == 1 || k == nz - 2) ? kZFaceLevelCost : 0.0);
       if (acc >= target || k == nz - 2) {
         items.push_back({acc, {t.si, t.tile, z0, k + 1}});
         z0 = k + 1;
@@ -683,25 +675,6 @@ hyb_status build_refined(hyb_mesh* m, const uint8_t* mask) {
         rzr[2 * c + 1] = std::max(rzr[2 * c + 1], m->fl[2] + k);
       }
   HYB_TRY(upload(m, m->rzr, rzr));
-  // tile rows (32 nodes in x at one y and z) holding refined corners, per
-  // interior tile and plane, for the work-item cost model
-  {
-    const int x0 = tile_x0(m->d.precision);
-    const int ntx = (m->n[0] - 1 - x0 + kTileX - 1) / kTileX, nty = (m->n[1] - 2 + kTileY - 1) / kTileY;
-    m->ref_rows.assign((size_t)ntx * nty * m->n[2], 0);
-    std::vector<unsigned char> seen((size_t)ntx * m->n[1] * m->n[2], 0);
-    for (int k = 0; k < m->fn[2]; ++k)
-      for (int j = 0; j < m->fn[1]; ++j)
-        for (int i = 0; i < m->fn[0]; ++i) {
-          const int x = m->fl[0] + i, y = m->fl[1] + j, z = m->fl[2] + k;
-          if (!rmask[(size_t)(x - m->hx0) + (size_t)m->hpx * (j + (size_t)m->fn[1] * k)]) continue;
-          const int tx = (x - x0) / kTileX, ty = (y - 1) / kTileY;
-          unsigned char& sr = seen[(size_t)tx + (size_t)ntx * (y + (size_t)m->n[1] * z)];
-          if (sr) continue;
-          sr = 1;
-          ++m->ref_rows[((size_t)ty * ntx + tx) * m->n[2] + z];
-        }
-  }
   HYB_TRY(upload(m, m->refvox, refv));
   HYB_TRY(upload(m, m->refvox_id, refid));
   // the refined voxels' origins packed for the kernel: (x | y << 16, z) in unknown-voxel coordinates
