@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=512, help="requests of the serving stream (0: skip)")
     p.add_argument("--serve-workers", type=int, default=4)
     p.add_argument("--serve-batch", type=int, default=8, help="requests of one class per batched solve")
+    p.add_argument("--serve-batch-work", type=float, default=6.5e9,
+                   help="cap on a batch's lattice node-steps (default: about two 129^3 x 1500-step requests)")
     p.add_argument("--sources", type=int, default=0, help="with --sweeps-only: use the first K sources")
     p.add_argument("--no-refine", action="store_true", help="with --sweeps-only: the large workload unrefined")
     p.add_argument("--sweeps-only", type=int, default=0,
@@ -447,7 +449,8 @@ def run_serving(args, dev):
     import synth
     from paper_1509_01399_gb300.serve import Request, ServingEngine, latency_stats, poisson_arrivals
     R = args.serve_requests
-    eng = ServingEngine(workers=args.serve_workers, device=str(dev), max_batch=args.serve_batch)
+    eng = ServingEngine(workers=args.serve_workers, device=str(dev), max_batch=args.serve_batch,
+                        batch_work=args.serve_batch_work)
     sizes = (33, 65, 97, 129)
     warm = []
     for N in sizes:  # pools and sweep graphs of every class, outside timing
@@ -478,7 +481,8 @@ def run_serving(args, dev):
     for r in r64:
         g32 = res[r.rid].gradient
         errs.append(float(np.linalg.norm(g32 - r.gradient) / np.linalg.norm(r.gradient)))
-    return {"requests": R, "workers": args.serve_workers, "max_batch": args.serve_batch, **batches,
+    return {"requests": R, "workers": args.serve_workers, "max_batch": args.serve_batch,
+            "batch_work": args.serve_batch_work, **batches,
             "capacity_solves_per_s": mu, "rate_per_s": lam,
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "mean_ms": st["mean_ms"], "dtype": "f32",

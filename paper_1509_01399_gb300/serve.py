@@ -93,10 +93,14 @@ class ServingEngine:
     hbm_budget: bytes of device memory the pooled meshes may hold (default:
     half of the free memory at start).  workers: concurrent batches (one CUDA
     stream each).  max_batch: requests of one lattice class advanced by the
-    same launches (iteration-level batching, hyb_forward_batch)."""
+    same launches (iteration-level batching, hyb_forward_batch).  batch_work:
+    cap on a batch's lattice node-steps (nodes x time levels, summed over its
+    requests; at least one request): small lattices batch up to max_batch,
+    large ones in small batches, so that a batch's time, which every request
+    in it waits for, stays bounded (None: no cap)."""
 
     def __init__(self, hbm_budget: Optional[int] = None, workers: int = 8, precision: str = "fp32",
-                 device: str = "cuda:0", max_batch: int = 8):
+                 device: str = "cuda:0", max_batch: int = 8, batch_work: Optional[float] = None):
         self.device = torch.device(device)
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
@@ -104,6 +108,7 @@ class ServingEngine:
         self.budget = int(hbm_budget)
         self.workers = int(workers)
         self.max_batch = max(1, min(int(max_batch), H.MAX_SOURCES))
+        self.batch_work = batch_work
         self.precision = precision
         self._cv = threading.Condition()
         self._free: Dict[tuple, List[_Pooled]] = {}
@@ -237,6 +242,14 @@ class ServingEngine:
         key = class_key(w, self.precision)
         return [Result(r.rid, g[i], J[i], r.arrival, start, finish, key) for i, r in enumerate(reqs)]
 
+    def batch_size(self, w) -> int:
+        """Requests of w's class that one batch takes: max_batch, lowered so
+        that the batch's node-steps stay within batch_work."""
+        if self.batch_work is None:
+            return self.max_batch
+        work = float(np.prod(w.n)) * w.nsteps
+        return max(1, min(self.max_batch, int(self.batch_work // work)))
+
     def solve(self, req: Request, t0: float = 0.0) -> Result:
         return self.solve_batch([req], t0)[0]
 
@@ -268,7 +281,7 @@ class ServingEngine:
                         ready = [(q[0].arrival, k) for k, q in queues.items() if q]
                         if ready:
                             _, k = min(ready)
-                            batch = queues[k][: self.max_batch]
+                            batch = queues[k][: self.batch_size(queues[k][0].workload)]
                             del queues[k][: len(batch)]
                             break
                         qcv.wait()
