@@ -557,6 +557,18 @@ def describe(w):
                w.dt, w.ckpt_every))
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of every rank's value (one all-reduce; the identity
+    without a process group): the timed region of N replicas ends when the
+    slowest one does."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     from paper_1509_01399_gb300 import hyb as H
@@ -579,10 +591,7 @@ def run_ours(args):
     r = run_cg(H, w, dev, args.steps, args.warmup, args.e2e_steps, clocks=ClockSampler(local))
     el_ms = r["el_ms"]
     if dist:
-        t = torch.tensor([el_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
-        r["el_ms"] = el_ms
+        r["el_ms"] = el_ms = max_over_ranks(el_ms, dist, dev)
         dist.barrier()
     rec = cg_record(r, args.steps)
     per_step = r["S"] * r["n_nodes"] * w.nsteps
@@ -608,6 +617,12 @@ def run_ours(args):
                                            "at": "true coefficient, all steps"}}
     del r
     torch.cuda.empty_cache()
+    if dist:  # the secondary record, serving and the baselines: rank 0 alone
+        dist.barrier()
+        dist.destroy_process_group()
+        dist = None
+        if rank != 0:
+            return 0
     if not args.no_secondary and args.workload != "inverse_129":
         w2 = make_workload("inverse_129")
         r2 = run_cg(H, w2, dev, 20, 3, 2)
