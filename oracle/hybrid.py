@@ -41,6 +41,9 @@ float64 throughout):
   form of int_0^T grad u . grad lambda dt.
 * Tikhonov functional (Eq. (functional)) and one conjugate-gradient update of
   Algorithm 3 (Sec. 8) with a quadratic-fit step length.
+* The telegraph reading u_tt + sigma u_t - div grad u = 0 (a = 1, sigma on the
+  unknown voxels): the damping lumped like the mass and central in time, its
+  exact discrete adjoint and the gradient with respect to sigma.
 """
 from __future__ import annotations
 
@@ -409,9 +412,11 @@ class Problem:
         return E, B, C.tocsr()
 
     # --------------------------------------------------------------- forward
-    def forward(self, a_unknown, src, nsteps, dt, init=None, keep_hist=False, keep_fields=False):
+    def forward(self, a_unknown, src, nsteps, dt, init=None, keep_hist=False, keep_fields=False, damp=None):
         """Algorithm 2, forward in time, with separate FDM and FEM arrays and
-        the two copies of Algorithm 1 per step.
+        the two copies of Algorithm 1 per step.  damp: the telegraph reading's
+        s_i = tau D_i / (2 M^L_i) per node (see `damping_ratio`), which turns
+        the FEM rows into (1 + s) u^{k+1} = 2 u^k - (1 - s) u^{k-1} - tau^2 (M^L)^{-1} K u^k.
 
         Returns a dict with the trace on the source face (rows t_0 .. t_N),
         the final level u^N (and u^{N-1}), optionally u^k on the FEM-owned
@@ -449,7 +454,11 @@ class Problem:
             new_fe = np.zeros(self.NT)
             if self.has_fem:
                 Ku = K @ u_fe
-                new_fe[own] = 2.0 * u_fe[own] - u_fe_prev[own] - tau2 * Ku[own] / ML[own]
+                if damp is None:
+                    new_fe[own] = 2.0 * u_fe[own] - u_fe_prev[own] - tau2 * Ku[own] / ML[own]
+                else:
+                    so = damp[own]
+                    new_fe[own] = (2.0 * u_fe[own] - (1.0 - so) * u_fe_prev[own] - tau2 * Ku[own] / ML[own]) / (1.0 + so)
                 # 3. FEM values at omega_diamond become FDM boundary values
                 new_fd[self.omega_diamond] = new_fe[self.omega_diamond]
             # absorbing rows, Eq. (eq:abs2), faces before edges before corners
@@ -767,6 +776,116 @@ def cg_step(prob: Problem, a, sources, nsteps, dt, obs_traces, state: dict, gamm
     report = dict(J=J0, gnorm=math.sqrt(vol * float(np.sum(g * g))), gpnorm=math.sqrt(gn2), alpha=alpha,
                   beta=beta, dJ0=dJ0, J_trial=Jt, alpha_trial=alpha_t)
     return a_new, new_state, report
+
+
+# ------------------------------------------------------ telegraph reading
+# u_tt + sigma u_t - div grad u = 0 (the damped reading of the model, with
+# a = 1 and the unknown sigma >= 0 on the unknown voxels, 0 elsewhere).  The
+# damping term is discretised like the mass: central in time,
+# D (u^{k+1} - u^{k-1}) / (2 tau) with D lumped by rows over the Kuhn
+# tetrahedra of the voxels carrying sigma.
+def damping_weights(prob: Problem):
+    """W (unknown voxels x nodes): W[v, i] = the lumped mass voxel v gives
+    node i, |K| / 4 summed over v's tetrahedra with i as a vertex, so that
+    the lumped damping is D = W^T sigma."""
+    m = prob.tet_unknown >= 0
+    rows = np.repeat(prob.tet_unknown[m], 4)
+    cols = prob.tet_nodes[m].ravel()
+    vals = np.repeat(prob.tet_vol[m] / 4.0, 4)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(prob.n_unknown, prob.NT))
+
+
+def damping_ratio(prob: Problem, sigma, dt):
+    """s_i = tau D_i / (2 M^L_i) on the FEM-owned rows (0 elsewhere)."""
+    _, ML = prob.assemble(np.ones(prob.n_unknown))
+    D = damping_weights(prob).T @ np.asarray(sigma, dtype=np.float64)
+    s = np.zeros(prob.NT)
+    own = prob.owned
+    s[own] = 0.5 * dt * D[own] / ML[own]
+    return s
+
+
+def telegraph_forward(prob: Problem, sigma, src, nsteps, dt, init=None, keep_levels=False):
+    """The forward of the telegraph reading (Algorithm 2 with the damped FEM
+    rows).  keep_levels: also the FEM-owned values of u^{-1} .. u^N (rows
+    0 .. N + 1), which the sigma-gradient pairs."""
+    s = damping_ratio(prob, sigma, dt)
+    res = prob.forward(np.ones(prob.n_unknown), src, nsteps, dt, init=init, keep_hist=keep_levels, damp=s)
+    if keep_levels:
+        own = prob.owned_nodes
+        first = np.zeros(own.size) if init is None else np.asarray(init[1], dtype=np.float64)[own]
+        res["levels"] = np.vstack([first[None, :], res["hist"], res["u"][own][None, :]])
+    return res
+
+
+def telegraph_adjoint(prob: Problem, sigma, src, nsteps, dt, cot, levels):
+    """Exact discrete adjoint of the damped recursion, written per step as
+    E_k u^{k+1} = B_k u^k - C_k u^{k-1} + s_k with E_k = E_k^0 + S and
+    C_k = C_k^0 - S (S = diag(s), the undamped matrices of `step_matrices`):
+    E_{j-1}^T lambda^j = B_j^T lambda^{j+1} - C_{j+1}^T lambda^{j+2} + c^j.
+    Returns dJ/dsigma_v = -sum_k (lambda^{k+1})^T (dS/dsigma_v) (u^{k+1} - u^{k-1})
+    with dS_ii/dsigma_v = tau W[v, i] / (2 M^L_i)."""
+    s = damping_ratio(prob, sigma, dt)
+    S = sp.diags(s)
+    Lop = prob.space_operator(np.ones(prob.n_unknown))
+    _, ML = prob.assemble(np.ones(prob.n_unknown))
+    cache, seq = {}, []
+    for k in range(nsteps + 2):
+        ph = prob.phase(src, k, dt)
+        key = (ph.abc_faces, ph.src_faces)
+        if key not in cache:
+            E, B, C = prob.step_matrices(Lop, ph, dt)
+            Et = (E + S).T.tocsr()
+            dg = Et.diagonal()
+            Nt = (Et - sp.diags(dg)).tocsr()
+            Nt.eliminate_zeros()
+            cache[key] = (Nt, dg, B.T.tocsr(), (C - S).T.tocsr())
+        seq.append(key)
+    obs = prob.face_nodes(src.face)
+    Wd = damping_weights(prob)
+    scale = np.zeros(prob.NT)
+    scale[prob.owned] = 0.5 * dt / ML[prob.owned]
+    own = prob.owned_nodes
+    lam1 = np.zeros(prob.NT)
+    lam2 = np.zeros(prob.NT)
+    G = np.zeros(prob.n_unknown)
+
+    def pair(k, lam):  # (lambda^{k+1})^T (dS/dsigma) (u^{k+1} - u^{k-1}), all voxels
+        v = np.zeros(prob.NT)
+        v[own] = levels[k + 2] - levels[k]
+        return Wd @ (scale * lam * v)
+
+    for j in range(nsteps, 0, -1):
+        _, _, BT, _ = cache[seq[j]]
+        _, _, _, CT = cache[seq[j + 1]]
+        Nt, dg, _, _ = cache[seq[j - 1]]
+        rhs = BT @ lam1 - CT @ lam2
+        rhs[obs] += cot[j]
+        lam = rhs / dg  # (D + N)^T x = y by the fixed point x = (y - N^T x) / D: N couples
+        for _ in range(4):  # absorbing rows only (where D = 1) and is nilpotent
+            lam = (rhs - Nt @ lam) / dg
+        if j <= nsteps - 1 and prob.n_unknown:
+            G -= pair(j, lam1)
+        lam2, lam1 = lam1, lam
+    if prob.n_unknown:
+        G -= pair(0, lam1)
+    return G
+
+
+def telegraph_value_and_grad(prob: Problem, sigma, sources, nsteps, dt, obs_traces, mode="plain", init=None):
+    """Data misfit of the telegraph reading summed over sources, and its
+    gradient with respect to sigma on the unknown voxels."""
+    J = 0.0
+    g = np.zeros(prob.n_unknown)
+    traces = []
+    for s_, src in enumerate(sources):
+        res = telegraph_forward(prob, sigma, src, nsteps, dt, init=init, keep_levels=True)
+        wk, mj = data_weights(prob, src.face, nsteps, dt, mode)
+        Jd, cot = misfit(res["trace"], obs_traces[s_], wk, mj)
+        J += Jd
+        traces.append(res["trace"])
+        g = g + telegraph_adjoint(prob, sigma, src, nsteps, dt, cot, res["levels"])
+    return J, g, traces
 
 
 def problem_from_workload(w) -> Problem:
