@@ -114,11 +114,27 @@ typedef struct {
                           the outer boundary rows stay FDM.  A checking path
                           (slow, no refinement): on structured meshes the two
                           paths agree (the schemes coincide, Sec. 1, Sec. 7). */
+  int32_t model;       /* HYB_MODEL_WAVE: u_tt = div(a grad u), the coefficient
+                          arrays of the calls below are a.  HYB_MODEL_TELEGRAPH:
+                          the damped reading u_tt + sigma u_t - div grad u = 0
+                          (a = 1), the coefficient arrays are sigma >= 0 on the
+                          unknown voxels (0 elsewhere); the damping is lumped
+                          like the mass and central in time, so a FEM row reads
+                          (1 + s) u^{k+1} = 2 u^k - (1 - s) u^{k-1} - tau^2 (M^L)^{-1} K u^k,
+                          s_i = tau D_i / (2 M^L_i), and hyb_adjoint accumulates
+                          dJ/dsigma_v = -tau/2 sum_k sum_i m_{v,i} lambda_i^{k+1} (u_i^{k+1} - u_i^{k-1})
+                          (m_{v,i}: voxel v's lumped mass share of node i, in
+                          units of h^3).  Needs a FEM block with fem_lo >= 2 and
+                          fem_hi <= n - 3 on every axis, no refinement, the exact
+                          adjoint and the stencil path, and no batches; a
+                          negative sigma is reported by hyb_sync as HYB_ERR_CFL.
+                          a_max keeps its role for the time step (a = 1). */
 } hyb_mesh_desc;
 
 #define HYB_WAIT_NONE (-1)
 enum { HYB_ADJ_EXACT = 0, HYB_ADJ_PAPER = 1 };
 enum { HYB_FEM_STENCIL = 0, HYB_FEM_TET_ALL = 1 };
+enum { HYB_MODEL_WAVE = 0, HYB_MODEL_TELEGRAPH = 1 };
 
 typedef struct {
   int64_t n_nodes;         /* lattice nodes */

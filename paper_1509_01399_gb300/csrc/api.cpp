@@ -105,6 +105,7 @@ struct hyb_mesh {
   int nc = 0, nr = 0, nrl = 0, nnz = 0;
   double dt_max = 0.0;
   DevBuf rmask, rzr, refvox, refvox_id, k9, rcid, avox, rpos, rvxyz;
+  DevBuf sdamp, ones;  // telegraph model: damping ratios (history-box layout), a = 1 on the unknown voxels
   double uK9[81], uK8[64], um9[9], um8[8];  // unit-voxel stiffness and lumped masses (refined, Kuhn)
   DevBuf CU, CL, chist, cckpt;  // centre values (levels, history, checkpoints)
   DevBuf I0, IC0;               // initial state of Model Problem 1: u^0, u^{-1} (padded fields), centres
@@ -793,6 +794,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.W = (const T*)m->W.p;
   A.G = (double*)m->G.p;
   A.avox = (const T*)m->avox.p;
+  A.sdamp = m->d.model == HYB_MODEL_TELEGRAPH ? (const T*)m->sdamp.p : nullptr;
   const double h = m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
   A.r = (T)((h - dt) / (h + dt));
@@ -932,11 +934,19 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
   base_args(m, A, dt, nsrc);
   HYB_TRY(step_maps<T>(m, A, m->U, nsrc, 0));
   HYB_TRY(step_items<T>(m, A, nsrc, false));
+  const bool tel = m->d.model == HYB_MODEL_TELEGRAPH;
+  if (tel) {  // the edge weights of a = 1, the damping ratios from sigma
+    if (!m->ones.p) HYB_TRY(upload(m, m->ones, std::vector<double>((size_t)std::max(m->nu, 1LL), 1.0)));
+    HYB_TRY(ensure(m, m->sdamp, (size_t)std::max(m->hbox, 1LL) * sizeof(T)));
+    A.sdamp = (const T*)m->sdamp.p;
+    launch_set_damp<T>(A, (T*)m->sdamp.p, a, dt, (int*)m->flag.p, m->st);
+    HYB_LAUNCHED(m);
+  }
   if (m->fem)
     for (int q = 0; q < ncoef; ++q) {
       launch_set_coef<T>(A, (T*)m->W.p + (size_t)q * 3 * m->wsz,
-                         m->nc > 0 ? (T*)m->avox.p + (size_t)q * m->nu : nullptr, a + (size_t)q * m->nu,
-                         m->d.a_max, (int*)m->flag.p, m->st);
+                         m->nc > 0 ? (T*)m->avox.p + (size_t)q * m->nu : nullptr,
+                         tel ? (const double*)m->ones.p : a + (size_t)q * m->nu, m->d.a_max, (int*)m->flag.p, m->st);
       HYB_LAUNCHED(m);
     }
   if (A.tet && m->nu > 0)  // the all-FEM rows read a itself
@@ -988,9 +998,12 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
           }
         }
       }
-      const bool hk = keep && !ckpt && m->nown > 0 && k + 1 <= nsteps - 1;
-      T* hl = hk ? hist + (size_t)(k + 1) * lvl : nullptr;
-      T* chl = hk ? chist + (size_t)(k + 1) * clvl : nullptr;
+      // history slot of step k: u^{k+1} in slot k + 1 (the wave model; slot 0
+      // holds u^0), or, in the telegraph model, u^{k+1} - u^{k-1} in slot k
+      const int slot = tel ? k : k + 1;
+      const bool hk = keep && !ckpt && m->nown > 0 && slot <= nsteps - 1;
+      T* hl = hk ? hist + (size_t)slot * lvl : nullptr;
+      T* chl = hk ? chist + (size_t)slot * clvl : nullptr;
       forward_slots<T>(m, A, src, nsrc, nsteps, dt, k, trace, hl, chl);
       HYB_TRY(step_launch(m, st, [&](cudaStream_t q) { launch_forward_step<T>(A, q); }));
     }
@@ -1109,6 +1122,7 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   const size_t fb = (size_t)m->Np * sizeof(T);
   const int C = m->d.ckpt_every;
   const bool ckpt = C > 0;
+  const bool tel = m->d.model == HYB_MODEL_TELEGRAPH;
   const size_t cb = (size_t)m->nc * sizeof(T);
   HYB_TRY(ensure(m, m->L, 3 * (size_t)nsrc * fb));
   HYB_TRY(ensure(m, m->CL, 3 * (size_t)nsrc * cb));
@@ -1197,8 +1211,11 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
           HYB_LAUNCHED(m);
           if (m->nc) HYB_CU(cudaMemcpyAsync(chist + (size_t)s * m->nc, c0, cb, cudaMemcpyDeviceToDevice, st));
         }
-        for (int k = kb; k < ke; ++k)
-          HYB_TRY(fwd_step(k, hist + (size_t)(k + 1 - kb) * lvl, chist + (size_t)(k + 1 - kb) * clvl));
+        // recompute the segment's history (telegraph: one step further, for
+        // u^{ke+1} - u^{ke-1} in the last slot)
+        const int sh = tel ? 0 : 1;
+        for (int k = kb; k < ke + 1 - sh; ++k)
+          HYB_TRY(fwd_step(k, hist + (size_t)(k + sh - kb) * lvl, chist + (size_t)(k + sh - kb) * clvl));
       }
       for (int j = ke; j >= std::max(kb, 1); --j)
         HYB_TRY(adj_step(j, pairing ? hist + (size_t)(j - kb) * lvl : nullptr,
@@ -1220,6 +1237,7 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
 double grad_scale(const hyb_mesh* m) {
   const double h = m->d.h, dt = m->dt;
   if (m->d.adjoint_mode == HYB_ADJ_PAPER) return dt * h / kGradPairScale;
+  if (m->d.model == HYB_MODEL_TELEGRAPH) return -dt / 24.0;  // the kernels accumulate 12 sum_i m_i lambda_i v_i
   return -dt * dt / (h * h) / kGradPairScale;
 }
 
@@ -1438,6 +1456,14 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   if (d->fem_path != HYB_FEM_STENCIL && d->fem_path != HYB_FEM_TET_ALL) return fail(HYB_ERR_ARG, "bad fem_path");
   if (d->fem_path == HYB_FEM_TET_ALL && d->refine_mask)
     return fail(HYB_ERR_ARG, "fem_path HYB_FEM_TET_ALL takes no refinement");
+  if (d->model != HYB_MODEL_WAVE && d->model != HYB_MODEL_TELEGRAPH) return fail(HYB_ERR_ARG, "bad model");
+  if (d->model == HYB_MODEL_TELEGRAPH) {
+    if (d->refine_mask || d->adjoint_mode != HYB_ADJ_EXACT || d->fem_path != HYB_FEM_STENCIL)
+      return fail(HYB_ERR_ARG, "the telegraph model takes no refinement, the exact adjoint and the stencil path");
+    for (int a = 0; a < 3; ++a)
+      if (d->fem_lo[a] < 2 || d->fem_hi[a] > d->n[a] - 3)
+        return fail(HYB_ERR_ARG, "the telegraph model needs 2 <= fem_lo and fem_hi <= n - 3 on every axis");
+  }
   if (!(d->a_max > 0.0)) return fail(HYB_ERR_ARG, "a_max must be > 0");
   for (int f = 0; f < 6; ++f)
     if (d->bc[f] != HYB_BC_NEUMANN0 && d->bc[f] != HYB_BC_ABC) return fail(HYB_ERR_ARG, "bad bc[%d]", f);
@@ -1547,7 +1573,7 @@ hyb_status hyb_mesh_destroy(hyb_mesh* m) {
   cudaStreamSynchronize(m->st);
   DevBuf* bufs[] = {&m->W, &m->G, &m->flag, &m->U, &m->L, &m->hist, &m->ckpt, &m->part, &m->scal,
                     &m->g, &m->atrial, &m->cot, &m->trace, &m->rmask, &m->rzr, &m->refvox, &m->refvox_id,
-                    &m->k9, &m->rcid, &m->avox, &m->rpos, &m->rvxyz,
+                    &m->k9, &m->rcid, &m->avox, &m->rpos, &m->rvxyz, &m->sdamp, &m->ones,
                     &m->CU, &m->CL, &m->chist, &m->cckpt, &m->I0, &m->IC0, &m->acopy, &m->kuhn, &m->kuhn_v};
   for (DevBuf* b : bufs) release(*b);
   for (auto& dir : m->items)
@@ -1608,6 +1634,7 @@ hyb_status hyb_forward_batch(hyb_mesh* m, const double* a, const hyb_source* src
   if (!m || !trace) return fail(HYB_ERR_ARG, "null argument");
   if (m->nu > 0 && !a) return fail(HYB_ERR_ARG, "null coefficient");
   if (m->d.fem_path == HYB_FEM_TET_ALL) return fail(HYB_ERR_ARG, "no batches on the HYB_FEM_TET_ALL path");
+  if (m->d.model == HYB_MODEL_TELEGRAPH) return fail(HYB_ERR_ARG, "no batches with the telegraph model");
   HYB_TRY(check_sources(m, src, n_src));
   HYB_TRY(check_time(m, nsteps, dt));
   if (m->d.precision == HYB_FP64)

@@ -152,6 +152,13 @@ struct StepArgs {
   const double* acoef;        // a on the unknown voxels (1 on the other voxels)
   const double* kuhn;         // [6][4][4] element stiffness (unit spacing, a = 1), then [6] volumes
   const int* kuhn_v;          // [6][4] corner ids (a + 2b + 4c) of each tetrahedron's vertices
+  // telegraph reading (HYB_MODEL_TELEGRAPH; nullptr: the wave model): per
+  // FEM-owned node (history-box layout) s = tau D / (2 M), D the damping
+  // lumped like the mass.  FEM rows then read
+  // u^{k+1} = u^k + ((u^k - u^{k-1})(1 - s) + tau^2/h^2 lap) / (1 + s), the
+  // forward's history keeps u^{k+1} - u^{k-1}, and the adjoint pairs it
+  // with lambda^{k+1} weighted by the lumped mass shares (damp_sum).
+  const T* sdamp;
   Slot<T> s[kMaxSlots];
 };
 
@@ -173,9 +180,15 @@ void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t
 template <typename T>
 void launch_set_coef(const StepArgs<T>& a, T* W, T* avox, const double* acoef, double a_max, int* flag,
                      cudaStream_t st);
+// Telegraph reading: sdamp (history-box layout) from sigma on the unknown
+// voxels, s_i = (tau / 2) sum over the voxels v around node i of
+// sigma_v m_{v,i} (m = 1/4 on a voxel's diagonal corners, 1/12 on the
+// others); raises *flag when a sigma is negative or not finite.
+template <typename T>
+void launch_set_damp(const StepArgs<T>& a, T* sdamp, const double* sigma, double dt, int* flag, cudaStream_t st);
 // (The rows of the refined region, identical for the forward and the
 // mass-scaled adjoint, and the adjoint's gradient pairing of refined voxels
-// run in the interior blocks of the step kernel.)
+// run in trailing blocks of the step kernel.)
 // Gradient pairing of refined voxels for level 0 (u^0 from the history
 // slots `hist`/`chist`, lambda^1 as the slots' cur/ccur).
 template <typename T>

@@ -481,6 +481,17 @@ __device__ __forceinline__ T pair_sum(const T u[8], const T l[8]) {
   return T(2) * d3 + d6;
 }
 
+// Telegraph reading: 12 times the pairing sum_i m_i lambda_i v_i of a voxel,
+// v = u^{k+1} - u^{k-1} at its corners (the stored history) and m_i its lumped
+// mass share of corner i in units of h^3: 1/4 on the diagonal corners 0 and
+// 7, 1/12 on the others.
+template <typename T>
+__device__ __forceinline__ T damp_sum(const T u[8], const T l[8]) {
+  const T d = u[0] * l[0] + u[7] * l[7];
+  const T o = ((u[1] * l[1] + u[2] * l[2]) + (u[3] * l[3] + u[4] * l[4])) + (u[5] * l[5] + u[6] * l[6]);
+  return T(3) * d + o;
+}
+
 // pair_sum of voxel (i,j,k): u from the FEM-owned box hb, lambda from the lattice
 template <typename T>
 __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restrict__ hb,
@@ -498,7 +509,7 @@ __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restric
     u[c] = hb[h0 + a + b * hy + d * hz];
     l[c] = lam[l0 + a + b * ly + d * lz];
   }
-  return pair_sum(u, l);
+  return A.sdamp ? damp_sum(u, l) : pair_sum(u, l);
 }
 
 // Laplacian part (without 1/h^2) of a 7-point row with unit weights.
@@ -768,11 +779,11 @@ struct Producer {
 // one step inside a z face (dzs = -1 / +1: the low / high one) and the node
 // also produces the face node next to it.  Tiles without FACE hold no node
 // one step inside an x or y face.
-template <typename T, bool ADJ, bool FEMT, bool FACE, bool ZF, bool REF>
+template <typename T, bool ADJ, bool FEMT, bool FACE, bool ZF, bool REF, bool TEL>
 __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T>& S, T* __restrict__ gnext,
                                               const Col& C, int k, int off, int dzs, const T* Ck, const T* Cm,
                                               const T* Cp, const T* Pk, const T* Wk, const T* Wm, const T* Hk,
-                                              const T* Hp, int rf) {
+                                              const T* Hp, int rf, T sd) {
   using P = kPipe<T>;
   constexpr int kBoxX = Box<T>::BX;
   if (ZF && FACE && (C.dxs != 0 || C.dys != 0)) return;  // near two faces: edge tiles
@@ -793,7 +804,10 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     wzm = Wm[2 * P::WS];
     const T lap =
         wxp * (xp - c0) + wxm * (xm - c0) + wyp * (yp - c0) + wym * (ym - c0) + wzp * (cp - c0) + wzm * (cm - c0);
-    val = c0 + ((c0 - pv) + c2 * lap);
+    if constexpr (TEL)  // damped row (sd: the node's damping ratio)
+      val = c0 + ((c0 - pv) * (T(1) - sd) + c2 * lap) / (T(1) + sd);
+    else
+      val = c0 + ((c0 - pv) + c2 * lap);
   } else if constexpr (sizeof(T) == 4) {  // unit weights: the neighbour sum minus 6 u^k
     val = c0 + ((c0 - pv) + c2 * ((((xm + xp) + (ym + yp)) + (cm + cp)) - T(6) * c0));
   } else {  // FP64 sums the six differences
@@ -889,7 +903,7 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
   // rf: the node's refinement flags (0 off the columns' refined z ranges)
   if (!(REF && (rf & 1))) {  // (the refined rows write those)
     gnext[off] = val;
-    if (!ADJ && S.hist_w) S.hist_w[bo] = val;
+    if (!ADJ && S.hist_w) S.hist_w[bo] = TEL ? val - pv : val;  // (telegraph: u^{k+1} - u^{k-1})
   }
   if constexpr (ADJ) {
     const int vz = A.un[0] * A.un[1];
@@ -897,7 +911,7 @@ __device__ __forceinline__ void interior_node(const StepArgs<T>& A, const Slot<T
     if (C.xy_vox && k < A.fl[2] + A.un[2] && !(REF && (rf & 2))) {
       const T u[8] = {Hk[0], Hk[1], Hk[kBoxX], Hk[kBoxX + 1], Hp[0], Hp[1], Hp[kBoxX], Hp[kBoxX + 1]};
       const T l[8] = {c0, xp, yp, Ck[kBoxX + 1], cp, Cp[1], Cp[kBoxX], Cp[kBoxX + 1]};
-      atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)pair_sum(u, l));
+      atomicAdd(A.G + (long long)C.si * ((long long)vz * A.un[2]) + vid, (double)(TEL ? damp_sum(u, l) : pair_sum(u, l)));
     }
   }
 }
@@ -990,7 +1004,7 @@ __device__ __forceinline__ void xface_levels(const StepArgs<T>& A, const Slot<T>
 // Consumer loop of an interior block, specialised by whether the tile meets
 // the FEM block (FEMT) and whether it holds nodes one step inside an x or y
 // face (FACE).  Each consumer thread owns two tile rows (ty and ty + 8).
-template <typename T, bool ADJ, bool FEMT, bool FACE, bool REF>
+template <typename T, bool ADJ, bool FEMT, bool FACE, bool REF, bool TEL = false>
 __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot<T>& S, const Col (&C)[2],
                                                 const Producer<T, !FEMT>& pr, const bool (&active)[2],
                                                 const XFace& X, int z0, int z1) {
@@ -1056,6 +1070,16 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     rfn0 = rflag(C[0], z0);
     rfn1 = rflag(C[1], z0);
   }
+  // telegraph reading: the nodes' damping ratios, likewise a level ahead
+  auto sdamp = [&](const Col& c, int kk) -> T {
+    if (!TEL || !c.xy_fem || kk < A.fl[2] || kk > A.fh[2]) return T(0);
+    return A.sdamp[(c.i - A.hx0) + A.hpx * ((c.j - A.fl[1]) + A.fn[1] * (kk - A.fl[2]))];
+  };
+  T sdn0 = T(0), sdn1 = T(0);
+  if constexpr (TEL) {
+    sdn0 = sdamp(C[0], z0);
+    sdn1 = sdamp(C[1], z0);
+  }
   // ring stages of planes k - 1, k, k + 1 (rotated from level to level
   // instead of reduced modulo the ring size at every level)
   int scm = ring<R::SC>(z0 - 1), sck = ring<R::SC>(z0), scp = ring<R::SC>(z0 + 1);
@@ -1073,6 +1097,13 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
       if (k + 1 < z1) {
         rfn0 = rflag(C[0], k + 1);
         rfn1 = rflag(C[1], k + 1);
+      }
+    }
+    const T sd0 = sdn0, sd1 = sdn1;
+    if constexpr (TEL) {
+      if (k + 1 < z1) {
+        sdn0 = sdamp(C[0], k + 1);
+        sdn1 = sdamp(C[1], k + 1);
       }
     }
     const bool ok = mbar_wait(pr.full + (q & (R::NB - 1)), (uint32_t)((q / R::NB) & 1), budget, A.err);
@@ -1098,18 +1129,18 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
     const int dzs = k == 1 ? -1 : (k == nz - 2 ? 1 : 0);
     if (dzs != 0) {
       if (act0)
-        interior_node<T, ADJ, FEMT, FACE, true, REF>(A, S, gnext, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0,
-                                                Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0, rf0);
+        interior_node<T, ADJ, FEMT, FACE, true, REF, TEL>(A, S, gnext, C[0], k, off0, dzs, Ck + o0, Cm + o0, Cp + o0,
+                                                Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0, rf0, sd0);
       if (act1)
-        interior_node<T, ADJ, FEMT, FACE, true, REF>(A, S, gnext, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1,
-                                                Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1, rf1);
+        interior_node<T, ADJ, FEMT, FACE, true, REF, TEL>(A, S, gnext, C[1], k, off1, dzs, Ck + o1, Cm + o1, Cp + o1,
+                                                Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1, rf1, sd1);
     } else {
       if (act0)
-        interior_node<T, ADJ, FEMT, FACE, false, REF>(A, S, gnext, C[0], k, off0, 0, Ck + o0, Cm + o0, Cp + o0,
-                                                 Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0, rf0);
+        interior_node<T, ADJ, FEMT, FACE, false, REF, TEL>(A, S, gnext, C[0], k, off0, 0, Ck + o0, Cm + o0, Cp + o0,
+                                                 Pk + p0, Wk + o0, Wm + o0, Hk + h0, Hp + h0, rf0, sd0);
       if (act1)
-        interior_node<T, ADJ, FEMT, FACE, false, REF>(A, S, gnext, C[1], k, off1, 0, Ck + o1, Cm + o1, Cp + o1,
-                                                 Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1, rf1);
+        interior_node<T, ADJ, FEMT, FACE, false, REF, TEL>(A, S, gnext, C[1], k, off1, 0, Ck + o1, Cm + o1, Cp + o1,
+                                                 Pk + p1, Wk + o1, Wm + o1, Hk + h1, Hp + h1, rf1, sd1);
     }
     __syncwarp();  // the warp's reads of level k's stages are done
     if (tx == 0) mbar_arrive(pr.empty + (q & (R::NB - 1)));
@@ -1130,7 +1161,7 @@ __device__ __forceinline__ void interior_levels(const StepArgs<T>& A, const Slot
 // (slot, tile, z range; the host balances the items by cost): eight
 // consumer warps (two tile rows per thread) and a producer warp.  Nodes one
 // step inside a face also produce the face node next to them.
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, bool TEL>
 __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* sm) {
   static_assert(kTileX == 32, "one warp per tile row");
   static_assert(kTileX * kTileY / 2 + 32 == kStepBlock, "eight consumer warps (two rows each) and a producer warp");
@@ -1211,7 +1242,12 @@ __device__ __forceinline__ void interior_block(const StepArgs<T>& A, int b, T* s
   if (fem_tile) {
     Producer<T, false> pr;
     pr.setup(A, S, sm, full, z0, z1, i0, j0, pairing, face_tile);
-    if (ref_tile) {
+    if constexpr (TEL) {  // telegraph reading (no refinement)
+      if (face_tile)
+        interior_levels<T, ADJ, true, true, false, true>(A, S, C, pr, active, X, z0, z1);
+      else
+        interior_levels<T, ADJ, true, false, false, true>(A, S, C, pr, active, X, z0, z1);
+    } else if (ref_tile) {
       if (face_tile)
         interior_levels<T, ADJ, true, true, true>(A, S, C, pr, active, X, z0, z1);
       else
@@ -1331,7 +1367,7 @@ __device__ __forceinline__ void refined_rows(const StepArgs<T>& A, long long t);
 // the refined region (gathers of short latency-bound rows, which fill the
 // slots the interior blocks free towards the end of the level).  All blocks
 // read levels k, k-1 and write disjoint nodes of level k+1.
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, bool TEL>
 __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 4 : 2) step_kernel(const __grid_constant__ StepArgs<T> A) {
   extern __shared__ __align__(128) unsigned char hyb_smem[];  // kPipe<T>::bytes
   T* sh = reinterpret_cast<T*>(hyb_smem);
@@ -1356,7 +1392,7 @@ __global__ void __launch_bounds__(kStepBlock, sizeof(T) == 4 ? 4 : 2) step_kerne
     refined_rows<T, ADJ>(A, (long long)(b - A.nitems) * kStepBlock + threadIdx.x);
     return;
   }
-  interior_block<T, ADJ>(A, b, sh);
+  interior_block<T, ADJ, TEL>(A, b, sh);
 }
 
 // Lattices with fewer than 5 nodes on some axis: every node by the generic
@@ -1593,6 +1629,31 @@ __global__ void refined_pair_kernel(const __grid_constant__ StepArgs<T> A) {
   A.G[(long long)si * nv + A.refvox_id[v]] += (double)refined_pair(A, v, S.hist_r, S.chist_r, S.cur, S.ccur, A.k9);
 }
 
+// Damping ratio of the telegraph reading per FEM-owned node (one thread per
+// node of the FEM-owned box): s_i = (tau / 2) sum_v sigma_v m_{v,i} over the
+// eight voxels with a corner at i (sigma = 0 off the unknown voxels).
+template <typename T>
+__global__ void set_damp_kernel(const __grid_constant__ StepArgs<T> A, T* __restrict__ sd,
+                                const double* __restrict__ sigma, double dt, int* flag) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nv = (long long)A.un[0] * A.un[1] * A.un[2];
+  if (t < nv) {
+    const double v = sigma[t];
+    if (!(v >= 0.0) || !(v <= 1e300)) atomicExch(flag, 1);
+  }
+  const long long nown = (long long)A.fn[0] * A.fn[1] * A.fn[2];
+  if (t >= nown) return;
+  const int x = (int)(t % A.fn[0]), y = (int)((t / A.fn[0]) % A.fn[1]), z = (int)(t / ((long long)A.fn[0] * A.fn[1]));
+  double acc = 0.0;
+  for (int c = 0; c < 8; ++c) {  // node (x, y, z) is corner c of the voxel with origin (x, y, z) - c
+    const int ox = x - (c & 1), oy = y - ((c >> 1) & 1), oz = z - (c >> 2);
+    if (ox < 0 || oy < 0 || oz < 0 || ox >= A.un[0] || oy >= A.un[1] || oz >= A.un[2]) continue;
+    const double sv = sigma[ox + (long long)A.un[0] * (oy + (long long)A.un[1] * oz)];
+    acc += sv * ((c == 0 || c == 7) ? 0.25 : 1.0 / 12.0);
+  }
+  sd[hidx(A, A.fl[0] + x, A.fl[1] + y, A.fl[2] + z)] = (T)(0.5 * dt * acc);
+}
+
 template <typename T>
 __global__ void set_coef_kernel(const __grid_constant__ StepArgs<T> A, T* __restrict__ W, T* __restrict__ avox,
                                 const double* __restrict__ a, double a_max, int* flag) {
@@ -1693,7 +1754,10 @@ void launch_step(const StepArgs<T>& a, cudaStream_t st) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, step_kernel<T, ADJ>, b);
+  if (a.sdamp)
+    cudaLaunchKernelEx(&cfg, step_kernel<T, ADJ, true>, b);
+  else
+    cudaLaunchKernelEx(&cfg, step_kernel<T, ADJ, false>, b);
 }
 
 template <typename T>
@@ -1709,9 +1773,11 @@ void launch_adjoint_step(const StepArgs<T>& a, cudaStream_t st) {
 template <typename T, bool ADJ>
 int step_occupancy() {
   int n = 0;
-  if (cudaFuncSetAttribute(step_kernel<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipe<T>::bytes) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, ADJ>, kStepBlock, kPipe<T>::bytes) !=
+  if (cudaFuncSetAttribute(step_kernel<T, ADJ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kPipe<T>::bytes) != cudaSuccess ||
+      cudaFuncSetAttribute(step_kernel<T, ADJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kPipe<T>::bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, ADJ, false>, kStepBlock, kPipe<T>::bytes) !=
           cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -1739,6 +1805,15 @@ void launch_pair(const StepArgs<T>& a, const T* hist, const T* lam, cudaStream_t
 }
 
 template <typename T>
+void launch_set_damp(const StepArgs<T>& a, T* sdamp, const double* sigma, double dt, int* flag, cudaStream_t st) {
+  const long long nv = (long long)a.un[0] * a.un[1] * a.un[2];
+  const long long nown = (long long)a.fn[0] * a.fn[1] * a.fn[2];
+  const long long n = nown > nv ? nown : nv;
+  if (n == 0) return;
+  set_damp_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, sdamp, sigma, dt, flag);
+}
+
+template <typename T>
 void launch_set_coef(const StepArgs<T>& a, T* W, T* avox, const double* acoef, double a_max, int* flag,
                      cudaStream_t st) {
   const long long nv = (long long)a.un[0] * a.un[1] * a.un[2];
@@ -1760,6 +1835,7 @@ void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStre
   template void launch_pair<T>(const StepArgs<T>&, const T*, const T*, cudaStream_t);            \
   template void launch_set_coef<T>(const StepArgs<T>&, T*, T*, const double*, double, int*,     \
                                    cudaStream_t);                                                \
+  template void launch_set_damp<T>(const StepArgs<T>&, T*, const double*, double, int*, cudaStream_t); \
   template void launch_extract_owned<T>(const StepArgs<T>&, const T*, T*, cudaStream_t);              \
   template void launch_extract_face<T>(const StepArgs<T>&, const T*, int, T*, cudaStream_t);        \
   template void launch_refined_pair<T>(const StepArgs<T>&, cudaStream_t);

@@ -25,6 +25,7 @@ HYB_FIELD_U_LAST, HYB_FIELD_U_PREV, HYB_FIELD_LAMBDA_FIRST = 0, 1, 2
 HYB_WAIT_NONE = -1
 HYB_ADJ_EXACT, HYB_ADJ_PAPER = 0, 1
 HYB_FEM_STENCIL, HYB_FEM_TET_ALL = 0, 1
+HYB_MODEL_WAVE, HYB_MODEL_TELEGRAPH = 0, 1
 MAX_SOURCES = 16
 
 
@@ -39,7 +40,7 @@ class hyb_mesh_desc(ctypes.Structure):
                 ("fem_lo", c_int32 * 3), ("fem_hi", c_int32 * 3), ("bc", c_int32 * 6),
                 ("precision", c_int32), ("ckpt_every", c_int32), ("a_max", c_double),
                 ("refine_mask", c_void_p), ("wait_cycles", c_int64), ("adjoint_mode", c_int32),
-                ("fem_path", c_int32)]
+                ("fem_path", c_int32), ("model", c_int32)]
 
 
 class hyb_mesh_info(ctypes.Structure):
@@ -229,7 +230,7 @@ class HybMesh:
 
     def __init__(self, n, h, fem_lo=None, fem_hi=None, bc=(1,) * 6, precision="fp64", ckpt_every=0,
                  a_max=4.0, origin=(0.0, 0.0, 0.0), device="cuda", stream=None, refine=None, wait_cycles=0,
-                 adjoint_mode=HYB_ADJ_EXACT, fem_path=HYB_FEM_STENCIL):
+                 adjoint_mode=HYB_ADJ_EXACT, fem_path=HYB_FEM_STENCIL, model=HYB_MODEL_WAVE):
         import torch
 
         self.torch = torch
@@ -249,6 +250,7 @@ class HybMesh:
         d.wait_cycles = int(wait_cycles)
         d.adjoint_mode = int(adjoint_mode)
         d.fem_path = int(fem_path)
+        d.model = int(model)
         self._refine = None
         if refine is not None:
             import numpy as _np
