@@ -229,6 +229,67 @@ def make_data(H, w, dev, m32):
     return obs, errs
 
 
+def run_telegraph(H, dev, nsteps=800, reps=3, sweep_levels=300):
+    """The telegraph reading (damping sigma on the unknown voxels, a = 1) on
+    the large workload's lattice, FEM block and eight sources (no
+    refinement): sigma = the workload's Gaussian bumps generates the data
+    (800 steps: the waves reach the damped region and come back to the
+    faces), then `reps` gradient evaluations at half of it (forward with
+    checkpoints every 50 steps, misfit, adjoint with recompute, gradient),
+    timed with CUDA events; and the step launch times of sweeps with the
+    history kept."""
+    import numpy as np
+    import torch
+    import synth
+    w = synth.large_257(nsteps=nsteps, refine=False)
+    srcs, dt = w.sources, w.dt
+    S = len(srcs)
+    m = H.HybMesh.from_workload(w, precision="fp32", ckpt_every=50, device=dev, model=H.HYB_MODEL_TELEGRAPH)
+    sig_true = torch.tensor(w.sigma, dtype=torch.float64, device=dev)
+    sig = 0.5 * sig_true
+    obs = m.forward(sig_true, srcs, nsteps, dt).clone()
+
+    def grad():
+        tr = m.forward(sig, srcs, nsteps, dt)
+        J, cot = m.misfit(tr, obs, H.HYB_WEIGHTS_QUADRATURE, want_cot=True)
+        m.adjoint(cot)
+        return m.gradient(sig, 0.0, 0.0), J
+
+    grad()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(m.stream)
+    for _ in range(reps):
+        g, J = grad()
+    ev1.record(m.stream)
+    torch.cuda.synchronize(dev)
+    el = ev0.elapsed_time(ev1) / reps
+    gn = float(torch.linalg.vector_norm(g))
+    m.close()
+    nl = sweep_levels
+    mr = H.HybMesh.from_workload(w, precision="fp32", ckpt_every=0, device=dev, model=H.HYB_MODEL_TELEGRAPH)
+    tr = mr.new_trace(S, nl)
+    cot = torch.randn_like(tr) * 1e-3
+    for _ in range(2):
+        mr.forward(sig, srcs, nl, dt, tr)
+        mr.adjoint(cot)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(mr.stream)
+    mr.forward(sig, srcs, nl, dt, tr)
+    e[1].record(mr.stream)
+    mr.adjoint(cot)
+    e[2].record(mr.stream)
+    torch.cuda.synchronize(dev)
+    mr.close()
+    per = S * w.n_nodes * nsteps * 2
+    return {"workload": "257^3 lattice, FEM block nodes 64..192, 8 sources, damping sigma on the unknown voxels "
+                        "(the large workload's bumps), %d steps, checkpoints every 50, FP32" % nsteps,
+            "gradient_ms": el, "value": per / (el * 1e-3) / 1e9, "unit": UNIT,
+            "counted": "n_src x lattice nodes x N_t x 2 (forward + adjoint) per gradient evaluation",
+            "forward_launch_ms": e[0].elapsed_time(e[1]) / nl, "adjoint_launch_ms": e[1].elapsed_time(e[2]) / nl,
+            "J": J, "gnorm": gn}
+
+
 def run_cg(H, w, dev, steps, warmup, e2e_steps, clocks=None):
     """W warm-up CG iterations, then the first K iterations of a fresh CG
     loop timed with CUDA events on the mesh's stream; per-iteration F and
@@ -636,6 +697,10 @@ def run_ours(args):
             "roofline_l2_resident": roofline(r2, peak, peak_kind, w2.name), "cg": rec2["cg"],
             "fp32_vs_fp64": {"trace_rel_l2": max(r2["trace_errs"]), **err}}
         del r2
+        torch.cuda.empty_cache()
+    if not args.no_secondary and args.workload != "inverse_129":
+        from paper_1509_01399_gb300 import hyb as H
+        line["telegraph"] = run_telegraph(H, dev)
         torch.cuda.empty_cache()
     if args.serve_requests > 0:
         line["serving"] = run_serving(args, dev)
