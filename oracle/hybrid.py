@@ -8,9 +8,11 @@ never calls it.
 What it computes, in the paper's order and notation (numpy / scipy.sparse,
 float64 throughout):
 
-* Mesh (Sec. 7.1, Sec. 3): a structured lattice of nodes x = origin + h (i, j, k);
-  a finite-element block of nodes lo..hi whose voxels are each cut into the six
-  Kuhn tetrahedra along the voxel diagonal; the node classes of Algorithm 1:
+* Mesh (Sec. 7.1, Sec. 3): a structured lattice of nodes
+  x = origin + (dx_1 i, dx_2 j, dx_3 k) (one spacing h on every axis, or the
+  steps dx_1, dx_2, dx_3 of the 7-point Laplacian of Sec. 7.3); a
+  finite-element block of nodes lo..hi whose voxels (bricks) are each cut into
+  the six Kuhn tetrahedra along the voxel diagonal; the node classes of Algorithm 1:
   omega_o (the block's boundary shell, owned by the FDM), omega_diamond (the
   next shell inward, owned by the FEM), omega_* (the FEM interior) and
   omega_+ (every other lattice node, FDM).
@@ -22,14 +24,15 @@ float64 throughout):
   rows of nodes on the FEM block boundary, which Algorithm 1 overwrites from
   the FDM, so it never reaches an owned row).
 * FDM (Sec. 7.3): the leapfrog Eq. (fdmschemeforward) with the 7-point
-  Laplacian; Neumann faces by a mirror ghost; the plane-wave source
-  d_n u = p(t) of Model Problem 2 (Eq. (model2), Eq. (f)) by the ghost
-  u_g = u_in + 2 h p.
+  Laplacian (a second difference over dx_d^2 per axis d); Neumann faces by a
+  mirror ghost; the plane-wave source d_n u = p(t) of Model Problem 2
+  (Eq. (model2), Eq. (f)) by the ghost u_g = u_in + 2 h p (h the spacing
+  normal to the face).
 * Absorbing faces (Sec. 7.4): Eq. (eq:abs2),
-  u_b^{k+1} = u_{b1}^k + r u_b^k - r u_{b1}^{k+1},  r = (h - tau) / (h + tau),
-  applied after the interior rows of the same time level; a node on several
-  absorbing faces takes the mean of its per-face formulas, faces before edges
-  before corners.
+  u_b^{k+1} = u_{b1}^k + r u_b^k - r u_{b1}^{k+1},  r = (h - tau) / (h + tau)
+  with h the spacing normal to the face, applied after the interior rows of
+  the same time level; a node on several absorbing faces takes the mean of
+  its per-face formulas, faces before edges before corners.
 * Algorithm 2 (Sec. 7.5): per time step, update the FDM-owned rows, update
   the FEM-owned rows, copy omega_diamond from FEM to FDM and omega_o from FDM
   to FEM, swap levels.
@@ -137,12 +140,19 @@ class Problem:
     """Lattice, FEM block, node classes and assembled operators."""
 
     def __init__(self, n, h, fem_lo=None, fem_hi=None, bc=(BC_ABC,) * 6, origin=(0.0, 0.0, 0.0), refine=None):
-        """refine: optional boolean per unknown voxel (x fastest); each marked
-        voxel is refined once by bisection (see `refine_voxels`)."""
+        """h: one spacing for every axis, or the three steps (dx_1, dx_2, dx_3)
+        of Sec. 7.3 (then `h` is None and `hv` holds them).  refine: optional
+        boolean per unknown voxel (x fastest); each marked voxel is refined
+        once by bisection (see `refine_voxels`)."""
         self.n = tuple(int(v) for v in n)
         if min(self.n) < 3:
             raise ValueError("every axis needs at least 3 nodes")
-        self.h = float(h)
+        hv = np.asarray(h, dtype=np.float64)
+        self.hv = np.full(3, float(hv)) if hv.ndim == 0 else np.array(hv, dtype=np.float64).reshape(3)
+        if not (self.hv > 0).all():
+            raise ValueError("spacings must be > 0")
+        self.iso = bool(self.hv[0] == self.hv[1] == self.hv[2])
+        self.h = float(self.hv[0]) if self.iso else None
         self.bc = tuple(int(b) for b in bc)
         self.origin = tuple(float(o) for o in origin)
         nx, ny, nz = self.n
@@ -180,7 +190,7 @@ class Problem:
             tets = kuhn_tets(vox)  # (V, 6, 4, 3)
             tet_nodes = self.node_id(tets.reshape(-1, 3)).reshape(-1, 4)
             tet_unknown = np.repeat(uid, 6)
-            X_all = self.h * self.I.astype(np.float64)
+            X_all = self.I.astype(np.float64) * self.hv
             self.NC = 0
             self.center_of_unknown = np.full(self.n_unknown, -1, dtype=np.int64)
             if refine is not None and self.n_unknown:
@@ -192,18 +202,18 @@ class Problem:
                 self.center_of_unknown[np.flatnonzero(refine)] = self.N + np.arange(self.NC)
                 rel_ids = np.flatnonzero(refine)
                 cvox = np.stack([rel_ids % ud[0], (rel_ids // ud[0]) % ud[1], rel_ids // (ud[0] * ud[1])], axis=1)
-                X_all = np.concatenate([X_all, self.h * (cvox + lo + 1 + 0.5)], axis=0)
+                X_all = np.concatenate([X_all, (cvox + lo + 1 + 0.5) * self.hv], axis=0)
             self.tet_nodes = tet_nodes
             self.tet_unknown = tet_unknown
             self.tet_vol, self.tet_grads = p1_element(X_all[tet_nodes])
-            self.voxel_volume = self.h ** 3
+            self.voxel_volume = self.cell_volume()
         else:
             self.owned = np.zeros(self.N, dtype=bool)
             self.omega_o = np.zeros(self.N, dtype=bool)
             self.omega_diamond = np.zeros(self.N, dtype=bool)
             self.unknown_dims = (0, 0, 0)
             self.n_unknown = 0
-            self.voxel_volume = self.h ** 3
+            self.voxel_volume = self.cell_volume()
             self.NC = 0
         # state vectors hold the lattice nodes, then the refinement centres
         self.NT = self.N + self.NC
@@ -220,6 +230,15 @@ class Problem:
         self._phase_cache = {}
 
     # ------------------------------------------------------------------ mesh
+    def cell_volume(self):
+        """Volume of one lattice cell: h^3, or dx_1 dx_2 dx_3."""
+        return self.h ** 3 if self.iso else float(self.hv[0] * self.hv[1] * self.hv[2])
+
+    def r_abc(self, dt):
+        """r = (h - tau) / (h + tau) of Eq. (eq:abs2) per axis, h the spacing
+        normal to the face."""
+        return (self.hv - dt) / (self.hv + dt)
+
     def node_id(self, ijk):
         ijk = np.asarray(ijk, dtype=np.int64)
         return ijk[..., 0] + self.n[0] * (ijk[..., 1] + self.n[1] * ijk[..., 2])
@@ -234,11 +253,13 @@ class Problem:
         return nodes[np.argsort(key, kind="stable")]
 
     def face_weights(self, f):
-        """Lumped surface quadrature weight of each face node: h^2 halved for
-        every in-face coordinate that sits on the face's own border."""
+        """Lumped surface quadrature weight of each face node: the in-face cell
+        area (h^2, or dx_p dx_q for the face's axes p, q) halved for every
+        in-face coordinate that sits on the face's own border."""
         nodes = self.face_nodes(f)
         ax = f // 2
-        w = np.full(nodes.size, self.h ** 2)
+        p, q = [d for d in range(3) if d != ax]
+        w = np.full(nodes.size, self.h ** 2 if self.iso else float(self.hv[p] * self.hv[q]))
         for d in range(3):
             if d == ax:
                 continue
@@ -248,13 +269,14 @@ class Problem:
 
     # ------------------------------------------------------------- operators
     def _fdm_laplacian(self):
-        """7-point Delta_h of Sec. 7.3 on every lattice node, Neumann mirror
-        ghost u_{-1} = u_{1} on the outer faces (the ghost values of source
-        faces add a constant, handled in the source term)."""
+        """7-point Delta_h of Sec. 7.3 on every lattice node (the second
+        difference along axis d over dx_d^2), Neumann mirror ghost
+        u_{-1} = u_{1} on the outer faces (the ghost values of source faces add
+        a constant, handled in the source term)."""
         rows, cols, vals = [], [], []
         ids = np.arange(self.N)
-        inv_h2 = 1.0 / self.h ** 2
         for d in range(3):
+            inv_h2 = 1.0 / self.hv[d] ** 2
             c = self.I[:, d]
             st = self.stride[d]
             lowb = c == 0
@@ -332,7 +354,10 @@ class Problem:
         d, i0, _ = self.plane_wave(src)
         ax = f // 2
         p, q = [b for b in range(3) if b != ax]
-        return 2.0 * math.pi / src.omega + self.h * (abs(d[p]) * (self.n[p] - 1) + abs(d[q]) * (self.n[q] - 1))
+        if self.iso:
+            return 2.0 * math.pi / src.omega + self.h * (abs(d[p]) * (self.n[p] - 1) + abs(d[q]) * (self.n[q] - 1))
+        return 2.0 * math.pi / src.omega + (abs(d[p]) * (self.n[p] - 1) * self.hv[p] +
+                                            abs(d[q]) * (self.n[q] - 1) * self.hv[q])
 
     def phase(self, src, k, dt):
         """Boundary state for the step from t_k = k dt: an entry face of the
@@ -350,24 +375,29 @@ class Problem:
 
     def source_term(self, src, ph: Phase, dt):
         """s with s_i = tau^2 (2 / h) g_i on the non-absorbing nodes of the
-        flux faces: the mirror ghost u_g = u_in + 2 h g of d_n u = g, summed over
-        the flux faces a node lies on; g = amp (-(d . n_f)) p(t_k - d.(x_i - x0))."""
+        flux faces (h the spacing normal to the face): the mirror ghost
+        u_g = u_in + 2 h g of d_n u = g, summed over the flux faces a node lies
+        on; g = amp (-(d . n_f)) p(t_k - d.(x_i - x0))."""
         s = np.zeros(self.NT)
         if not ph.src_faces:
             return s
         d, i0, entry = self.plane_wave(src)
         level, _ = self.abc_structure(ph.abc_faces)
-        delay = self.h * (d[0] * (self.I[:, 0] - i0[0]) + d[1] * (self.I[:, 1] - i0[1]) +
-                          d[2] * (self.I[:, 2] - i0[2]))
+        if self.iso:
+            delay = self.h * (d[0] * (self.I[:, 0] - i0[0]) + d[1] * (self.I[:, 1] - i0[1]) +
+                              d[2] * (self.I[:, 2] - i0[2]))
+        else:
+            delay = (d[0] * self.hv[0] * (self.I[:, 0] - i0[0]) + d[1] * self.hv[1] * (self.I[:, 1] - i0[1]) +
+                     d[2] * self.hv[2] * (self.I[:, 2] - i0[2]))
         p = pulse(src.omega, ph.t - delay)
         for f in ph.src_faces:
             m = self.on_face[f][: self.N] & (level[: self.N] == 0)
-            s[: self.N][m] += dt * dt * 2.0 / self.h * src.amp * entry[f] * p[m]
+            s[: self.N][m] += dt * dt * 2.0 / self.hv[f // 2] * src.amp * entry[f] * p[m]
         return s
 
     def abc_structure(self, abc_faces):
         """Level (number of absorbing faces a node lies on) and, per absorbing
-        face, its nodes b with the inward neighbours b1."""
+        face, its nodes b with the inward neighbours b1 and the face's axis."""
         key = tuple(abc_faces)
         if key in self._phase_cache:
             return self._phase_cache[key]
@@ -379,15 +409,26 @@ class Problem:
             ax, side = divmod(f, 2)
             b = np.flatnonzero(self.on_face[f])
             b1 = b + (self.stride[ax] if side == 0 else -self.stride[ax])
-            pairs.append((b, b1))
+            pairs.append((b, b1, ax))
         self._phase_cache[key] = (level, pairs)
         return level, pairs
+
+    def abc_self(self, level, pairs, r):
+        """Coefficient of u_b^k in the absorbing row of node b: r, or on
+        anisotropic lattices the mean of the r of the node's absorbing faces."""
+        if self.iso:
+            return np.full(self.NT, r[0])
+        acc = np.zeros(self.NT)
+        for b, _, ax in pairs:
+            acc[b] += r[ax]
+        return acc / np.maximum(level, 1)
 
     def step_matrices(self, Lop, phase: Phase, dt):
         """E, B, C of one step written as E u^{k+1} = B u^k - C u^{k-1} + s
         (the source vector s is `source_term`)."""
         level, pairs = self.abc_structure(phase.abc_faces)
-        r = (self.h - dt) / (self.h + dt)
+        r = self.r_abc(dt)
+        rself = self.abc_self(level, pairs, r)
         nonabc = (level == 0).astype(float)
         I = sp.identity(self.NT, format="csr")
         Dn = sp.diags(nonabc)
@@ -398,14 +439,14 @@ class Problem:
         abcn = np.flatnonzero(level > 0)
         rb.append(abcn)
         cb.append(abcn)
-        vb.append(np.full(abcn.size, r))
+        vb.append(rself[abcn])
         ve.append(np.ones(abcn.size))
-        for b, b1 in pairs:
+        for b, b1, ax in pairs:
             Lb = level[b].astype(float)
             rb.append(b)
             cb.append(b1)
             vb.append(1.0 / Lb)
-            ve.append(r / Lb)
+            ve.append(r[ax] / Lb)
         rr, cc = np.concatenate(rb), np.concatenate(cb)
         B = (B + sp.csr_matrix((np.concatenate(vb), (rr, cc)), shape=B.shape)).tocsr()
         E = (E + sp.csr_matrix((np.concatenate(ve), (rr, cc)), shape=E.shape)).tocsr()
@@ -421,9 +462,8 @@ class Problem:
         Returns a dict with the trace on the source face (rows t_0 .. t_N),
         the final level u^N (and u^{N-1}), optionally u^k on the FEM-owned
         nodes for k = 0 .. N-1 (for the gradient) and every full level."""
-        h = self.h
         tau2 = dt * dt
-        r = (h - dt) / (h + dt)
+        r = self.r_abc(dt)
         K, ML = self.assemble(a_unknown)
         own = self.owned
         obs = self.face_nodes(src.face) if src is not None else np.zeros(0, dtype=np.int64)
@@ -462,19 +502,20 @@ class Problem:
                 # 3. FEM values at omega_diamond become FDM boundary values
                 new_fd[self.omega_diamond] = new_fe[self.omega_diamond]
             # absorbing rows, Eq. (eq:abs2), faces before edges before corners
+            rself = self.abc_self(level, pairs, r)
             for L in (1, 2, 3):
                 acc = None
-                for b, b1 in pairs:
+                for b, b1, ax in pairs:
                     sel = level[b] == L
                     if not sel.any():
                         continue
                     bb, bb1 = b[sel], b1[sel]
                     if acc is None:
                         acc = np.zeros(self.NT)
-                    acc[bb] += u_fd[bb1] - r * new_fd[bb1]
+                    acc[bb] += u_fd[bb1] - r[ax] * new_fd[bb1]
                 if acc is not None:
                     m = level == L
-                    new_fd[m] = r * u_fd[m] + acc[m] / L
+                    new_fd[m] = rself[m] * u_fd[m] + acc[m] / L
             if self.has_fem:
                 # 4. FDM values at omega_o become FEM boundary values
                 new_fe[self.omega_o] = new_fd[self.omega_o]
@@ -582,10 +623,10 @@ class Problem:
 
     def lumped_mass(self, a_unknown):
         """Diagonal mass M in which the hybrid operator is symmetric: on
-        FDM-owned rows the lumped lattice mass h^3, halved for every axis on
-        which the node lies on the outer boundary; on FEM-owned rows the
-        lumped finite-element mass M^L (Sec. 7.2)."""
-        M = np.full(self.NT, self.h ** 3)
+        FDM-owned rows the lumped lattice mass (the cell volume), halved for
+        every axis on which the node lies on the outer boundary; on FEM-owned
+        rows the lumped finite-element mass M^L (Sec. 7.2)."""
+        M = np.full(self.NT, self.cell_volume())
         for d in range(3):
             b = np.concatenate([(self.I[:, d] == 0) | (self.I[:, d] == self.n[d] - 1), np.zeros(self.NC, dtype=bool)])
             M[b] *= 0.5
@@ -606,7 +647,6 @@ class Problem:
         cotangent c^k = dJ/d(trace row k) = w_k m_j (u - u~), s^k_j = -tau c^k_j / M_j.
         Returns g_c = tau sum_k int_c grad u^k . grad lambda^k (Eq. (gradient1),
         same time index), the paper's approximation of dJ/da_c."""
-        h = self.h
         tau2 = dt * dt
         K, ML = self.assemble(a_unknown)
         M = self.lumped_mass(a_unknown)
@@ -890,4 +930,5 @@ def telegraph_value_and_grad(prob: Problem, sigma, sources, nsteps, dt, obs_trac
 
 def problem_from_workload(w) -> Problem:
     refine = getattr(w, "refine", None)
-    return Problem(w.n, w.h, w.fem_lo, w.fem_hi, w.bc, w.origin, refine=refine)
+    spacing = getattr(w, "spacing", None)
+    return Problem(w.n, w.h if spacing is None else spacing, w.fem_lo, w.fem_hi, w.bc, w.origin, refine=refine)

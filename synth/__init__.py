@@ -70,6 +70,12 @@ class Workload:
     ckpt_every: int = 0
     extra: dict = field(default_factory=dict)
     refine: Optional[np.ndarray] = None  # bool per unknown voxel: refined once
+    spacing: Optional[Tuple[float, float, float]] = None  # per-axis steps dx_1, dx_2, dx_3 (None: h on every axis)
+
+    @property
+    def hv(self) -> Tuple[float, float, float]:
+        """The lattice step along each axis."""
+        return tuple(self.spacing) if self.spacing is not None else (self.h, self.h, self.h)
 
     @property
     def unknown_dims(self) -> Tuple[int, int, int]:
@@ -222,6 +228,13 @@ def refined_dt(h: float, a_max: float, safety: float = 0.9) -> float:
     return safety * 2.0 * h / math.sqrt(32.0 * a_max)
 
 
+def anisotropic_dt(spacing, a_max: float, safety: float = 0.9) -> float:
+    """Time step for per-axis steps dx_d: tau <= 1 / sqrt(a sum_d 1 / dx_d^2)
+    (the bound h / sqrt(3 a) of Eq. (CFL) when the steps are equal), scaled
+    by a safety factor."""
+    return safety / math.sqrt(a_max * sum(1.0 / (d * d) for d in spacing))
+
+
 def structured_dt(h: float, a_max: float, safety: float = 0.9) -> float:
     """Time step from the CFL bound tau <= h / sqrt(3 a) (Eq. (CFL)) scaled by
     a safety factor."""
@@ -323,11 +336,12 @@ def large_batched(N: int = 257, nsteps: int = 3000, n_src: int = 8, refine: bool
 
 def small_problem(n=9, fem=(2, 6), nsteps=60, bc=ALL_ABC, src_face=FACE_ZP, omega=12.0,
                   sigma_seed=0, sigma_scale=1.0, a_max=4.0, courant=0.5, cubic=True,
-                  name="small", refine_frac=0.0, refine_seed=5) -> Workload:
+                  name="small", refine_frac=0.0, refine_seed=5, spacing=None) -> Workload:
     """Tiny problem for unit and parity tests: n^3 (or n = (nx, ny, nz))
-    lattice with spacing 1 / (n - 1) on [-1/2, 1/2]^3-ish, FEM block nodes
-    fem[0]..fem[1] on every axis, random sigma in [0, sigma_scale) on the
-    unknown voxels."""
+    lattice with spacing 1 / (n - 1) on [-1/2, 1/2]^3-ish (or the per-axis
+    steps `spacing`, with the time step of `anisotropic_dt` at the given
+    courant factor), FEM block nodes fem[0]..fem[1] on every axis, random
+    sigma in [0, sigma_scale) on the unknown voxels."""
     if isinstance(n, int):
         n = (n, n, n)
     h = 1.0 / (max(n) - 1)
@@ -348,9 +362,13 @@ def small_problem(n=9, fem=(2, 6), nsteps=60, bc=ALL_ABC, src_face=FACE_ZP, omeg
         dt = courant * 2.0 * h / math.sqrt(32.0 * a_max)
     else:
         dt = courant * h / math.sqrt(3.0 * a_max)
+    if spacing is not None:
+        spacing = tuple(float(v) for v in spacing)
+        h = spacing[0]
+        dt = anisotropic_dt(spacing, a_max, courant)
     srcs = [] if src_face is None else [Source(src_face, omega)]
     return Workload(name, n, h, origin, lo, hi, tuple(bc), srcs, nsteps, dt, a_max, sigma, "fp64",
-                    refine=refine)
+                    refine=refine, spacing=spacing)
 
 
 def model1_initial(w: Workload):
@@ -362,14 +380,15 @@ def model1_initial(w: Workload):
     (in unknown-voxel order), each a float64 array."""
     nx, ny, nz = w.n
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    X = [w.origin[0] + w.h * x, w.origin[1] + w.h * y, w.origin[2] + w.h * z]
+    hv = w.hv
+    X = [w.origin[0] + hv[0] * x, w.origin[1] + hv[1] * y, w.origin[2] + hv[2] * z]
     u0 = np.exp(-(X[0] ** 2 + X[1] ** 2 + X[2] ** 2)).ravel()
     c0 = np.zeros(0)
     if w.refine is not None and np.any(w.refine):
         ud = w.unknown_dims
         ids = np.flatnonzero(w.refine)
         cv = [ids % ud[0], (ids // ud[0]) % ud[1], ids // (ud[0] * ud[1])]
-        C = [w.origin[d] + w.h * (cv[d] + w.fem_lo[d] + 1 + 0.5) for d in range(3)]
+        C = [w.origin[d] + hv[d] * (cv[d] + w.fem_lo[d] + 1 + 0.5) for d in range(3)]
         c0 = np.exp(-(C[0] ** 2 + C[1] ** 2 + C[2] ** 2))
     return (u0, u0.copy()), (c0, c0.copy())
 
