@@ -63,7 +63,8 @@ enum { HYB_FIELD_U_LAST = 0, HYB_FIELD_U_PREV = 1, HYB_FIELD_LAMBDA_FIRST = 2 };
 /* Mesh description (Sec. 9 geometry; Algorithm 1 node classes). */
 typedef struct {
   int32_t n[3];        /* lattice nodes per axis, each >= 3 */
-  double h;            /* lattice spacing, the same on every axis (Eq. (CFL)) */
+  double h;            /* lattice spacing, the same on every axis (Eq. (CFL));
+                          ignored when `spacing` is set */
   double origin[3];    /* world coordinates of node (0,0,0) */
   int32_t fem_lo[3];   /* FEM block node range, inclusive; fem_lo[0] < 0 = no */
   int32_t fem_hi[3];   /*   FEM block.  Needs 0 <= lo, hi <= n-1, hi - lo >= 2 */
@@ -129,6 +130,22 @@ typedef struct {
                           adjoint and the stencil path, and no batches; a
                           negative sigma is reported by hyb_sync as HYB_ERR_CFL.
                           a_max keeps its role for the time step (a = 1). */
+  double spacing[3];   /* lattice steps dx_1, dx_2, dx_3 per axis (the 7-point
+                          Laplacian of Sec. 7.3 with unequal steps; the FEM
+                          block's voxels are bricks, each cut into the six
+                          Kuhn tetrahedra).  All 0: h on every axis.  Otherwise
+                          each must be > 0 and h is ignored; equal steps are
+                          the isotropic lattice.  Unequal steps: Eq. (eq:abs2)
+                          takes r = (dx - tau) / (dx + tau) with dx the step
+                          normal to each face (a node on several absorbing
+                          faces: the mean of its per-face rows), the source
+                          ghost 2 dx g uses that step too, the quadrature
+                          weight of a face node is its in-face cell area
+                          dx_p dx_q (halved on the face's border), and
+                          dt_max = 1 / sqrt(a_max sum 1 / dx^2).  Every level
+                          then runs the generic all-node kernels (no staged
+                          tiles).  Needs no refinement, the exact adjoint and
+                          the wave model, and no batches (HYB_ERR_ARG). */
 } hyb_mesh_desc;
 
 #define HYB_WAIT_NONE (-1)
@@ -144,8 +161,9 @@ typedef struct {
   int32_t obs_stride;      /* padded length of one trace row */
   double dt_max;           /* stability bound for a <= a_max: h / sqrt(3 a_max)
                               (Eq. (CFL)), lowered by a row-sum bound of the
-                              refined rows when voxels are refined */
-  double voxel_volume;     /* h^3 */
+                              refined rows when voxels are refined; with
+                              per-axis steps 1 / sqrt(a_max sum 1 / dx^2) */
+  double voxel_volume;     /* h^3, or dx_1 dx_2 dx_3 */
   int64_t device_bytes;    /* device memory currently held by the mesh */
   int64_t launches;        /* kernels launched by this mesh so far */
   int64_t n_centres;       /* centre nodes of refined voxels */
@@ -325,7 +343,9 @@ hyb_status hyb_get_field(hyb_mesh* mesh, int32_t which, int32_t isrc, void* out)
    hyb_misfit computes, without a mesh: trace, u_obs (device fields of
    `precision`, shape [n_src][nsteps + 1][obs_stride]), face_dims (HOST
    int32[n_src][2]: the in-face extents (n_p, n_q) of each source's face),
-   dt, h and `weights` as for hyb_misfit.  Writes J_data to *J_dev (a DEVICE
+   dt, h and `weights` as for hyb_misfit (one step h on every axis: the
+   quadrature weight of a face node is h^2; meshes with per-axis steps use
+   hyb_misfit).  Writes J_data to *J_dev (a DEVICE
    double) and, if cotangent != NULL, the cotangent, asynchronously on
    `stream` (a cudaStream_t; NULL = legacy default stream).
    It allocates nothing: its per-block partial sums live in a static

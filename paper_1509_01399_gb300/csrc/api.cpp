@@ -111,6 +111,8 @@ struct hyb_mesh {
   DevBuf I0, IC0;               // initial state of Model Problem 1: u^0, u^{-1} (padded fields), centres
   DevBuf acopy, kuhn, kuhn_v;   // all-FEM path: coefficient of the last forward, Kuhn element tables
   bool have_init = false;
+  bool ani = false;          // the lattice steps differ per axis (every level by the all-node kernels)
+  double hv[3] = {0, 0, 0};  // lattice step per axis
   cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
   // interior work items of the forward / transposed step per slot count; built
   // once and kept (captured sweep graphs refer to them)
@@ -273,7 +275,10 @@ Wave wave_of(const hyb_mesh* m, const hyb_source& s) {
     const double dn = w.d[ax] * ((f & 1) ? 1.0 : -1.0);
     w.fac[f] = dn < 0.0 ? -dn : 0.0;
     const int p = ax == 0 ? 1 : 0, q = ax == 2 ? 1 : 2;
-    w.tsw[f] = t1 + m->d.h * (std::fabs(w.d[p]) * (m->n[p] - 1) + std::fabs(w.d[q]) * (m->n[q] - 1));
+    if (m->ani)
+      w.tsw[f] = t1 + (std::fabs(w.d[p]) * (m->n[p] - 1) * m->hv[p] + std::fabs(w.d[q]) * (m->n[q] - 1) * m->hv[q]);
+    else
+      w.tsw[f] = t1 + m->d.h * (std::fabs(w.d[p]) * (m->n[p] - 1) + std::fabs(w.d[q]) * (m->n[q] - 1));
   }
   return w;
 }
@@ -308,12 +313,12 @@ void set_wave(const hyb_mesh* m, Slot<T>& S, const hyb_source& src, int k, doubl
   S.src_mask = sm;
   S.st = k * dt;
   const double h = m->d.h;
-  for (int f = 0; f < 6; ++f) S.sf[f] = dt * dt * 2.0 / h * src.amp * w.fac[f];
+  for (int f = 0; f < 6; ++f) S.sf[f] = dt * dt * 2.0 / (m->ani ? m->hv[f >> 1] : h) * src.amp * w.fac[f];
   for (int a = 0; a < 3; ++a) {
-    S.sd[a] = w.d[a];
+    S.sd[a] = m->ani ? w.d[a] * m->hv[a] : w.d[a];  // per-axis steps: the delay d . (x - x0) axis by axis
     S.si0[a] = w.i0[a];
   }
-  S.sh = h;
+  S.sh = m->ani ? 1.0 : h;
   S.somega = src.omega;
   S.st1 = 2.0 * M_PI / src.omega;
 }
@@ -505,6 +510,10 @@ hyb_status upload(hyb_mesh* m, DevBuf& b, const std::vector<V>& host) {
 hyb_status build_kuhn(hyb_mesh* m) {
   std::vector<double> tab(6 * 16 + 6);
   std::vector<int> verts(6 * 4);
+  // per-axis steps: the brick in units of dx_1, its tables divided by its
+  // volume (every interior node's lumped mass stays 1, as on the unit cube)
+  const double sc[3] = {1.0, m->ani ? m->hv[1] / m->hv[0] : 1.0, m->ani ? m->hv[2] / m->hv[0] : 1.0};
+  const double bvol = sc[0] * sc[1] * sc[2];
   const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   for (int t = 0; t < 6; ++t) {
     const int v1 = 1 << perms[t][0], v2 = v1 | (1 << perms[t][1]);
@@ -512,14 +521,14 @@ hyb_status build_kuhn(hyb_mesh* m) {
     double X[4][3], vol, K[4][4];
     for (int q = 0; q < 4; ++q) {
       verts[4 * t + q] = v[q];
-      X[q][0] = v[q] & 1;
-      X[q][1] = (v[q] >> 1) & 1;
-      X[q][2] = v[q] >> 2;
+      X[q][0] = (v[q] & 1) * sc[0];
+      X[q][1] = ((v[q] >> 1) & 1) * sc[1];
+      X[q][2] = (v[q] >> 2) * sc[2];
     }
     p1_tet(X, &vol, K);
     for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) tab[16 * t + 4 * a + b] = K[a][b];
-    tab[96 + t] = vol;
+      for (int b = 0; b < 4; ++b) tab[16 * t + 4 * a + b] = m->ani ? K[a][b] / bvol : K[a][b];
+    tab[96 + t] = m->ani ? vol / bvol : vol;
   }
   HYB_TRY(upload(m, m->kuhn, tab));
   HYB_TRY(upload(m, m->kuhn_v, verts));
@@ -795,10 +804,19 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.G = (double*)m->G.p;
   A.avox = (const T*)m->avox.p;
   A.sdamp = m->d.model == HYB_MODEL_TELEGRAPH ? (const T*)m->sdamp.p : nullptr;
-  const double h = m->d.h;
+  const double h = m->ani ? m->hv[0] : m->d.h;
   A.c2 = (T)(dt * dt / (h * h));
   A.r = (T)((h - dt) / (h + dt));
   step_geometry(m, &A.npb, &A.ntx, &A.small, &A.nedge);
+  if (m->ani) {  // every level by the all-node kernels, axis terms weighed by kap
+    A.ani = 1;
+    A.small = 1;
+    A.nedge = 0;
+    for (int a = 0; a < 3; ++a) {
+      A.kap[a] = (h * h) / (m->hv[a] * m->hv[a]);
+      A.ra[a] = (T)((m->hv[a] - dt) / (m->hv[a] + dt));
+    }
+  }
   if (m->d.fem_path == HYB_FEM_TET_ALL) {  // every level by the all-node kernels
     A.tet = 1;
     A.small = 1;
@@ -1230,12 +1248,26 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
   return HYB_OK;
 }
 
+// Volume of one lattice cell: h^3, or dx_1 dx_2 dx_3.
+double cell_volume(const hyb_mesh* m) {
+  return m->ani ? m->hv[0] * m->hv[1] * m->hv[2] : m->d.h * m->d.h * m->d.h;
+}
+
+// In-face cell area of face f: h^2, or dx_p dx_q (p, q its in-face axes).
+double face_cell_area(const hyb_mesh* m, int f) {
+  const int ax = f >> 1, p = ax == 0 ? 1 : 0, q = ax == 2 ? 1 : 2;
+  return m->ani ? m->hv[p] * m->hv[q] : m->d.h * m->d.h;
+}
+
 // Factor from the accumulated pairing sums (kGradPairScale / h times
 // u^T K_c lambda per voxel) to dJ/da: exact adjoint, dJ/da_c =
 // -tau^2 u^T K_c (lambda~ / h^3) summed over steps; paper mode,
-// g_c = tau u^T K_c lambda summed over steps.
+// g_c = tau u^T K_c lambda summed over steps.  Per-axis steps: the kernels
+// accumulate kGradPairScale sum_ax kap_ax u^T K^ax_c lambda~ (the unit-cube
+// edge parts K^ax, kap_ax = dx_1^2 / dx_ax^2) and K_c = (|c| / dx_1^2)
+// sum_ax kap_ax K^ax_c, so h reads dx_1.
 double grad_scale(const hyb_mesh* m) {
-  const double h = m->d.h, dt = m->dt;
+  const double h = m->ani ? m->hv[0] : m->d.h, dt = m->dt;
   if (m->d.adjoint_mode == HYB_ADJ_PAPER) return dt * h / kGradPairScale;
   if (m->d.model == HYB_MODEL_TELEGRAPH) return -dt / 24.0;  // the kernels accumulate 12 sum_i m_i lambda_i v_i
   return -dt * dt / (h * h) / kGradPairScale;
@@ -1259,7 +1291,7 @@ hyb_status misfit_impl(hyb_mesh* m, const T* trace, const T* obs, int weights, d
   }
   const bool quad = weights == HYB_WEIGHTS_QUADRATURE;
   g.wt = quad ? m->dt : 1.0;
-  g.hh = quad ? m->d.h * m->d.h : 1.0;
+  for (int s = 0; s < m->nsrc; ++s) g.hh[s] = quad ? face_cell_area(m, m->src[s].face) : 1.0;
   g.halve = quad ? 1 : 0;
   HYB_TRY(ensure(m, m->part, 2 * (size_t)kReduceBlocks * sizeof(double)));
   HYB_TRY(ensure(m, m->scal, 16 * sizeof(double)));
@@ -1298,7 +1330,7 @@ hyb_status misfit_batch_impl(hyb_mesh* m, const T* trace, const T* obs, int weig
     g.np[0] = m->n[ax == 0 ? 1 : 0];
     g.nq[0] = m->n[ax == 2 ? 1 : 2];
     g.wt = quad ? m->dt : 1.0;
-    g.hh = quad ? m->d.h * m->d.h : 1.0;
+    g.hh[0] = quad ? face_cell_area(m, m->src[s].face) : 1.0;
     g.halve = quad ? 1 : 0;
     launch_misfit<T>(g, trace + s * rows, obs + s * rows, cot ? cot + s * rows : nullptr, (double*)m->part.p, m->st);
     HYB_LAUNCHED(m);
@@ -1324,7 +1356,7 @@ hyb_status cg_impl(hyb_mesh* m, double* a, const T* obs, const hyb_source* src, 
                    double dt, const hyb_cg_params* P, hyb_cg_state* S, hyb_cg_report* R) {
   const size_t tb = (size_t)nsrc * (nsteps + 1) * m->obs_stride * sizeof(T);
   const long long nu = m->nu;
-  const double vol = m->d.h * m->d.h * m->d.h;
+  const double vol = cell_volume(m);
   HYB_TRY(ensure(m, m->trace, tb));
   HYB_TRY(ensure(m, m->cot, tb));
   HYB_TRY(ensure(m, m->g, (size_t)nu * sizeof(double)));
@@ -1448,7 +1480,8 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   for (int a = 0; a < 3; ++a)
     if (d->n[a] < 3) return fail(HYB_ERR_ARG, "n[%d] = %d must be >= 3", a, d->n[a]);
   if ((long long)d->n[0] * d->n[1] >= (1LL << 31)) return fail(HYB_ERR_ARG, "lattice plane too large");
-  if (!(d->h > 0.0)) return fail(HYB_ERR_ARG, "h must be > 0");
+  const bool spaced = d->spacing[0] != 0.0 || d->spacing[1] != 0.0 || d->spacing[2] != 0.0;
+  if (!spaced && !(d->h > 0.0)) return fail(HYB_ERR_ARG, "h must be > 0");
   if (d->precision != HYB_FP64 && d->precision != HYB_FP32) return fail(HYB_ERR_ARG, "bad precision");
   if (d->ckpt_every < 0) return fail(HYB_ERR_ARG, "ckpt_every must be >= 0");
   if (d->wait_cycles < HYB_WAIT_NONE) return fail(HYB_ERR_ARG, "wait_cycles must be >= 0 or HYB_WAIT_NONE");
@@ -1465,6 +1498,12 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
         return fail(HYB_ERR_ARG, "the telegraph model needs 2 <= fem_lo and fem_hi <= n - 3 on every axis");
   }
   if (!(d->a_max > 0.0)) return fail(HYB_ERR_ARG, "a_max must be > 0");
+  for (int a = 0; spaced && a < 3; ++a)
+    if (!(d->spacing[a] > 0.0 && d->spacing[a] < 1e300))
+      return fail(HYB_ERR_ARG, "spacing[%d] must be > 0 (or all three 0)", a);
+  const bool ani = spaced && !(d->spacing[0] == d->spacing[1] && d->spacing[1] == d->spacing[2]);
+  if (ani && (d->refine_mask || d->adjoint_mode != HYB_ADJ_EXACT || d->model != HYB_MODEL_WAVE))
+    return fail(HYB_ERR_ARG, "per-axis steps take no refinement, the exact adjoint and the wave model");
   for (int f = 0; f < 6; ++f)
     if (d->bc[f] != HYB_BC_NEUMANN0 && d->bc[f] != HYB_BC_ABC) return fail(HYB_ERR_ARG, "bad bc[%d]", f);
   const bool fem = d->fem_lo[0] >= 0;
@@ -1477,6 +1516,9 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   hyb_mesh* m = new (std::nothrow) hyb_mesh();
   if (!m) return fail(HYB_ERR_OOM, "host allocation failed");
   m->d = *d;
+  if (spaced) m->d.h = d->spacing[0];  // equal steps: the isotropic lattice of that step
+  m->ani = ani;
+  for (int a = 0; a < 3; ++a) m->hv[a] = spaced ? d->spacing[a] : d->h;
   m->st = (cudaStream_t)stream;
   for (int a = 0; a < 3; ++a) m->n[a] = d->n[a];
   m->N = (long long)d->n[0] * d->n[1] * d->n[2];
@@ -1513,7 +1555,11 @@ hyb_status hyb_mesh_create(const hyb_mesh_desc* d, void* stream, hyb_mesh** out)
   m->obs_stride = std::max(d->n[0] * d->n[1], std::max(d->n[0] * d->n[2], d->n[1] * d->n[2]));
   for (int f = 0; f < 6; ++f)
     if (d->bc[f] == HYB_BC_ABC) m->abc_mask |= 1 << f;
-  m->dt_max = d->h / std::sqrt(3.0 * d->a_max);
+  if (ani)  // tau^2 a sum_ax 4 / dx_ax^2 <= 4: the 7-point row's bound (Eq. (CFL) for equal steps)
+    m->dt_max = 1.0 / std::sqrt(d->a_max * (1.0 / (m->hv[0] * m->hv[0]) + 1.0 / (m->hv[1] * m->hv[1]) +
+                                            1.0 / (m->hv[2] * m->hv[2])));
+  else
+    m->dt_max = m->d.h / std::sqrt(3.0 * d->a_max);
   hyb_status st = HYB_OK;
   if (fem) st = ensure(m, m->W, 3 * (size_t)m->wsz * esize(m));
   if (st == HYB_OK) st = ensure(m, m->flag, 2 * sizeof(int));
@@ -1562,7 +1608,7 @@ hyb_status hyb_mesh_query(const hyb_mesh* m, hyb_mesh_info* o) {
   o->n_centres = m->nc;
   o->n_sparse_rows = m->nr;
   o->n_sparse_nnz = m->nnz;
-  o->voxel_volume = m->d.h * m->d.h * m->d.h;
+  o->voxel_volume = cell_volume(m);
   o->device_bytes = m->bytes;
   o->launches = m->launches;
   return HYB_OK;
@@ -1635,6 +1681,7 @@ hyb_status hyb_forward_batch(hyb_mesh* m, const double* a, const hyb_source* src
   if (m->nu > 0 && !a) return fail(HYB_ERR_ARG, "null coefficient");
   if (m->d.fem_path == HYB_FEM_TET_ALL) return fail(HYB_ERR_ARG, "no batches on the HYB_FEM_TET_ALL path");
   if (m->d.model == HYB_MODEL_TELEGRAPH) return fail(HYB_ERR_ARG, "no batches with the telegraph model");
+  if (m->ani) return fail(HYB_ERR_ARG, "no batches with per-axis steps");
   HYB_TRY(check_sources(m, src, n_src));
   HYB_TRY(check_time(m, nsteps, dt));
   if (m->d.precision == HYB_FP64)
@@ -1657,10 +1704,9 @@ hyb_status hyb_gradient_batch(hyb_mesh* m, const double* a, double gamma, double
   if (!m->have_adj) return fail(HYB_ERR_STATE, "hyb_gradient_batch needs a preceding hyb_adjoint");
   if (!m->batch) return fail(HYB_ERR_STATE, "hyb_gradient_batch needs a preceding hyb_forward_batch");
   if (m->nu == 0) return HYB_OK;
-  const double h = m->d.h;
   for (int s = 0; s < m->nsrc; ++s) {
     launch_grad_finalize((const double*)m->G.p + (size_t)s * m->nu, 1, a + (size_t)s * m->nu, grad_scale(m), gamma,
-                         h * h * h, a0, g_out + (size_t)s * m->nu, m->nu, m->st);
+                         cell_volume(m), a0, g_out + (size_t)s * m->nu, m->nu, m->st);
     HYB_LAUNCHED(m);
   }
   return HYB_OK;
@@ -1678,8 +1724,8 @@ hyb_status hyb_gradient(hyb_mesh* m, const double* a, double gamma, double a0, d
   if (!m->have_adj) return fail(HYB_ERR_STATE, "hyb_gradient needs a preceding hyb_adjoint");
   if (m->batch) return fail(HYB_ERR_STATE, "the last forward was a batch: use hyb_gradient_batch");
   if (m->nu == 0) return HYB_OK;
-  const double h = m->d.h;
-  launch_grad_finalize((const double*)m->G.p, m->nsrc, a, grad_scale(m), gamma, h * h * h, a0, g_out, m->nu, m->st);
+  launch_grad_finalize((const double*)m->G.p, m->nsrc, a, grad_scale(m), gamma, cell_volume(m), a0, g_out, m->nu,
+                       m->st);
   HYB_LAUNCHED(m);
   return HYB_OK;
 }
@@ -1760,7 +1806,7 @@ hyb_status hyb_misfit_noalloc(const void* trace, const void* u_obs, int32_t prec
   }
   const bool quad = weights == HYB_WEIGHTS_QUADRATURE;
   g.wt = quad ? dt : 1.0;
-  g.hh = quad ? h * h : 1.0;
+  for (int s = 0; s < n_src; ++s) g.hh[s] = quad ? h * h : 1.0;
   g.halve = quad ? 1 : 0;
   double* scratch = nullptr;
   HYB_CU(noalloc_scratch(&scratch));

@@ -112,8 +112,15 @@ struct StepArgs {
   const T* W;        // [3][wsz]: weight of the edge (p, p + e_axis) (of slot 0)
   double* G;         // FP64 gradient accumulator over unknown voxels (adjoint)
   int un[3];         // unknown voxel dims; voxel origins fl .. fl + un - 1
-  T c2;              // tau^2 / h^2
+  T c2;              // tau^2 / h^2 (per-axis steps: tau^2 / dx_1^2)
   T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
+  // per-axis steps dx_1, dx_2, dx_3 that differ (ani = 1; every level then
+  // runs the all-node kernels): kap[ax] = dx_1^2 / dx_ax^2 weighs the axis-ax
+  // terms of the lattice rows and the edge weights, ra[ax] = (dx_ax - tau) /
+  // (dx_ax + tau) is the absorbing coefficient of the faces normal to axis ax
+  int ani;
+  double kap[3];
+  T ra[3];
   int npb;           // interior: tiles per plane of the interior box
   int ntx;           // interior: tiles along x
   const int* items;  // interior work items, one per block: (slot, tile, z0, z1)
@@ -208,7 +215,7 @@ struct MisfitGeom {
   int face[kMaxSlots];
   int np[kMaxSlots], nq[kMaxSlots];  // in-face extents (fast, slow)
   double wt;                         // time weight for k >= 1
-  double hh;                         // face weight scale (1 or h^2)
+  double hh[kMaxSlots];              // face weight scale per source (1, or the in-face cell area)
   int halve;                         // halve the face weight on the face border
 };
 template <typename T>

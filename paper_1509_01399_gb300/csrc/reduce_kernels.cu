@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kReduceThreads) misfit_kernel(const MisfitGeom
     const int np = g.np[s], nq = g.nq[s];
     T cv = T(0);
     if (k >= 1 && jj < np * nq) {
-      double m = g.hh;
+      double m = g.hh[s];
       if (g.halve) {
         const int cp = jj % np, cq = jj / np;
         if (cp == 0 || cp == np - 1) m *= 0.5;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) misfit_chunk_kernel(const hyb
     const int np = g.np[s], nq = g.nq[s];
     T cv = T(0);
     if (k >= 1 && jj < np * nq) {
-      double m = g.hh;
+      double m = g.hh[s];
       if (g.halve) {
         const int cp = jj % np, cq = jj / np;
         if (cp == 0 || cp == np - 1) m *= 0.5;

@@ -185,12 +185,13 @@ template <typename T>
 __device__ __forceinline__ T tet_coef(const StepArgs<T>& A, int ni, int nj, int nk, int mi, int mj, int mk) {
   if (lattice_interior(A, ni, nj, nk)) return tet_row<T>(A, nullptr, ni, nj, nk, mi, mj, mk);
   const int d0 = mi - ni, d1 = mj - nj, d2 = mk - nk;
-  if (d0 == 0 && d1 == 0 && d2 == 0) return T(-6);
+  if (d0 == 0 && d1 == 0 && d2 == 0) return A.ani ? (T)(-2.0 * (A.kap[0] + A.kap[1] + A.kap[2])) : T(-6);
   if (abs(d0) + abs(d1) + abs(d2) != 1) return T(0);
   const int ax = d0 ? 0 : (d1 ? 1 : 2), s = d0 + d1 + d2;
   const int c = ax == 0 ? ni : (ax == 1 ? nj : nk);
   const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
-  return ((s > 0 && c == 0) || (s < 0 && c == n - 1)) ? T(2) : T(1);
+  const T w = ((s > 0 && c == 0) || (s < 0 && c == n - 1)) ? T(2) : T(1);
+  return A.ani ? w * (T)A.kap[ax] : w;
 }
 
 // Pairing of the voxel with origin (i, j, k) on the all-FEM path:
@@ -223,17 +224,28 @@ __device__ __noinline__ T row_lap(const StepArgs<T>& A, const T* __restrict__ W,
   const long long sz = (long long)A.px * A.ny;
   const T c = u[id];
   if (fem_owned(A, i, j, k)) return fem_lap(A, W, u, id, i, j, k, c, u[id - sz], u[id + sz]);
-  T lap = T(0);
-  if (i == 0) lap += T(2) * (u[id + 1] - c);
-  else if (i == A.nx - 1) lap += T(2) * (u[id - 1] - c);
-  else lap += (u[id - 1] - c) + (u[id + 1] - c);
-  if (j == 0) lap += T(2) * (u[id + A.px] - c);
-  else if (j == A.ny - 1) lap += T(2) * (u[id - A.px] - c);
-  else lap += (u[id - A.px] - c) + (u[id + A.px] - c);
-  if (k == 0) lap += T(2) * (u[id + sz] - c);
-  else if (k == A.nz - 1) lap += T(2) * (u[id - sz] - c);
-  else lap += (u[id - sz] - c) + (u[id + sz] - c);
-  return lap;
+  T lx, ly, lz;
+  if (i == 0) lx = T(2) * (u[id + 1] - c);
+  else if (i == A.nx - 1) lx = T(2) * (u[id - 1] - c);
+  else lx = (u[id - 1] - c) + (u[id + 1] - c);
+  if (j == 0) ly = T(2) * (u[id + A.px] - c);
+  else if (j == A.ny - 1) ly = T(2) * (u[id - A.px] - c);
+  else ly = (u[id - A.px] - c) + (u[id + A.px] - c);
+  if (k == 0) lz = T(2) * (u[id + sz] - c);
+  else if (k == A.nz - 1) lz = T(2) * (u[id - sz] - c);
+  else lz = (u[id - sz] - c) + (u[id + sz] - c);
+  if (A.ani) return ((T)A.kap[0] * lx + (T)A.kap[1] * ly) + (T)A.kap[2] * lz;
+  return (lx + ly) + lz;
+}
+
+// Coefficient of u_b^k in the absorbing row of a node on the absorbing faces
+// fb (bits): r, or with per-axis steps the mean of its faces' coefficients.
+template <typename T>
+__device__ __forceinline__ T abc_self(const StepArgs<T>& A, int fb) {
+  if (!A.ani) return A.r;
+  T rs = T(0);
+  for (int b = fb; b; b &= b - 1) rs += A.ra[(__ffs(b) - 1) >> 1];
+  return rs / T(__popc(fb));
 }
 
 // u^{k+1} at any node, recursing into the inward neighbours of absorbing
@@ -254,10 +266,11 @@ __device__ __noinline__ T fwd_new(const StepArgs<T>& A, const Slot<T>& S, int i,
           const int i1 = i + (ax == 0 ? step : 0);
           const int j1 = j + (ax == 1 ? step : 0);
           const int k1 = k + (ax == 2 ? step : 0);
-          acc += S.cur[lin(A, i1, j1, k1)] - A.r * fwd_new<T, D - 1>(A, S, i1, j1, k1);
+          const T rf = A.ani ? A.ra[ax] : A.r;
+          acc += S.cur[lin(A, i1, j1, k1)] - rf * fwd_new<T, D - 1>(A, S, i1, j1, k1);
         }
       }
-      return A.r * S.cur[id] + acc / T(__popc(fb));
+      return abc_self(A, fb) * S.cur[id] + acc / T(__popc(fb));
     }
   }
   const T c = S.cur[id];
@@ -279,8 +292,8 @@ __device__ __forceinline__ T row_coef(const StepArgs<T>& A, const T* __restrict_
   }
   const int c = ax == 0 ? i : (ax == 1 ? j : k);
   const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
-  if ((s > 0 && c == 0) || (s < 0 && c == n - 1)) return T(2);
-  return T(1);
+  const T w = ((s > 0 && c == 0) || (s < 0 && c == n - 1)) ? T(2) : T(1);
+  return A.ani ? w * (T)A.kap[ax] : w;
 }
 
 template <typename T>
@@ -292,7 +305,7 @@ __device__ __forceinline__ T row_diag(const StepArgs<T>& A, const T* __restrict_
     return -(W[w] + W[w - 1] + W[A.wsz + w] + W[A.wsz + w - wy] + W[2 * A.wsz + w] +
              W[2 * A.wsz + w - wz]);
   }
-  return T(-6);
+  return A.ani ? (T)(-2.0 * (A.kap[0] + A.kap[1] + A.kap[2])) : T(-6);
 }
 
 __device__ __forceinline__ int face_index(int f, int i, int j, int k, int nx, int ny) {
@@ -310,7 +323,7 @@ __device__ __noinline__ T adj_rhs(const StepArgs<T>& A, const Slot<T>& S, int i,
   const long long id = lin(A, i, j, k);
   const int fbm = face_bits(i, j, k, A.nx, A.ny, A.nz);
   T rhs;
-  if (fbm & S.mask_f) rhs = A.r * l1[id];
+  if (fbm & S.mask_f) rhs = abc_self(A, fbm & S.mask_f) * l1[id];
   else rhs = (T(2) + A.c2 * row_diag(A, S.W, i, j, k)) * l1[id];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
@@ -346,7 +359,7 @@ __device__ __noinline__ T adj_rhs_tet(const StepArgs<T>& A, const Slot<T>& S, in
   const long long id = lin(A, i, j, k);
   const int fbm = face_bits(i, j, k, A.nx, A.ny, A.nz);
   T rhs;
-  if (fbm & S.mask_f) rhs = A.r * l1[id];
+  if (fbm & S.mask_f) rhs = abc_self(A, fbm & S.mask_f) * l1[id];
   else rhs = (T(2) + A.c2 * tet_coef(A, i, j, k, i, j, k)) * l1[id];
   for (int d = 0; d < 27; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
@@ -458,7 +471,7 @@ __device__ __noinline__ T adj_new(const StepArgs<T>& A, const Slot<T>& S, int i,
         if (bi < 0 || bi >= A.nx || bj < 0 || bj >= A.ny || bk < 0 || bk >= A.nz) continue;
         const int f = 2 * ax + (s > 0 ? 1 : 0);
         const int fbb = face_bits(bi, bj, bk, A.nx, A.ny, A.nz) & S.mask_e;
-        if (fbb & (1 << f)) v -= (A.r / T(__popc(fbb))) * adj_new<T, D - 1>(A, S, bi, bj, bk);
+        if (fbb & (1 << f)) v -= ((A.ani ? A.ra[ax] : A.r) / T(__popc(fbb))) * adj_new<T, D - 1>(A, S, bi, bj, bk);
       }
     }
   }
@@ -492,6 +505,19 @@ __device__ __forceinline__ T damp_sum(const T u[8], const T l[8]) {
   return T(3) * d + o;
 }
 
+// pair_sum with per-axis steps: the sums over the x, y and z edges weighed by
+// kap (the voxel is a brick; dx_1^2 / dx_ax^2 relative to the x edges).
+template <typename T>
+__device__ __forceinline__ T pair_sum_ani(const StepArgs<T>& A, const T u[8], const T l[8]) {
+  const T x = T(2) * ((u[1] - u[0]) * (l[1] - l[0]) + (u[7] - u[6]) * (l[7] - l[6])) +
+              ((u[3] - u[2]) * (l[3] - l[2]) + (u[5] - u[4]) * (l[5] - l[4]));
+  const T y = T(2) * ((u[2] - u[0]) * (l[2] - l[0]) + (u[7] - u[5]) * (l[7] - l[5])) +
+              ((u[3] - u[1]) * (l[3] - l[1]) + (u[6] - u[4]) * (l[6] - l[4]));
+  const T z = T(2) * ((u[4] - u[0]) * (l[4] - l[0]) + (u[7] - u[3]) * (l[7] - l[3])) +
+              ((u[5] - u[1]) * (l[5] - l[1]) + (u[6] - u[2]) * (l[6] - l[2]));
+  return ((T)A.kap[0] * x + (T)A.kap[1] * y) + (T)A.kap[2] * z;
+}
+
 // pair_sum of voxel (i,j,k): u from the FEM-owned box hb, lambda from the lattice
 template <typename T>
 __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restrict__ hb,
@@ -510,6 +536,19 @@ __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restric
     l[c] = lam[l0 + a + b * ly + d * lz];
   }
   return A.sdamp ? damp_sum(u, l) : pair_sum(u, l);
+}
+
+// voxel_pair with per-axis steps (the all-node kernels)
+template <typename T>
+__device__ __noinline__ T voxel_pair_ani(const StepArgs<T>& A, const T* __restrict__ hb, const T* __restrict__ lam,
+                                         int i, int j, int k) {
+  T u[8], l[8];
+  for (int c = 0; c < 8; ++c) {
+    const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+    u[c] = hb[hidx(A, i + a, j + b, k + d)];
+    l[c] = lam[lin(A, i + a, j + b, k + d)];
+  }
+  return pair_sum_ani(A, u, l);
 }
 
 // Laplacian part (without 1/h^2) of a 7-point row with unit weights.
@@ -548,6 +587,7 @@ __device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T
                         (long long)A.un[0] * ((j - A.fl[1]) + (long long)A.un[1] * (k - A.fl[2]));
   if (A.refvox && A.refvox[vid]) return;
   if (TET && A.tet) A.G[(long long)si * nv + vid] += (double)tet_pair(A, S.hist_r, S.cur, i, j, k);
+  else if (TET && A.ani) A.G[(long long)si * nv + vid] += (double)voxel_pair_ani(A, S.hist_r, S.cur, i, j, k);
   else A.G[(long long)si * nv + vid] += (double)voxel_pair(A, S.hist_r, S.cur, i, j, k);
 }
 
@@ -1443,7 +1483,8 @@ __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __re
   const int z = (int)(r / A.un[1]);
   if (A.refvox && A.refvox[t]) return;
   const int i = A.fl[0] + x, j = A.fl[1] + y, k = A.fl[2] + z;
-  grad[t] += (double)(A.tet ? tet_pair(A, hist, lam, i, j, k) : voxel_pair(A, hist, lam, i, j, k));
+  grad[t] += (double)(A.tet ? tet_pair(A, hist, lam, i, j, k)
+                             : (A.ani ? voxel_pair_ani(A, hist, lam, i, j, k) : voxel_pair(A, hist, lam, i, j, k)));
 }
 
 // Refined region of one time level, in the trailing blocks of the step
@@ -1688,7 +1729,7 @@ __global__ void set_coef_kernel(const __grid_constant__ StepArgs<T> A, T* __rest
         }
       }
     }
-    W[ax * A.wsz + t] = (T)w;
+    W[ax * A.wsz + t] = (T)(A.ani ? w * A.kap[ax] : w);
   }
 }
 

@@ -40,7 +40,7 @@ class hyb_mesh_desc(ctypes.Structure):
                 ("fem_lo", c_int32 * 3), ("fem_hi", c_int32 * 3), ("bc", c_int32 * 6),
                 ("precision", c_int32), ("ckpt_every", c_int32), ("a_max", c_double),
                 ("refine_mask", c_void_p), ("wait_cycles", c_int64), ("adjoint_mode", c_int32),
-                ("fem_path", c_int32), ("model", c_int32)]
+                ("fem_path", c_int32), ("model", c_int32), ("spacing", c_double * 3)]
 
 
 class hyb_mesh_info(ctypes.Structure):
@@ -230,7 +230,7 @@ class HybMesh:
 
     def __init__(self, n, h, fem_lo=None, fem_hi=None, bc=(1,) * 6, precision="fp64", ckpt_every=0,
                  a_max=4.0, origin=(0.0, 0.0, 0.0), device="cuda", stream=None, refine=None, wait_cycles=0,
-                 adjoint_mode=HYB_ADJ_EXACT, fem_path=HYB_FEM_STENCIL, model=HYB_MODEL_WAVE):
+                 adjoint_mode=HYB_ADJ_EXACT, fem_path=HYB_FEM_STENCIL, model=HYB_MODEL_WAVE, spacing=None):
         import torch
 
         self.torch = torch
@@ -242,6 +242,9 @@ class HybMesh:
             d.fem_lo[i] = -1 if fem_lo is None else int(fem_lo[i])
             d.fem_hi[i] = -1 if fem_hi is None else int(fem_hi[i])
         d.h = float(h)
+        if spacing is not None:
+            for i in range(3):
+                d.spacing[i] = float(spacing[i])
         for f in range(6):
             d.bc[f] = int(bc[f])
         d.precision = HYB_FP64 if precision == "fp64" else HYB_FP32
@@ -273,6 +276,7 @@ class HybMesh:
     @classmethod
     def from_workload(cls, w, precision=None, ckpt_every=None, **kw):
         kw.setdefault("refine", getattr(w, "refine", None))
+        kw.setdefault("spacing", getattr(w, "spacing", None))
         return cls(w.n, w.h, w.fem_lo, w.fem_hi, w.bc, precision or w.precision,
                    w.ckpt_every if ckpt_every is None else ckpt_every, w.a_max, w.origin, **kw)
 
