@@ -414,7 +414,8 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
 // One time level: a single launch on `st`.
 template <class Launch>
 hyb_status step_launch(hyb_mesh* m, cudaStream_t st, Launch launch) {
-  launch(st);
+  const int n = launch(st);  // kernels the level took (two with per-axis steps)
+  m->launches += n - 1;
   HYB_LAUNCHED(m);
   return HYB_OK;
 }
@@ -1023,7 +1024,7 @@ hyb_status forward_impl(hyb_mesh* m, const double* a, const hyb_source* src, int
       T* hl = hk ? hist + (size_t)slot * lvl : nullptr;
       T* chl = hk ? chist + (size_t)slot * clvl : nullptr;
       forward_slots<T>(m, A, src, nsrc, nsteps, dt, k, trace, hl, chl);
-      HYB_TRY(step_launch(m, st, [&](cudaStream_t q) { launch_forward_step<T>(A, q); }));
+      HYB_TRY(step_launch(m, st, [&](cudaStream_t q) { return launch_forward_step<T>(A, q); }));
     }
     return HYB_OK;
   };
@@ -1180,10 +1181,10 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
       if (paper) {  // pair (u^j, lambda^j), then lambda^{j-1}
         paper_slots<T>(m, Pp, cot, j, hl, chl);
         if (hl) HYB_TRY(paper_pair<T>(m, Pp, st));
-        return step_launch(m, st, [&](cudaStream_t q) { launch_forward_step<T>(Pp, q); });
+        return step_launch(m, st, [&](cudaStream_t q) { return launch_forward_step<T>(Pp, q); });
       }
       adjoint_slots<T>(m, A, cot, j, hl, chl);
-      return step_launch(m, st, [&](cudaStream_t q) { launch_adjoint_step<T>(A, q); });
+      return step_launch(m, st, [&](cudaStream_t q) { return launch_adjoint_step<T>(A, q); });
     };
     auto first_pair = [&]() -> hyb_status {
       if (!paper) return pair_first<T>(m, A, hist, chist, st);
@@ -1192,7 +1193,7 @@ hyb_status adjoint_impl(hyb_mesh* m, const T* cot, int accumulate) {
     };
     auto fwd_step = [&](int k, T* hl, T* chl) -> hyb_status {
       forward_slots<T>(m, F, m->src, nsrc, nsteps, dt, k, nullptr, hl, chl);
-      return step_launch(m, st, [&](cudaStream_t q) { launch_forward_step<T>(F, q); });
+      return step_launch(m, st, [&](cudaStream_t q) { return launch_forward_step<T>(F, q); });
     };
     if (!ckpt) {
       for (int j = nsteps; j >= 1; --j) {

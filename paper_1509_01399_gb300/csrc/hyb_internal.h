@@ -173,9 +173,9 @@ struct StepArgs {
 // refined rows and interior blocks), or on lattices with fewer than 5 nodes
 // on an axis one generic kernel over every node.
 template <typename T>
-void launch_forward_step(const StepArgs<T>& a, cudaStream_t st);
+int launch_forward_step(const StepArgs<T>& a, cudaStream_t st);
 template <typename T>
-void launch_adjoint_step(const StepArgs<T>& a, cudaStream_t st);
+int launch_adjoint_step(const StepArgs<T>& a, cudaStream_t st);
 // Resident blocks per SM of the step kernel (for grid sizing), at least 1.
 int step_blocks_per_sm(int precision, int adjoint);
 // G[c] += voxel pairing of (u^0 in hist box, lambda^1) for one slot.

@@ -1471,6 +1471,134 @@ __global__ void __launch_bounds__(128) adj_all_kernel(const __grid_constant__ St
   pair_if_voxel<T, true>(A, S, si, i, j, k);
 }
 
+// Per-axis steps: each level by two launches that partition the lattice.
+// The bulk launch covers the nodes at least w nodes from every face (w = 1
+// forward, 2 transposed) on a grid of 128-node row segments (blockIdx.y =
+// j - w, blockIdx.z = slot (nz - 2w) + k - w) and takes their plain rows,
+// which need no face logic; the shell launch enumerates the other nodes
+// (the w layers next to each face) and takes them through the generic rows.
+template <typename T, int W>
+__device__ __forceinline__ bool ani_bulk_node(const StepArgs<T>& A, int& i, int& j, int& k, int& si) {
+  i = W + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  j = W + (int)blockIdx.y;
+  const int nzi = A.nz - 2 * W;
+  si = (int)blockIdx.z / nzi;
+  k = W + (int)blockIdx.z - si * nzi;
+  return i <= A.nx - 1 - W;
+}
+
+// Nodes of the shell of width W of one slot: the W planes at each z face,
+// then the W rows at each y face of the remaining planes, then the W nodes
+// at each x face of the remaining rows.
+template <typename T, int W>
+__device__ __forceinline__ long long ani_shell_count(const StepArgs<T>& A) {
+  return 2LL * W * ((long long)A.nx * A.ny + (long long)A.nx * (A.nz - 2 * W) +
+                    (long long)(A.ny - 2 * W) * (A.nz - 2 * W));
+}
+
+template <typename T, int W>
+__device__ __forceinline__ bool ani_shell_node(const StepArgs<T>& A, int& i, int& j, int& k, int& si) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long cnt = ani_shell_count<T, W>(A);
+  if (t >= cnt * A.nslots) return false;
+  si = (int)(t / cnt);
+  long long r = t - (long long)si * cnt;
+  const long long pa = 2LL * W * A.nx * A.ny;
+  const long long pb = 2LL * W * A.nx * (A.nz - 2 * W);
+  auto layer = [](int q, int n) { return q < W ? q : n - 2 * W + q; };  // q in [0, 2W)
+  if (r < pa) {
+    i = (int)(r % A.nx);
+    r /= A.nx;
+    j = (int)(r % A.ny);
+    k = layer((int)(r / A.ny), A.nz);
+  } else if ((r -= pa) < pb) {
+    i = (int)(r % A.nx);
+    r /= A.nx;
+    j = layer((int)(r % (2 * W)), A.ny);
+    k = W + (int)(r / (2 * W));
+  } else {
+    r -= pb;
+    i = layer((int)(r % (2 * W)), A.nx);
+    r /= 2 * W;
+    j = W + (int)(r % (A.ny - 2 * W));
+    k = W + (int)(r / (A.ny - 2 * W));
+  }
+  return true;
+}
+
+// Forward: bulk = every node off the faces (lattice rows with kap, FEM rows
+// with the edge weights, which carry kap), shell = the face nodes.
+template <typename T>
+__global__ void __launch_bounds__(128) ani_fwd_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
+  int i, j, k, si;
+  if (!ani_bulk_node<T, 1>(A, i, j, k, si)) return;
+  const Slot<T>& S = A.s[si];
+  const long long id = lin(A, i, j, k);
+  const long long sz = (long long)A.px * A.ny;
+  const T* __restrict__ u = S.cur;
+  const T c = u[id];
+  const bool fo = fem_owned(A, i, j, k);
+  T lap;
+  if (fo) {
+    lap = fem_lap(A, S.W, u, id, i, j, k, c, u[id - sz], u[id + sz]);
+  } else {
+    const T lx = (u[id - 1] - c) + (u[id + 1] - c);
+    const T ly = (u[id - A.px] - c) + (u[id + A.px] - c);
+    const T lz = (u[id - sz] - c) + (u[id + sz] - c);
+    lap = ((T)A.kap[0] * lx + (T)A.kap[1] * ly) + (T)A.kap[2] * lz;
+  }
+  const T val = c + ((c - S.prev[id]) + A.c2 * lap);
+  S.next[id] = val;
+  if (fo && S.hist_w) S.hist_w[hidx(A, i, j, k)] = val;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) ani_fwd_shell_kernel(const __grid_constant__ StepArgs<T> A) {
+  int i, j, k, si;
+  if (!ani_shell_node<T, 1>(A, i, j, k, si)) return;
+  const Slot<T>& S = A.s[si];
+  const long long id = lin(A, i, j, k);
+  const T val = fwd_new<T, 3>(A, S, i, j, k);
+  S.next[id] = val;
+  if (S.obs_w && ((face_bits(i, j, k, A.nx, A.ny, A.nz) >> S.obs_face) & 1))
+    S.obs_w[face_index(S.obs_face, i, j, k, A.nx, A.ny)] = val;
+}
+
+// Transposed step: bulk = every node two or more nodes from the faces (no
+// absorbing row among its neighbours, no observation), its transposed row
+// gathered from the neighbours' rows (edge weight of a FEM-owned neighbour,
+// kap of a lattice one) in the order of adj_rhs, plus the voxel pairing;
+// shell = the nodes within one node of a face.
+template <typename T>
+__global__ void __launch_bounds__(128) ani_adj_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
+  int i, j, k, si;
+  if (!ani_bulk_node<T, 2>(A, i, j, k, si)) return;
+  const Slot<T>& S = A.s[si];
+  const long long id = lin(A, i, j, k);
+  const T* __restrict__ l1 = S.cur;
+  T rhs = (T(2) + A.c2 * row_diag(A, S.W, i, j, k)) * l1[id];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int s = t ? 1 : -1;
+      const int ni = i + (ax == 0 ? s : 0), nj = j + (ax == 1 ? s : 0), nk = k + (ax == 2 ? s : 0);
+      rhs += A.c2 * row_coef(A, S.W, ni, nj, nk, ax, -s) * l1[lin(A, ni, nj, nk)];
+    }
+  }
+  S.next[id] = rhs - S.prev[id];
+  pair_if_voxel<T, true>(A, S, si, i, j, k);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) ani_adj_shell_kernel(const __grid_constant__ StepArgs<T> A) {
+  int i, j, k, si;
+  if (!ani_shell_node<T, 2>(A, i, j, k, si)) return;
+  const Slot<T>& S = A.s[si];
+  S.next[lin(A, i, j, k)] = adj_new<T, 3>(A, S, i, j, k);
+  pair_if_voxel<T, true>(A, S, si, i, j, k);
+}
+
 template <typename T>
 __global__ void pair_kernel(const __grid_constant__ StepArgs<T> A, const T* __restrict__ hist,
                             const T* __restrict__ lam, double* __restrict__ grad) {
@@ -1769,14 +1897,32 @@ void launch_extract_face(const StepArgs<T>& a, const T* field, int f, T* row, cu
 }
 
 template <typename T, bool ADJ>
-void launch_step(const StepArgs<T>& a, cudaStream_t st) {
+int launch_step(const StepArgs<T>& a, cudaStream_t st) {
   if (a.small) {
+    const int w = ADJ ? 2 : 1;  // shell width
+    if (a.ani && !a.tet && a.nx >= 5 && a.ny >= 5 && a.nz >= 5 && a.ny <= 65535 &&
+        (long long)(a.nz - 2 * w) * a.nslots <= 65535) {
+      const dim3 grid((unsigned)((a.nx - 2 * w + 127) / 128), (unsigned)(a.ny - 2 * w),
+                      (unsigned)((a.nz - 2 * w) * a.nslots));
+      const long long shell = 2LL * w *
+                              ((long long)a.nx * a.ny + (long long)a.nx * (a.nz - 2 * w) +
+                               (long long)(a.ny - 2 * w) * (a.nz - 2 * w)) * a.nslots;
+      const unsigned sgrid = (unsigned)((shell + 127) / 128);
+      if (ADJ) {
+        ani_adj_bulk_kernel<T><<<grid, 128, 0, st>>>(a);
+        ani_adj_shell_kernel<T><<<sgrid, 128, 0, st>>>(a);
+      } else {
+        ani_fwd_bulk_kernel<T><<<grid, 128, 0, st>>>(a);
+        ani_fwd_shell_kernel<T><<<sgrid, 128, 0, st>>>(a);
+      }
+      return 2;
+    }
     const long long n = (long long)a.nx * a.ny * a.nz * a.nslots;
     if (ADJ)
       adj_all_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
     else
       fwd_all_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
-    return;
+    return 1;
   }
   StepArgs<T> b = a;
   b.nhe = ((a.nedge + 1) / 2) * a.nslots;
@@ -1799,16 +1945,17 @@ void launch_step(const StepArgs<T>& a, cudaStream_t st) {
     cudaLaunchKernelEx(&cfg, step_kernel<T, ADJ, true>, b);
   else
     cudaLaunchKernelEx(&cfg, step_kernel<T, ADJ, false>, b);
+  return 1;
 }
 
 template <typename T>
-void launch_forward_step(const StepArgs<T>& a, cudaStream_t st) {
-  launch_step<T, false>(a, st);
+int launch_forward_step(const StepArgs<T>& a, cudaStream_t st) {
+  return launch_step<T, false>(a, st);
 }
 
 template <typename T>
-void launch_adjoint_step(const StepArgs<T>& a, cudaStream_t st) {
-  launch_step<T, true>(a, st);
+int launch_adjoint_step(const StepArgs<T>& a, cudaStream_t st) {
+  return launch_step<T, true>(a, st);
 }
 
 template <typename T, bool ADJ>
@@ -1871,8 +2018,8 @@ void launch_extract_owned(const StepArgs<T>& a, const T* field, T* box, cudaStre
 }
 
 #define HYB_INSTANTIATE(T)                                                                       \
-  template void launch_forward_step<T>(const StepArgs<T>&, cudaStream_t);                        \
-  template void launch_adjoint_step<T>(const StepArgs<T>&, cudaStream_t);                        \
+  template int launch_forward_step<T>(const StepArgs<T>&, cudaStream_t);                         \
+  template int launch_adjoint_step<T>(const StepArgs<T>&, cudaStream_t);                         \
   template void launch_pair<T>(const StepArgs<T>&, const T*, const T*, cudaStream_t);            \
   template void launch_set_coef<T>(const StepArgs<T>&, T*, T*, const double*, double, int*,     \
                                    cudaStream_t);                                                \

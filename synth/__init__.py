@@ -170,9 +170,11 @@ def random_box_inclusions(fem_lo, fem_hi, count, side_range, sigma_range, rng, m
 
 
 def gaussian_bumps(fem_lo, fem_hi, h, origin, count, amp_range, width_range, rng):
-    """Smooth sigma made of Gaussian bumps centred in the unknown block."""
+    """Smooth sigma made of Gaussian bumps centred in the unknown block (h:
+    the lattice step, or one per axis)."""
     ud = unknown_dims(fem_lo, fem_hi)
-    cs = [voxel_centres(ud[d], fem_lo[d] + 1, h, origin[d]) for d in range(3)]
+    hs = tuple(h) if isinstance(h, (tuple, list)) else (h, h, h)
+    cs = [voxel_centres(ud[d], fem_lo[d] + 1, hs[d], origin[d]) for d in range(3)]
     Z, Y, X = np.meshgrid(cs[2], cs[1], cs[0], indexing="ij")
     sigma = np.zeros_like(X)
     for _ in range(count):
@@ -332,6 +334,28 @@ def large_batched(N: int = 257, nsteps: int = 3000, n_src: int = 8, refine: bool
     return Workload("large_%d" % N, n, h, origin, lo, hi, ALL_ABC, srcs[:n_src], nsteps, dt, 2.5, sigma, "fp32",
                     ckpt_every=50, refine=ref,
                     extra=dict(cg_iters=10, gamma=0.01, a0=1.0, noise=0.03, noise_seed=1))
+
+
+def anisotropic_box(nsteps: int = 600, n_src: int = 8) -> Workload:
+    """257 x 193 x 321 lattice on [-1,1]^3 (steps 2/256, 2/192, 2/320: the
+    7-point Laplacian with unequal steps), FEM block = the central half of
+    every axis, the large workload's smooth sigma recipe (Gaussian bumps,
+    seed 5) on the brick voxels, no refinement, a_max = 2.5, 0.9 of the
+    stability bound 1 / sqrt(a_max sum 1 / dx^2), its eight plane-wave
+    sources, checkpoints every 50 steps, FP32 fields with FP64 gradient
+    accumulation."""
+    n = (257, 193, 321)
+    spacing = tuple(2.0 / (v - 1) for v in n)
+    origin = (-1.0, -1.0, -1.0)
+    lo = tuple((v - 1) // 4 for v in n)
+    hi = tuple(3 * (v - 1) // 4 for v in n)
+    rng = np.random.Generator(np.random.PCG64(5))
+    sigma = gaussian_bumps(lo, hi, spacing, origin, int(rng.integers(4, 9)), (0.0, 1.5), (0.05, 0.15), rng)
+    srcs = [Source(f, 40.0) for f in (FACE_XM, FACE_XP, FACE_YM, FACE_YP, FACE_ZM, FACE_ZP)]
+    srcs += [Source(FACE_ZM, 40.0, 1.0, (1.0, 1.0, 1.0)), Source(FACE_ZP, 40.0, 1.0, (-1.0, -1.0, -1.0))]
+    return Workload("anisotropic_box", n, spacing[0], origin, lo, hi, ALL_ABC, srcs[:n_src], nsteps,
+                    anisotropic_dt(spacing, 2.5), 2.5, sigma, "fp32", ckpt_every=50, spacing=spacing,
+                    extra=dict(gamma=0.01, a0=1.0, noise=0.03, noise_seed=1))
 
 
 def small_problem(n=9, fem=(2, 6), nsteps=60, bc=ALL_ABC, src_face=FACE_ZP, omega=12.0,

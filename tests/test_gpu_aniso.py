@@ -39,6 +39,9 @@ CASES = {
                                                      src_face=synth.FACE_XP, spacing=(0.06, 0.09, 0.075)),
     "wide": lambda: synth.small_problem(n=(37, 21, 19), fem=((5, 4, 4), (30, 16, 15)), nsteps=70, omega=15.0,
                                         courant=0.9, spacing=(0.03, 0.05, 0.045)),
+    # most nodes away from the faces and the FEM block (the kernels' plain rows)
+    "fast_rows_41": lambda: synth.small_problem(n=(41, 33, 49), fem=((8, 8, 10), (32, 24, 38)), nsteps=120,
+                                                omega=20.0, courant=0.85, spacing=(0.025, 0.03, 0.02)),
 }
 
 
@@ -196,3 +199,27 @@ def test_step_bound_volume_and_refusals(H):
         H.hyb_forward_batch(m.handle, a.data_ptr(), w.sources, 5, w.dt, tr.data_ptr())
     assert e.value.status == H.HYB_ERR_ARG
     m.close()
+
+
+def test_full_size_plane_wave_is_one_dimensional(H):
+    """The anisotropic box at its full size (257 x 193 x 321 nodes, the
+    bench's lattice, FEM block and launch configuration, FP64) with
+    reflecting x and y faces, a = 1 and a source on the high z face: every
+    node of the z face records the 1-D leapfrog along z with step 2/320
+    (written out in the oracle pins).  500 steps: the pulse crosses the FEM
+    block (z nodes 80..240) and anything a wrong row there reflected would
+    be back on the face."""
+    from test_oracle_aniso import _leapfrog_1d
+    w = synth.anisotropic_box(nsteps=500, n_src=1)
+    w.bc = (0, 0, 0, 0, 1, 1)
+    src = synth.Source(synth.FACE_ZP, 40.0)
+    m = H.HybMesh.from_workload(w, precision="fp64", ckpt_every=0)
+    tr = m.forward(np.ones(w.n_unknown), [src], w.nsteps, w.dt)
+    m.sync()
+    nf = w.n[0] * w.n[1]
+    t = tr[0, :, :nf].cpu().numpy()
+    m.close()
+    ref = _leapfrog_1d(w.n[2], w.hv[2], w.dt, w.nsteps, 40.0, 1.0, True)
+    assert np.abs(ref).max() > 1e-3
+    err = np.abs(t - ref[:, None]).max() / np.abs(ref).max()
+    assert err <= 1e-12, err
