@@ -815,8 +815,10 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
     A.nedge = 0;
     for (int a = 0; a < 3; ++a) {
       A.kap[a] = (h * h) / (m->hv[a] * m->hv[a]);
+      A.kapt[a] = (T)A.kap[a];
       A.ra[a] = (T)((m->hv[a] - dt) / (m->hv[a] + dt));
     }
+    A.kdiag = (T)(-2.0 * (A.kap[0] + A.kap[1] + A.kap[2]));
   }
   if (m->d.fem_path == HYB_FEM_TET_ALL) {  // every level by the all-node kernels
     A.tet = 1;

@@ -120,6 +120,8 @@ struct StepArgs {
   // (dx_ax + tau) is the absorbing coefficient of the faces normal to axis ax
   int ani;
   double kap[3];
+  T kapt[3];         // kap in the field's precision
+  T kdiag;           // -2 (kap[0] + kap[1] + kap[2]) in the field's precision: a lattice row's diagonal
   T ra[3];
   int npb;           // interior: tiles per plane of the interior box
   int ntx;           // interior: tiles along x

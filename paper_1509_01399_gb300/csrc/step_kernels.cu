@@ -185,13 +185,13 @@ template <typename T>
 __device__ __forceinline__ T tet_coef(const StepArgs<T>& A, int ni, int nj, int nk, int mi, int mj, int mk) {
   if (lattice_interior(A, ni, nj, nk)) return tet_row<T>(A, nullptr, ni, nj, nk, mi, mj, mk);
   const int d0 = mi - ni, d1 = mj - nj, d2 = mk - nk;
-  if (d0 == 0 && d1 == 0 && d2 == 0) return A.ani ? (T)(-2.0 * (A.kap[0] + A.kap[1] + A.kap[2])) : T(-6);
+  if (d0 == 0 && d1 == 0 && d2 == 0) return A.ani ? A.kdiag : T(-6);
   if (abs(d0) + abs(d1) + abs(d2) != 1) return T(0);
   const int ax = d0 ? 0 : (d1 ? 1 : 2), s = d0 + d1 + d2;
   const int c = ax == 0 ? ni : (ax == 1 ? nj : nk);
   const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
   const T w = ((s > 0 && c == 0) || (s < 0 && c == n - 1)) ? T(2) : T(1);
-  return A.ani ? w * (T)A.kap[ax] : w;
+  return A.ani ? w * A.kapt[ax] : w;
 }
 
 // Pairing of the voxel with origin (i, j, k) on the all-FEM path:
@@ -234,7 +234,7 @@ __device__ __noinline__ T row_lap(const StepArgs<T>& A, const T* __restrict__ W,
   if (k == 0) lz = T(2) * (u[id + sz] - c);
   else if (k == A.nz - 1) lz = T(2) * (u[id - sz] - c);
   else lz = (u[id - sz] - c) + (u[id + sz] - c);
-  if (A.ani) return ((T)A.kap[0] * lx + (T)A.kap[1] * ly) + (T)A.kap[2] * lz;
+  if (A.ani) return (A.kapt[0] * lx + A.kapt[1] * ly) + A.kapt[2] * lz;
   return (lx + ly) + lz;
 }
 
@@ -293,7 +293,7 @@ __device__ __forceinline__ T row_coef(const StepArgs<T>& A, const T* __restrict_
   const int c = ax == 0 ? i : (ax == 1 ? j : k);
   const int n = ax == 0 ? A.nx : (ax == 1 ? A.ny : A.nz);
   const T w = ((s > 0 && c == 0) || (s < 0 && c == n - 1)) ? T(2) : T(1);
-  return A.ani ? w * (T)A.kap[ax] : w;
+  return A.ani ? w * A.kapt[ax] : w;
 }
 
 template <typename T>
@@ -305,7 +305,7 @@ __device__ __forceinline__ T row_diag(const StepArgs<T>& A, const T* __restrict_
     return -(W[w] + W[w - 1] + W[A.wsz + w] + W[A.wsz + w - wy] + W[2 * A.wsz + w] +
              W[2 * A.wsz + w - wz]);
   }
-  return A.ani ? (T)(-2.0 * (A.kap[0] + A.kap[1] + A.kap[2])) : T(-6);
+  return A.ani ? A.kdiag : T(-6);
 }
 
 __device__ __forceinline__ int face_index(int f, int i, int j, int k, int nx, int ny) {
@@ -515,7 +515,7 @@ __device__ __forceinline__ T pair_sum_ani(const StepArgs<T>& A, const T u[8], co
               ((u[3] - u[1]) * (l[3] - l[1]) + (u[6] - u[4]) * (l[6] - l[4]));
   const T z = T(2) * ((u[4] - u[0]) * (l[4] - l[0]) + (u[7] - u[3]) * (l[7] - l[3])) +
               ((u[5] - u[1]) * (l[5] - l[1]) + (u[6] - u[2]) * (l[6] - l[2]));
-  return ((T)A.kap[0] * x + (T)A.kap[1] * y) + (T)A.kap[2] * z;
+  return (A.kapt[0] * x + A.kapt[1] * y) + A.kapt[2] * z;
 }
 
 // pair_sum of voxel (i,j,k): u from the FEM-owned box hb, lambda from the lattice
@@ -540,9 +540,10 @@ __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restric
 
 // voxel_pair with per-axis steps (the all-node kernels)
 template <typename T>
-__device__ __noinline__ T voxel_pair_ani(const StepArgs<T>& A, const T* __restrict__ hb, const T* __restrict__ lam,
-                                         int i, int j, int k) {
+__device__ __forceinline__ T voxel_pair_ani(const StepArgs<T>& A, const T* __restrict__ hb,
+                                            const T* __restrict__ lam, int i, int j, int k) {
   T u[8], l[8];
+#pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
     u[c] = hb[hidx(A, i + a, j + b, k + d)];
@@ -1473,17 +1474,22 @@ __global__ void __launch_bounds__(128) adj_all_kernel(const __grid_constant__ St
 
 // Per-axis steps: each level by two launches that partition the lattice.
 // The bulk launch covers the nodes at least w nodes from every face (w = 1
-// forward, 2 transposed) on a grid of 128-node row segments (blockIdx.y =
-// j - w, blockIdx.z = slot (nz - 2w) + k - w) and takes their plain rows,
-// which need no face logic; the shell launch enumerates the other nodes
-// (the w layers next to each face) and takes them through the generic rows.
+// forward, 2 transposed): each thread marches kAniZ consecutive planes of one
+// node column (blockIdx.x: 128-node segment of the row, blockIdx.y = j - w,
+// blockIdx.z = slot * chunks + chunk), keeping u of the planes below and
+// above in registers, and takes their plain rows, which need no face logic;
+// the shell launch enumerates the other nodes (the w layers next to each
+// face) and takes them through the generic rows.
+constexpr int kAniZ = 8;
+
 template <typename T, int W>
-__device__ __forceinline__ bool ani_bulk_node(const StepArgs<T>& A, int& i, int& j, int& k, int& si) {
+__device__ __forceinline__ bool ani_bulk_column(const StepArgs<T>& A, int& i, int& j, int& k0, int& k1, int& si) {
   i = W + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   j = W + (int)blockIdx.y;
-  const int nzi = A.nz - 2 * W;
-  si = (int)blockIdx.z / nzi;
-  k = W + (int)blockIdx.z - si * nzi;
+  const int chunks = (A.nz - 2 * W + kAniZ - 1) / kAniZ;
+  si = (int)blockIdx.z / chunks;
+  k0 = W + ((int)blockIdx.z - si * chunks) * kAniZ;
+  k1 = min(k0 + kAniZ, A.nz - W);  // exclusive
   return i <= A.nx - 1 - W;
 }
 
@@ -1530,26 +1536,32 @@ __device__ __forceinline__ bool ani_shell_node(const StepArgs<T>& A, int& i, int
 // with the edge weights, which carry kap), shell = the face nodes.
 template <typename T>
 __global__ void __launch_bounds__(128) ani_fwd_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
-  int i, j, k, si;
-  if (!ani_bulk_node<T, 1>(A, i, j, k, si)) return;
+  int i, j, k0, k1, si;
+  if (!ani_bulk_column<T, 1>(A, i, j, k0, k1, si)) return;
   const Slot<T>& S = A.s[si];
-  const long long id = lin(A, i, j, k);
   const long long sz = (long long)A.px * A.ny;
   const T* __restrict__ u = S.cur;
-  const T c = u[id];
-  const bool fo = fem_owned(A, i, j, k);
-  T lap;
-  if (fo) {
-    lap = fem_lap(A, S.W, u, id, i, j, k, c, u[id - sz], u[id + sz]);
-  } else {
-    const T lx = (u[id - 1] - c) + (u[id + 1] - c);
-    const T ly = (u[id - A.px] - c) + (u[id + A.px] - c);
-    const T lz = (u[id - sz] - c) + (u[id + sz] - c);
-    lap = ((T)A.kap[0] * lx + (T)A.kap[1] * ly) + (T)A.kap[2] * lz;
+  long long id = lin(A, i, j, k0);
+  T zm = u[id - sz], c = u[id];
+  const bool col_fem = i >= A.fl[0] && i <= A.fh[0] && j >= A.fl[1] && j <= A.fh[1];
+  for (int k = k0; k < k1; ++k, id += sz) {
+    const T zp = u[id + sz];
+    const bool fo = col_fem && k >= A.fl[2] && k <= A.fh[2];
+    T lap;
+    if (fo) {
+      lap = fem_lap(A, S.W, u, id, i, j, k, c, zm, zp);
+    } else {
+      const T lx = (u[id - 1] - c) + (u[id + 1] - c);
+      const T ly = (u[id - A.px] - c) + (u[id + A.px] - c);
+      const T lz = (zm - c) + (zp - c);
+      lap = (A.kapt[0] * lx + A.kapt[1] * ly) + A.kapt[2] * lz;
+    }
+    const T val = c + ((c - S.prev[id]) + A.c2 * lap);
+    S.next[id] = val;
+    if (fo && S.hist_w) S.hist_w[hidx(A, i, j, k)] = val;
+    zm = c;
+    c = zp;
   }
-  const T val = c + ((c - S.prev[id]) + A.c2 * lap);
-  S.next[id] = val;
-  if (fo && S.hist_w) S.hist_w[hidx(A, i, j, k)] = val;
 }
 
 template <typename T>
@@ -1570,24 +1582,42 @@ __global__ void __launch_bounds__(128) ani_fwd_shell_kernel(const __grid_constan
 // kap of a lattice one) in the order of adj_rhs, plus the voxel pairing;
 // shell = the nodes within one node of a face.
 template <typename T>
-__global__ void __launch_bounds__(128) ani_adj_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
-  int i, j, k, si;
-  if (!ani_bulk_node<T, 2>(A, i, j, k, si)) return;
+__global__ void __launch_bounds__(128, 8) ani_adj_bulk_kernel(const __grid_constant__ StepArgs<T> A) {
+  int i, j, k0, k1, si;
+  if (!ani_bulk_column<T, 2>(A, i, j, k0, k1, si)) return;
   const Slot<T>& S = A.s[si];
-  const long long id = lin(A, i, j, k);
+  const long long sz = (long long)A.px * A.ny;
   const T* __restrict__ l1 = S.cur;
-  T rhs = (T(2) + A.c2 * row_diag(A, S.W, i, j, k)) * l1[id];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int s = t ? 1 : -1;
-      const int ni = i + (ax == 0 ? s : 0), nj = j + (ax == 1 ? s : 0), nk = k + (ax == 2 ? s : 0);
-      rhs += A.c2 * row_coef(A, S.W, ni, nj, nk, ax, -s) * l1[lin(A, ni, nj, nk)];
+  long long id = lin(A, i, j, k0);
+  T zm = l1[id - sz], c = l1[id];
+  // columns next to the FEM block: some rows around them carry edge weights
+  const bool col_near = i >= A.fl[0] - 1 && i <= A.fh[0] + 1 && j >= A.fl[1] - 1 && j <= A.fh[1] + 1;
+  const T cx = A.c2 * A.kapt[0], cy = A.c2 * A.kapt[1], cz = A.c2 * A.kapt[2];
+  for (int k = k0; k < k1; ++k, id += sz) {
+    const T zp = l1[id + sz];
+    T rhs;
+    if (col_near && k >= A.fl[2] - 1 && k <= A.fh[2] + 1) {
+      rhs = (T(2) + A.c2 * row_diag(A, S.W, i, j, k)) * c;
+      rhs += A.c2 * row_coef(A, S.W, i - 1, j, k, 0, 1) * l1[id - 1];
+      rhs += A.c2 * row_coef(A, S.W, i + 1, j, k, 0, -1) * l1[id + 1];
+      rhs += A.c2 * row_coef(A, S.W, i, j - 1, k, 1, 1) * l1[id - A.px];
+      rhs += A.c2 * row_coef(A, S.W, i, j + 1, k, 1, -1) * l1[id + A.px];
+      rhs += A.c2 * row_coef(A, S.W, i, j, k - 1, 2, 1) * zm;
+      rhs += A.c2 * row_coef(A, S.W, i, j, k + 1, 2, -1) * zp;
+    } else {  // the same sums with every coefficient a lattice one
+      rhs = (T(2) + A.c2 * A.kdiag) * c;
+      rhs += cx * l1[id - 1];
+      rhs += cx * l1[id + 1];
+      rhs += cy * l1[id - A.px];
+      rhs += cy * l1[id + A.px];
+      rhs += cz * zm;
+      rhs += cz * zp;
     }
+    S.next[id] = rhs - S.prev[id];
+    pair_if_voxel<T, true>(A, S, si, i, j, k);
+    zm = c;
+    c = zp;
   }
-  S.next[id] = rhs - S.prev[id];
-  pair_if_voxel<T, true>(A, S, si, i, j, k);
 }
 
 template <typename T>
@@ -1903,7 +1933,7 @@ int launch_step(const StepArgs<T>& a, cudaStream_t st) {
     if (a.ani && !a.tet && a.nx >= 5 && a.ny >= 5 && a.nz >= 5 && a.ny <= 65535 &&
         (long long)(a.nz - 2 * w) * a.nslots <= 65535) {
       const dim3 grid((unsigned)((a.nx - 2 * w + 127) / 128), (unsigned)(a.ny - 2 * w),
-                      (unsigned)((a.nz - 2 * w) * a.nslots));
+                      (unsigned)(((a.nz - 2 * w + kAniZ - 1) / kAniZ) * a.nslots));
       const long long shell = 2LL * w *
                               ((long long)a.nx * a.ny + (long long)a.nx * (a.nz - 2 * w) +
                                (long long)(a.ny - 2 * w) * (a.nz - 2 * w)) * a.nslots;
