@@ -52,7 +52,8 @@ def parse():
     p.add_argument("--steps", type=int, default=10, help="timed CG iterations (the first K of a fresh loop)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="large_257", choices=["large_257", "inverse_129"])
+    p.add_argument("--workload", default="large_257", choices=["large_257", "inverse_129", "anisotropic_box"],
+                   help="anisotropic_box: with --sweeps-only (its bench record is the anisotropic block)")
     p.add_argument("--nsteps", type=int, default=0, help="time steps (0: the workload's own)")
     p.add_argument("--e2e-steps", type=int, default=2, help="CG iterations of the end-to-end measurement")
     p.add_argument("--no-secondary", action="store_true", help="skip the 129^3 record")
@@ -178,6 +179,8 @@ def make_workload(name, nsteps=0, refine=True):
     import synth
     if name == "large_257":
         return synth.large_257(refine=refine, **({"nsteps": nsteps} if nsteps else {}))
+    if name == "anisotropic_box":
+        return synth.anisotropic_box(**({"nsteps": nsteps} if nsteps else {}))
     return synth.inverse_129(**({"nsteps": nsteps} if nsteps else {}))
 
 
@@ -348,11 +351,12 @@ def run_anisotropic(H, dev, peak, peak_kind, nsteps=600, reps=2, sweep_levels=10
     roof = {}
     for k, b, ms in (("forward", fb, fwd_ms), ("adjoint", ab, adj_ms)):
         gbs = b / (ms * 1e-3) / 1e9
-        roof[k] = {"kernel": "fwd_all_kernel<float>" if k == "forward" else "adj_all_kernel<float>",
+        roof[k] = {"kernel": ("ani_fwd_bulk_kernel<float> + ani_fwd_shell_kernel<float>" if k == "forward" else
+                              "ani_adj_bulk_kernel<float> + ani_adj_shell_kernel<float>") + " (one level)",
                    "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                    "peak_kind": peak_kind, "algorithmic_bytes_per_launch": b, "launch_ms": ms}
     return {"workload": "257 x 193 x 321 lattice on [-1,1]^3, steps 2/256, 2/192, 2/320, FEM block = central half, "
-                        "8 sources, no refinement, %d steps, checkpoints every 50, FP32 (the all-node kernels)" % nsteps,
+                        "8 sources, no refinement, %d steps, checkpoints every 50, FP32 (bulk and face-shell kernels)" % nsteps,
             "gradient_ms": el, "value": per / (el * 1e-3) / 1e9, "unit": UNIT,
             "counted": "n_src x lattice nodes x N_t x 2 (forward + adjoint) per gradient evaluation",
             "roofline": roof, "J": J, "gnorm": gn}
@@ -791,6 +795,8 @@ def main():
         return run_reference(args)
     if args.sweeps_only:
         return run_sweeps_only(args)
+    if args.workload == "anisotropic_box":
+        sys.exit("--workload anisotropic_box needs --sweeps-only")
     return run_ours(args)
 
 

@@ -143,7 +143,8 @@ typedef struct {
                           weight of a face node is its in-face cell area
                           dx_p dx_q (halved on the face's border), and
                           dt_max = 1 / sqrt(a_max sum 1 / dx^2).  Every level
-                          then runs the generic all-node kernels (no staged
+                          then takes two launches (the rows off the faces,
+                          then the face layers by the generic rows; no staged
                           tiles).  Needs no refinement, the exact adjoint and
                           the wave model, and no batches (HYB_ERR_ARG). */
 } hyb_mesh_desc;
