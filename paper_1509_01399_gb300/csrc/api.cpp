@@ -111,7 +111,7 @@ struct hyb_mesh {
   DevBuf I0, IC0;               // initial state of Model Problem 1: u^0, u^{-1} (padded fields), centres
   DevBuf acopy, kuhn, kuhn_v;   // all-FEM path: coefficient of the last forward, Kuhn element tables
   bool have_init = false;
-  bool ani = false;          // the lattice steps differ per axis (every level by the all-node kernels)
+  bool ani = false;          // the lattice steps differ per axis (every level by the bulk and shell kernels)
   double hv[3] = {0, 0, 0};  // lattice step per axis
   cudaStream_t cap = nullptr;  // private stream used only to capture sweep graphs
   // interior work items of the forward / transposed step per slot count; built
@@ -411,7 +411,7 @@ std::vector<int> build_items(const hyb_mesh* m, int nslots, bool adjoint) {
   return out;
 }
 
-// One time level: a single launch on `st`.
+// One time level on `st`: one launch (two with per-axis steps).
 template <class Launch>
 hyb_status step_launch(hyb_mesh* m, cudaStream_t st, Launch launch) {
   const int n = launch(st);  // kernels the level took (two with per-axis steps)
@@ -809,7 +809,7 @@ void base_args(const hyb_mesh* m, StepArgs<T>& A, double dt, int nslots) {
   A.c2 = (T)(dt * dt / (h * h));
   A.r = (T)((h - dt) / (h + dt));
   step_geometry(m, &A.npb, &A.ntx, &A.small, &A.nedge);
-  if (m->ani) {  // every level by the all-node kernels, axis terms weighed by kap
+  if (m->ani) {  // every level by the bulk and shell kernels, axis terms weighed by kap
     A.ani = 1;
     A.small = 1;
     A.nedge = 0;

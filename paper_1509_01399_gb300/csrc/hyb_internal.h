@@ -115,7 +115,7 @@ struct StepArgs {
   T c2;              // tau^2 / h^2 (per-axis steps: tau^2 / dx_1^2)
   T r;               // (h - tau) / (h + tau), Eq. (eq:abs2)
   // per-axis steps dx_1, dx_2, dx_3 that differ (ani = 1; every level then
-  // runs the all-node kernels): kap[ax] = dx_1^2 / dx_ax^2 weighs the axis-ax
+  // runs the per-axis kernels): kap[ax] = dx_1^2 / dx_ax^2 weighs the axis-ax
   // terms of the lattice rows and the edge weights, ra[ax] = (dx_ax - tau) /
   // (dx_ax + tau) is the absorbing coefficient of the faces normal to axis ax
   int ani;

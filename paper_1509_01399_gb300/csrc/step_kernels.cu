@@ -40,6 +40,11 @@
 // the voxel's 12 axis edges of w_e (u_p - u_q)(lambda_p - lambda_q) with
 // w_e = 2 or 1 (six times the edge weights 1/3 and 1/6); the host scales it
 // by -tau^2 / (6 h^2) (Eq. (gradient1)).
+//
+// Lattices whose steps differ per axis (the 7-point Laplacian of Sec. 7.3
+// with dx_1, dx_2, dx_3) do not use step_kernel: each level is a bulk launch
+// over the nodes off the faces (plain rows with per-axis weights) and a shell
+// launch over the face layers (the generic rows), see ani_fwd_bulk_kernel.
 #include "async_copy.cuh"
 #include "hyb_internal.h"
 
@@ -538,7 +543,7 @@ __device__ __forceinline__ T voxel_pair(const StepArgs<T>& A, const T* __restric
   return A.sdamp ? damp_sum(u, l) : pair_sum(u, l);
 }
 
-// voxel_pair with per-axis steps (the all-node kernels)
+// voxel_pair with per-axis steps (the per-axis and all-node kernels)
 template <typename T>
 __device__ __forceinline__ T voxel_pair_ani(const StepArgs<T>& A, const T* __restrict__ hb,
                                             const T* __restrict__ lam, int i, int j, int k) {
@@ -575,7 +580,7 @@ __device__ __forceinline__ T row_lap_inl(const StepArgs<T>& A, const T* __restri
   return lap7(xm, xp, ym, yp, zm, zp, c);
 }
 
-// (TET: the all-node kernels, which also serve the all-FEM path)
+// (TET: the all-node and per-axis kernels; the all-node ones also serve the all-FEM path)
 template <typename T, bool TET>
 __device__ __forceinline__ void pair_if_voxel(const StepArgs<T>& A, const Slot<T>& S, int si, int i, int j,
                                               int k) {
