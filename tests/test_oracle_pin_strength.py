@@ -1,8 +1,8 @@
 """Planted mistakes in a copy of the oracle, on the CPU: each mutation below
-of the per-axis-step arithmetic (a plausible slip: an axis, a step or a
-factor taken from the wrong place) must make at least one pin of
-tests/test_oracle_aniso.py fail, and the unmutated copy must pass them.  Each
-run is a pytest subprocess with the copy first on the import path."""
+(a plausible slip: a factor, a sign, an index, an axis or a step taken from
+the wrong place) must make at least one of the oracle's pins fail, and the
+unmutated copy must pass them all.  Each run is a pytest subprocess over the
+pin files with the copy first on the import path."""
 import os
 import shutil
 import subprocess
@@ -12,9 +12,43 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HYBRID = os.path.join(ROOT, "oracle", "hybrid.py")
-PINS = os.path.join(ROOT, "tests", "test_oracle_aniso.py")
+PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_refinement.py",
+                                                  "test_oracle_sources.py", "test_oracle_telegraph.py",
+                                                  "test_oracle_aniso.py")]
 
 MUTANTS = {
+    # ---- the scheme
+    # the mirror ghost's factor 2 dropped on the low faces
+    "mirror_ghost": ("np.full(lowb.sum(), 2 * inv_h2), np.full(highb.sum(), 2 * inv_h2)]",
+                     "np.full(lowb.sum(), inv_h2), np.full(highb.sum(), 2 * inv_h2)]"),
+    # the absorbing coefficient (tau - h) / (h + tau)
+    "abc_sign": ("        return (self.hv - dt) / (self.hv + dt)", "        return (dt - self.hv) / (self.hv + dt)"),
+    # the absorbing row's coupling to the inward neighbour halved
+    "abc_coupling": ("            vb.append(1.0 / Lb)", "            vb.append(0.5 / Lb)"),
+    # corners before edges before faces
+    "abc_order": ("            for L in (1, 2, 3):", "            for L in (3, 2, 1):"),
+    # the flux ghost u_in + h g
+    "source_factor": ("dt * dt * 2.0 / self.hv[f // 2] * src.amp", "dt * dt * 1.0 / self.hv[f // 2] * src.amp"),
+    # an oblique wave's flux without its factor -(d . n)
+    "oblique_factor": ("                entry[f] = -dn", "                entry[f] = 1.0"),
+    # the lumped mass |K| / 3 per vertex
+    "lumped_mass": ("weights=np.repeat(self.tet_vol / 4.0, 4),", "weights=np.repeat(self.tet_vol / 3.0, 4),"),
+    # Algorithm 1's copy of omega_diamond into the FDM array left out
+    "exchange": ("                # 3. FEM values at omega_diamond become FDM boundary values\n"
+                 "                new_fd[self.omega_diamond] = new_fe[self.omega_diamond]",
+                 "                # 3. FEM values at omega_diamond become FDM boundary values\n                pass"),
+    # ---- adjoint, gradient, CG, telegraph
+    "adjoint_data_index": ("            rhs[obs] += cot[j]\n            lam = self._solve_unit(NT, rhs)",
+                           "            rhs[obs] += cot[j - 1]\n            lam = self._solve_unit(NT, rhs)"),
+    "gradient_sign": ("        out = -dt * dt * Gacc", "        out = dt * dt * Gacc"),
+    "pairing_time_index": ("                Gacc += self.pair(hist[j], lam1, ML)",
+                           "                Gacc += self.pair(hist[j - 1], lam1, ML)"),
+    "step_parabola": ("        alpha = -dJ0 * alpha_t * alpha_t / (2.0 * curv)",
+                      "        alpha = -dJ0 * alpha_t * alpha_t / curv"),
+    "fr_beta": ("    beta = gn2 / gn2_prev", "    beta = gn2_prev / gn2"),
+    "face_weight_border": ("            w[edge] *= 0.5", "            w[edge] *= 1.0"),
+    "damping_ratio": ("    s[own] = 0.5 * dt * D[own] / ML[own]", "    s[own] = dt * D[own] / ML[own]"),
+    # ---- per-axis steps
     # the second difference of axis d over the step of the next axis
     "laplacian_axis": ("            inv_h2 = 1.0 / self.hv[d] ** 2",
                        "            inv_h2 = 1.0 / self.hv[(d + 1) % 3] ** 2"),
@@ -47,8 +81,8 @@ def _run_pins(tmp_path, src):
     which = subprocess.run([sys.executable, "-c", "import oracle; print(oracle.__file__)"], env=env,
                            cwd=str(tmp_path), capture_output=True, text=True, timeout=300)
     assert which.stdout.strip().startswith(str(pkg)), which.stdout + which.stderr
-    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", PINS], env=env,
-                          cwd=str(tmp_path), capture_output=True, text=True, timeout=600)
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider"] + PINS, env=env,
+                          cwd=str(tmp_path), capture_output=True, text=True, timeout=900)
 
 
 def test_unmutated_copy_passes_the_pins(tmp_path):
