@@ -48,6 +48,32 @@ MUTANTS = {
     "fr_beta": ("    beta = gn2 / gn2_prev", "    beta = gn2_prev / gn2"),
     "face_weight_border": ("            w[edge] *= 0.5", "            w[edge] *= 1.0"),
     "damping_ratio": ("    s[own] = 0.5 * dt * D[own] / ML[own]", "    s[own] = dt * D[own] / ML[own]"),
+    "telegraph_pair_sign": ("            G -= pair(j, lam1)", "            G += pair(j, lam1)"),
+    # ---- elements, mesh, sources
+    "tet_volume": ("    vol = np.abs(np.linalg.det(e)) / 6.0", "    vol = np.abs(np.linalg.det(e)) / 2.0"),
+    "bisection_child": ("    ch1 = np.stack([pn[:, 0], pn[:, 1], pn[:, 2], c], axis=1)",
+                        "    ch1 = np.stack([pn[:, 0], pn[:, 1], pn[:, 3], c], axis=1)"),
+    "owned_nodes": ("            self.owned = np.all((self.I >= lo + 1) & (self.I <= hi - 1), axis=1)",
+                    "            self.owned = np.all((self.I >= lo + 1) & (self.I <= hi - 2), axis=1)"),
+    "unknown_voxels": ("            unk = np.all((vox >= lo + 1) & (vox <= hi - 2), axis=1)",
+                       "            unk = np.all((vox >= lo + 1) & (vox <= hi - 3), axis=1)"),
+    "exchange_omega_o": ("                # 4. FDM values at omega_o become FEM boundary values\n"
+                         "                new_fe[self.omega_o] = new_fd[self.omega_o]",
+                         "                # 4. FDM values at omega_o become FEM boundary values\n                pass"),
+    "pulse_window": ("    return np.where((s >= 0.0) & (s <= t1), np.sin(omega * s), 0.0)",
+                     "    return np.where((s >= 0.0) & (s <= 2 * t1), np.sin(omega * s), 0.0)"),
+    "entry_corner": ("        i0 = [0 if d[ax] >= 0.0 else self.n[ax] - 1 for ax in range(3)]",
+                     "        i0 = [0 for ax in range(3)]"),
+    # ---- the paper's adjoint, the functional, the projection
+    "paper_data_sign": ("            new_fd[obs] += -dt * cot[k] / M[obs]", "            new_fd[obs] += dt * cot[k] / M[obs]"),
+    "paper_gradient_scale": ("        out = dt * G", "        out = dt * dt * G"),
+    "time_weight_k0": ("    wk[0] = 0.0", "    wk[0] = 1.0"),
+    "misfit_half": ("    return 0.5 * float(np.sum(wk[:, None] * mj[None, :] * d * d)), wk[:, None] * mj[None, :] * d",
+                    "    return float(np.sum(wk[:, None] * mj[None, :] * d * d)), wk[:, None] * mj[None, :] * d"),
+    "tikhonov_volume": ("    J = 0.5 * gamma * prob.voxel_volume * float(np.sum((a - a0) ** 2))",
+                        "    J = 0.5 * gamma * float(np.sum((a - a0) ** 2))"),
+    "projection_side": ("    blocked = ((a <= a_min) & (g > 0.0)) | ((a >= a_max) & (g < 0.0))",
+                        "    blocked = ((a <= a_min) & (g < 0.0)) | ((a >= a_max) & (g > 0.0))"),
     # ---- per-axis steps
     # the second difference of axis d over the step of the next axis
     "laplacian_axis": ("            inv_h2 = 1.0 / self.hv[d] ** 2",
