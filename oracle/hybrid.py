@@ -53,7 +53,6 @@ from __future__ import annotations
 import itertools
 import math
 from dataclasses import dataclass
-from typing import List, Optional, Sequence
 
 import numpy as np
 import scipy.sparse as sp

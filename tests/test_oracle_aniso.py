@@ -26,7 +26,6 @@ import pytest
 
 import oracle
 import synth
-from oracle import hybrid as O
 from oracle.hybrid import Problem
 
 HV = (0.05, 0.0625, 0.08)
